@@ -1,0 +1,230 @@
+"""FP64 CPU oracle: test infrastructure, never part of the product path.
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` import this package. It wraps ``oracle.c`` (plain C, FP64,
+full lattice) through ctypes and shares no code with the CUDA library;
+the only thing both sides read is the seeded input from ``synth.py``.
+
+Every function takes and returns canonical complex128 arrays:
+gauge (4, Lt, Lz, Ly, Lx, 3, 3), Wilson spinor (Lt, Lz, Ly, Lx, 4, 3),
+staggered vector (Lt, Lz, Ly, Lx, 3), clover (Lt, Lz, Ly, Lx, 12, 12);
+dims are given as (Lx, Ly, Lz, Lt).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c (gcc, -O2, OpenMP, no fast-math) into liboracle.so."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", _LIB, _SRC, "-lm"]
+        subprocess.check_call(cmd)
+    return _LIB
+
+
+class _Wilson(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int * 4), ("bc_t", ctypes.c_int), ("U", ctypes.c_void_p),
+                ("clover", ctypes.c_void_p), ("m", ctypes.c_double), ("mu", ctypes.c_double),
+                ("twist_mode", ctypes.c_int)]
+
+
+class _Hisq(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int * 4), ("bc_t", ctypes.c_int), ("V", ctypes.c_void_p),
+                ("W", ctypes.c_void_p), ("c_naik", ctypes.c_double), ("m", ctypes.c_double),
+                ("conv", ctypes.c_int), ("hop_sign", ctypes.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        _lib.or_plaquette.restype = ctypes.c_double
+        _lib.or_wilson_cgnr_fixed.restype = ctypes.c_double
+    return _lib
+
+
+def _c(a: np.ndarray) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    return a
+
+
+def _p(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None else None
+
+
+def _dims(dims):
+    return (ctypes.c_int * 4)(*[int(d) for d in dims])
+
+
+def _np(a):
+    """Accept torch tensors or numpy arrays."""
+    if hasattr(a, "detach"):
+        a = a.detach().cpu().numpy()
+    return _c(a)
+
+
+def gamma(mu: int) -> np.ndarray:
+    """The oracle's gamma matrix mu (0..3 for x,y,z,t; 4 for gamma_5)."""
+    out = np.zeros((4, 4, 2))
+    lib().or_gamma(ctypes.c_int(mu), out.ctypes.data_as(ctypes.c_void_p))
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def eta(conv: int, mu: int, coords) -> float:
+    out = ctypes.c_double()
+    c = (ctypes.c_int * 4)(*coords)
+    lib().or_staggered_eta(ctypes.c_int(conv), ctypes.c_int(mu), c, ctypes.byref(out))
+    return out.value
+
+
+def plaquette(dims, U) -> float:
+    U = _np(U)
+    return lib().or_plaquette(_dims(dims), _p(U))
+
+
+class Wilson:
+    """Wilson twisted-mass (optionally clover) operator M of Sec. 2.1 Eq. 2-3."""
+
+    def __init__(self, dims, U, m, mu, clover=None, bc_t=-1, twist_mode=0):
+        self.dims = tuple(int(d) for d in dims)
+        self.U = _np(U)
+        self.clover = _np(clover) if clover is not None else None
+        self.s = _Wilson(_dims(dims), bc_t, self.U.ctypes.data,
+                         self.clover.ctypes.data if self.clover is not None else None,
+                         float(m), float(mu), int(twist_mode))
+        self.bc_t = bc_t
+
+    def shape(self):
+        lx, ly, lz, lt = self.dims
+        return (lt, lz, ly, lx, 4, 3)
+
+    def apply(self, psi, dagger=False):
+        psi = _np(psi)
+        out = np.empty(self.shape(), dtype=np.complex128)
+        lib().or_wilson_apply(ctypes.byref(self.s), ctypes.c_int(int(dagger)), _p(psi), _p(out))
+        return out
+
+    def hop(self, psi, dagger=False):
+        psi = _np(psi)
+        out = np.empty(self.shape(), dtype=np.complex128)
+        lib().or_wilson_hop(_dims(self.dims), ctypes.c_int(self.bc_t), _p(self.U), ctypes.c_int(int(dagger)),
+                            _p(psi), _p(out))
+        return out
+
+    def apply_sites(self, psi, sites, dagger=False):
+        psi = _np(psi)
+        sites = np.ascontiguousarray(sites, dtype=np.int64)
+        out = np.empty((len(sites), 4, 3), dtype=np.complex128)
+        lib().or_wilson_apply_sites(ctypes.byref(self.s), ctypes.c_int(int(dagger)), _p(psi),
+                                    ctypes.c_void_p(sites.ctypes.data), ctypes.c_int64(len(sites)), _p(out))
+        return out
+
+    def hop_sites(self, psi, sites, dagger=False):
+        psi = _np(psi)
+        sites = np.ascontiguousarray(sites, dtype=np.int64)
+        out = np.empty((len(sites), 4, 3), dtype=np.complex128)
+        lib().or_wilson_hop_sites(_dims(self.dims), ctypes.c_int(self.bc_t), _p(self.U),
+                                  ctypes.c_int(int(dagger)), _p(psi), ctypes.c_void_p(sites.ctypes.data),
+                                  ctypes.c_int64(len(sites)), _p(out))
+        return out
+
+    def _solve(self, fn, b, tol, maxiter):
+        b = _np(b)
+        x = np.zeros(self.shape(), dtype=np.complex128)
+        it = ctypes.c_int()
+        rel = ctypes.c_double()
+        st = fn(ctypes.byref(self.s), _p(b), _p(x), ctypes.c_double(tol), ctypes.c_int(maxiter),
+                ctypes.byref(it), ctypes.byref(rel))
+        return x, {"status": st, "iters": it.value, "true_rel_residual": rel.value}
+
+    def cgnr(self, b, tol=1e-12, maxiter=100000):
+        return self._solve(lib().or_wilson_cgnr, b, tol, maxiter)
+
+    def bicgstab(self, b, tol=1e-12, maxiter=100000):
+        return self._solve(lib().or_wilson_bicgstab, b, tol, maxiter)
+
+    def cgnr_fixed(self, b, niter):
+        """niter CGNR iterations from x = 0 (a bounded timing sample); returns x, rel. residual."""
+        b = _np(b)
+        x = np.zeros(self.shape(), dtype=np.complex128)
+        rel = lib().or_wilson_cgnr_fixed(ctypes.byref(self.s), _p(b), _p(x), ctypes.c_int(niter))
+        return x, rel
+
+
+def clover(dims, U, c_sw):
+    """Clover term C(x) (Sec. 2.1 Eq. 3), shape (Lt, Lz, Ly, Lx, 12, 12)."""
+    U = _np(U)
+    lx, ly, lz, lt = (int(d) for d in dims)
+    out = np.empty((lt, lz, ly, lx, 12, 12), dtype=np.complex128)
+    lib().or_clover_build(_dims(dims), _p(U), ctypes.c_double(c_sw), _p(out))
+    return out
+
+
+class Hisq:
+    """Staggered/HISQ operator D = m + s_h H of Sec. 2.2 Eq. 4 (s_h = hop_sign)."""
+
+    def __init__(self, dims, V, W, m, c_naik=-1.0 / 24.0, bc_t=-1, conv=0, hop_sign=1):
+        self.dims = tuple(int(d) for d in dims)
+        self.V = _np(V)
+        self.W = _np(W) if W is not None else None
+        self.s = _Hisq(_dims(dims), bc_t, self.V.ctypes.data,
+                       self.W.ctypes.data if self.W is not None else None,
+                       float(c_naik), float(m), int(conv), int(hop_sign))
+
+    def shape(self):
+        lx, ly, lz, lt = self.dims
+        return (lt, lz, ly, lx, 3)
+
+    def apply(self, psi, dagger=False):
+        psi = _np(psi)
+        out = np.empty(self.shape(), dtype=np.complex128)
+        lib().or_hisq_apply(ctypes.byref(self.s), ctypes.c_int(int(dagger)), _p(psi), _p(out))
+        return out
+
+    def hop(self, psi, dagger=False):
+        psi = _np(psi)
+        out = np.empty(self.shape(), dtype=np.complex128)
+        lib().or_hisq_hop(ctypes.byref(self.s), ctypes.c_int(int(dagger)), _p(psi), _p(out))
+        return out
+
+    def hop_sites(self, psi, sites, dagger=False):
+        psi = _np(psi)
+        sites = np.ascontiguousarray(sites, dtype=np.int64)
+        out = np.empty((len(sites), 3), dtype=np.complex128)
+        lib().or_hisq_hop_sites(ctypes.byref(self.s), ctypes.c_int(int(dagger)), _p(psi),
+                                ctypes.c_void_p(sites.ctypes.data), ctypes.c_int64(len(sites)), _p(out))
+        return out
+
+    def cgnr(self, b, tol=1e-12, maxiter=100000):
+        b = _np(b)
+        x = np.zeros(self.shape(), dtype=np.complex128)
+        it = ctypes.c_int()
+        rel = ctypes.c_double()
+        st = lib().or_hisq_cgnr(ctypes.byref(self.s), _p(b), _p(x), ctypes.c_double(tol), ctypes.c_int(maxiter),
+                                ctypes.byref(it), ctypes.byref(rel))
+        return x, {"status": st, "iters": it.value, "true_rel_residual": rel.value}
+
+    def multishift(self, b, masses, tol=1e-12, maxiter=100000):
+        """Solves (m_i + s_h H) x_i = b for all masses (ascending) with one multi-shift CG."""
+        b = _np(b)
+        masses = np.ascontiguousarray(masses, dtype=np.float64)
+        xs = [np.zeros(self.shape(), dtype=np.complex128) for _ in masses]
+        ptrs = (ctypes.c_void_p * len(xs))(*[x.ctypes.data for x in xs])
+        it = ctypes.c_int()
+        rel = np.zeros(len(masses))
+        st = lib().or_hisq_multishift(ctypes.byref(self.s), ctypes.c_int(len(masses)),
+                                      ctypes.c_void_p(masses.ctypes.data), _p(b), ptrs, ctypes.c_double(tol),
+                                      ctypes.c_int(maxiter), ctypes.byref(it), ctypes.c_void_p(rel.ctypes.data))
+        return xs, {"status": st, "iters": it.value, "true_rel_residual": rel.tolist()}
