@@ -1,0 +1,263 @@
+/*
+ * lq.h -- C ABI of the B300 lattice Dirac-operator library.
+ *
+ * The library applies the lattice Dirac operators of arXiv:2201.09004
+ * ("Performance of the GPU inverters with Chroma+QUDA for various fermion
+ * actions") and solves D x = b with them, on one CUDA GPU:
+ *   - Wilson twisted mass, optional clover term: Sec. 2.1, Eq. 1-3;
+ *   - HISQ staggered with fat one-hop and long three-hop links: Sec. 2.2, Eq. 4.
+ * The paper's own contribution is an interface through which an application
+ * calls GPU inverters for several actions (Sec. 1, Sec. 3); this header is that
+ * interface for this library.
+ *
+ * Conventions (the paper is silent or garbled on these; every entry point uses them):
+ *   Geometry: dims = {Lx, Ly, Lz, Lt}, all even and >= 2. Site index
+ *     i = x + Lx*(y + Ly*(z + Lz*t)); parity (x+y+z+t) & 1, even = 0.
+ *     Periodic in space; in time the boundary sign t_boundary (+1 or -1)
+ *     multiplies each hop once per crossing of t = Lt-1 -> 0.
+ *   Links: U_mu(x) transports from x+mu to x; the backward hop uses U_mu(x-mu)^+.
+ *   Gamma matrices: DeGrand-Rossi basis, g5 = g1 g2 g3 g4 = diag(1,1,-1,-1).
+ *   Wilson operator (Sec. 2.1 Eq. 2 with an overall sign -1):
+ *     M = (4+m) + i mu g5 + C - H,
+ *     H psi(x) = 1/2 sum_mu [(1+g_mu) U_mu(x) psi(x+mu) + (1-g_mu) U_mu(x-mu)^+ psi(x-mu)].
+ *     The complex mass of Sec. 2.1 Eq. 1 is m + i mu g5 (twisted reading).
+ *   Clover (Sec. 2.1 Eq. 3): C = c_sw (i/2) sum_{mu<nu} sigma_{mu nu} Fhat_{mu nu},
+ *     sigma = (i/2)[g_mu, g_nu], Fhat = (Q - Q^+)/8 traceless, Q = sum of the
+ *     four plaquette leaves at x.
+ *   Staggered/HISQ (Sec. 2.2 Eq. 4): D = m + H,
+ *     H psi(x) = 1/2 sum_mu eta_mu(x) [V_mu(x) psi(x+mu) - V_mu(x-mu)^+ psi(x-mu)
+ *                 + c_naik (W_mu(x) psi(x+3mu) - W_mu(x-3mu)^+ psi(x-3mu))],
+ *     MILC phases eta_1 = (-1)^t, eta_2 = (-1)^(t+x), eta_3 = (-1)^(t+x+y), eta_4 = 1.
+ *
+ * Canonical layouts (FP64 complex, interleaved re/im, C order) used by every
+ * pointer argument below unless stated otherwise:
+ *   gauge    [mu][t][z][y][x][3][3]        (4*V*9 complex)
+ *   spinor   [t][z][y][x][spin 4][colour 3] (V*12 complex)
+ *   colour   [t][z][y][x][colour 3]         (V*3 complex)
+ *   clover   [t][z][y][x][12][12]           (V*144 complex, index 3*spin+colour)
+ *
+ * Errors: every function returns an lq_status; LQ_OK is 0. No C++ exception
+ * crosses this boundary. lq_last_error() gives a thread-local message for the
+ * last failure on the calling thread.
+ *
+ * Memory: the library copies what it is given (gauge, clover) into its own
+ * device memory, which lives until lq_destroy_lattice. Caller buffers (sources,
+ * solutions) stay owned by the caller; loc says whether a pointer is host or
+ * device memory. Nothing returned by the library must be freed by the caller.
+ *
+ * Threads: a lattice handle may be used by one thread at a time. The server
+ * functions are thread-safe.
+ */
+#ifndef LQ_H
+#define LQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lq_lattice_s* lq_lattice;
+typedef struct lq_server_s* lq_server;
+typedef struct lq_field_s* lq_field;
+
+typedef enum {
+    LQ_OK = 0,
+    LQ_EINVAL = 1,      /* bad argument (odd extent, null pointer, unknown enum, missing gauge) */
+    LQ_ENOMEM = 2,      /* device or host allocation failed, or over the server's HBM budget */
+    LQ_ENOTCONV = 3,    /* solver hit maxiter; x holds the best iterate, info is filled */
+    LQ_EBREAKDOWN = 4,  /* Krylov breakdown (non-positive curvature) */
+    LQ_ENAN = 5,        /* NaN or Inf in the source or during the solve */
+    LQ_EAGAIN = 6,      /* lq_poll: the request is not finished yet */
+    LQ_ETIMEOUT = 7,    /* lq_wait timed out */
+    LQ_ECUDA = 8,       /* a CUDA runtime call failed; see lq_last_error */
+    LQ_EBUSY = 9        /* server is shutting down or the queue is full */
+} lq_status;
+
+typedef enum { LQ_F64 = 0, LQ_F32 = 1, LQ_F16 = 2 } lq_prec;  /* F16 = int16 fixed point + per-site norm */
+typedef enum { LQ_R18 = 18, LQ_R12 = 12 } lq_recon;            /* link compression (R12: two rows of SU(3)) */
+typedef enum { LQ_THIN = 0, LQ_FAT = 1, LQ_LONG = 2 } lq_gauge_kind;
+typedef enum { LQ_HOST = 0, LQ_DEVICE = 1 } lq_loc;
+typedef enum { LQ_WILSON_TM = 0, LQ_WILSON_TM_CLOVER = 1, LQ_HISQ = 2 } lq_action;
+typedef enum { LQ_CGNR = 0, LQ_MIXED_CGNR = 1, LQ_MULTISHIFT_CG = 2 } lq_solver;
+typedef enum { LQ_OP_FULL = 0, LQ_OP_SCHUR = 1 } lq_op_form;
+typedef enum { LQ_WILSON_FIELD = 0, LQ_STAGGERED_FIELD = 1 } lq_field_kind;
+typedef enum { LQ_EVEN = 0, LQ_ODD = 1 } lq_parity;
+
+/* Operator parameters. For Wilson actions m and mu are the real and twisted
+ * mass (M = (4+m) + i mu g5 + C - H); c_sw is used only for
+ * LQ_WILSON_TM_CLOVER and must match the c_sw of lq_load_clover. For LQ_HISQ,
+ * m is the staggered mass and c_naik the coefficient of the three-hop term
+ * (tree level: -1/24). */
+typedef struct {
+    int action;      /* lq_action */
+    double m;
+    double mu;
+    double c_sw;
+    double c_naik;
+} lq_op_params;
+
+/* Solver parameters.
+ *   LQ_CGNR:          CG on the normal equations of the even-odd Schur operator
+ *                     (plain CG on the hermitian Schur operator for HISQ),
+ *                     everything in prec_sloppy (LQ_F64 gives the FP64 solver).
+ *   LQ_MIXED_CGNR:    same, with the Krylov vectors and operator in prec_sloppy
+ *                     and reliable updates in FP64 whenever the iterated residual
+ *                     falls below delta times its maximum since the last update.
+ *   LQ_MULTISHIFT_CG: HISQ only; one Krylov space for all nshift masses
+ *                     masses[0..nshift-1] (ascending) in prec_sloppy, then each
+ *                     mass refined by the mixed-precision CG; x gets nrhs*nshift
+ *                     solutions, x[rhs*nshift + shift].
+ * tol is the target of the FP64 true residual |b - D x|/|b| of the full system. */
+typedef struct {
+    int solver;       /* lq_solver */
+    double tol;
+    double delta;     /* reliable-update threshold (0.1) */
+    int maxiter;
+    int prec_sloppy;  /* lq_prec */
+    int recon_sloppy; /* lq_recon for thin/long links in the sloppy operator */
+    int nshift;
+    const double* masses;
+} lq_solve_params;
+
+typedef struct {
+    int status;               /* lq_status of this right-hand side */
+    int iters;                /* Krylov iterations */
+    int reliable_updates;
+    int operator_applications;
+    double true_rel_residual; /* FP64 |b - D x|/|b| on the full lattice (max over shifts) */
+    double seconds;           /* device time of the solve (CUDA events on its stream) */
+} lq_solve_info;
+
+/* ------------------------------------------------------------------ errors */
+
+/* Message of the last failure on the calling thread ("" if none). The pointer
+ * stays valid until the next failing call on the same thread. */
+const char* lq_last_error(void);
+
+/* --------------------------------------------------------------- lattices */
+
+/* Creates a lattice of extents dims[4] = {Lx, Ly, Lz, Lt} (each even, >= 2) with
+ * time boundary sign t_boundary (+1 periodic, -1 antiperiodic), on the current
+ * CUDA device. *out receives the handle. LQ_EINVAL for odd or too small extents. */
+int lq_create_lattice(const int dims[4], int t_boundary, lq_lattice* out);
+
+/* Frees every device buffer of the lattice. Accepts NULL. */
+int lq_destroy_lattice(lq_lattice lat);
+
+/* Device bytes the lattice currently holds (links, clover, caches). */
+int lq_lattice_bytes(lq_lattice lat, size_t* bytes);
+
+/* Loads links in the canonical gauge layout (host or device, FP64). kind
+ * selects the thin links of the Wilson actions, or the fat / long links of
+ * HISQ (Sec. 2.2). The library packs them into its even-odd layout in every
+ * precision it needs; the caller may free its buffer after the call. */
+int lq_load_gauge(lq_lattice lat, int kind, int loc, const double* links);
+
+/* Clover term of Sec. 2.1 Eq. 3. clover == NULL builds it on the device from
+ * the thin links already loaded, with coefficient c_sw; otherwise clover is a
+ * canonical 12x12-per-site array (host or device) that must be hermitian and
+ * commute with g5 (its two 6x6 chiral blocks are used). */
+int lq_load_clover(lq_lattice lat, int loc, const double* clover, double c_sw);
+
+/* ----------------------------------------------------- operator application */
+
+/* Hopping term H restricted to output parity `parity` (0/1): out(x) = (H in)(x)
+ * for x of that parity and 0 elsewhere; dagger = 1 applies H^+. For LQ_HISQ it
+ * is the staggered H of Eq. 4. in/out are canonical spinors (colour vectors for
+ * HISQ) in FP64, at loc; the operator runs in precision prec (inputs are
+ * rounded to it). stream is a cudaStream_t or NULL for the default stream;
+ * the call returns after the result is in out. */
+int lq_dslash_apply(lq_lattice lat, const lq_op_params* op, int parity, int dagger, int prec, int loc,
+                    const double* in, double* out, void* stream);
+
+/* Whole operator. form = LQ_OP_FULL: out = D in (D = M for Wilson, m + H for
+ * HISQ) on the full lattice. form = LQ_OP_SCHUR: the even-odd Schur operator
+ * on even sites, Mhat = A_ee - H_eo A_oo^{-1} H_oe for Wilson (A = 4+m+i mu g5+C)
+ * and m^2 - H_eo H_oe for HISQ; only the even sites of in are read and only
+ * the even sites of out are written (odd sites of out are set to 0). */
+int lq_operator_apply(lq_lattice lat, const lq_op_params* op, int form, int dagger, int prec, int loc,
+                      const double* in, double* out, void* stream);
+
+/* ------------------------------------------------------------------ solves */
+
+/* Solves D x_k = b_k for k < nrhs (Wilson: M; HISQ: m + H, and for
+ * LQ_MULTISHIFT_CG every mass of params->masses). rhs[k] and x[k] are canonical
+ * FP64 arrays at loc (x must hold nrhs*nshift arrays for multi-shift). info
+ * (may be NULL) receives one entry per right-hand side. Right-hand sides are
+ * solved together with the multi-right-hand-side operator.
+ * Returns LQ_OK if every system reached tol, LQ_ENOTCONV if any did not. */
+int lq_solve(lq_lattice lat, const lq_op_params* op, const lq_solve_params* params, int nrhs,
+             const double* const* rhs, double* const* x, int loc, lq_solve_info* info, void* stream);
+
+/* ----------------------------------------------------------- device fields */
+
+/* A spinor or colour field resident on the device in the library's internal
+ * even-odd layout and precision, for callers that keep data on the GPU across
+ * calls (and for timing the kernels alone): nrhs fields of one parity. */
+int lq_field_create(lq_lattice lat, int kind, int prec, int nrhs, lq_field* out);
+int lq_field_destroy(lq_field f);
+/* copy canonical FP64 data (host or device; only sites of `parity` are read)
+ * into right-hand side k of the field, and back (sites of the other parity in
+ * `canonical` are left untouched) */
+int lq_field_import(lq_field f, int k, int parity, int loc, const double* canonical, void* stream);
+int lq_field_export(lq_field f, int k, int parity, int loc, double* canonical, void* stream);
+
+/* out = H_{parity, 1-parity} in on resident fields, all right-hand sides of the
+ * field at once (multi-right-hand-side kernel). Asynchronous on stream. */
+int lq_dslash_field(lq_lattice lat, const lq_op_params* op, int parity, int dagger, lq_field in,
+                    lq_field out, void* stream);
+/* out = Mhat in (Schur operator, even parity) on resident fields; tmp is a
+ * scratch field of the same shape used for the odd sites. Asynchronous on stream. */
+int lq_schur_field(lq_lattice lat, const lq_op_params* op, int dagger, lq_field in, lq_field out,
+                   lq_field tmp, void* stream);
+
+/* ----------------------------------------------------------- instrumentation */
+
+/* When enabled, every kernel launch of the library is bracketed with CUDA
+ * events on its own stream; lq_profile_query returns, for kernels whose name
+ * contains `name`, the number of launches and their summed device time since
+ * the last reset (this synchronises the recorded events). */
+int lq_profile_enable(int on);
+int lq_profile_reset(void);
+int lq_profile_query(const char* name, int64_t* launches, double* total_ms);
+/* number of kernel launches the library issued since the last reset */
+int64_t lq_launch_count(void);
+
+/* ----------------------------------------------------------------- serving */
+
+/* A request server: solves submitted asynchronously, admitted while their
+ * estimated device memory fits in hbm_budget_bytes, at most max_slots at once,
+ * each admitted request on its own CUDA stream so that solves overlap on the
+ * device. Lattices and gauge fields are created from (dims, gauge_seed) by the
+ * server's loader and cached on the device across requests. */
+typedef struct {
+    int dims[4];
+    int t_boundary;
+    uint64_t gauge_seed;
+    lq_op_params op;
+    lq_solve_params solve;
+    int nrhs;
+} lq_request;
+
+typedef struct {
+    double submitted;  /* seconds since server creation */
+    double admitted;
+    double finished;
+} lq_request_times;
+
+int lq_server_create(size_t hbm_budget_bytes, int max_slots, lq_server* out);
+int lq_server_destroy(lq_server s);
+/* rhs: nrhs canonical FP64 host arrays, copied before the call returns */
+int lq_submit(lq_server s, const lq_request* req, const double* const* rhs, uint64_t* ticket);
+/* LQ_EAGAIN until done; then copies nrhs*max(1,nshift) solutions into x (host
+ * arrays), per-rhs info and the request's timestamps, and forgets the ticket */
+int lq_poll(lq_server s, uint64_t ticket, double* const* x, lq_solve_info* info, lq_request_times* times);
+/* blocks up to timeout_ms for the ticket to finish; LQ_ETIMEOUT otherwise */
+int lq_wait(lq_server s, uint64_t ticket, int timeout_ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LQ_H */

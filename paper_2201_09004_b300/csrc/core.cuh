@@ -1,0 +1,291 @@
+// core.cuh -- device-side building blocks shared by the kernels of the library:
+// complex arithmetic, the even-odd site geometry, and the storage formats of
+// spinors, colour vectors, links and clover fields in FP64 / FP32 / FP16.
+//
+// Storage: every field is an array of per-site records of NR reals, stored as
+// "chunk-major" structure of arrays so that a warp reading chunk k of 32
+// consecutive sites touches one contiguous segment:
+//     chunk k of site s lives at  base[k * stride + s]   (in units of a chunk).
+// Chunk types: FP64 double2 (2 reals); FP32 float4 (4 reals) when NR % 4 == 0,
+// else float2; FP16 = int16 fixed point, 8 / 4 / 2 values per 16 / 8 / 4-byte
+// chunk, value = q * scale / 32767 with scale either a per-site norm (spinors,
+// clover) or one constant (links).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+namespace lq {
+
+enum Prec { P64 = 0, P32 = 1, P16 = 2 };
+
+// site-local epilogues fused into the hopping kernels (see wilson.cuh, hisq.cuh)
+enum Epi { EPI_HOP = 0, EPI_AINV = 1, EPI_XPAY = 2 };
+
+template <int P> struct RealT { typedef float T; };
+template <> struct RealT<P64> { typedef double T; };
+
+// ------------------------------------------------------------------ complex
+template <typename T> struct cx {
+    T r, i;
+};
+
+template <typename T> __device__ __forceinline__ cx<T> mk(T r, T i) { cx<T> c; c.r = r; c.i = i; return c; }
+template <typename T> __device__ __forceinline__ cx<T> operator+(cx<T> a, cx<T> b) { return mk(a.r + b.r, a.i + b.i); }
+template <typename T> __device__ __forceinline__ cx<T> operator-(cx<T> a, cx<T> b) { return mk(a.r - b.r, a.i - b.i); }
+template <typename T> __device__ __forceinline__ cx<T> operator*(cx<T> a, cx<T> b) {
+    return mk(a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r);
+}
+template <typename T> __device__ __forceinline__ cx<T> operator*(T s, cx<T> a) { return mk(s * a.r, s * a.i); }
+template <typename T> __device__ __forceinline__ cx<T> cj(cx<T> a) { return mk(a.r, -a.i); }
+// i * a
+template <typename T> __device__ __forceinline__ cx<T> ti(cx<T> a) { return mk(-a.i, a.r); }
+// acc += a * b
+template <typename T> __device__ __forceinline__ void cmac(cx<T>& acc, cx<T> a, cx<T> b) {
+    acc.r = fma(a.r, b.r, acc.r); acc.r = fma(-a.i, b.i, acc.r);
+    acc.i = fma(a.r, b.i, acc.i); acc.i = fma(a.i, b.r, acc.i);
+}
+// acc += conj(a) * b
+template <typename T> __device__ __forceinline__ void cjmac(cx<T>& acc, cx<T> a, cx<T> b) {
+    acc.r = fma(a.r, b.r, acc.r); acc.r = fma(a.i, b.i, acc.r);
+    acc.i = fma(a.r, b.i, acc.i); acc.i = fma(-a.i, b.r, acc.i);
+}
+
+// ---------------------------------------------------------------- geometry
+// Even-odd ("checkerboard") order: within parity p, site cb = lex / 2 with
+// lex = x + Lx*(y + Ly*(z + Lz*t)); Lx is even, so x = 2*(cb % (Lx/2)) + ((y+z+t+p) & 1).
+struct Geo {
+    int L[4];
+    int lxh;      // Lx / 2
+    int vh;       // V / 2 (sites per parity)
+    int bc_t;     // time boundary sign, +1 or -1
+};
+
+__device__ __forceinline__ void cb_coords(const Geo& g, int cb, int p, int c[4]) {
+    int xh = cb % g.lxh;
+    int r = cb / g.lxh;
+    c[1] = r % g.L[1];
+    r /= g.L[1];
+    c[2] = r % g.L[2];
+    c[3] = r / g.L[2];
+    c[0] = 2 * xh + ((c[1] + c[2] + c[3] + p) & 1);
+}
+
+__device__ __forceinline__ int cb_index(const Geo& g, const int c[4]) {
+    return (c[0] + g.L[0] * (c[1] + g.L[1] * (c[2] + g.L[2] * c[3]))) >> 1;
+}
+
+// checkerboard index of x + k mu (wrapping several times for tiny extents) and
+// the boundary sign picked up on the straight path
+__device__ __forceinline__ int cb_hop(const Geo& g, const int c[4], int mu, int k, float& sign) {
+    int n[4] = {c[0], c[1], c[2], c[3]};
+    int L = g.L[mu];
+    int v = c[mu] + k;
+    int wraps = 0;
+    while (v >= L) { v -= L; wraps++; }
+    while (v < 0) { v += L; wraps++; }
+    n[mu] = v;
+    sign = (mu == 3 && g.bc_t < 0 && (wraps & 1)) ? -1.f : 1.f;
+    return cb_index(g, n);
+}
+
+// ----------------------------------------------------------------- storage
+template <int P, int NR> struct Chunk;
+template <int NR> struct Chunk<P64, NR> { typedef double2 C; enum { RPC = 2 }; };
+template <int NR> struct Chunk<P32, NR> {
+    typedef typename std::conditional<NR % 4 == 0, float4, float2>::type C;
+    enum { RPC = (NR % 4 == 0) ? 4 : 2 };
+};
+template <int NR> struct Chunk<P16, NR> {
+    typedef typename std::conditional<NR % 8 == 0, int4, typename std::conditional<NR % 4 == 0, int2, int>::type>::type C;
+    enum { RPC = (NR % 8 == 0) ? 8 : ((NR % 4 == 0) ? 4 : 2) };
+};
+
+template <int P, int NR> struct Layout {
+    typedef typename Chunk<P, NR>::C C;
+    enum { RPC = Chunk<P, NR>::RPC, NC = NR / Chunk<P, NR>::RPC };
+};
+
+__device__ __forceinline__ float s16lo(int w) { return (float)(short)(w & 0xffff); }
+__device__ __forceinline__ float s16hi(int w) { return (float)(short)(((unsigned)w) >> 16); }
+__device__ __forceinline__ int pack16(float a, float b) {
+    int qa = __float2int_rn(a), qb = __float2int_rn(b);
+    return (int)(((unsigned)qa & 0xffffu) | ((unsigned)qb << 16));
+}
+
+// unpack one chunk c into RPC reals (FP16: times f = scale/32767)
+template <int P, int NR, typename T>
+__device__ __forceinline__ void unpack_chunk(const typename Layout<P, NR>::C& c, float f, T* v) {
+    typedef Layout<P, NR> Lay;
+    if constexpr (P == P64) {
+        v[0] = (T)c.x; v[1] = (T)c.y;
+    } else if constexpr (P == P32) {
+        if constexpr (Lay::RPC == 4) {
+            v[0] = (T)c.x; v[1] = (T)c.y; v[2] = (T)c.z; v[3] = (T)c.w;
+        } else {
+            v[0] = (T)c.x; v[1] = (T)c.y;
+        }
+    } else {
+        if constexpr (Lay::RPC == 8) {
+            v[0] = (T)(s16lo(c.x) * f); v[1] = (T)(s16hi(c.x) * f);
+            v[2] = (T)(s16lo(c.y) * f); v[3] = (T)(s16hi(c.y) * f);
+            v[4] = (T)(s16lo(c.z) * f); v[5] = (T)(s16hi(c.z) * f);
+            v[6] = (T)(s16lo(c.w) * f); v[7] = (T)(s16hi(c.w) * f);
+        } else if constexpr (Lay::RPC == 4) {
+            v[0] = (T)(s16lo(c.x) * f); v[1] = (T)(s16hi(c.x) * f);
+            v[2] = (T)(s16lo(c.y) * f); v[3] = (T)(s16hi(c.y) * f);
+        } else {
+            v[0] = (T)(s16lo(c) * f); v[1] = (T)(s16hi(c) * f);
+        }
+    }
+}
+
+// load NR reals of site s; for P16 multiply by scale/32767
+template <int P, int NR, typename T>
+__device__ __forceinline__ void load_reals(const void* base, int stride, int s, float scale, T* v) {
+    typedef Layout<P, NR> Lay;
+    const typename Lay::C* b = (const typename Lay::C*)base;
+    const float f = scale * (1.f / 32767.f);
+#pragma unroll
+    for (int k = 0; k < Lay::NC; k++) {
+        typename Lay::C c = __ldg(&b[(size_t)k * stride + s]);
+        unpack_chunk<P, NR, T>(c, f, v + k * Lay::RPC);
+    }
+}
+
+// load the reals of chunk k only (RPC of them)
+template <int P, int NR, typename T>
+__device__ __forceinline__ void load_chunk(const void* base, int stride, int s, int k, float scale, T* v) {
+    typedef Layout<P, NR> Lay;
+    const typename Lay::C* b = (const typename Lay::C*)base;
+    typename Lay::C c = __ldg(&b[(size_t)k * stride + s]);
+    unpack_chunk<P, NR, T>(c, scale * (1.f / 32767.f), v);
+}
+
+// store NR reals of site s. For P16 with a per-site norm the norm is computed
+// here (max |v|) and written to norm[s]; with norm == nullptr `scale` is used.
+template <int P, int NR, typename T>
+__device__ __forceinline__ void store_reals(void* base, int stride, int s, float* norm, float scale, const T* v) {
+    typedef Layout<P, NR> Lay;
+    typename Lay::C* b = (typename Lay::C*)base;
+    if constexpr (P == P16) {
+        float nrm = scale;
+        if (norm) {
+            float m = 0.f;
+#pragma unroll
+            for (int k = 0; k < NR; k++) m = fmaxf(m, fabsf((float)v[k]));
+            nrm = m;
+            norm[s] = m;
+        }
+        const float f = nrm > 0.f ? 32767.f / nrm : 0.f;
+#pragma unroll
+        for (int k = 0; k < Lay::NC; k++) {
+            typename Lay::C c;
+            if constexpr (Lay::RPC == 8) {
+                c.x = pack16((float)v[8 * k + 0] * f, (float)v[8 * k + 1] * f);
+                c.y = pack16((float)v[8 * k + 2] * f, (float)v[8 * k + 3] * f);
+                c.z = pack16((float)v[8 * k + 4] * f, (float)v[8 * k + 5] * f);
+                c.w = pack16((float)v[8 * k + 6] * f, (float)v[8 * k + 7] * f);
+            } else if constexpr (Lay::RPC == 4) {
+                c.x = pack16((float)v[4 * k + 0] * f, (float)v[4 * k + 1] * f);
+                c.y = pack16((float)v[4 * k + 2] * f, (float)v[4 * k + 3] * f);
+            } else {
+                c = pack16((float)v[2 * k + 0] * f, (float)v[2 * k + 1] * f);
+            }
+            b[(size_t)k * stride + s] = c;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < Lay::NC; k++) {
+            typename Lay::C c;
+            if constexpr (P == P64) {
+                c.x = (double)v[2 * k]; c.y = (double)v[2 * k + 1];
+            } else if constexpr (Lay::RPC == 4) {
+                c.x = (float)v[4 * k]; c.y = (float)v[4 * k + 1]; c.z = (float)v[4 * k + 2]; c.w = (float)v[4 * k + 3];
+            } else {
+                c.x = (float)v[2 * k]; c.y = (float)v[2 * k + 1];
+            }
+            b[(size_t)k * stride + s] = c;
+        }
+    }
+}
+
+// A field of one parity with nrhs right-hand sides: rhs k starts at
+// data + k * rhs_bytes; norm (FP16 only) at norm + k * vh.
+struct FieldV {
+    void* data;
+    float* norm;
+    int vh;
+    size_t rhs_bytes;
+};
+
+template <int P, int NR, typename T>
+__device__ __forceinline__ void fload(const FieldV& f, int k, int s, T* v) {
+    const char* base = (const char*)f.data + (size_t)k * f.rhs_bytes;
+    float sc = 1.f;
+    if constexpr (P == P16) sc = __ldg(f.norm + (size_t)k * f.vh + s);
+    load_reals<P, NR, T>(base, f.vh, s, sc, v);
+}
+
+template <int P, int NR, typename T>
+__device__ __forceinline__ void fstore(const FieldV& f, int k, int s, const T* v) {
+    char* base = (char*)f.data + (size_t)k * f.rhs_bytes;
+    store_reals<P, NR, T>(base, f.vh, s, P == P16 ? f.norm + (size_t)k * f.vh : nullptr, 1.f, v);
+}
+
+// --------------------------------------------------------------- links
+// Links of parity p and direction mu: block (p*4 + mu) of NC chunks x vh.
+// R = 18: all nine entries. R = 12: rows 0 and 1; row 2 = conj(row0 x row1),
+// exact for SU(3). Boundary signs are never stored in links.
+struct GaugeV {
+    const void* data;
+    int vh;
+    float scale;  // FP16 fixed-point scale (max |entry| of the field); 1 otherwise
+};
+
+template <int P, int R, typename T>
+__device__ __forceinline__ void load_link(const GaugeV& g, int p, int mu, int s, cx<T> U[3][3]) {
+    typedef Layout<P, R> Lay;
+    const char* base = (const char*)g.data + (size_t)(p * 4 + mu) * Lay::NC * g.vh * sizeof(typename Lay::C);
+    T v[R];
+    load_reals<P, R, T>(base, g.vh, s, g.scale, v);
+#pragma unroll
+    for (int a = 0; a < 2; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++) U[a][b] = mk(v[(a * 3 + b) * 2], v[(a * 3 + b) * 2 + 1]);
+    if constexpr (R == 18) {
+#pragma unroll
+        for (int b = 0; b < 3; b++) U[2][b] = mk(v[(6 + b) * 2], v[(6 + b) * 2 + 1]);
+    } else {
+        // row2 = conj(row0 x row1)
+        U[2][0] = cj(U[0][1] * U[1][2] - U[0][2] * U[1][1]);
+        U[2][1] = cj(U[0][2] * U[1][0] - U[0][0] * U[1][2]);
+        U[2][2] = cj(U[0][0] * U[1][1] - U[0][1] * U[1][0]);
+    }
+}
+
+// out = U v, out = U^+ v
+template <typename T>
+__device__ __forceinline__ void su3_mv(const cx<T> U[3][3], const cx<T> v[3], cx<T> out[3]) {
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        cx<T> acc = U[a][0] * v[0];
+        cmac(acc, U[a][1], v[1]);
+        cmac(acc, U[a][2], v[2]);
+        out[a] = acc;
+    }
+}
+template <typename T>
+__device__ __forceinline__ void su3_dmv(const cx<T> U[3][3], const cx<T> v[3], cx<T> out[3]) {
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        cx<T> acc = mk((T)0, (T)0);
+        cjmac(acc, U[0][a], v[0]);
+        cjmac(acc, U[1][a], v[1]);
+        cjmac(acc, U[2][a], v[2]);
+        out[a] = acc;
+    }
+}
+
+}  // namespace lq

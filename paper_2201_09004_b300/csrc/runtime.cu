@@ -1,0 +1,212 @@
+// runtime.cu -- errors, launch bookkeeping, profiling events, autotuner, device
+// memory and fields.
+#include <string.h>
+
+#include <atomic>
+#include <mutex>
+#include <unordered_map>
+
+#include "runtime.h"
+
+namespace lq {
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string g_last_error;
+
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+void fail(int code, const std::string& msg) { throw Error{code, msg}; }
+
+// ----------------------------------------------------------------- launches
+static std::atomic<int64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+struct ProfRec {
+    std::string name;
+    cudaEvent_t a, b;
+};
+static std::mutex g_prof_mu;
+static std::atomic<bool> g_prof_on{false};
+static std::vector<ProfRec> g_prof;                                   // recorded launches since reset
+static std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_prof_free;  // reusable event pairs
+
+bool stream_capturing(cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return cs != cudaStreamCaptureStatusNone;
+}
+
+int prof_begin(const char* name, cudaStream_t st) {
+    if (!g_prof_on.load()) return -1;
+    if (stream_capturing(st)) return -1;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    std::pair<cudaEvent_t, cudaEvent_t> ev;
+    if (!g_prof_free.empty()) {
+        ev = g_prof_free.back();
+        g_prof_free.pop_back();
+    } else {
+        cudaEventCreate(&ev.first);
+        cudaEventCreate(&ev.second);
+    }
+    cudaEventRecord(ev.first, st);
+    g_prof.push_back(ProfRec{name, ev.first, ev.second});
+    return (int)g_prof.size() - 1;
+}
+
+void prof_end(int slot, cudaStream_t st) {
+    if (slot < 0) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    cudaEventRecord(g_prof[slot].b, st);
+}
+
+// ------------------------------------------------------------------- tuner
+static std::mutex g_tune_mu;
+static std::unordered_map<std::string, int> g_tuned;
+
+int num_sms() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        n = v > 0 ? v : 148;
+    }
+    return n;
+}
+
+int tuned_block(const std::string& key, cudaStream_t st, const std::function<void(int)>& run) {
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) return it->second;
+    }
+    if (stream_capturing(st)) return 128;
+    static const int cand[] = {64, 128, 256};
+    cudaEvent_t a, b;
+    LQ_CUDA(cudaEventCreate(&a));
+    LQ_CUDA(cudaEventCreate(&b));
+    // tuning launches are not part of the caller's profile
+    bool was_on = g_prof_on.exchange(false);
+    int best = 128;
+    float best_ms = 1e30f;
+    try {
+        for (int bs : cand) {
+            run(bs);  // warm-up
+            LQ_CUDA(cudaEventRecord(a, st));
+            for (int r = 0; r < 3; r++) run(bs);
+            LQ_CUDA(cudaEventRecord(b, st));
+            LQ_CUDA(cudaEventSynchronize(b));
+            float ms = 0.f;
+            LQ_CUDA(cudaEventElapsedTime(&ms, a, b));
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = bs;
+            }
+        }
+    } catch (...) {
+        g_prof_on.store(was_on);
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        throw;
+    }
+    g_prof_on.store(was_on);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[key] = best;
+    return best;
+}
+
+// ------------------------------------------------------------------- memory
+void* dev_alloc(Lattice* lat, size_t bytes) {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        fail(LQ_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+    }
+    if (lat) lat->bytes += bytes;
+    return p;
+}
+
+void dev_free(Lattice* lat, void* p, size_t bytes) {
+    if (!p) return;
+    cudaFree(p);
+    if (lat) lat->bytes -= bytes;
+}
+
+static size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
+
+static size_t rhs_bytes_of(int kind, int prec, int vh) {
+    int nr = kind == LQ_WILSON_FIELD ? 24 : 6;
+    return align256((size_t)nr * (prec == LQ_F64 ? 8 : (prec == LQ_F32 ? 4 : 2)) * vh);
+}
+
+size_t field_bytes(int kind, int prec, int nrhs, int vh) {
+    size_t b = rhs_bytes_of(kind, prec, vh) * nrhs;
+    if (prec == LQ_F16) b += align256((size_t)vh * 4 * nrhs);
+    return b;
+}
+
+Field field_alloc(int kind, int prec, int nrhs, int vh) {
+    Field f;
+    f.kind = kind;
+    f.prec = prec;
+    f.nrhs = nrhs;
+    f.vh = vh;
+    f.rhs_bytes = rhs_bytes_of(kind, prec, vh);
+    f.data = dev_alloc(nullptr, field_bytes(kind, prec, nrhs, vh));
+    if (prec == LQ_F16) f.norm = (float*)((char*)f.data + f.rhs_bytes * nrhs);
+    return f;
+}
+
+void field_free(Field& f) {
+    if (f.data) cudaFree(f.data);
+    f.data = nullptr;
+    f.norm = nullptr;
+}
+
+}  // namespace lq
+
+// ------------------------------------------------------------- C ABI parts
+using namespace lq;
+
+extern "C" const char* lq_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" int lq_profile_enable(int on) {
+    g_prof_on.store(on != 0);
+    return LQ_OK;
+}
+
+extern "C" int lq_profile_reset(void) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto& r : g_prof) g_prof_free.push_back({r.a, r.b});
+    g_prof.clear();
+    g_launches.store(0);
+    return LQ_OK;
+}
+
+extern "C" int lq_profile_query(const char* name, int64_t* launches, double* total_ms) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    int64_t n = 0;
+    double t = 0.0;
+    for (auto& r : g_prof) {
+        if (name && *name && r.name.find(name) == std::string::npos) continue;
+        if (cudaEventSynchronize(r.b) != cudaSuccess) {
+            set_last_error("lq_profile_query: event synchronisation failed");
+            return LQ_ECUDA;
+        }
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            t += ms;
+            n++;
+        }
+    }
+    if (launches) *launches = n;
+    if (total_ms) *total_ms = t;
+    return LQ_OK;
+}
+
+extern "C" int64_t lq_launch_count(void) { return g_launches.load(); }

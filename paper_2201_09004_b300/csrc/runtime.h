@@ -1,0 +1,191 @@
+// runtime.h -- host-side runtime of the library: error handling, kernel launch
+// bookkeeping (launch counter, optional per-launch CUDA-event timing), the
+// block-size autotuner, and the lattice / field objects behind the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <functional>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/lq.h"
+#include "core.cuh"
+
+namespace lq {
+
+// ------------------------------------------------------------------ errors
+struct Error {
+    int code;
+    std::string msg;
+};
+void set_last_error(const std::string& msg);
+[[noreturn]] void fail(int code, const std::string& msg);
+
+#define LQ_CUDA(call)                                                                        \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            ::lq::fail(e_ == cudaErrorMemoryAllocation ? LQ_ENOMEM : LQ_ECUDA,               \
+                       std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+    } while (0)
+
+// ----------------------------------------------------------------- launches
+// Every kernel launch of the library goes through launch(): the launch counter
+// is always kept; with profiling on, CUDA events bracket the launch on its
+// stream (not while the stream is being captured into a graph).
+int prof_begin(const char* name, cudaStream_t st);
+void prof_end(int slot, cudaStream_t st);
+void count_launch();
+bool stream_capturing(cudaStream_t st);
+
+template <typename... KArgs, typename... Args>
+inline void launch(const char* name, void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t st,
+                   Args&&... args) {
+    if (grid.x == 0 || grid.y == 0) return;
+    int slot = prof_begin(name, st);
+    kernel<<<grid, block, 0, st>>>(std::forward<Args>(args)...);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) fail(LQ_ECUDA, std::string("launch of ") + name + ": " + cudaGetErrorString(e));
+    prof_end(slot, st);
+    count_launch();
+}
+
+// Block-size autotuner: the first call for a key times each candidate block
+// size on the real arguments (the launch must be idempotent) and caches the
+// fastest; later calls reuse it. While a stream is capturing, an untuned key
+// falls back to 128 threads.
+int tuned_block(const std::string& key, cudaStream_t st, const std::function<void(int)>& run);
+int num_sms();
+
+// ------------------------------------------------------------------- fields
+// A spinor (24 reals/site) or staggered colour vector (6 reals/site) field of
+// one parity with nrhs right-hand sides in one allocation.
+struct Field {
+    int kind = 0;  // LQ_WILSON_FIELD / LQ_STAGGERED_FIELD
+    int prec = 0;
+    int nrhs = 0;
+    int vh = 0;
+    void* data = nullptr;
+    float* norm = nullptr;
+    size_t rhs_bytes = 0;
+    int nreals() const { return kind == LQ_WILSON_FIELD ? 24 : 6; }
+    FieldV view() const { return FieldV{data, norm, vh, rhs_bytes}; }
+    FieldV view_rhs(int k) const {
+        return FieldV{(char*)data + (size_t)k * rhs_bytes, norm ? norm + (size_t)k * vh : nullptr, vh, rhs_bytes};
+    }
+    // non-owning view of right-hand sides [k0, k0 + n)
+    Field sub(int k0, int n) const {
+        Field f = *this;
+        f.nrhs = n;
+        f.data = (char*)data + (size_t)k0 * rhs_bytes;
+        f.norm = norm ? norm + (size_t)k0 * vh : nullptr;
+        return f;
+    }
+};
+Field field_alloc(int kind, int prec, int nrhs, int vh);
+void field_free(Field& f);
+size_t field_bytes(int kind, int prec, int nrhs, int vh);
+
+// ------------------------------------------------------------------ lattice
+struct PackedGauge {
+    void* data = nullptr;
+    float scale = 1.f;
+    size_t bytes = 0;
+};
+
+struct Lattice {
+    int L[4];
+    int bc_t;
+    int V, vh;
+    Geo geo;
+    int device;
+    double* canon[3] = {nullptr, nullptr, nullptr};  // canonical FP64 links per kind (device)
+    float maxabs[3] = {1.f, 1.f, 1.f};               // max |re|,|im| per kind (FP16 scale)
+    std::map<std::tuple<int, int, int>, PackedGauge> packed;  // (kind, prec, recon)
+    bool has_clover = false;
+    double c_sw = 0.0;
+    void* clovC[3] = {nullptr, nullptr, nullptr};  // clover C per precision, [2 parities][72 reals][vh]
+    float* clovC_norm = nullptr;                     // FP16 norms [2][vh]
+    struct Ainv {
+        void* data[3] = {nullptr, nullptr, nullptr};
+        float* norm = nullptr;
+    };
+    std::map<std::pair<double, double>, Ainv> ainv;  // (m, mu) -> A^{-1} per precision
+    size_t bytes = 0;                                // device bytes held
+};
+
+GaugeV gauge_view(Lattice& lat, int kind, int prec, int recon);
+// pointer to parity block of the clover (C, 72 reals) / inverse (144 reals)
+const void* clover_block(Lattice& lat, int prec, int parity, const float** norm);
+const void* ainv_block(Lattice& lat, double m, double mu, int prec, int parity, const float** norm, cudaStream_t st);
+void free_clover(Lattice& lat);
+
+void* dev_alloc(Lattice* lat, size_t bytes);
+void dev_free(Lattice* lat, void* p, size_t bytes);
+
+// ------------------------------------------------------------ pack / unpack
+void pack_gauge(Lattice& lat, int kind, int prec, int recon, PackedGauge& out, cudaStream_t st);
+// canonical FP64 (device) <-> field rhs k of parity p
+void import_field(const Lattice& lat, Field& f, int k, int parity, const double* canon_dev, cudaStream_t st);
+void export_field(const Lattice& lat, const Field& f, int k, int parity, double* canon_dev, cudaStream_t st);
+void gauge_maxabs(const double* canon, int V, float* out, cudaStream_t st);
+
+// ------------------------------------------------------------------ clover
+void build_clover(Lattice& lat, double c_sw, cudaStream_t st);
+void load_clover_canonical(Lattice& lat, const double* canon_dev, cudaStream_t st);
+void build_ainv(Lattice& lat, double m, double mu, Lattice::Ainv& out, cudaStream_t st);
+
+// ------------------------------------------------------------------ dslash
+struct OpDesc {
+    int action;
+    double m, mu, c_naik;
+    int prec;
+    int recon;   // thin (Wilson) / long (HISQ) link compression
+};
+
+// out = epilogue(D in) for output parity; `y` used by EPI_XPAY (same parity as out).
+// norm_out: optional per-block partials of |out|^2 (nrhs * blocks).
+// Returns the number of thread blocks per right-hand side (the partial-sum stride).
+int wilson_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int epi, const Field& in,
+                  Field& out, const Field* y, double* norm_out, cudaStream_t st);
+int hisq_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int epi, double a, const Field& in,
+                Field& out, const Field* y, double* norm_out, cudaStream_t st);
+// site-local out = A_pp^{-1} in (Wilson twisted mass / clover), parity of both fields
+void wilson_ainv_site(Lattice& lat, const OpDesc& op, int parity, int dagger, const Field& in, Field& out,
+                      cudaStream_t st);
+
+// ------------------------------------------------------------------- blas
+// All BLAS kernels work on whole fields of one parity, per right-hand side.
+// Reductions write per-block partials to `part`, then finalize into dev scalars.
+enum { RED_BLOCKS = 148 * 4, RED_THREADS = 256 };
+void blas_norm2(const Field& x, double* part, cudaStream_t st);          // part[k*RED_BLOCKS + b]
+void blas_copy(Field& dst, const Field& src, cudaStream_t st);           // with precision conversion
+void blas_zero(Field& x, cudaStream_t st);
+void blas_axpy_h(Field& y, const double* a_host, const Field& x, cudaStream_t st);  // y += a_k x (host scalars)
+// y = a_k x + b_k y per right-hand side k (host scalars), optional partial |y|^2
+void blas_axpby_h(Field& y, const double* a, const Field& x, const double* b, double* part, cudaStream_t st);
+// s = b - q, with partial |s|^2
+void blas_xmy_norm(Field& s, const Field& b, const Field& q, double* part, cudaStream_t st);
+// CG update: alpha_k = sc[k*SC_N + SC_ALPHA]; x += alpha p; s -= alpha q; partial |s|^2
+void blas_cg_xs(Field& x, const Field& p, Field& s, const Field& q, const double* sc, double* part,
+                cudaStream_t st);
+// p = r + beta p, beta_k = sc[k*SC_N + SC_BETA]
+void blas_cg_p(Field& p, const Field& r, const double* sc, cudaStream_t st);
+
+// scalar slots per right-hand side in the solver scalar block
+enum { SC_RR = 0, SC_QQ, SC_SS, SC_RRN, SC_ALPHA, SC_BETA, SC_B2, SC_FROZEN, SC_PP, SC_N };
+enum { FIN_SET = 0, FIN_ALPHA = 1, FIN_BETA = 2 };
+// sum part[k*nblocks ...] (compensated, fixed order) into sc[k*SC_N + slot], or apply `op`
+void blas_finalize(const double* part, int nblocks, int nrhs, double* sc, int slot, int op, cudaStream_t st);
+
+// ----------------------------------------------------------------- solvers
+int solve_wilson(Lattice& lat, const lq_op_params& op, const lq_solve_params& sp, int nrhs, const double* const* b,
+                 double* const* x, lq_solve_info* info, cudaStream_t st);
+int solve_hisq(Lattice& lat, const lq_op_params& op, const lq_solve_params& sp, int nrhs, const double* const* b,
+               double* const* x, lq_solve_info* info, cudaStream_t st);
+
+}  // namespace lq

@@ -1,0 +1,390 @@
+// wilson.cuh -- Wilson hopping term with fused site-local epilogues.
+//
+// For output parity p, each thread takes one site x and NB right-hand sides:
+//   D psi(x) = 1/2 sum_mu [(1 + s g_mu) U_mu(x) psi(x+mu) + (1 - s g_mu) U_mu(x-mu)^+ psi(x-mu)]
+// with s = +1 (H, Sec. 2.1 Eq. 2 with M = -D_w) or s = -1 (H^+). Each
+// neighbour is spin-projected to a half spinor (two spin components, since
+// (1 +- g_mu) has rank two), multiplied by the link once per half spinor, and
+// expanded back, so a hop costs 2 SU(3) mat-vecs instead of 4. The link of a
+// direction is loaded once and used for all NB right-hand sides.
+//
+// Epilogues (A = (4+m) + i mu g5 + C is site-local; mu's sign is flipped by
+// the host for the adjoint, and C is hermitian):
+//   EPI_HOP   out = D psi
+//   EPI_AINV  out = A^{-1} D psi     (A^{-1} stored per site, or analytic without clover)
+//   EPI_XPAY  out = A y - D psi      (y: same-parity input; gives M = A - H and the
+//                                     Schur operator A_ee - H_eo (A_oo^{-1} H_oe v))
+// Gamma basis DeGrand-Rossi, g5 = diag(1,1,-1,-1): the chiral blocks are spins
+// {0,1} and {2,3}; C and A^{-1} are stored as two 6x6 blocks (index 3*spin'+colour).
+#pragma once
+#include "core.cuh"
+
+namespace lq {
+
+struct WilsonArgs {
+    Geo g;
+    GaugeV U;
+    FieldV in, out, y;
+    const void* clov;       // output parity block: C (72 reals) for XPAY, A^{-1} (144) for AINV
+    const float* clov_norm; // FP16 per-site norms of that block
+    int parity;             // output parity
+    int dagger;
+    int has_clover;
+    double m4;              // 4 + m
+    double mu;              // twisted mass, already negated for the adjoint
+    int nrhs;
+    double* norm_out;       // if non-null: per-block partial sums of |out|^2, per rhs
+};
+
+// spin projection h = top two spins of (1 + s g_mu) psi, for psi as cx[4][3]
+template <int MU, typename T>
+__device__ __forceinline__ void proj(const cx<T> ps[4][3], T s, cx<T> h0[3], cx<T> h1[3]) {
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        if constexpr (MU == 0) {        // g1: h0 = p0 + s i p3, h1 = p1 + s i p2
+            h0[c] = ps[0][c] + s * ti(ps[3][c]);
+            h1[c] = ps[1][c] + s * ti(ps[2][c]);
+        } else if constexpr (MU == 1) { // g2: h0 = p0 - s p3, h1 = p1 + s p2
+            h0[c] = ps[0][c] - s * ps[3][c];
+            h1[c] = ps[1][c] + s * ps[2][c];
+        } else if constexpr (MU == 2) { // g3: h0 = p0 + s i p2, h1 = p1 - s i p3
+            h0[c] = ps[0][c] + s * ti(ps[2][c]);
+            h1[c] = ps[1][c] - s * ti(ps[3][c]);
+        } else {                        // g4: h0 = p0 + s p2, h1 = p1 + s p3
+            h0[c] = ps[0][c] + s * ps[2][c];
+            h1[c] = ps[1][c] + s * ps[3][c];
+        }
+    }
+}
+
+// acc += full spinor reconstructed from the rotated half spinor r0, r1
+template <int MU, typename T>
+__device__ __forceinline__ void recon_acc(cx<T> acc[4][3], const cx<T> r0[3], const cx<T> r1[3], T s) {
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        acc[0][c] = acc[0][c] + r0[c];
+        acc[1][c] = acc[1][c] + r1[c];
+        if constexpr (MU == 0) {        // comp2 = -s i h1, comp3 = -s i h0
+            acc[2][c] = acc[2][c] - s * ti(r1[c]);
+            acc[3][c] = acc[3][c] - s * ti(r0[c]);
+        } else if constexpr (MU == 1) { // comp2 = s h1, comp3 = -s h0
+            acc[2][c] = acc[2][c] + s * r1[c];
+            acc[3][c] = acc[3][c] - s * r0[c];
+        } else if constexpr (MU == 2) { // comp2 = -s i h0, comp3 = s i h1
+            acc[2][c] = acc[2][c] - s * ti(r0[c]);
+            acc[3][c] = acc[3][c] + s * ti(r1[c]);
+        } else {                        // comp2 = s h0, comp3 = s h1
+            acc[2][c] = acc[2][c] + s * r0[c];
+            acc[3][c] = acc[3][c] + s * r1[c];
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void to_spinor(const T* v, cx<T> ps[4][3]) {
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) ps[a][c] = mk(v[(a * 3 + c) * 2], v[(a * 3 + c) * 2 + 1]);
+}
+
+template <int MU, int P, int R, int NB, typename T>
+__device__ __forceinline__ void hop_dir(const WilsonArgs& a, const int c[4], int s, int kb, T sf,
+                                        cx<T> acc[NB][4][3]) {
+    // forward: (1 + sf g_mu) U_mu(x) psi(x+mu)
+    {
+        float bs;
+        const int n = cb_hop(a.g, c, MU, +1, bs);
+        cx<T> U[3][3];
+        load_link<P, R, T>(a.U, a.parity, MU, s, U);
+        const T sg = (T)bs;
+#pragma unroll
+        for (int b = 0; b < NB; b++) {
+            if (kb + b >= a.nrhs) break;
+            T v[24];
+            fload<P, 24, T>(a.in, kb + b, n, v);
+            cx<T> ps[4][3], h0[3], h1[3], r0[3], r1[3];
+            to_spinor(v, ps);
+            proj<MU>(ps, sf, h0, h1);
+            su3_mv(U, h0, r0);
+            su3_mv(U, h1, r1);
+            if constexpr (MU == 3) {
+#pragma unroll
+                for (int k = 0; k < 3; k++) { r0[k] = sg * r0[k]; r1[k] = sg * r1[k]; }
+            }
+            recon_acc<MU>(acc[b], r0, r1, sf);
+        }
+    }
+    // backward: (1 - sf g_mu) U_mu(x-mu)^+ psi(x-mu)
+    {
+        float bs;
+        const int n = cb_hop(a.g, c, MU, -1, bs);
+        cx<T> U[3][3];
+        load_link<P, R, T>(a.U, 1 - a.parity, MU, n, U);
+        const T sg = (T)bs;
+#pragma unroll
+        for (int b = 0; b < NB; b++) {
+            if (kb + b >= a.nrhs) break;
+            T v[24];
+            fload<P, 24, T>(a.in, kb + b, n, v);
+            cx<T> ps[4][3], h0[3], h1[3], r0[3], r1[3];
+            to_spinor(v, ps);
+            proj<MU>(ps, -sf, h0, h1);
+            su3_dmv(U, h0, r0);
+            su3_dmv(U, h1, r1);
+            if constexpr (MU == 3) {
+#pragma unroll
+                for (int k = 0; k < 3; k++) { r0[k] = sg * r0[k]; r1[k] = sg * r1[k]; }
+            }
+            recon_acc<MU>(acc[b], r0, r1, -sf);
+        }
+    }
+}
+
+// element j of the chiral 6-vector of block bl: spin 2*bl + j/3, colour j%3
+template <typename T>
+__device__ __forceinline__ cx<T>& blk(cx<T> v[4][3], int bl, int j) { return v[2 * bl + j / 3][j % 3]; }
+
+// (i, j) of the q-th upper off-diagonal entry of a 6x6 matrix, row-major, i < j
+__host__ __device__ constexpr int offd_row(int q) { return q < 5 ? 0 : q < 9 ? 1 : q < 12 ? 2 : q < 14 ? 3 : 4; }
+__host__ __device__ constexpr int offd_col(int q) {
+    return q < 5 ? 1 + q : q < 9 ? 2 + (q - 5) : q < 12 ? 3 + (q - 9) : q < 14 ? 4 + (q - 12) : 5;
+}
+
+// out_b += C_b w_b for both chiral blocks, C packed per block as 6 real
+// diagonal entries then the 15 upper off-diagonal entries (row-major, i<j)
+template <int P, int NB, typename T>
+__device__ __forceinline__ void clover_apply(const WilsonArgs& a, int s, cx<T> w[NB][4][3], cx<T> out[NB][4][3]) {
+    typedef Layout<P, 72> Lay;
+    const float sc = (P == P16) ? __ldg(a.clov_norm + s) : 1.f;
+#pragma unroll
+    for (int k = 0; k < Lay::NC; k++) {
+        T v[Lay::RPC];
+        load_chunk<P, 72, T>(a.clov, a.g.vh, s, k, sc, v);
+#pragma unroll
+        for (int u = 0; u < Lay::RPC / 2; u++) {
+            const int r = k * Lay::RPC + 2 * u;  // real index of this pair
+            const int bl = r / 36;
+            const int l = r - 36 * bl;
+            if (l < 6) {
+#pragma unroll
+                for (int b = 0; b < NB; b++) {
+                    blk(out[b], bl, l) = blk(out[b], bl, l) + v[2 * u] * blk(w[b], bl, l);
+                    blk(out[b], bl, l + 1) = blk(out[b], bl, l + 1) + v[2 * u + 1] * blk(w[b], bl, l + 1);
+                }
+            } else {
+                const int q = (l - 6) / 2;
+                const int i = offd_row(q), j = offd_col(q);
+                const cx<T> e = mk(v[2 * u], v[2 * u + 1]);
+#pragma unroll
+                for (int b = 0; b < NB; b++) {
+                    cmac(blk(out[b], bl, i), e, blk(w[b], bl, j));
+                    cjmac(blk(out[b], bl, j), e, blk(w[b], bl, i));
+                }
+            }
+        }
+    }
+}
+
+// out_b = A^{-1}_b w_b (dagger: (A^{-1}_b)^+ w_b), A^{-1} stored row-major per block (36 complex)
+template <int P, int NB, typename T>
+__device__ __forceinline__ void ainv_apply(const WilsonArgs& a, int s, cx<T> w[NB][4][3], cx<T> out[NB][4][3]) {
+    typedef Layout<P, 144> Lay;
+    const float sc = (P == P16) ? __ldg(a.clov_norm + s) : 1.f;
+#pragma unroll
+    for (int k = 0; k < Lay::NC; k++) {
+        T v[Lay::RPC];
+        load_chunk<P, 144, T>(a.clov, a.g.vh, s, k, sc, v);
+#pragma unroll
+        for (int u = 0; u < Lay::RPC / 2; u++) {
+            const int e = (k * Lay::RPC) / 2 + u;
+            const int bl = e / 36;
+            const int i = (e % 36) / 6;
+            const int j = e % 6;
+            const cx<T> m = mk(v[2 * u], v[2 * u + 1]);
+#pragma unroll
+            for (int b = 0; b < NB; b++) {
+                if (a.dagger)
+                    cjmac(blk(out[b], bl, j), m, blk(w[b], bl, i));
+                else
+                    cmac(blk(out[b], bl, i), m, blk(w[b], bl, j));
+            }
+        }
+    }
+}
+
+// block reduction of per-thread |out|^2 (one value per rhs) into
+// norm_out[(kb+b) * gridDim.x + blockIdx.x]
+template <int NB>
+__device__ __forceinline__ void reduce_norms(const double nrm[NB], double* norm_out, int kb, int nrhs) {
+    __shared__ double red[NB][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int b = 0; b < NB; b++) {
+        double v = nrm[b];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[b][wid] = v;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+#pragma unroll
+        for (int b = 0; b < NB; b++) {
+            double v = lane < nw ? red[b][lane] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0 && kb + b < nrhs) norm_out[(size_t)(kb + b) * gridDim.x + blockIdx.x] = v;
+        }
+    }
+}
+
+template <int P, int R, int EPI, int NB>
+__global__ void __launch_bounds__(256) wilson_dslash_kernel(WilsonArgs a) {
+    typedef typename RealT<P>::T T;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int kb = blockIdx.y * NB;
+    double nrm[NB];
+#pragma unroll
+    for (int b = 0; b < NB; b++) nrm[b] = 0.0;
+    if (s < a.g.vh) {
+        int c[4];
+        cb_coords(a.g, s, a.parity, c);
+        cx<T> acc[NB][4][3];
+#pragma unroll
+        for (int b = 0; b < NB; b++)
+#pragma unroll
+            for (int sp = 0; sp < 4; sp++)
+#pragma unroll
+                for (int cc = 0; cc < 3; cc++) acc[b][sp][cc] = mk((T)0, (T)0);
+        const T sf = a.dagger ? (T)-1 : (T)1;
+        hop_dir<0, P, R, NB, T>(a, c, s, kb, sf, acc);
+        hop_dir<1, P, R, NB, T>(a, c, s, kb, sf, acc);
+        hop_dir<2, P, R, NB, T>(a, c, s, kb, sf, acc);
+        hop_dir<3, P, R, NB, T>(a, c, s, kb, sf, acc);
+#pragma unroll
+        for (int b = 0; b < NB; b++)
+#pragma unroll
+            for (int sp = 0; sp < 4; sp++)
+#pragma unroll
+                for (int cc = 0; cc < 3; cc++) acc[b][sp][cc] = (T)0.5 * acc[b][sp][cc];
+
+        cx<T> res[NB][4][3];
+        if constexpr (EPI == EPI_HOP) {
+#pragma unroll
+            for (int b = 0; b < NB; b++)
+#pragma unroll
+                for (int sp = 0; sp < 4; sp++)
+#pragma unroll
+                    for (int cc = 0; cc < 3; cc++) res[b][sp][cc] = acc[b][sp][cc];
+        } else if constexpr (EPI == EPI_AINV) {
+            if (a.has_clover) {
+#pragma unroll
+                for (int b = 0; b < NB; b++)
+#pragma unroll
+                    for (int sp = 0; sp < 4; sp++)
+#pragma unroll
+                        for (int cc = 0; cc < 3; cc++) res[b][sp][cc] = mk((T)0, (T)0);
+                ainv_apply<P, NB, T>(a, s, acc, res);
+            } else {
+                // A^{-1} = ((4+m) - i mu g5) / ((4+m)^2 + mu^2)
+                const T m4 = (T)a.m4, mu = (T)a.mu;
+                const T inv = (T)1 / (m4 * m4 + mu * mu);
+#pragma unroll
+                for (int b = 0; b < NB; b++)
+#pragma unroll
+                    for (int sp = 0; sp < 4; sp++) {
+                        const T chi = sp < 2 ? (T)1 : (T)-1;
+                        const cx<T> f = mk(m4 * inv, -chi * mu * inv);
+#pragma unroll
+                        for (int cc = 0; cc < 3; cc++) res[b][sp][cc] = f * acc[b][sp][cc];
+                    }
+            }
+        } else {  // EPI_XPAY: out = A y - D psi
+            cx<T> yv[NB][4][3];
+#pragma unroll
+            for (int b = 0; b < NB; b++) {
+                T v[24];
+                if (kb + b < a.nrhs) {
+                    fload<P, 24, T>(a.y, kb + b, s, v);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 24; q++) v[q] = (T)0;
+                }
+                to_spinor(v, yv[b]);
+            }
+            const T m4 = (T)a.m4, mu = (T)a.mu;
+#pragma unroll
+            for (int b = 0; b < NB; b++)
+#pragma unroll
+                for (int sp = 0; sp < 4; sp++) {
+                    const T chi = sp < 2 ? (T)1 : (T)-1;
+                    const cx<T> f = mk(m4, chi * mu);
+#pragma unroll
+                    for (int cc = 0; cc < 3; cc++) res[b][sp][cc] = f * yv[b][sp][cc] - acc[b][sp][cc];
+                }
+            if (a.has_clover) clover_apply<P, NB, T>(a, s, yv, res);
+        }
+#pragma unroll
+        for (int b = 0; b < NB; b++) {
+            if (kb + b >= a.nrhs) break;
+            T v[24];
+#pragma unroll
+            for (int sp = 0; sp < 4; sp++)
+#pragma unroll
+                for (int cc = 0; cc < 3; cc++) {
+                    v[(sp * 3 + cc) * 2] = res[b][sp][cc].r;
+                    v[(sp * 3 + cc) * 2 + 1] = res[b][sp][cc].i;
+                }
+            if (a.norm_out) {
+                // per-site sum in the kernel's precision, blocks reduce in FP64
+                T t = (T)0;
+#pragma unroll
+                for (int q = 0; q < 24; q++) t = fma(v[q], v[q], t);
+                nrm[b] = (double)t;
+            }
+            fstore<P, 24, T>(a.out, kb + b, s, v);
+        }
+    }
+    if (a.norm_out) reduce_norms<NB>(nrm, a.norm_out, kb, a.nrhs);
+}
+
+// site-local out = A^{-1} in (dagger: (A^{-1})^+ in) on fields of parity a.parity
+template <int P>
+__global__ void __launch_bounds__(256) wilson_ainv_site_kernel(WilsonArgs a) {
+    typedef typename RealT<P>::T T;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.y;
+    if (s >= a.g.vh || k >= a.nrhs) return;
+    T v[24];
+    fload<P, 24, T>(a.in, k, s, v);
+    cx<T> w[1][4][3], res[1][4][3];
+    to_spinor(v, w[0]);
+    if (a.has_clover) {
+#pragma unroll
+        for (int sp = 0; sp < 4; sp++)
+#pragma unroll
+            for (int cc = 0; cc < 3; cc++) res[0][sp][cc] = mk((T)0, (T)0);
+        ainv_apply<P, 1, T>(a, s, w, res);
+    } else {
+        const T m4 = (T)a.m4, mu = (T)a.mu;
+        const T inv = (T)1 / (m4 * m4 + mu * mu);
+#pragma unroll
+        for (int sp = 0; sp < 4; sp++) {
+            const T chi = sp < 2 ? (T)1 : (T)-1;
+            const cx<T> f = mk(m4 * inv, -chi * mu * inv);
+#pragma unroll
+            for (int cc = 0; cc < 3; cc++) res[0][sp][cc] = f * w[0][sp][cc];
+        }
+    }
+#pragma unroll
+    for (int sp = 0; sp < 4; sp++)
+#pragma unroll
+        for (int cc = 0; cc < 3; cc++) {
+            v[(sp * 3 + cc) * 2] = res[0][sp][cc].r;
+            v[(sp * 3 + cc) * 2 + 1] = res[0][sp][cc].i;
+        }
+    fstore<P, 24, T>(a.out, k, s, v);
+}
+
+}  // namespace lq
