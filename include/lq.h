@@ -227,17 +227,17 @@ int64_t lq_launch_count(void);
 
 /* ----------------------------------------------------------------- serving */
 
-/* A request server: solves submitted asynchronously, admitted while their
- * estimated device memory fits in hbm_budget_bytes, at most max_slots at once,
- * each admitted request on its own CUDA stream so that solves overlap on the
- * device. Lattices and gauge fields are created from (dims, gauge_seed) by the
- * server's loader and cached on the device across requests. */
+/* A request server for continuous batching of solves: requests are queued,
+ * admitted while their estimated device memory fits in hbm_budget_bytes (next
+ * to the lattices they use), at most max_slots at once; each admitted request
+ * runs on its own worker thread and CUDA stream, so solves that arrive while
+ * others are on the GPU start as soon as a slot and memory free up and then
+ * overlap with them on the device. Lattices (gauge and clover fields) are
+ * created and loaded by the caller and stay resident across requests. */
 typedef struct {
-    int dims[4];
-    int t_boundary;
-    uint64_t gauge_seed;
+    lq_lattice lat;           /* resident lattice; must outlive the request */
     lq_op_params op;
-    lq_solve_params solve;
+    lq_solve_params solve;    /* solve.masses is copied at submission */
     int nrhs;
 } lq_request;
 
@@ -248,14 +248,19 @@ typedef struct {
 } lq_request_times;
 
 int lq_server_create(size_t hbm_budget_bytes, int max_slots, lq_server* out);
+/* stops the workers after the admitted requests finish; queued ones are dropped */
 int lq_server_destroy(lq_server s);
-/* rhs: nrhs canonical FP64 host arrays, copied before the call returns */
+/* rhs: nrhs canonical FP64 host arrays, copied before the call returns.
+ * LQ_ENOMEM if the request alone can never fit in the budget. */
 int lq_submit(lq_server s, const lq_request* req, const double* const* rhs, uint64_t* ticket);
 /* LQ_EAGAIN until done; then copies nrhs*max(1,nshift) solutions into x (host
- * arrays), per-rhs info and the request's timestamps, and forgets the ticket */
+ * arrays), per-rhs info and the timestamps (either may be NULL), forgets the
+ * ticket and returns the solve's status */
 int lq_poll(lq_server s, uint64_t ticket, double* const* x, lq_solve_info* info, lq_request_times* times);
 /* blocks up to timeout_ms for the ticket to finish; LQ_ETIMEOUT otherwise */
 int lq_wait(lq_server s, uint64_t ticket, int timeout_ms);
+/* requests queued, running, and device bytes currently reserved by running requests */
+int lq_server_stats(lq_server s, int* queued, int* running, size_t* reserved_bytes);
 
 #ifdef __cplusplus
 }

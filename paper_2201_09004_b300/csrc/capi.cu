@@ -1,0 +1,412 @@
+// capi.cu -- the extern "C" entry points of include/lq.h. Every entry point
+// catches the library's exceptions and turns them into an lq_status plus a
+// thread-local message; no exception crosses the boundary.
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "runtime.h"
+
+using namespace lq;
+
+struct lq_field_s {
+    Lattice* lat;
+    Field f;
+};
+
+#define LQ_TRY try {
+#define LQ_CATCH                                          \
+    }                                                     \
+    catch (const Error& e) {                              \
+        set_last_error(e.msg);                            \
+        return e.code;                                    \
+    }                                                     \
+    catch (const std::bad_alloc&) {                       \
+        set_last_error("host allocation failed");         \
+        return LQ_ENOMEM;                                 \
+    }                                                     \
+    catch (...) {                                         \
+        set_last_error("unexpected internal error");      \
+        return LQ_EINVAL;                                 \
+    }
+
+static cudaStream_t as_stream(void* s) { return (cudaStream_t)s; }
+
+// device staging buffer, freed on scope exit
+struct DevBuf {
+    void* p = nullptr;
+    size_t n = 0;
+    explicit DevBuf(size_t bytes) : n(bytes) {
+        if (bytes) {
+            cudaError_t e = cudaMalloc(&p, bytes);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                fail(LQ_ENOMEM, "staging allocation failed");
+            }
+        }
+    }
+    ~DevBuf() {
+        if (p) cudaFree(p);
+    }
+};
+
+static void check_lattice(lq_lattice lat) {
+    if (!lat) fail(LQ_EINVAL, "null lattice handle");
+}
+
+static void check_op(const lq_op_params* op) {
+    if (!op) fail(LQ_EINVAL, "null operator parameters");
+    if (op->action < LQ_WILSON_TM || op->action > LQ_HISQ) fail(LQ_EINVAL, "unknown action");
+}
+
+static void check_prec(int prec) {
+    if (prec < LQ_F64 || prec > LQ_F16) fail(LQ_EINVAL, "unknown precision");
+}
+
+static size_t field_canon_bytes(const Lattice& L, int action) {
+    return (size_t)L.V * (action == LQ_HISQ ? 6 : 24) * sizeof(double);
+}
+
+extern "C" int lq_create_lattice(const int dims[4], int t_boundary, lq_lattice* out) {
+    LQ_TRY
+    if (!dims || !out) fail(LQ_EINVAL, "null argument");
+    if (t_boundary != 1 && t_boundary != -1) fail(LQ_EINVAL, "t_boundary must be +1 or -1");
+    long long v = 1;
+    for (int d = 0; d < 4; d++) {
+        if (dims[d] < 2 || (dims[d] & 1)) fail(LQ_EINVAL, "every extent must be even and >= 2");
+        v *= dims[d];
+    }
+    if (v > (1ll << 30)) fail(LQ_EINVAL, "lattice volume above 2^30 sites");
+    lq_lattice h = new lq_lattice_s();
+    Lattice& L = h->lat;
+    for (int d = 0; d < 4; d++) L.L[d] = dims[d];
+    L.bc_t = t_boundary;
+    L.V = (int)v;
+    L.vh = (int)(v / 2);
+    for (int d = 0; d < 4; d++) L.geo.L[d] = dims[d];
+    L.geo.lxh = dims[0] / 2;
+    L.geo.vh = L.vh;
+    L.geo.bc_t = t_boundary;
+    cudaGetDevice(&L.device);
+    *out = h;
+    return LQ_OK;
+    LQ_CATCH
+}
+
+extern "C" int lq_destroy_lattice(lq_lattice h) {
+    LQ_TRY
+    if (!h) return LQ_OK;
+    Lattice& L = h->lat;
+    cudaDeviceSynchronize();
+    free_clover(L);
+    for (auto& kv : L.packed) dev_free(&L, kv.second.data, kv.second.bytes);
+    for (int k = 0; k < 3; k++) dev_free(&L, L.canon[k], (size_t)L.V * 4 * 18 * sizeof(double));
+    delete h;
+    return LQ_OK;
+    LQ_CATCH
+}
+
+extern "C" int lq_lattice_bytes(lq_lattice h, size_t* bytes) {
+    LQ_TRY
+    check_lattice(h);
+    if (bytes) *bytes = h->lat.bytes;
+    return LQ_OK;
+    LQ_CATCH
+}
+
+extern "C" int lq_load_gauge(lq_lattice h, int kind, int loc, const double* links) {
+    LQ_TRY
+    check_lattice(h);
+    if (kind < LQ_THIN || kind > LQ_LONG) fail(LQ_EINVAL, "unknown gauge kind");
+    if (!links) fail(LQ_EINVAL, "null links");
+    Lattice& L = h->lat;
+    std::lock_guard<std::mutex> lk(L.mu);
+    const size_t bytes = (size_t)L.V * 4 * 18 * sizeof(double);
+    if (!L.canon[kind]) L.canon[kind] = (double*)dev_alloc(&L, bytes);
+    LQ_CUDA(cudaMemcpy(L.canon[kind], links, bytes, loc == LQ_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice));
+    gauge_maxabs(L.canon[kind], L.V, &L.maxabs[kind], 0);
+    // drop packed copies of this kind: they are rebuilt on demand
+    for (auto it = L.packed.begin(); it != L.packed.end();) {
+        if (std::get<0>(it->first) == kind) {
+            dev_free(&L, it->second.data, it->second.bytes);
+            it = L.packed.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    if (kind == LQ_THIN && L.has_clover) free_clover(L);  // the clover belongs to the old links
+    return LQ_OK;
+    LQ_CATCH
+}
+
+extern "C" int lq_load_clover(lq_lattice h, int loc, const double* clover, double c_sw) {
+    LQ_TRY
+    check_lattice(h);
+    Lattice& L = h->lat;
+    std::lock_guard<std::mutex> lk(L.mu);
+    if (!clover) {
+        build_clover(L, c_sw, 0);
+    } else {
+        const size_t bytes = (size_t)L.V * 288 * sizeof(double);
+        if (loc == LQ_HOST) {
+            DevBuf tmp(bytes);
+            LQ_CUDA(cudaMemcpy(tmp.p, clover, bytes, cudaMemcpyHostToDevice));
+            load_clover_canonical(L, (const double*)tmp.p, 0);
+        } else {
+            load_clover_canonical(L, clover, 0);
+        }
+        L.c_sw = c_sw;
+    }
+    return LQ_OK;
+    LQ_CATCH
+}
+
+static OpDesc make_desc(const lq_op_params* op, int prec) {
+    OpDesc d;
+    d.action = op->action;
+    d.m = op->m;
+    d.mu = op->action == LQ_HISQ ? 0.0 : op->mu;
+    d.c_naik = op->c_naik;
+    d.prec = prec;
+    d.recon = prec == LQ_F64 ? 18 : 12;
+    return d;
+}
+
+// stage canonical in (host or device) to device; returns device pointer
+static const double* stage_in(const double* p, size_t bytes, int loc, DevBuf& buf, cudaStream_t st) {
+    if (loc == LQ_DEVICE) return p;
+    LQ_CUDA(cudaMemcpyAsync(buf.p, p, bytes, cudaMemcpyHostToDevice, st));
+    return (const double*)buf.p;
+}
+
+extern "C" int lq_dslash_apply(lq_lattice h, const lq_op_params* op, int parity, int dagger, int prec, int loc,
+                               const double* in, double* out, void* stream) {
+    LQ_TRY
+    check_lattice(h);
+    check_op(op);
+    check_prec(prec);
+    if (parity != 0 && parity != 1) fail(LQ_EINVAL, "parity must be 0 or 1");
+    if (!in || !out) fail(LQ_EINVAL, "null field");
+    Lattice& L = h->lat;
+    cudaStream_t st = as_stream(stream);
+    const bool hisq = op->action == LQ_HISQ;
+    const int kind = hisq ? LQ_STAGGERED_FIELD : LQ_WILSON_FIELD;
+    const size_t bytes = field_canon_bytes(L, op->action);
+    DevBuf bin(loc == LQ_HOST ? bytes : 0), bout(loc == LQ_HOST ? bytes : 0);
+    const double* din = stage_in(in, bytes, loc, bin, st);
+    double* dout = loc == LQ_HOST ? (double*)bout.p : out;
+    Field fi = field_alloc(kind, prec, 1, L.vh), fo = field_alloc(kind, prec, 1, L.vh);
+    try {
+        OpDesc d = make_desc(op, prec);
+        import_field(L, fi, 0, 1 - parity, din, st);
+        if (hisq) hisq_dslash(L, d, parity, dagger, EPI_HOP, 0.0, fi, fo, nullptr, nullptr, st);
+        else wilson_dslash(L, d, parity, dagger, EPI_HOP, fi, fo, nullptr, nullptr, st);
+        LQ_CUDA(cudaMemsetAsync(dout, 0, bytes, st));
+        export_field(L, fo, 0, parity, dout, st);
+        if (loc == LQ_HOST) LQ_CUDA(cudaMemcpyAsync(out, dout, bytes, cudaMemcpyDeviceToHost, st));
+        LQ_CUDA(cudaStreamSynchronize(st));
+    } catch (...) {
+        field_free(fi);
+        field_free(fo);
+        throw;
+    }
+    field_free(fi);
+    field_free(fo);
+    return LQ_OK;
+    LQ_CATCH
+}
+
+extern "C" int lq_operator_apply(lq_lattice h, const lq_op_params* op, int form, int dagger, int prec, int loc,
+                                 const double* in, double* out, void* stream) {
+    LQ_TRY
+    check_lattice(h);
+    check_op(op);
+    check_prec(prec);
+    if (form != LQ_OP_FULL && form != LQ_OP_SCHUR) fail(LQ_EINVAL, "unknown operator form");
+    if (!in || !out) fail(LQ_EINVAL, "null field");
+    Lattice& L = h->lat;
+    cudaStream_t st = as_stream(stream);
+    const bool hisq = op->action == LQ_HISQ;
+    const int kind = hisq ? LQ_STAGGERED_FIELD : LQ_WILSON_FIELD;
+    const size_t bytes = field_canon_bytes(L, op->action);
+    DevBuf bin(loc == LQ_HOST ? bytes : 0), bout(loc == LQ_HOST ? bytes : 0);
+    const double* din = stage_in(in, bytes, loc, bin, st);
+    double* dout = loc == LQ_HOST ? (double*)bout.p : out;
+    std::vector<Field> fs;
+    try {
+        for (int i = 0; i < 4; i++) fs.push_back(field_alloc(kind, prec, 1, L.vh));
+        Field &fe = fs[0], &fo = fs[1], &oe = fs[2], &oo = fs[3];
+        OpDesc d = make_desc(op, prec);
+        LQ_CUDA(cudaMemsetAsync(dout, 0, bytes, st));
+        import_field(L, fe, 0, 0, din, st);
+        if (form == LQ_OP_FULL) {
+            import_field(L, fo, 0, 1, din, st);
+            if (hisq) {
+                // out_p = m in_p + s H in_{1-p}; the XPAY epilogue gives m y - D, and the
+                // kernel's adjoint flag negates D, so H (dagger 0) needs the flag set
+                hisq_dslash(L, d, 0, !dagger, EPI_XPAY, op->m, fo, oe, &fe, nullptr, st);
+                hisq_dslash(L, d, 1, !dagger, EPI_XPAY, op->m, fe, oo, &fo, nullptr, st);
+            } else {
+                wilson_dslash(L, d, 0, dagger, EPI_XPAY, fo, oe, &fe, nullptr, st);
+                wilson_dslash(L, d, 1, dagger, EPI_XPAY, fe, oo, &fo, nullptr, st);
+            }
+            export_field(L, oe, 0, 0, dout, st);
+            export_field(L, oo, 0, 1, dout, st);
+        } else {
+            if (hisq) schur_hisq(L, d, op->m * op->m, fe, oe, fo, nullptr, st);
+            else schur_wilson(L, d, dagger, fe, oe, fo, nullptr, st);
+            export_field(L, oe, 0, 0, dout, st);
+        }
+        if (loc == LQ_HOST) LQ_CUDA(cudaMemcpyAsync(out, dout, bytes, cudaMemcpyDeviceToHost, st));
+        LQ_CUDA(cudaStreamSynchronize(st));
+    } catch (...) {
+        for (auto& f : fs) field_free(f);
+        throw;
+    }
+    for (auto& f : fs) field_free(f);
+    return LQ_OK;
+    LQ_CATCH
+}
+
+extern "C" int lq_solve(lq_lattice h, const lq_op_params* op, const lq_solve_params* sp, int nrhs,
+                        const double* const* rhs, double* const* x, int loc, lq_solve_info* info, void* stream) {
+    LQ_TRY
+    check_lattice(h);
+    check_op(op);
+    if (!sp || !rhs || !x) fail(LQ_EINVAL, "null argument");
+    if (nrhs < 1) fail(LQ_EINVAL, "nrhs must be positive");
+    Lattice& L = h->lat;
+    cudaStream_t st = as_stream(stream);
+    const size_t bytes = field_canon_bytes(L, op->action);
+    const int nsol = nrhs * ((op->action == LQ_HISQ && sp->solver == LQ_MULTISHIFT_CG) ? std::max(1, sp->nshift) : 1);
+    for (int k = 0; k < nrhs; k++)
+        if (!rhs[k]) fail(LQ_EINVAL, "null right-hand side");
+    for (int k = 0; k < nsol; k++)
+        if (!x[k]) fail(LQ_EINVAL, "null solution pointer");
+    std::vector<const double*> db(nrhs);
+    std::vector<double*> dx(nsol);
+    DevBuf stage(loc == LQ_HOST ? bytes * (nrhs + nsol) : 0);
+    if (loc == LQ_HOST) {
+        for (int k = 0; k < nrhs; k++) {
+            double* d = (double*)stage.p + (size_t)k * (bytes / sizeof(double));
+            LQ_CUDA(cudaMemcpyAsync(d, rhs[k], bytes, cudaMemcpyHostToDevice, st));
+            db[k] = d;
+        }
+        for (int k = 0; k < nsol; k++) dx[k] = (double*)stage.p + (size_t)(nrhs + k) * (bytes / sizeof(double));
+    } else {
+        for (int k = 0; k < nrhs; k++) db[k] = rhs[k];
+        for (int k = 0; k < nsol; k++) dx[k] = x[k];
+    }
+    int ret;
+    if (op->action == LQ_HISQ) ret = solve_hisq(L, *op, *sp, nrhs, db.data(), dx.data(), info, st);
+    else ret = solve_wilson(L, *op, *sp, nrhs, db.data(), dx.data(), info, st);
+    if (loc == LQ_HOST)
+        for (int k = 0; k < nsol; k++) LQ_CUDA(cudaMemcpyAsync(x[k], dx[k], bytes, cudaMemcpyDeviceToHost, st));
+    LQ_CUDA(cudaStreamSynchronize(st));
+    return ret;
+    LQ_CATCH
+}
+
+// ----------------------------------------------------------------- fields
+extern "C" int lq_field_create(lq_lattice h, int kind, int prec, int nrhs, lq_field* out) {
+    LQ_TRY
+    check_lattice(h);
+    check_prec(prec);
+    if (kind != LQ_WILSON_FIELD && kind != LQ_STAGGERED_FIELD) fail(LQ_EINVAL, "unknown field kind");
+    if (nrhs < 1 || nrhs > 64 || !out) fail(LQ_EINVAL, "nrhs must be in [1, 64]");
+    lq_field f = new lq_field_s();
+    f->lat = &h->lat;
+    try {
+        f->f = field_alloc(kind, prec, nrhs, h->lat.vh);
+    } catch (...) {
+        delete f;
+        throw;
+    }
+    *out = f;
+    return LQ_OK;
+    LQ_CATCH
+}
+
+extern "C" int lq_field_destroy(lq_field f) {
+    LQ_TRY
+    if (!f) return LQ_OK;
+    cudaDeviceSynchronize();
+    field_free(f->f);
+    delete f;
+    return LQ_OK;
+    LQ_CATCH
+}
+
+extern "C" int lq_field_import(lq_field f, int k, int parity, int loc, const double* canonical, void* stream) {
+    LQ_TRY
+    if (!f || !canonical) fail(LQ_EINVAL, "null argument");
+    if (k < 0 || k >= f->f.nrhs || (parity != 0 && parity != 1)) fail(LQ_EINVAL, "rhs index or parity");
+    cudaStream_t st = as_stream(stream);
+    const size_t bytes = (size_t)f->lat->V * f->f.nreals() * sizeof(double);
+    DevBuf b(loc == LQ_HOST ? bytes : 0);
+    const double* d = stage_in(canonical, bytes, loc, b, st);
+    import_field(*f->lat, f->f, k, parity, d, st);
+    if (loc == LQ_HOST) LQ_CUDA(cudaStreamSynchronize(st));
+    return LQ_OK;
+    LQ_CATCH
+}
+
+extern "C" int lq_field_export(lq_field f, int k, int parity, int loc, double* canonical, void* stream) {
+    LQ_TRY
+    if (!f || !canonical) fail(LQ_EINVAL, "null argument");
+    if (k < 0 || k >= f->f.nrhs || (parity != 0 && parity != 1)) fail(LQ_EINVAL, "rhs index or parity");
+    cudaStream_t st = as_stream(stream);
+    const size_t bytes = (size_t)f->lat->V * f->f.nreals() * sizeof(double);
+    if (loc == LQ_HOST) {
+        DevBuf b(bytes);
+        LQ_CUDA(cudaMemcpyAsync(b.p, canonical, bytes, cudaMemcpyHostToDevice, st));
+        export_field(*f->lat, f->f, k, parity, (double*)b.p, st);
+        LQ_CUDA(cudaMemcpyAsync(canonical, b.p, bytes, cudaMemcpyDeviceToHost, st));
+        LQ_CUDA(cudaStreamSynchronize(st));
+    } else {
+        export_field(*f->lat, f->f, k, parity, canonical, st);
+    }
+    return LQ_OK;
+    LQ_CATCH
+}
+
+static void check_pair(lq_lattice h, lq_field a, lq_field b) {
+    if (!a || !b) fail(LQ_EINVAL, "null field");
+    if (a->lat != &h->lat || b->lat != &h->lat) fail(LQ_EINVAL, "field belongs to another lattice");
+    if (a->f.kind != b->f.kind || a->f.prec != b->f.prec || a->f.nrhs != b->f.nrhs)
+        fail(LQ_EINVAL, "fields differ in kind, precision or nrhs");
+}
+
+extern "C" int lq_dslash_field(lq_lattice h, const lq_op_params* op, int parity, int dagger, lq_field in,
+                               lq_field out, void* stream) {
+    LQ_TRY
+    check_lattice(h);
+    check_op(op);
+    check_pair(h, in, out);
+    if (parity != 0 && parity != 1) fail(LQ_EINVAL, "parity must be 0 or 1");
+    OpDesc d = make_desc(op, in->f.prec);
+    if (op->action == LQ_HISQ) {
+        if (in->f.kind != LQ_STAGGERED_FIELD) fail(LQ_EINVAL, "HISQ needs staggered fields");
+        hisq_dslash(h->lat, d, parity, dagger, EPI_HOP, 0.0, in->f, out->f, nullptr, nullptr, as_stream(stream));
+    } else {
+        if (in->f.kind != LQ_WILSON_FIELD) fail(LQ_EINVAL, "Wilson actions need Wilson fields");
+        wilson_dslash(h->lat, d, parity, dagger, EPI_HOP, in->f, out->f, nullptr, nullptr, as_stream(stream));
+    }
+    return LQ_OK;
+    LQ_CATCH
+}
+
+extern "C" int lq_schur_field(lq_lattice h, const lq_op_params* op, int dagger, lq_field in, lq_field out,
+                              lq_field tmp, void* stream) {
+    LQ_TRY
+    check_lattice(h);
+    check_op(op);
+    check_pair(h, in, out);
+    check_pair(h, in, tmp);
+    OpDesc d = make_desc(op, in->f.prec);
+    if (op->action == LQ_HISQ) schur_hisq(h->lat, d, op->m * op->m, in->f, out->f, tmp->f, nullptr, as_stream(stream));
+    else schur_wilson(h->lat, d, dagger, in->f, out->f, tmp->f, nullptr, as_stream(stream));
+    return LQ_OK;
+    LQ_CATCH
+}

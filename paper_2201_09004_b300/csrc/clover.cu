@@ -370,6 +370,7 @@ const void* clover_block(Lattice& lat, int prec, int parity, const float** norm)
 }
 
 const void* ainv_block(Lattice& lat, double m, double mu, int prec, int parity, const float** norm, cudaStream_t st) {
+    std::lock_guard<std::mutex> lk(lat.mu);
     if (!lat.has_clover) fail(LQ_EINVAL, "clover term not loaded");
     auto key = std::make_pair(m, mu);
     auto it = lat.ainv.find(key);
@@ -377,6 +378,7 @@ const void* ainv_block(Lattice& lat, double m, double mu, int prec, int parity, 
         if (stream_capturing(st)) fail(LQ_EINVAL, "clover inverse for a new (m, mu) requested during capture");
         Lattice::Ainv a;
         build_ainv(lat, m, mu, a, st);
+        LQ_CUDA(cudaStreamSynchronize(st));
         it = lat.ainv.emplace(key, a).first;
     }
     size_t per = rec_bytes(prec, 144, lat.vh) / 2;

@@ -53,6 +53,7 @@ void pack_gauge(Lattice& lat, int kind, int prec, int recon, PackedGauge& out, c
 }
 
 GaugeV gauge_view(Lattice& lat, int kind, int prec, int recon) {
+    std::lock_guard<std::mutex> lk(lat.mu);
     auto key = std::make_tuple(kind, prec, recon);
     auto it = lat.packed.find(key);
     if (it == lat.packed.end()) {

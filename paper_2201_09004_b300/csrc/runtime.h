@@ -116,6 +116,7 @@ struct Lattice {
     };
     std::map<std::pair<double, double>, Ainv> ainv;  // (m, mu) -> A^{-1} per precision
     size_t bytes = 0;                                // device bytes held
+    std::mutex mu;  // guards the lazily filled caches when several streams share the lattice
 };
 
 GaugeV gauge_view(Lattice& lat, int kind, int prec, int recon);
@@ -183,9 +184,21 @@ enum { FIN_SET = 0, FIN_ALPHA = 1, FIN_BETA = 2 };
 void blas_finalize(const double* part, int nblocks, int nrhs, double* sc, int slot, int op, cudaStream_t st);
 
 // ----------------------------------------------------------------- solvers
+// Schur operators on resident fields (see solver.cu)
+int schur_wilson(Lattice& lat, const OpDesc& op, int dagger, const Field& in, Field& out, Field& tmp, double* part,
+                 cudaStream_t st);
+int schur_hisq(Lattice& lat, const OpDesc& op, double sigma, const Field& in, Field& out, Field& t, double* part_t,
+               cudaStream_t st);
+// estimated device bytes of a solve's work fields
+size_t solve_workspace_bytes(const Lattice& lat, const lq_op_params& op, const lq_solve_params& sp, int nrhs);
 int solve_wilson(Lattice& lat, const lq_op_params& op, const lq_solve_params& sp, int nrhs, const double* const* b,
                  double* const* x, lq_solve_info* info, cudaStream_t st);
 int solve_hisq(Lattice& lat, const lq_op_params& op, const lq_solve_params& sp, int nrhs, const double* const* b,
                double* const* x, lq_solve_info* info, cudaStream_t st);
 
 }  // namespace lq
+
+// the opaque handle of include/lq.h
+struct lq_lattice_s {
+    lq::Lattice lat;
+};

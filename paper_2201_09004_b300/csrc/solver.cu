@@ -1,0 +1,652 @@
+// solver.cu -- even-odd preconditioned Krylov solvers on the device.
+//
+// Wilson twisted mass (+clover), asymmetric even-odd Schur complement:
+//   M = [[A_ee, -H_eo], [-H_oe, A_oo]],  Mhat = A_ee - H_eo A_oo^{-1} H_oe,
+//   bhat = b_e + H_eo A_oo^{-1} b_o,  Mhat x_e = bhat,  x_o = A_oo^{-1} (b_o + H_oe x_e).
+// The odd rows are then solved exactly, so the full residual of M x = b is
+// bhat - Mhat x_e. Mhat is solved by CG on the normal equations (CGNR), in one
+// precision or mixed with FP64 reliable updates (the mixed-precision solvers
+// the paper's GPU inverters rest on, refs. of Sec. 1).
+//
+// HISQ: D = m + H with H anti-hermitian and connecting even and odd sites only:
+//   (m^2 - H_eo H_oe) x_e = m b_e - H_eo b_o,  x_o = (b_o - H_oe x_e) / m,
+// and m^2 - H_eo H_oe = m^2 + H_oe^+ H_oe is hermitian positive definite, so
+// plain CG applies; several masses share one Krylov space through multi-shift
+// CG (Jegerlehner, the multi-mass algorithm named in Sec. 2.3), and each mass
+// is then refined by the mixed-precision CG.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "runtime.h"
+
+namespace lq {
+
+// device scalars, their pinned host copy and the partial-sum buffer of one solve
+struct Scalars {
+    double* dev = nullptr;
+    double* host = nullptr;
+    double* part = nullptr;
+    int nrhs = 0;
+    void init(int n, int vh) {
+        nrhs = n;
+        size_t per = std::max<size_t>((size_t)(vh + 63) / 64, (size_t)RED_BLOCKS);
+        LQ_CUDA(cudaMalloc(&dev, sizeof(double) * SC_N * n));
+        LQ_CUDA(cudaMemset(dev, 0, sizeof(double) * SC_N * n));
+        LQ_CUDA(cudaMalloc(&part, sizeof(double) * per * n));
+        LQ_CUDA(cudaMallocHost(&host, sizeof(double) * SC_N * n));
+    }
+    void pull(cudaStream_t st) {
+        LQ_CUDA(cudaMemcpyAsync(host, dev, sizeof(double) * SC_N * nrhs, cudaMemcpyDeviceToHost, st));
+        LQ_CUDA(cudaStreamSynchronize(st));
+    }
+    double& h(int k, int slot) { return host[(size_t)k * SC_N + slot]; }
+    void set(int k, int slot, double v, cudaStream_t st) {
+        h(k, slot) = v;
+        LQ_CUDA(cudaMemcpyAsync(dev + (size_t)k * SC_N + slot, &host[(size_t)k * SC_N + slot], sizeof(double),
+                                cudaMemcpyHostToDevice, st));
+        LQ_CUDA(cudaStreamSynchronize(st));
+    }
+    void fin(int nb, int slot, cudaStream_t st) { blas_finalize(part, nb, nrhs, dev, slot, FIN_SET, st); }
+    ~Scalars() {
+        if (dev) cudaFree(dev);
+        if (part) cudaFree(part);
+        if (host) cudaFreeHost(host);
+    }
+};
+
+// fields of one solve, freed together
+struct Pool {
+    std::vector<Field> owned;
+    int vh;
+    explicit Pool(int v) : vh(v) {}
+    Field get(int kind, int prec, int n) {
+        owned.push_back(field_alloc(kind, prec, n, vh));
+        return owned.back();
+    }
+    ~Pool() {
+        for (auto& f : owned) field_free(f);
+    }
+};
+
+static void check_finite(double v, const char* what) {
+    if (!std::isfinite(v)) fail(LQ_ENAN, std::string("non-finite value in ") + what);
+}
+
+struct CgResult {
+    std::vector<int> iters, updates, applications, status;
+    explicit CgResult(int n) : iters(n, 0), updates(n, 0), applications(n, 0), status(n, LQ_ENOTCONV) {}
+};
+
+// =================================================================== Wilson
+static OpDesc wilson_desc(const lq_op_params& op, int prec, int recon) {
+    OpDesc d;
+    d.action = op.action;
+    d.m = op.m;
+    d.mu = op.mu;
+    d.c_naik = op.c_naik;
+    d.prec = prec;
+    d.recon = prec == LQ_F64 ? 18 : recon;
+    return d;
+}
+
+// out = Mhat in (dagger: Mhat^+); tmp holds the odd sites. Returns the blocks of the |out|^2 partials.
+int schur_wilson(Lattice& lat, const OpDesc& op, int dagger, const Field& in, Field& out, Field& tmp, double* part,
+                 cudaStream_t st) {
+    wilson_dslash(lat, op, 1, dagger, EPI_AINV, in, tmp, nullptr, nullptr, st);
+    return wilson_dslash(lat, op, 0, dagger, EPI_XPAY, tmp, out, &in, part, st);
+}
+
+// CGNR on Mhat for all right-hand sides of bhat at once (FP64, even sites).
+// x_hi receives the solution; tol_abs[k] is the target of |bhat - Mhat x|.
+// The iteration keeps alpha and beta on the device; the host reads |s|^2 once
+// per iteration to decide on reliable updates and convergence.
+static CgResult cgnr_mixed(Lattice& lat, const OpDesc& ops, const OpDesc& op64, Field& bhat, Field& x_hi,
+                           const std::vector<double>& tol_abs, double delta, int maxiter, cudaStream_t st) {
+    const int n = bhat.nrhs;
+    const int ps = ops.prec;
+    const int px = ps == LQ_F16 ? LQ_F32 : ps;  // the sloppy solution accumulates in at least FP32
+    Pool pool(lat.vh);
+    Field s_hi = pool.get(LQ_WILSON_FIELD, LQ_F64, n), q64 = pool.get(LQ_WILSON_FIELD, LQ_F64, n);
+    Field t64 = pool.get(LQ_WILSON_FIELD, LQ_F64, n), x_lo = pool.get(LQ_WILSON_FIELD, px, n);
+    Field s_lo = pool.get(LQ_WILSON_FIELD, ps, n), r = pool.get(LQ_WILSON_FIELD, ps, n);
+    Field p = pool.get(LQ_WILSON_FIELD, ps, n), q = pool.get(LQ_WILSON_FIELD, ps, n);
+    Field t = pool.get(LQ_WILSON_FIELD, ps, n);
+    Scalars sc;
+    sc.init(n, lat.vh);
+    CgResult res(n);
+    std::vector<double> rmax(n, 0.0), ones(n, 1.0);
+    std::vector<char> done(n, 0);
+
+    blas_zero(x_hi, st);
+    blas_copy(s_hi, bhat, st);
+    blas_norm2(bhat, sc.part, st);
+    sc.fin(RED_BLOCKS, SC_SS, st);
+    blas_copy(s_lo, s_hi, st);
+    blas_zero(x_lo, st);
+    int nb = schur_wilson(lat, ops, 1, s_lo, r, t, sc.part, st);
+    sc.fin(nb, SC_RR, st);
+    blas_copy(p, r, st);
+    sc.pull(st);
+    for (int k = 0; k < n; k++) {
+        check_finite(sc.h(k, SC_SS), "source");
+        rmax[k] = sqrt(sc.h(k, SC_SS));
+        if (rmax[k] <= tol_abs[k]) {
+            done[k] = 1;
+            res.status[k] = LQ_OK;
+            sc.set(k, SC_FROZEN, 1.0, st);
+        }
+    }
+    auto all_done = [&]() {
+        for (int k = 0; k < n; k++)
+            if (!done[k]) return false;
+        return true;
+    };
+    int it = 0;
+    while (!all_done() && it < maxiter) {
+        nb = schur_wilson(lat, ops, 0, p, q, t, sc.part, st);
+        blas_finalize(sc.part, nb, n, sc.dev, 0, FIN_ALPHA, st);
+        blas_cg_xs(x_lo, p, s_lo, q, sc.dev, sc.part, st);
+        sc.fin(RED_BLOCKS, SC_SS, st);
+        nb = schur_wilson(lat, ops, 1, s_lo, r, t, sc.part, st);
+        blas_finalize(sc.part, nb, n, sc.dev, 0, FIN_BETA, st);
+        blas_cg_p(p, r, sc.dev, st);
+        it++;
+        sc.pull(st);
+        bool update = it == maxiter;
+        for (int k = 0; k < n; k++) {
+            if (done[k]) continue;
+            res.iters[k]++;
+            res.applications[k] += 2;
+            double ss = sqrt(sc.h(k, SC_SS));
+            check_finite(ss, "iterated residual");
+            if (ss < delta * rmax[k] || ss <= tol_abs[k]) update = true;
+        }
+        if (!update) continue;
+        // reliable update: fold the sloppy solution into FP64 and recompute the true residual
+        blas_axpy_h(x_hi, ones.data(), x_lo, st);
+        blas_zero(x_lo, st);
+        schur_wilson(lat, op64, 0, x_hi, q64, t64, nullptr, st);
+        blas_xmy_norm(s_hi, bhat, q64, sc.part, st);
+        sc.fin(RED_BLOCKS, SC_SS, st);
+        blas_copy(s_lo, s_hi, st);
+        nb = schur_wilson(lat, ops, 1, s_lo, r, t, sc.part, st);
+        sc.fin(nb, SC_RR, st);  // keep p, restart the norm recurrence from the new r
+        sc.pull(st);
+        for (int k = 0; k < n; k++) {
+            if (done[k]) continue;
+            res.updates[k]++;
+            res.applications[k] += 2;
+            double ss = sqrt(sc.h(k, SC_SS));
+            check_finite(ss, "true residual");
+            rmax[k] = ss;
+            if (ss <= tol_abs[k]) {
+                done[k] = 1;
+                res.status[k] = LQ_OK;
+                sc.set(k, SC_FROZEN, 1.0, st);
+            }
+        }
+    }
+    return res;
+}
+
+int solve_wilson(Lattice& lat, const lq_op_params& opp, const lq_solve_params& sp, int nrhs, const double* const* b,
+                 double* const* x, lq_solve_info* info, cudaStream_t st) {
+    if (opp.action == LQ_WILSON_TM_CLOVER && !lat.has_clover) fail(LQ_EINVAL, "clover action without clover term");
+    if (!lat.canon[LQ_THIN]) fail(LQ_EINVAL, "thin gauge field not loaded");
+    if (nrhs < 1 || nrhs > 64) fail(LQ_EINVAL, "nrhs must be in [1, 64]");
+    int ps = sp.prec_sloppy;
+    if (ps < LQ_F64 || ps > LQ_F16) fail(LQ_EINVAL, "prec_sloppy");
+    if (sp.solver != LQ_CGNR && sp.solver != LQ_MIXED_CGNR) fail(LQ_EINVAL, "solver kind for a Wilson action");
+    if (!(sp.tol > 0)) fail(LQ_EINVAL, "tol must be positive");
+    const int recon = sp.recon_sloppy == 12 ? 12 : 18;
+    const OpDesc op64 = wilson_desc(opp, LQ_F64, 18);
+    const OpDesc ops = wilson_desc(opp, ps, recon);
+    double delta = sp.solver == LQ_MIXED_CGNR ? (sp.delta > 0 ? sp.delta : 0.1) : 0.0;
+    if (ps == LQ_F64) delta = 0.0;
+    const int maxiter = sp.maxiter > 0 ? sp.maxiter : 100000;
+
+    cudaEvent_t e0, e1;
+    LQ_CUDA(cudaEventCreate(&e0));
+    LQ_CUDA(cudaEventCreate(&e1));
+    LQ_CUDA(cudaEventRecord(e0, st));
+    Pool pool(lat.vh);
+    Field be = pool.get(LQ_WILSON_FIELD, LQ_F64, nrhs), bo = pool.get(LQ_WILSON_FIELD, LQ_F64, nrhs);
+    Field bhat = pool.get(LQ_WILSON_FIELD, LQ_F64, nrhs), xe = pool.get(LQ_WILSON_FIELD, LQ_F64, nrhs);
+    Field xo = pool.get(LQ_WILSON_FIELD, LQ_F64, nrhs), te = pool.get(LQ_WILSON_FIELD, LQ_F64, nrhs);
+    Field to = pool.get(LQ_WILSON_FIELD, LQ_F64, nrhs);
+    Scalars sc;
+    sc.init(nrhs, lat.vh);
+    std::vector<double> ones(nrhs, 1.0);
+    int ret = LQ_OK;
+    try {
+        for (int k = 0; k < nrhs; k++) {
+            import_field(lat, be, k, 0, b[k], st);
+            import_field(lat, bo, k, 1, b[k], st);
+        }
+        blas_norm2(be, sc.part, st);
+        sc.fin(RED_BLOCKS, SC_B2, st);
+        blas_norm2(bo, sc.part, st);
+        sc.fin(RED_BLOCKS, SC_SS, st);
+        sc.pull(st);
+        std::vector<double> bn(nrhs), tol_abs(nrhs);
+        for (int k = 0; k < nrhs; k++) {
+            double b2 = sc.h(k, SC_B2) + sc.h(k, SC_SS);
+            check_finite(b2, "source");
+            bn[k] = sqrt(b2);
+            tol_abs[k] = 0.5 * sp.tol * bn[k];
+        }
+        // bhat = b_e + H_eo A_oo^{-1} b_o
+        wilson_ainv_site(lat, op64, 1, 0, bo, to, st);
+        wilson_dslash(lat, op64, 0, 0, EPI_HOP, to, te, nullptr, nullptr, st);
+        blas_copy(bhat, be, st);
+        blas_axpy_h(bhat, ones.data(), te, st);
+
+        CgResult cr = cgnr_mixed(lat, ops, op64, bhat, xe, tol_abs, delta, maxiter, st);
+
+        // x_o = A_oo^{-1} (b_o + H_oe x_e)
+        wilson_dslash(lat, op64, 1, 0, EPI_HOP, xe, to, nullptr, nullptr, st);
+        blas_axpy_h(to, ones.data(), bo, st);
+        wilson_ainv_site(lat, op64, 1, 0, to, xo, st);
+        for (int k = 0; k < nrhs; k++) {
+            export_field(lat, xe, k, 0, x[k], st);
+            export_field(lat, xo, k, 1, x[k], st);
+        }
+        // FP64 true residual of the full system: r_p = b_p - (A_pp x_p - H_{p,1-p} x_{1-p})
+        wilson_dslash(lat, op64, 0, 0, EPI_XPAY, xo, te, &xe, nullptr, st);
+        blas_xmy_norm(te, be, te, sc.part, st);
+        sc.fin(RED_BLOCKS, SC_RR, st);
+        wilson_dslash(lat, op64, 1, 0, EPI_XPAY, xe, to, &xo, nullptr, st);
+        blas_xmy_norm(to, bo, to, sc.part, st);
+        sc.fin(RED_BLOCKS, SC_QQ, st);
+        LQ_CUDA(cudaEventRecord(e1, st));
+        sc.pull(st);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        for (int k = 0; k < nrhs; k++) {
+            double rr = sqrt(sc.h(k, SC_RR) + sc.h(k, SC_QQ)) / bn[k];
+            int stt = cr.status[k];
+            if (stt == LQ_OK && !(rr <= sp.tol)) stt = LQ_ENOTCONV;
+            if (!std::isfinite(rr)) stt = LQ_ENAN;
+            if (stt != LQ_OK && ret == LQ_OK) ret = stt;
+            if (info) {
+                info[k].status = stt;
+                info[k].iters = cr.iters[k];
+                info[k].reliable_updates = cr.updates[k];
+                info[k].operator_applications = cr.applications[k];
+                info[k].true_rel_residual = rr;
+                info[k].seconds = ms * 1e-3;
+            }
+        }
+    } catch (...) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (ret != LQ_OK) set_last_error("solve: not every right-hand side reached the tolerance");
+    return ret;
+}
+
+// ===================================================================== HISQ
+static OpDesc hisq_desc(const lq_op_params& op, int prec, int recon) {
+    OpDesc d;
+    d.action = LQ_HISQ;
+    d.m = op.m;
+    d.mu = 0.0;
+    d.c_naik = op.c_naik;
+    d.prec = prec;
+    d.recon = prec == LQ_F64 ? 18 : recon;
+    return d;
+}
+
+// out = sigma in - H_eo H_oe in; t = H_oe in (odd). part_t receives |t|^2 partials,
+// so that (in, out) = sigma |in|^2 + |t|^2 (since -H_eo = H_oe^+).
+int schur_hisq(Lattice& lat, const OpDesc& op, double sigma, const Field& in, Field& out, Field& t, double* part_t,
+               cudaStream_t st) {
+    int nb = hisq_dslash(lat, op, 1, 0, EPI_HOP, 0.0, in, t, nullptr, part_t, st);
+    hisq_dslash(lat, op, 0, 0, EPI_XPAY, sigma, t, out, &in, nullptr, st);
+    return nb;
+}
+
+// Mixed-precision CG for (sigma - H_eo H_oe) x = b from the initial guess in x_hi.
+static CgResult cg_hisq(Lattice& lat, const OpDesc& ops, const OpDesc& op64, double sigma, const Field& b,
+                        Field& x_hi, const std::vector<double>& tol_abs, double delta, int maxiter, cudaStream_t st) {
+    const int n = b.nrhs;
+    const int ps = ops.prec, px = ps == LQ_F16 ? LQ_F32 : ps;
+    Pool pool(lat.vh);
+    Field r_hi = pool.get(LQ_STAGGERED_FIELD, LQ_F64, n), q64 = pool.get(LQ_STAGGERED_FIELD, LQ_F64, n);
+    Field t64 = pool.get(LQ_STAGGERED_FIELD, LQ_F64, n), x_lo = pool.get(LQ_STAGGERED_FIELD, px, n);
+    Field r = pool.get(LQ_STAGGERED_FIELD, ps, n), p = pool.get(LQ_STAGGERED_FIELD, ps, n);
+    Field q = pool.get(LQ_STAGGERED_FIELD, ps, n), t = pool.get(LQ_STAGGERED_FIELD, ps, n);
+    Scalars sc;
+    sc.init(n, lat.vh);
+    CgResult res(n);
+    std::vector<double> rr(n), pp(n), rmax(n), a(n), bb(n), ones(n, 1.0);
+    std::vector<char> done(n, 0);
+
+    // r = b - A x_hi in FP64; restart the sloppy recurrence from it
+    auto true_residual = [&]() {
+        schur_hisq(lat, op64, sigma, x_hi, q64, t64, nullptr, st);
+        blas_xmy_norm(r_hi, b, q64, sc.part, st);
+        sc.fin(RED_BLOCKS, SC_SS, st);
+        blas_copy(r, r_hi, st);
+        blas_copy(p, r, st);
+        sc.pull(st);
+        for (int k = 0; k < n; k++) {
+            double ss = sc.h(k, SC_SS);
+            check_finite(ss, "true residual");
+            rr[k] = pp[k] = ss;
+            rmax[k] = sqrt(ss);
+            if (!done[k] && sqrt(ss) <= tol_abs[k]) {
+                done[k] = 1;
+                res.status[k] = LQ_OK;
+            }
+        }
+    };
+    blas_zero(x_lo, st);
+    true_residual();
+    auto all_done = [&]() {
+        for (int k = 0; k < n; k++)
+            if (!done[k]) return false;
+        return true;
+    };
+    int it = 0;
+    while (!all_done() && it < maxiter) {
+        int nb = schur_hisq(lat, ops, sigma, p, q, t, sc.part, st);
+        sc.fin(nb, SC_QQ, st);
+        sc.pull(st);
+        for (int k = 0; k < n; k++) {
+            double pap = sigma * pp[k] + sc.h(k, SC_QQ);
+            if (!done[k] && !(pap > 0.0)) fail(LQ_EBREAKDOWN, "CG breakdown: non-positive curvature");
+            a[k] = done[k] ? 0.0 : rr[k] / pap;
+        }
+        blas_axpy_h(x_lo, a.data(), p, st);
+        for (int k = 0; k < n; k++) a[k] = -a[k];
+        blas_axpby_h(r, a.data(), q, ones.data(), sc.part, st);
+        sc.fin(RED_BLOCKS, SC_RRN, st);
+        sc.pull(st);
+        bool update = false;
+        for (int k = 0; k < n; k++) {
+            double rn = sc.h(k, SC_RRN);
+            check_finite(rn, "iterated residual");
+            bb[k] = done[k] ? 0.0 : rn / rr[k];
+            if (!done[k]) {
+                res.iters[k]++;
+                res.applications[k]++;
+                rr[k] = rn;
+                if (sqrt(rn) < delta * rmax[k] || sqrt(rn) <= tol_abs[k]) update = true;
+            }
+        }
+        blas_axpby_h(p, ones.data(), r, bb.data(), sc.part, st);
+        sc.fin(RED_BLOCKS, SC_PP, st);
+        it++;
+        if (it == maxiter) update = true;
+        if (update) {
+            blas_axpy_h(x_hi, ones.data(), x_lo, st);
+            blas_zero(x_lo, st);
+            std::vector<char> was = done;
+            true_residual();
+            for (int k = 0; k < n; k++)
+                if (!was[k]) {
+                    res.updates[k]++;
+                    res.applications[k]++;
+                }
+        } else {
+            sc.pull(st);
+            for (int k = 0; k < n; k++) pp[k] = sc.h(k, SC_PP);
+        }
+    }
+    return res;
+}
+
+// Multi-shift CG in one precision for (sigma_i - H_eo H_oe) y_i = b, shifts
+// ascending, one Krylov space. Stops when every shift's iterated residual
+// |zeta_i| |r| is below tol_rel |b|. Returns the iterations.
+static int multishift_hisq(Lattice& lat, const OpDesc& op, const std::vector<double>& sigma, const Field& b,
+                           std::vector<Field>& y, double tol_rel, int maxiter, cudaStream_t st) {
+    const int n = b.nrhs, ns = (int)sigma.size();
+    Pool pool(lat.vh);
+    Field r = pool.get(LQ_STAGGERED_FIELD, op.prec, n), q = pool.get(LQ_STAGGERED_FIELD, op.prec, n);
+    Field t = pool.get(LQ_STAGGERED_FIELD, op.prec, n);
+    std::vector<Field> p;
+    for (int i = 0; i < ns; i++) p.push_back(pool.get(LQ_STAGGERED_FIELD, op.prec, n));
+    Scalars sc;
+    sc.init(n, lat.vh);
+    blas_copy(r, b, st);
+    for (int i = 0; i < ns; i++) {
+        blas_copy(p[i], b, st);
+        blas_zero(y[i], st);
+    }
+    blas_norm2(r, sc.part, st);
+    sc.fin(RED_BLOCKS, SC_RR, st);
+    sc.pull(st);
+    std::vector<double> rr(n), pp(n), b2(n), alpha_prev(n, 1.0), beta_prev(n, 0.0), alpha(n), beta(n);
+    std::vector<std::vector<double>> zeta(ns, std::vector<double>(n, 1.0)), zeta_prev = zeta, zn = zeta;
+    std::vector<std::vector<char>> active(ns, std::vector<char>(n, 1));
+    for (int k = 0; k < n; k++) {
+        rr[k] = pp[k] = b2[k] = sc.h(k, SC_RR);
+        check_finite(b2[k], "source");
+        if (b2[k] == 0.0)
+            for (int i = 0; i < ns; i++) active[i][k] = 0;
+    }
+    std::vector<double> a(n), bz(n), zz(n), ones(n, 1.0);
+    auto any_active = [&]() {
+        for (int i = 0; i < ns; i++)
+            for (int k = 0; k < n; k++)
+                if (active[i][k]) return true;
+        return false;
+    };
+    int iters = 0;
+    while (any_active() && iters < maxiter) {
+        int nb = schur_hisq(lat, op, sigma[0], p[0], q, t, sc.part, st);
+        sc.fin(nb, SC_QQ, st);
+        sc.pull(st);
+        for (int k = 0; k < n; k++) {
+            double pap = sigma[0] * pp[k] + sc.h(k, SC_QQ);
+            alpha[k] = (pap > 0.0 && b2[k] > 0.0) ? rr[k] / pap : 0.0;
+            for (int i = 1; i < ns; i++) {
+                double d = sigma[i] - sigma[0];
+                double den = alpha[k] * beta_prev[k] * (zeta_prev[i][k] - zeta[i][k]) +
+                             zeta_prev[i][k] * alpha_prev[k] * (1.0 + d * alpha[k]);
+                zn[i][k] = den != 0.0 ? zeta[i][k] * zeta_prev[i][k] * alpha_prev[k] / den : 0.0;
+            }
+        }
+        // y_i += alpha_i p_i, alpha_i = alpha zeta_i'/zeta_i
+        for (int i = 0; i < ns; i++) {
+            for (int k = 0; k < n; k++)
+                a[k] = !active[i][k] ? 0.0 : (i == 0 ? alpha[k] : alpha[k] * zn[i][k] / zeta[i][k]);
+            blas_axpy_h(y[i], a.data(), p[i], st);
+        }
+        for (int k = 0; k < n; k++) a[k] = -alpha[k];
+        blas_axpby_h(r, a.data(), q, ones.data(), sc.part, st);
+        sc.fin(RED_BLOCKS, SC_RRN, st);
+        sc.pull(st);
+        for (int k = 0; k < n; k++) {
+            double rn = sc.h(k, SC_RRN);
+            check_finite(rn, "multi-shift residual");
+            beta[k] = rr[k] > 0.0 ? rn / rr[k] : 0.0;
+            rr[k] = rn;
+        }
+        // p_0 = r + beta p_0 ; p_i = zeta_i' r + beta (zeta_i'/zeta_i)^2 p_i
+        blas_axpby_h(p[0], ones.data(), r, beta.data(), sc.part, st);
+        sc.fin(RED_BLOCKS, SC_PP, st);
+        for (int i = 1; i < ns; i++) {
+            for (int k = 0; k < n; k++) {
+                double zr = zeta[i][k] != 0.0 ? zn[i][k] / zeta[i][k] : 0.0;
+                zz[k] = active[i][k] ? zn[i][k] : 0.0;
+                bz[k] = active[i][k] ? beta[k] * zr * zr : 1.0;
+            }
+            blas_axpby_h(p[i], zz.data(), r, bz.data(), nullptr, st);
+        }
+        for (int k = 0; k < n; k++) {
+            for (int i = 1; i < ns; i++) {
+                zeta_prev[i][k] = zeta[i][k];
+                zeta[i][k] = zn[i][k];
+            }
+            alpha_prev[k] = alpha[k];
+            beta_prev[k] = beta[k];
+            for (int i = 0; i < ns; i++) {
+                double z = i == 0 ? 1.0 : fabs(zeta[i][k]);
+                if (active[i][k] && z * sqrt(rr[k]) <= tol_rel * sqrt(b2[k])) active[i][k] = 0;
+            }
+        }
+        sc.pull(st);
+        for (int k = 0; k < n; k++) pp[k] = sc.h(k, SC_PP);
+        iters++;
+    }
+    return iters;
+}
+
+int solve_hisq(Lattice& lat, const lq_op_params& opp, const lq_solve_params& sp, int nrhs, const double* const* b,
+               double* const* x, lq_solve_info* info, cudaStream_t st) {
+    if (!lat.canon[LQ_FAT] || !lat.canon[LQ_LONG]) fail(LQ_EINVAL, "HISQ needs fat and long links loaded");
+    if (nrhs < 1 || nrhs > 32) fail(LQ_EINVAL, "nrhs must be in [1, 32] for HISQ");
+    int ps = sp.prec_sloppy;
+    if (ps < LQ_F64 || ps > LQ_F16) fail(LQ_EINVAL, "prec_sloppy");
+    if (!(sp.tol > 0)) fail(LQ_EINVAL, "tol must be positive");
+    const int recon = sp.recon_sloppy == 12 ? 12 : 18;
+    const OpDesc op64 = hisq_desc(opp, LQ_F64, 18);
+    const OpDesc ops = hisq_desc(opp, ps, recon);
+    const double delta = (ps == LQ_F64) ? 0.0 : (sp.delta > 0 ? sp.delta : 0.1);
+    const int maxiter = sp.maxiter > 0 ? sp.maxiter : 100000;
+    std::vector<double> masses;
+    if (sp.solver == LQ_MULTISHIFT_CG) {
+        if (sp.nshift < 1 || sp.nshift > 16 || !sp.masses) fail(LQ_EINVAL, "multi-shift solve needs 1..16 masses");
+        for (int i = 0; i < sp.nshift; i++) masses.push_back(sp.masses[i]);
+        for (int i = 1; i < sp.nshift; i++)
+            if (masses[i] < masses[i - 1]) fail(LQ_EINVAL, "multi-shift masses must be ascending");
+    } else {
+        masses.push_back(opp.m);
+    }
+    for (double m : masses)
+        if (!(m > 0.0)) fail(LQ_EINVAL, "HISQ mass must be positive");
+    const int ns = (int)masses.size();
+
+    cudaEvent_t e0, e1;
+    LQ_CUDA(cudaEventCreate(&e0));
+    LQ_CUDA(cudaEventCreate(&e1));
+    LQ_CUDA(cudaEventRecord(e0, st));
+    Pool pool(lat.vh);
+    const int SF = LQ_STAGGERED_FIELD;
+    Field be = pool.get(SF, LQ_F64, nrhs), bo = pool.get(SF, LQ_F64, nrhs), c = pool.get(SF, LQ_F64, nrhs);
+    Field bh = pool.get(SF, LQ_F64, nrhs), xe = pool.get(SF, LQ_F64, nrhs), xo = pool.get(SF, LQ_F64, nrhs);
+    Field te = pool.get(SF, LQ_F64, nrhs), to = pool.get(SF, LQ_F64, nrhs);
+    Scalars sc;
+    sc.init(nrhs, lat.vh);
+    int ret = LQ_OK;
+    try {
+        for (int k = 0; k < nrhs; k++) {
+            import_field(lat, be, k, 0, b[k], st);
+            import_field(lat, bo, k, 1, b[k], st);
+        }
+        blas_norm2(be, sc.part, st);
+        sc.fin(RED_BLOCKS, SC_B2, st);
+        blas_norm2(bo, sc.part, st);
+        sc.fin(RED_BLOCKS, SC_SS, st);
+        sc.pull(st);
+        std::vector<double> bn(nrhs), tol_abs(nrhs);
+        for (int k = 0; k < nrhs; k++) {
+            double b2 = sc.h(k, SC_B2) + sc.h(k, SC_SS);
+            check_finite(b2, "source");
+            bn[k] = sqrt(b2);
+        }
+        // c = H_eo b_o
+        hisq_dslash(lat, op64, 0, 0, EPI_HOP, 0.0, bo, c, nullptr, nullptr, st);
+
+        // sloppy multi-shift stage on the 2*nrhs right-hand sides [b_e, c]:
+        // x_e,i = m_i (A + m_i^2)^{-1} b_e - (A + m_i^2)^{-1} c
+        std::vector<double> sigma(ns);
+        for (int i = 0; i < ns; i++) sigma[i] = masses[i] * masses[i];
+        std::vector<Field> ys;
+        int ms_iters = 0;
+        if (ns > 1) {
+            Field b2f = pool.get(SF, ps, 2 * nrhs);
+            Field lo = b2f.sub(0, nrhs), hi = b2f.sub(nrhs, nrhs);
+            blas_copy(lo, be, st);
+            blas_copy(hi, c, st);
+            for (int i = 0; i < ns; i++) ys.push_back(pool.get(SF, ps, 2 * nrhs));
+            const double tol_ms = ps == LQ_F64 ? 0.1 * sp.tol : (ps == LQ_F32 ? 1e-6 : 1e-3);
+            ms_iters = multishift_hisq(lat, ops, sigma, b2f, ys, tol_ms, maxiter, st);
+        }
+
+        std::vector<int> tot_iters(nrhs, ms_iters), tot_upd(nrhs, 0), tot_app(nrhs, ms_iters);
+        std::vector<double> worst(nrhs, 0.0);
+        std::vector<int> status(nrhs, LQ_OK);
+        std::vector<double> one(nrhs, 1.0), neg(nrhs, -1.0);
+        for (int i = 0; i < ns; i++) {
+            const double m = masses[i];
+            // bhat_i = m b_e - c
+            std::vector<double> am(nrhs, m);
+            blas_copy(bh, c, st);
+            blas_axpby_h(bh, am.data(), be, neg.data(), nullptr, st);
+            // initial guess: from the multi-shift stage, or zero
+            if (ns > 1) {
+                Field y1 = ys[i].sub(0, nrhs), y2 = ys[i].sub(nrhs, nrhs);
+                blas_copy(xe, y2, st);
+                blas_copy(te, y1, st);
+                blas_axpby_h(xe, am.data(), te, neg.data(), nullptr, st);
+            } else {
+                blas_zero(xe, st);
+            }
+            // the even part of the full residual is (bhat - A x_e) / m
+            for (int k = 0; k < nrhs; k++) tol_abs[k] = 0.5 * sp.tol * bn[k] * m;
+            CgResult cr = cg_hisq(lat, ops, op64, sigma[i], bh, xe, tol_abs, delta, maxiter, st);
+            // x_o = (b_o - H_oe x_e) / m
+            hisq_dslash(lat, op64, 1, 0, EPI_HOP, 0.0, xe, to, nullptr, nullptr, st);
+            blas_copy(xo, to, st);
+            std::vector<double> ai(nrhs, 1.0 / m), bi(nrhs, -1.0 / m);
+            blas_axpby_h(xo, ai.data(), bo, bi.data(), nullptr, st);
+            for (int k = 0; k < nrhs; k++) {
+                export_field(lat, xe, k, 0, x[k * ns + i], st);
+                export_field(lat, xo, k, 1, x[k * ns + i], st);
+            }
+            // FP64 true residual: r_p = b_p - (m x_p + H x_{1-p}); XPAY gives -(m x_p + H x_{1-p})
+            hisq_dslash(lat, op64, 0, 0, EPI_XPAY, -m, xo, te, &xe, nullptr, st);
+            blas_axpby_h(te, one.data(), be, one.data(), sc.part, st);
+            sc.fin(RED_BLOCKS, SC_RR, st);
+            hisq_dslash(lat, op64, 1, 0, EPI_XPAY, -m, xe, to, &xo, nullptr, st);
+            blas_axpby_h(to, one.data(), bo, one.data(), sc.part, st);
+            sc.fin(RED_BLOCKS, SC_QQ, st);
+            sc.pull(st);
+            for (int k = 0; k < nrhs; k++) {
+                double rr = sqrt(sc.h(k, SC_RR) + sc.h(k, SC_QQ)) / bn[k];
+                worst[k] = std::max(worst[k], rr);
+                tot_iters[k] += cr.iters[k];
+                tot_upd[k] += cr.updates[k];
+                tot_app[k] += cr.applications[k];
+                int stt = cr.status[k];
+                if (stt == LQ_OK && !(rr <= sp.tol)) stt = LQ_ENOTCONV;
+                if (!std::isfinite(rr)) stt = LQ_ENAN;
+                if (stt != LQ_OK) status[k] = stt;
+            }
+        }
+        LQ_CUDA(cudaEventRecord(e1, st));
+        LQ_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        for (int k = 0; k < nrhs; k++) {
+            if (status[k] != LQ_OK && ret == LQ_OK) ret = status[k];
+            if (info) {
+                info[k].status = status[k];
+                info[k].iters = tot_iters[k];
+                info[k].reliable_updates = tot_upd[k];
+                info[k].operator_applications = tot_app[k];
+                info[k].true_rel_residual = worst[k];
+                info[k].seconds = ms * 1e-3;
+            }
+        }
+    } catch (...) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (ret != LQ_OK) set_last_error("solve: not every right-hand side reached the tolerance");
+    return ret;
+}
+
+}  // namespace lq
