@@ -1,0 +1,50 @@
+"""The C-ABI library builds, loads, and exports every entry point include/lq.h declares.
+
+CPU only: no call here touches a GPU (argument validation fails before any
+CUDA call is made).
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+from helpers import ROOT, ensure_library
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "lq.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lq_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = header_functions()
+    for required in ["lq_create_lattice", "lq_load_gauge", "lq_load_clover", "lq_dslash_apply", "lq_solve",
+                     "lq_submit", "lq_poll"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    ensure_library()
+    from paper_2201_09004_b300 import lib
+    L = lib.lib()
+    names = header_functions()
+    assert sorted(lib.EXPORTS) == names
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_invalid_lattice_is_rejected_without_gpu():
+    ensure_library()
+    from paper_2201_09004_b300 import lib
+    h = ctypes.c_void_p()
+    code = lib.lib().lq_create_lattice((ctypes.c_int * 4)(4, 4, 5, 8), ctypes.c_int(-1), ctypes.byref(h))
+    assert code == lib.LQ_EINVAL
+    assert b"even" in lib.lib().lq_last_error()
+    code = lib.lib().lq_create_lattice((ctypes.c_int * 4)(4, 4, 4, 8), ctypes.c_int(3), ctypes.byref(h))
+    assert code == lib.LQ_EINVAL
+    code = lib.lib().lq_server_create(ctypes.c_size_t(1 << 30), ctypes.c_int(0), ctypes.byref(h))
+    assert code == lib.LQ_EINVAL
+    with pytest.raises(lib.LqError):
+        lib.Lattice((2, 2, 2, 3))

@@ -1,0 +1,235 @@
+"""Parity of the CUDA Wilson twisted-mass / clover path with the FP64 oracle.
+
+Every quantity goes through the C ABI (lib.py is marshalling only) and is
+compared element by element with the oracle on the same seeded inputs:
+hopping term per parity and adjoint, the full operator with clover, the
+even-odd Schur operator, and solves whose true residual the oracle recomputes.
+Tolerances of the operator: FP64 1e-13, FP32 1e-6, FP16 storage 5e-3 (relative
+L2); solutions: oracle true residual <= 1e-10.
+"""
+import numpy as np
+import pytest
+
+from helpers import TOL, ensure_library, parity_mask, rel_err
+from paper_2201_09004_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    ensure_library()
+    from paper_2201_09004_b300 import lib
+    return lib
+
+
+def make(L, dims, seed, c_sw=None, eps=0.3):
+    U = synth.thin_links(dims, seed, eps).numpy()
+    lat = L.Lattice(dims, -1)
+    lat.load_gauge(L.THIN, U)
+    if c_sw is not None:
+        lat.load_clover(c_sw)
+    return lat, U
+
+
+# 4^3x8 spans several thread blocks; 6x4x4x6 has a ragged last block (vh = 288);
+# 2^4 makes x+mu and x-mu the same site
+DIMS = [(4, 4, 4, 8), (6, 4, 4, 6), (2, 2, 2, 2)]
+
+
+@pytest.mark.parametrize("dims", DIMS)
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_hopping_term_each_parity_and_adjoint(L, orc, dims, prec):
+    lat, U = make(L, dims, 11)
+    psi = synth.gaussian_field(dims, 12).numpy()
+    W = orc.Wilson(dims, U, 0.1, 0.05)
+    op = L.op_params(L.WILSON_TM, 0.1, 0.05)
+    mask = parity_mask(dims)
+    for dagger in (False, True):
+        ref = W.hop(psi, dagger=dagger)
+        for p in (0, 1):
+            src = np.where((mask == 1 - p)[..., None, None], psi, 0)
+            got = lat.dslash_apply(op, p, src, dagger=dagger, prec=prec)
+            sel = (mask == p)
+            assert np.all(got[~sel] == 0)
+            assert rel_err(got[sel], ref[sel]) < TOL[prec], (dims, prec, dagger, p)
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("clover", [False, True])
+def test_full_operator_twisted_clover(L, orc, prec, clover):
+    dims = (4, 4, 4, 6)
+    lat, U = make(L, dims, 21, c_sw=1.05 if clover else None)
+    C = orc.clover(dims, U, 1.05) if clover else None
+    action = L.WILSON_TM_CLOVER if clover else L.WILSON_TM
+    op = L.op_params(action, 0.05, 0.1, c_sw=1.05)
+    psi = synth.gaussian_field(dims, 22).numpy()
+    for dagger in (False, True):
+        ref = orc.Wilson(dims, U, 0.05, 0.1, clover=C).apply(psi, dagger=dagger)
+        got = lat.operator_apply(op, psi, form=L.OP_FULL, dagger=dagger, prec=prec)
+        assert rel_err(got, ref) < TOL[prec], (prec, clover, dagger)
+
+
+def test_device_clover_matches_oracle_clover_loaded_canonically(L, orc):
+    """The on-device clover build equals loading the oracle's clover as an array."""
+    dims = (4, 4, 4, 4)
+    U = synth.thin_links(dims, 23).numpy()
+    C = orc.clover(dims, U, 1.3)
+    a = L.Lattice(dims)
+    a.load_gauge(L.THIN, U)
+    a.load_clover(1.3)
+    b = L.Lattice(dims)
+    b.load_gauge(L.THIN, U)
+    b.load_clover(1.3, clover=C)
+    op = L.op_params(L.WILSON_TM_CLOVER, 0.05, 0.02, c_sw=1.3)
+    psi = synth.gaussian_field(dims, 24).numpy()
+    ra = a.operator_apply(op, psi)
+    rb = b.operator_apply(op, psi)
+    assert rel_err(ra, rb) < 1e-14
+
+
+def schur_reference(orc, dims, U, C, m, mu, v_even, dagger=False):
+    """Mhat v = A_ee v - H_eo A_oo^{-1} H_oe v, composed from oracle pieces; the
+    site-local A^{-1} is a dense 12x12 solve per site (numpy LU)."""
+    mask = parity_mask(dims)
+    g5 = np.diag([1, 1, -1, -1]).astype(complex)
+    A = (4 + m) * np.eye(12, dtype=complex) + np.kron(1j * (-mu if dagger else mu) * g5, np.eye(3))
+    Afull = np.broadcast_to(A, mask.shape + (12, 12)).copy()
+    if C is not None:
+        Afull = Afull + C
+    W = orc.Wilson(dims, U, 0.0, 0.0)
+    v = np.where((mask == 0)[..., None, None], v_even, 0)
+    h = W.hop(v, dagger=dagger)                                   # H_oe v on odd sites
+    t = np.linalg.solve(Afull, h.reshape(h.shape[:4] + (12,))[..., None])[..., 0].reshape(h.shape)
+    t = np.where((mask == 1)[..., None, None], t, 0)
+    h2 = W.hop(t, dagger=dagger)                                  # H_eo A_oo^{-1} H_oe v
+    av = (Afull @ v.reshape(v.shape[:4] + (12, 1)))[..., 0].reshape(v.shape)
+    out = av - h2
+    return np.where((mask == 0)[..., None, None], out, 0)
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_schur_operator(L, orc, prec):
+    dims = (4, 4, 4, 6)
+    lat, U = make(L, dims, 31, c_sw=1.05)
+    C = orc.clover(dims, U, 1.05)
+    op = L.op_params(L.WILSON_TM_CLOVER, 0.05, 0.1, c_sw=1.05)
+    v = synth.gaussian_field(dims, 32).numpy()
+    mask = parity_mask(dims)
+    for dagger in (False, True):
+        ref = schur_reference(orc, dims, U, C, 0.05, 0.1, v, dagger=dagger)
+        got = lat.operator_apply(op, v, form=L.OP_SCHUR, dagger=dagger, prec=prec)
+        assert np.all(got[mask == 1] == 0)
+        assert rel_err(got, ref) < 10 * TOL[prec], (prec, dagger)
+
+
+def true_residual(orc, dims, U, C, m, mu, b, x):
+    r = b - orc.Wilson(dims, U, m, mu, clover=C).apply(x)
+    return np.linalg.norm(r) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("solver,prec", [(0, 0), (1, 1), (1, 2)])
+def test_solve_plain_method_tiny(L, orc, solver, prec):
+    """4^3x8 Wilson twisted mass, no clover, m = 0.1, mu = 0.05, Z2 source, 1e-10."""
+    dims = (4, 4, 4, 8)
+    lat, U = make(L, dims, 101)
+    b = synth.z2_source(dims, 201).numpy()
+    op = L.op_params(L.WILSON_TM, 0.1, 0.05)
+    sp = L.solve_params(solver=solver, tol=1e-10, prec_sloppy=prec)
+    xs, info = lat.solve(op, sp, [b])
+    assert info[0]["status"] == 0
+    assert info[0]["true_rel_residual"] <= 1e-10
+    res = true_residual(orc, dims, U, None, 0.1, 0.05, b, xs[0])
+    assert res <= 1e-10, res
+    x_ref, _ = orc.Wilson(dims, U, 0.1, 0.05).cgnr(b, tol=1e-13)
+    assert rel_err(xs[0], x_ref) < 1e-8
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_solve_clover_mixed_multi_rhs(L, orc, prec):
+    """Twisted clover, even-odd, three right-hand sides solved together equal the oracle."""
+    dims = (4, 4, 6, 8)
+    lat, U = make(L, dims, 102, c_sw=1.05)
+    C = orc.clover(dims, U, 1.05)
+    op = L.op_params(L.WILSON_TM_CLOVER, 0.05, 0.01, c_sw=1.05)
+    bs = [synth.z2_source(dims, 202 + k).numpy() for k in range(3)]
+    bs.append(synth.point_source(dims, (1, 2, 3, 4), 2, 1).numpy())
+    sp = L.solve_params(solver=L.MIXED_CGNR, tol=1e-10, prec_sloppy=prec)
+    xs, info = lat.solve(op, sp, bs)
+    for b, x, inf in zip(bs, xs, info):
+        assert inf["status"] == 0
+        assert true_residual(orc, dims, U, C, 0.05, 0.01, b, x) <= 1e-10
+    # one at a time gives the same solutions within the tolerance
+    x1, _ = lat.solve(op, sp, [bs[1]])
+    assert rel_err(x1[0], xs[1]) < 1e-8
+
+
+def test_solve_device_arrays_and_2x4(L, orc):
+    import torch
+    dims = (2, 2, 2, 2)
+    lat, U = make(L, dims, 103, c_sw=1.0)
+    C = orc.clover(dims, U, 1.0)
+    op = L.op_params(L.WILSON_TM_CLOVER, 0.1, 0.05, c_sw=1.0)
+    b = synth.z2_source(dims, 203)
+    xs, info = lat.solve(op, L.solve_params(tol=1e-12), [b.cuda()])
+    x = xs[0].cpu().numpy()
+    A_apply = orc.Wilson(dims, U, 0.1, 0.05, clover=C)
+    n = 192
+    A = np.zeros((n, n), dtype=complex)
+    e = np.zeros(n, dtype=complex)
+    for j in range(n):
+        e[:] = 0
+        e[j] = 1
+        A[:, j] = A_apply.apply(e.reshape(A_apply.shape())).ravel()
+    x_lu = np.linalg.solve(A, b.numpy().ravel())
+    assert rel_err(x.ravel(), x_lu) < 1e-10
+
+
+def test_zero_source_and_nan_source(L):
+    dims = (4, 4, 4, 4)
+    lat, U = make(L, dims, 104)
+    op = L.op_params(L.WILSON_TM, 0.1, 0.05)
+    b = np.zeros((4, 4, 4, 4, 4, 3), dtype=complex)
+    b[0, 0, 0, 0, 0, 0] = np.nan
+    with pytest.raises(L.LqError) as e:
+        lat.solve(op, L.solve_params(), [b])
+    assert e.value.code == L.LQ_ENAN
+
+
+def test_maxiter_reports_not_converged(L):
+    dims = (4, 4, 4, 4)
+    lat, U = make(L, dims, 105)
+    op = L.op_params(L.WILSON_TM, 0.1, 0.05)
+    b = synth.z2_source(dims, 205).numpy()
+    xs, info = lat.solve(op, L.solve_params(tol=1e-10, maxiter=3), [b], check=False)
+    assert info[0]["status"] == L.LQ_ENOTCONV
+    assert info[0]["iters"] == 3
+    assert info[0]["true_rel_residual"] > 1e-10
+
+
+def test_full_size_hopping_term_sampled_sites(L, orc):
+    """24^3x64 (the benchmark lattice), FP32 and FP16 kernels at full size, checked
+    on 2000 sampled output sites computed one by one by the oracle."""
+    import torch
+    dims = (24, 24, 24, 64)
+    U = synth.thin_links(dims, 102, device="cuda")
+    psi = synth.gaussian_field(dims, 303, device="cuda")
+    lat = L.Lattice(dims)
+    lat.load_gauge(L.THIN, U)
+    op = L.op_params(L.WILSON_TM, 0.05, 0.01)
+    Uh = U.cpu().numpy()
+    psih = psi.cpu().numpy()
+    rng = np.random.default_rng(5)
+    lx, ly, lz, lt = dims
+    for prec in (1, 2):
+        for p in (0, 1):
+            got = lat.dslash_apply(op, p, psi, prec=prec).cpu().numpy().reshape(-1, 4, 3)
+            cand = rng.integers(0, lx * ly * lz * lt, size=6000)
+            xs = cand % lx
+            ys = (cand // lx) % ly
+            zs = (cand // (lx * ly)) % lz
+            ts = cand // (lx * ly * lz)
+            sites = cand[((xs + ys + zs + ts) % 2) == p][:2000]
+            W = orc.Wilson(dims, Uh, 0.05, 0.01)
+            ref = W.hop_sites(psih, sites)
+            assert rel_err(got[sites], ref) < TOL[prec], (prec, p)
