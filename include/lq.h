@@ -172,6 +172,26 @@ int lq_load_clover(lq_lattice lat, int loc, const double* clover, double c_sw);
 int lq_dslash_apply(lq_lattice lat, const lq_op_params* op, int parity, int dagger, int prec, int loc,
                     const double* in, double* out, void* stream);
 
+/* lq_dslash_apply for callers that cannot allocate device memory (an
+ * application whose memory pool owns the GPU, a fixed memory budget, a loop
+ * that must not trigger the implicit synchronisation of cudaMalloc/cudaFree).
+ * The paper has no counterpart; this is a service of the library. Same result
+ * as lq_dslash_apply with loc = LQ_DEVICE (in/out are canonical FP64 device
+ * arrays), but the two internal packed fields live in a fixed scratch array of
+ * 32 MiB compiled into the library (held on every GPU that loads it until the
+ * process exits) and nothing is allocated. Limits and rules:
+ *   - LQ_EINVAL if the two packed fields need more than 32 MiB (FP64 Wilson:
+ *     up to 174762 sites, e.g. 16^3x32; FP32 twice that);
+ *   - LQ_EINVAL if the lattice's links are not yet packed in this precision:
+ *     one earlier lq_dslash_apply with the same action and precision does it;
+ *   - the first call on a device looks up the scratch array's device address,
+ *     so make it before any stream capture;
+ *   - all calls share the scratch array: calls that can overlap on the GPU
+ *     (other streams or threads) race, so the caller must order them.
+ * Returns after the result is in out. */
+int lq_dslash_apply_noalloc(lq_lattice lat, const lq_op_params* op, int parity, int dagger, int prec,
+                            const double* in, double* out, void* stream);
+
 /* Whole operator. form = LQ_OP_FULL: out = D in (D = M for Wilson, m + H for
  * HISQ) on the full lattice. form = LQ_OP_SCHUR: the even-odd Schur operator
  * on even sites, Mhat = A_ee - H_eo A_oo^{-1} H_oe for Wilson (A = 4+m+i mu g5+C)

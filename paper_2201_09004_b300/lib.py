@@ -39,7 +39,7 @@ EXPORTS = [
     "lq_load_clover", "lq_dslash_apply", "lq_operator_apply", "lq_solve", "lq_field_create",
     "lq_field_destroy", "lq_field_import", "lq_field_export", "lq_dslash_field", "lq_schur_field",
     "lq_profile_enable", "lq_profile_reset", "lq_profile_query", "lq_launch_count", "lq_server_create",
-    "lq_server_destroy", "lq_submit", "lq_poll", "lq_wait", "lq_server_stats",
+    "lq_server_destroy", "lq_submit", "lq_poll", "lq_wait", "lq_server_stats", "lq_dslash_apply_noalloc",
 ]
 
 
@@ -198,6 +198,16 @@ class Lattice:
         po, loco, keepo = _ptr(out)
         _check(lib().lq_dslash_apply(self.h, ctypes.byref(op), ctypes.c_int(parity), ctypes.c_int(int(dagger)),
                                      ctypes.c_int(prec), ctypes.c_int(loc), p, po, _stream(stream)))
+        return out
+
+    def dslash_apply_noalloc(self, op, parity, psi, out, dagger=False, prec=F64, stream=None):
+        """lq_dslash_apply_noalloc: device tensors in/out, no device allocation in the library."""
+        p, loc, keep = _ptr(psi)
+        po, loco, keepo = _ptr(out)
+        if loc != DEVICE or loco != DEVICE:
+            raise ValueError("lq_dslash_apply_noalloc takes device arrays")
+        _check(lib().lq_dslash_apply_noalloc(self.h, ctypes.byref(op), ctypes.c_int(parity), ctypes.c_int(int(dagger)),
+                                             ctypes.c_int(prec), p, po, _stream(stream)))
         return out
 
     def operator_apply(self, op, psi, form=OP_FULL, dagger=False, prec=F64, stream=None):
