@@ -7,9 +7,11 @@
 // consecutive sites touches one contiguous segment:
 //     chunk k of site s lives at  base[k * stride + s]   (in units of a chunk).
 // Chunk types: FP64 double2 (2 reals); FP32 float4 (4 reals) when NR % 4 == 0,
-// else float2; FP16 = int16 fixed point, 8 / 4 / 2 values per 16 / 8 / 4-byte
+// else float2; FP16 = 16-bit fixed point, 8 / 4 / 2 values per 16 / 8 / 4-byte
 // chunk, value = q * scale / 32767 with scale either a per-site norm (spinors,
-// clover) or one constant (links).
+// clover) or one constant (links). q in [-32767, 32767] is stored offset-binary
+// (u = q + 32768), so that decoding is a byte permute that places u in the
+// mantissa of 2^23 and one exact subtraction, both on full-rate pipes.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -107,11 +109,17 @@ template <int P, int NR> struct Layout {
     enum { RPC = Chunk<P, NR>::RPC, NC = NR / Chunk<P, NR>::RPC };
 };
 
-__device__ __forceinline__ float s16lo(int w) { return (float)(short)(w & 0xffff); }
-__device__ __forceinline__ float s16hi(int w) { return (float)(short)(((unsigned)w) >> 16); }
+// 2^23 + 32768: the float whose mantissa holds the offset-binary zero
+#define LQ_F16_MAGIC 8421376.0f
+__device__ __forceinline__ float s16lo(int w) {
+    return __int_as_float((int)__byte_perm((unsigned)w, 0x4B000000u, 0x7610)) - LQ_F16_MAGIC;
+}
+__device__ __forceinline__ float s16hi(int w) {
+    return __int_as_float((int)__byte_perm((unsigned)w, 0x4B000000u, 0x7632)) - LQ_F16_MAGIC;
+}
 __device__ __forceinline__ int pack16(float a, float b) {
-    int qa = __float2int_rn(a), qb = __float2int_rn(b);
-    return (int)(((unsigned)qa & 0xffffu) | ((unsigned)qb << 16));
+    unsigned qa = (unsigned)(__float2int_rn(a) + 32768), qb = (unsigned)(__float2int_rn(b) + 32768);
+    return (int)((qa & 0xffffu) | (qb << 16));
 }
 
 // unpack one chunk c into RPC reals (FP16: times f = scale/32767)
@@ -154,13 +162,50 @@ __device__ __forceinline__ void load_reals(const void* base, int stride, int s, 
     }
 }
 
-// load the reals of chunk k only (RPC of them)
-template <int P, int NR, typename T>
+// load the reals of chunk k only (RPC of them); SMEM: base is a shared-memory copy
+template <int P, int NR, typename T, bool SMEM = false>
 __device__ __forceinline__ void load_chunk(const void* base, int stride, int s, int k, float scale, T* v) {
     typedef Layout<P, NR> Lay;
     const typename Lay::C* b = (const typename Lay::C*)base;
-    typename Lay::C c = __ldg(&b[(size_t)k * stride + s]);
+    typename Lay::C c;
+    if constexpr (SMEM) c = b[(size_t)k * stride + s];
+    else c = __ldg(&b[(size_t)k * stride + s]);
     unpack_chunk<P, NR, T>(c, scale * (1.f / 32767.f), v);
+}
+
+// ------------------------------------------------------- async copies (cp.async)
+// Each thread copies its own records into a private slice of shared memory,
+// laid out chunk-major like global memory (chunk k of thread t at k*blockDim + t),
+// so that reading it back is conflict-free.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// copy the NR-real record of site s (chunk-major global array with stride vh)
+// into this thread's slice of smem (stride blockDim.x); returns bytes per thread used
+template <int P, int NR>
+__device__ __forceinline__ void prefetch_record(void* smem, const void* gbase, int vh, int s) {
+    typedef Layout<P, NR> Lay;
+    typedef typename Lay::C C;
+    C* d = (C*)smem;
+    const C* g = (const C*)gbase;
+#pragma unroll
+    for (int k = 0; k < Lay::NC; k++) {
+        if constexpr (sizeof(C) == 16) cp_async16(&d[k * blockDim.x + threadIdx.x], &g[(size_t)k * vh + s]);
+        else if constexpr (sizeof(C) == 8) cp_async8(&d[k * blockDim.x + threadIdx.x], &g[(size_t)k * vh + s]);
+        else cp_async4(&d[k * blockDim.x + threadIdx.x], &g[(size_t)k * vh + s]);
+    }
 }
 
 // store NR reals of site s. For P16 with a per-site norm the norm is computed

@@ -18,7 +18,8 @@ static int pick_nb(int nrhs) {
 template <int P, int R, int EPI, int NB>
 static void wl(const char* name, WilsonArgs a, int block, cudaStream_t st) {
     dim3 grid((a.g.vh + block - 1) / block, (a.nrhs + NB - 1) / NB);
-    launch(name, wilson_dslash_kernel<P, R, EPI, NB>, grid, dim3(block), st, a);
+    const size_t smem = NB == 1 ? (size_t)epi_smem_per_thread<P, EPI>() * block : 0;
+    launch_smem(name, wilson_dslash_kernel<P, R, EPI, NB>, grid, dim3(block), smem, st, a);
 }
 
 template <int P, int R, int EPI>

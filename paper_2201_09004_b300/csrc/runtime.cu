@@ -61,6 +61,21 @@ void prof_end(int slot, cudaStream_t st) {
     cudaEventRecord(g_prof[slot].b, st);
 }
 
+static std::mutex g_smem_mu;
+static std::unordered_map<const void*, size_t> g_smem_optin;
+
+void opt_in_smem(const void* kernel, size_t bytes) {
+    std::lock_guard<std::mutex> lk(g_smem_mu);
+    size_t& have = g_smem_optin[kernel];
+    if (have >= bytes) return;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        fail(LQ_ECUDA, "dynamic shared memory of " + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e));
+    }
+    have = bytes;
+}
+
 // ------------------------------------------------------------------- tuner
 static std::mutex g_tune_mu;
 static std::unordered_map<std::string, int> g_tuned;
@@ -93,7 +108,11 @@ int tuned_block(const std::string& key, cudaStream_t st, const std::function<voi
     float best_ms = 1e30f;
     try {
         for (int bs : cand) {
-            run(bs);  // warm-up
+            try {
+                run(bs);  // warm-up; a configuration that cannot launch is skipped
+            } catch (const Error&) {
+                continue;
+            }
             LQ_CUDA(cudaEventRecord(a, st));
             for (int r = 0; r < 3; r++) run(bs);
             LQ_CUDA(cudaEventRecord(b, st));

@@ -41,6 +41,21 @@ int prof_begin(const char* name, cudaStream_t st);
 void prof_end(int slot, cudaStream_t st);
 void count_launch();
 bool stream_capturing(cudaStream_t st);
+// raise a kernel's dynamic shared-memory limit to at least `bytes` (once per size)
+void opt_in_smem(const void* kernel, size_t bytes);
+
+template <typename... KArgs, typename... Args>
+inline void launch_smem(const char* name, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                        cudaStream_t st, Args&&... args) {
+    if (grid.x == 0 || grid.y == 0) return;
+    if (smem > 48 * 1024) opt_in_smem((const void*)kernel, smem);
+    int slot = prof_begin(name, st);
+    kernel<<<grid, block, smem, st>>>(std::forward<Args>(args)...);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) fail(LQ_ECUDA, std::string("launch of ") + name + ": " + cudaGetErrorString(e));
+    prof_end(slot, st);
+    count_launch();
+}
 
 template <typename... KArgs, typename... Args>
 inline void launch(const char* name, void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t st,

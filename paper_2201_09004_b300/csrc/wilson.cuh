@@ -152,15 +152,16 @@ __host__ __device__ constexpr int offd_col(int q) {
 }
 
 // out_b += C_b w_b for both chiral blocks, C packed per block as 6 real
-// diagonal entries then the 15 upper off-diagonal entries (row-major, i<j)
-template <int P, int NB, typename T>
-__device__ __forceinline__ void clover_apply(const WilsonArgs& a, int s, cx<T> w[NB][4][3], cx<T> out[NB][4][3]) {
+// diagonal entries then the 15 upper off-diagonal entries (row-major, i<j).
+// The record is read from base[k * stride + s] (global, or a shared-memory copy).
+template <int P, int NB, typename T, bool SMEM = false>
+__device__ __forceinline__ void clover_apply_src(const void* base, int stride, int s, float sc, cx<T> w[NB][4][3],
+                                                 cx<T> out[NB][4][3]) {
     typedef Layout<P, 72> Lay;
-    const float sc = (P == P16) ? __ldg(a.clov_norm + s) : 1.f;
 #pragma unroll
     for (int k = 0; k < Lay::NC; k++) {
         T v[Lay::RPC];
-        load_chunk<P, 72, T>(a.clov, a.g.vh, s, k, sc, v);
+        load_chunk<P, 72, T, SMEM>(base, stride, s, k, sc, v);
 #pragma unroll
         for (int u = 0; u < Lay::RPC / 2; u++) {
             const int r = k * Lay::RPC + 2 * u;  // real index of this pair
@@ -186,15 +187,21 @@ __device__ __forceinline__ void clover_apply(const WilsonArgs& a, int s, cx<T> w
     }
 }
 
-// out_b = A^{-1}_b w_b (dagger: (A^{-1}_b)^+ w_b), A^{-1} stored row-major per block (36 complex)
 template <int P, int NB, typename T>
-__device__ __forceinline__ void ainv_apply(const WilsonArgs& a, int s, cx<T> w[NB][4][3], cx<T> out[NB][4][3]) {
-    typedef Layout<P, 144> Lay;
+__device__ __forceinline__ void clover_apply(const WilsonArgs& a, int s, cx<T> w[NB][4][3], cx<T> out[NB][4][3]) {
     const float sc = (P == P16) ? __ldg(a.clov_norm + s) : 1.f;
+    clover_apply_src<P, NB, T, false>(a.clov, a.g.vh, s, sc, w, out);
+}
+
+// out_b = A^{-1}_b w_b (dagger: (A^{-1}_b)^+ w_b), A^{-1} stored row-major per block (36 complex)
+template <int P, int NB, typename T, bool SMEM = false>
+__device__ __forceinline__ void ainv_apply_src(const void* base, int stride, int s, float sc, int dagger,
+                                               cx<T> w[NB][4][3], cx<T> out[NB][4][3]) {
+    typedef Layout<P, 144> Lay;
 #pragma unroll
     for (int k = 0; k < Lay::NC; k++) {
         T v[Lay::RPC];
-        load_chunk<P, 144, T>(a.clov, a.g.vh, s, k, sc, v);
+        load_chunk<P, 144, T, SMEM>(base, stride, s, k, sc, v);
 #pragma unroll
         for (int u = 0; u < Lay::RPC / 2; u++) {
             const int e = (k * Lay::RPC) / 2 + u;
@@ -204,13 +211,19 @@ __device__ __forceinline__ void ainv_apply(const WilsonArgs& a, int s, cx<T> w[N
             const cx<T> m = mk(v[2 * u], v[2 * u + 1]);
 #pragma unroll
             for (int b = 0; b < NB; b++) {
-                if (a.dagger)
+                if (dagger)
                     cjmac(blk(out[b], bl, j), m, blk(w[b], bl, i));
                 else
                     cmac(blk(out[b], bl, i), m, blk(w[b], bl, j));
             }
         }
     }
+}
+
+template <int P, int NB, typename T>
+__device__ __forceinline__ void ainv_apply(const WilsonArgs& a, int s, cx<T> w[NB][4][3], cx<T> out[NB][4][3]) {
+    const float sc = (P == P16) ? __ldg(a.clov_norm + s) : 1.f;
+    ainv_apply_src<P, NB, T, false>(a.clov, a.g.vh, s, sc, a.dagger, w, out);
 }
 
 // block reduction of per-thread |out|^2 (one value per rhs) into
@@ -239,6 +252,112 @@ __device__ __forceinline__ void reduce_norms(const double nrm[NB], double* norm_
     }
 }
 
+// ---------------------------------------------------------------------------
+// Single right-hand side: the eight hops are software-pipelined. The raw
+// (still encoded) spinor and link chunks of hop h+1 are loaded before hop h is
+// decoded and computed, so every thread keeps one hop of gathers in flight
+// while it computes; the epilogue operands are copied to shared memory with
+// cp.async at kernel start and arrive while the hops are computed.
+template <int P, int R> struct HopRaw {
+    typename Layout<P, 24>::C sp[Layout<P, 24>::NC];
+    typename Layout<P, R>::C u[Layout<P, R>::NC];
+    float n;   // FP16 spinor norm
+    float bs;  // boundary sign of the hop
+};
+
+template <int H, int P, int R>
+__device__ __forceinline__ void fetch_hop(const WilsonArgs& a, const int c[4], int s, int k0, HopRaw<P, R>& h) {
+    constexpr int MU = H >> 1;
+    constexpr bool FWD = (H & 1) == 0;
+    typedef typename Layout<P, 24>::C CS;
+    typedef typename Layout<P, R>::C CU;
+    float bs;
+    const int n = cb_hop(a.g, c, MU, FWD ? 1 : -1, bs);
+    h.bs = bs;
+    const CS* sb = (const CS*)((const char*)a.in.data + (size_t)k0 * a.in.rhs_bytes);
+#pragma unroll
+    for (int k = 0; k < Layout<P, 24>::NC; k++) h.sp[k] = __ldg(&sb[(size_t)k * a.g.vh + n]);
+    if constexpr (P == P16) h.n = __ldg(a.in.norm + (size_t)k0 * a.g.vh + n);
+    const int lp = FWD ? a.parity : 1 - a.parity;
+    const CU* ub = (const CU*)a.U.data + (size_t)(lp * 4 + MU) * Layout<P, R>::NC * a.g.vh;
+    const int ls = FWD ? s : n;
+#pragma unroll
+    for (int k = 0; k < Layout<P, R>::NC; k++) h.u[k] = __ldg(&ub[(size_t)k * a.g.vh + ls]);
+}
+
+template <int H, int P, int R, typename T>
+__device__ __forceinline__ void process_hop(const WilsonArgs& a, const HopRaw<P, R>& h, T sf, cx<T> acc[4][3]) {
+    constexpr int MU = H >> 1;
+    constexpr bool FWD = (H & 1) == 0;
+    typedef Layout<P, 24> LS;
+    typedef Layout<P, R> LU;
+    T v[24];
+    const float fs = (P == P16) ? h.n * (1.f / 32767.f) : 1.f;
+#pragma unroll
+    for (int k = 0; k < LS::NC; k++) unpack_chunk<P, 24, T>(h.sp[k], fs, v + k * LS::RPC);
+    T lv[R];
+    const float fu = a.U.scale * (1.f / 32767.f);
+#pragma unroll
+    for (int k = 0; k < LU::NC; k++) unpack_chunk<P, R, T>(h.u[k], fu, lv + k * LU::RPC);
+    cx<T> U[3][3];
+#pragma unroll
+    for (int r = 0; r < 2; r++)
+#pragma unroll
+        for (int q = 0; q < 3; q++) U[r][q] = mk(lv[(r * 3 + q) * 2], lv[(r * 3 + q) * 2 + 1]);
+    if constexpr (R == 18) {
+#pragma unroll
+        for (int q = 0; q < 3; q++) U[2][q] = mk(lv[(6 + q) * 2], lv[(6 + q) * 2 + 1]);
+    } else {
+        U[2][0] = cj(U[0][1] * U[1][2] - U[0][2] * U[1][1]);
+        U[2][1] = cj(U[0][2] * U[1][0] - U[0][0] * U[1][2]);
+        U[2][2] = cj(U[0][0] * U[1][1] - U[0][1] * U[1][0]);
+    }
+    cx<T> ps[4][3], h0[3], h1[3], r0[3], r1[3];
+    to_spinor(v, ps);
+    const T sp = FWD ? sf : -sf;  // projector (1 + sp g_mu)
+    proj<MU>(ps, sp, h0, h1);
+    if constexpr (FWD) {
+        su3_mv(U, h0, r0);
+        su3_mv(U, h1, r1);
+    } else {
+        su3_dmv(U, h0, r0);
+        su3_dmv(U, h1, r1);
+    }
+    if constexpr (MU == 3) {
+        const T sg = (T)h.bs;
+#pragma unroll
+        for (int k = 0; k < 3; k++) { r0[k] = sg * r0[k]; r1[k] = sg * r1[k]; }
+    }
+    recon_acc<MU>(acc, r0, r1, sp);
+}
+
+// hops of right-hand side k0 (the kernel's grid row when NB = 1)
+template <int P, int R, typename T>
+__device__ __forceinline__ void hops_pipelined(const WilsonArgs& a, const int c[4], int s, int k0, T sf,
+                                               cx<T> acc[4][3]) {
+    HopRaw<P, R> A, B;
+    fetch_hop<0>(a, c, s, k0, A);
+    fetch_hop<1>(a, c, s, k0, B); process_hop<0>(a, A, sf, acc);
+    fetch_hop<2>(a, c, s, k0, A); process_hop<1>(a, B, sf, acc);
+    fetch_hop<3>(a, c, s, k0, B); process_hop<2>(a, A, sf, acc);
+    fetch_hop<4>(a, c, s, k0, A); process_hop<3>(a, B, sf, acc);
+    fetch_hop<5>(a, c, s, k0, B); process_hop<4>(a, A, sf, acc);
+    fetch_hop<6>(a, c, s, k0, A); process_hop<5>(a, B, sf, acc);
+    fetch_hop<7>(a, c, s, k0, B); process_hop<6>(a, A, sf, acc);
+    process_hop<7>(a, B, sf, acc);
+}
+
+// Shared-memory bytes per thread of the prefetched epilogue operands
+// (clover record or A^{-1} record, the y spinor, and their FP16 norms).
+template <int P, int EPI>
+__host__ __device__ constexpr int epi_smem_per_thread() {
+    return P == P64 ? 0
+         : EPI == EPI_AINV ? (int)(sizeof(typename Layout<P, 144>::C) * Layout<P, 144>::NC) + 8
+         : EPI == EPI_XPAY ? (int)(sizeof(typename Layout<P, 72>::C) * Layout<P, 72>::NC +
+                                   sizeof(typename Layout<P, 24>::C) * Layout<P, 24>::NC) + 8
+         : 0;
+}
+
 template <int P, int R, int EPI, int NB>
 __global__ void __launch_bounds__(256) wilson_dslash_kernel(WilsonArgs a) {
     typedef typename RealT<P>::T T;
@@ -247,9 +366,31 @@ __global__ void __launch_bounds__(256) wilson_dslash_kernel(WilsonArgs a) {
     double nrm[NB];
 #pragma unroll
     for (int b = 0; b < NB; b++) nrm[b] = 0.0;
+    // shared-memory copies of the epilogue operands (single right-hand side, FP32/FP16)
+    constexpr bool PF = (NB == 1) && (epi_smem_per_thread<P, EPI>() > 0);
+    extern __shared__ __align__(16) unsigned char lq_smem[];
+    typedef typename Layout<P, 144>::C CA;
+    typedef typename Layout<P, 72>::C CC;
+    typedef typename Layout<P, 24>::C CY;
+    unsigned char* sm_rec = lq_smem;  // clover / inverse record, chunk-major
+    unsigned char* sm_y = lq_smem + (EPI == EPI_AINV ? sizeof(CA) * Layout<P, 144>::NC : sizeof(CC) * Layout<P, 72>::NC) * blockDim.x;
+    float* sm_norm = (float*)(sm_y + (EPI == EPI_XPAY ? sizeof(CY) * Layout<P, 24>::NC * blockDim.x : 0));
     if (s < a.g.vh) {
         int c[4];
         cb_coords(a.g, s, a.parity, c);
+        if constexpr (PF) {
+            if (a.has_clover) {
+                if constexpr (EPI == EPI_AINV) prefetch_record<P, 144>(sm_rec, a.clov, a.g.vh, s);
+                else prefetch_record<P, 72>(sm_rec, a.clov, a.g.vh, s);
+                if constexpr (P == P16) cp_async4(&sm_norm[threadIdx.x], a.clov_norm + s);
+            }
+            if constexpr (EPI == EPI_XPAY) {
+                prefetch_record<P, 24>(sm_y, (const char*)a.y.data + (size_t)kb * a.y.rhs_bytes, a.g.vh, s);
+                if constexpr (P == P16)
+                    cp_async4(&sm_norm[blockDim.x + threadIdx.x], a.y.norm + (size_t)kb * a.g.vh + s);
+            }
+            cp_async_commit();
+        }
         cx<T> acc[NB][4][3];
 #pragma unroll
         for (int b = 0; b < NB; b++)
@@ -258,10 +399,15 @@ __global__ void __launch_bounds__(256) wilson_dslash_kernel(WilsonArgs a) {
 #pragma unroll
                 for (int cc = 0; cc < 3; cc++) acc[b][sp][cc] = mk((T)0, (T)0);
         const T sf = a.dagger ? (T)-1 : (T)1;
-        hop_dir<0, P, R, NB, T>(a, c, s, kb, sf, acc);
-        hop_dir<1, P, R, NB, T>(a, c, s, kb, sf, acc);
-        hop_dir<2, P, R, NB, T>(a, c, s, kb, sf, acc);
-        hop_dir<3, P, R, NB, T>(a, c, s, kb, sf, acc);
+        if constexpr (NB == 1) {
+            hops_pipelined<P, R, T>(a, c, s, kb, sf, acc[0]);
+        } else {
+            hop_dir<0, P, R, NB, T>(a, c, s, kb, sf, acc);
+            hop_dir<1, P, R, NB, T>(a, c, s, kb, sf, acc);
+            hop_dir<2, P, R, NB, T>(a, c, s, kb, sf, acc);
+            hop_dir<3, P, R, NB, T>(a, c, s, kb, sf, acc);
+        }
+        if constexpr (PF) cp_async_wait_all();
 #pragma unroll
         for (int b = 0; b < NB; b++)
 #pragma unroll
@@ -285,7 +431,11 @@ __global__ void __launch_bounds__(256) wilson_dslash_kernel(WilsonArgs a) {
                     for (int sp = 0; sp < 4; sp++)
 #pragma unroll
                         for (int cc = 0; cc < 3; cc++) res[b][sp][cc] = mk((T)0, (T)0);
-                ainv_apply<P, NB, T>(a, s, acc, res);
+                if constexpr (PF)
+                    ainv_apply_src<P, NB, T, true>(sm_rec, blockDim.x, threadIdx.x,
+                                                   P == P16 ? sm_norm[threadIdx.x] : 1.f, a.dagger, acc, res);
+                else
+                    ainv_apply<P, NB, T>(a, s, acc, res);
             } else {
                 // A^{-1} = ((4+m) - i mu g5) / ((4+m)^2 + mu^2)
                 const T m4 = (T)a.m4, mu = (T)a.mu;
@@ -305,7 +455,13 @@ __global__ void __launch_bounds__(256) wilson_dslash_kernel(WilsonArgs a) {
 #pragma unroll
             for (int b = 0; b < NB; b++) {
                 T v[24];
-                if (kb + b < a.nrhs) {
+                if constexpr (PF) {
+                    const float fy = (P == P16) ? sm_norm[blockDim.x + threadIdx.x] * (1.f / 32767.f) : 1.f;
+#pragma unroll
+                    for (int k = 0; k < Layout<P, 24>::NC; k++)
+                        unpack_chunk<P, 24, T>(((const CY*)sm_y)[k * blockDim.x + threadIdx.x], fy,
+                                               v + k * Layout<P, 24>::RPC);
+                } else if (kb + b < a.nrhs) {
                     fload<P, 24, T>(a.y, kb + b, s, v);
                 } else {
 #pragma unroll
@@ -323,7 +479,13 @@ __global__ void __launch_bounds__(256) wilson_dslash_kernel(WilsonArgs a) {
 #pragma unroll
                     for (int cc = 0; cc < 3; cc++) res[b][sp][cc] = f * yv[b][sp][cc] - acc[b][sp][cc];
                 }
-            if (a.has_clover) clover_apply<P, NB, T>(a, s, yv, res);
+            if (a.has_clover) {
+                if constexpr (PF)
+                    clover_apply_src<P, NB, T, true>(sm_rec, blockDim.x, threadIdx.x,
+                                                     P == P16 ? sm_norm[threadIdx.x] : 1.f, yv, res);
+                else
+                    clover_apply<P, NB, T>(a, s, yv, res);
+            }
         }
 #pragma unroll
         for (int b = 0; b < NB; b++) {
