@@ -75,7 +75,11 @@ typedef enum {
     LQ_EBUSY = 9        /* server is shutting down or the queue is full */
 } lq_status;
 
-typedef enum { LQ_F64 = 0, LQ_F32 = 1, LQ_F16 = 2 } lq_prec;  /* F16 = int16 fixed point + per-site norm */
+/* F16 = 16-bit fixed point + per-site norm, FP32 arithmetic. F32X2 = "double-float":
+ * each real is a pair of FP32 numbers (hi + lo, ~48 significant bits) stored in 8
+ * bytes and computed on the FP32 pipes; the mixed-precision solvers use it for
+ * their FP64-accuracy steps because B300's FP64 rate is 1/64 of its FP32 rate. */
+typedef enum { LQ_F64 = 0, LQ_F32 = 1, LQ_F16 = 2, LQ_F32X2 = 3 } lq_prec;
 typedef enum { LQ_R18 = 18, LQ_R12 = 12 } lq_recon;            /* link compression (R12: two rows of SU(3)) */
 typedef enum { LQ_THIN = 0, LQ_FAT = 1, LQ_LONG = 2 } lq_gauge_kind;
 typedef enum { LQ_HOST = 0, LQ_DEVICE = 1 } lq_loc;

@@ -3,14 +3,18 @@
 // deterministic: each thread sums its sites in a fixed order, blocks reduce by
 // warp shuffles, and one block per right-hand side adds the per-block partials
 // in index order with Neumaier-compensated summation.
+#include <type_traits>
+
 #include "runtime.h"
 
 namespace lq {
 
-template <int PA, int PB> struct MathT { typedef float T; };
-template <int PB> struct MathT<P64, PB> { typedef double T; };
-template <int PA> struct MathT<PA, P64> { typedef double T; };
-template <> struct MathT<P64, P64> { typedef double T; };
+// arithmetic type of an operation between two storage precisions: FP64 if
+// either side is FP64, else double-float if either side is double-float, else FP32
+template <int PA, int PB> struct MathT {
+    typedef typename std::conditional<PA == P64 || PB == P64, double,
+            typename std::conditional<PA == PDF || PB == PDF, df, float>::type>::type T;
+};
 
 struct HostScalars {
     double a[64];
@@ -227,11 +231,12 @@ static dim3 upd_grid(int vh, int nrhs) {
     return dim3(b < cap ? b : cap, nrhs);
 }
 
-#define DISPATCH_P(prec, MACRO)                 \
-    do {                                        \
-        if ((prec) == LQ_F64) { MACRO(P64); }    \
-        else if ((prec) == LQ_F32) { MACRO(P32); } \
-        else { MACRO(P16); }                     \
+#define DISPATCH_P(prec, MACRO)                    \
+    do {                                           \
+        if ((prec) == LQ_F64) { MACRO(P64); }       \
+        else if ((prec) == LQ_F32) { MACRO(P32); }  \
+        else if ((prec) == LQ_F16) { MACRO(P16); }  \
+        else { MACRO(PDF); }                        \
     } while (0)
 
 #define BY_KIND(f, NAME, KERNEL, GRID, ...)                                                     \
@@ -262,7 +267,8 @@ void blas_copy(Field& d, const Field& s, cudaStream_t st) {
     if (d.kind != s.kind || d.nrhs != s.nrhs) fail(LQ_EINVAL, "blas_copy: shape mismatch");
     if (d.prec == LQ_F64) copy_from<P64>(d, s, st);
     else if (d.prec == LQ_F32) copy_from<P32>(d, s, st);
-    else copy_from<P16>(d, s, st);
+    else if (d.prec == LQ_F16) copy_from<P16>(d, s, st);
+    else copy_from<PDF>(d, s, st);
 }
 
 void blas_zero(Field& x, cudaStream_t st) {
@@ -299,7 +305,8 @@ void blas_axpy_h(Field& y, const double* a, const Field& x, cudaStream_t st) {
     HostScalars h = hs(a, nullptr, y.nrhs);
     if (y.prec == LQ_F64) axpy_h_from<P64>(y, h, x, st);
     else if (y.prec == LQ_F32) axpy_h_from<P32>(y, h, x, st);
-    else axpy_h_from<P16>(y, h, x, st);
+    else if (y.prec == LQ_F16) axpy_h_from<P16>(y, h, x, st);
+    else axpy_h_from<PDF>(y, h, x, st);
 }
 
 void blas_axpby_h(Field& y, const double* a, const Field& x, const double* b, double* part, cudaStream_t st) {
@@ -337,7 +344,8 @@ void blas_cg_xs(Field& x, const Field& p, Field& s, const Field& q, const double
     if (p.prec != s.prec || p.prec != q.prec) fail(LQ_EINVAL, "blas_cg_xs: precision mismatch");
     if (x.prec == LQ_F64) cg_xs_from<P64>(x, p, s, q, sc, part, st);
     else if (x.prec == LQ_F32) cg_xs_from<P32>(x, p, s, q, sc, part, st);
-    else cg_xs_from<P16>(x, p, s, q, sc, part, st);
+    else if (x.prec == LQ_F16) cg_xs_from<P16>(x, p, s, q, sc, part, st);
+    else cg_xs_from<PDF>(x, p, s, q, sc, part, st);
 }
 
 void blas_cg_p(Field& p, const Field& r, const double* sc, cudaStream_t st) {

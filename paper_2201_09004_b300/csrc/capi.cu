@@ -61,7 +61,7 @@ static void check_op(const lq_op_params* op) {
 }
 
 static void check_prec(int prec) {
-    if (prec < LQ_F64 || prec > LQ_F16) fail(LQ_EINVAL, "unknown precision");
+    if (!valid_prec(prec)) fail(LQ_EINVAL, "unknown precision");
 }
 
 static size_t field_canon_bytes(const Lattice& L, int action) {
@@ -169,7 +169,7 @@ static OpDesc make_desc(const lq_op_params* op, int prec) {
     d.mu = op->action == LQ_HISQ ? 0.0 : op->mu;
     d.c_naik = op->c_naik;
     d.prec = prec;
-    d.recon = prec == LQ_F64 ? 18 : 12;
+    d.recon = (prec == LQ_F64 || prec == LQ_F32X2) ? 18 : 12;
     return d;
 }
 

@@ -299,7 +299,7 @@ __global__ void convert_sites_kernel(const void* src, Geo g, void* dst, float* n
 }
 
 static size_t rec_bytes(int prec, int nr, int vh) {
-    return (size_t)2 * nr * (prec == LQ_F64 ? 8 : (prec == LQ_F32 ? 4 : 2)) * vh;
+    return (size_t)2 * nr * prec_bytes(prec) * vh;
 }
 
 template <int NR>
@@ -308,22 +308,25 @@ static void make_precisions(Lattice& lat, void* d64, void* out[3], float** norm,
     out[LQ_F64] = d64;
     out[LQ_F32] = dev_alloc(&lat, rec_bytes(LQ_F32, NR, lat.vh));
     out[LQ_F16] = dev_alloc(&lat, rec_bytes(LQ_F16, NR, lat.vh));
+    out[LQ_F32X2] = dev_alloc(&lat, rec_bytes(LQ_F32X2, NR, lat.vh));
     *norm = (float*)dev_alloc(&lat, sizeof(float) * 2 * lat.vh);
     launch("convert_sites", convert_sites_kernel<P32, NR>, grid, dim3(128), st, (const void*)d64, lat.geo,
            out[LQ_F32], (float*)nullptr);
     launch("convert_sites", convert_sites_kernel<P16, NR>, grid, dim3(128), st, (const void*)d64, lat.geo,
            out[LQ_F16], *norm);
+    launch("convert_sites", convert_sites_kernel<PDF, NR>, grid, dim3(128), st, (const void*)d64, lat.geo,
+           out[LQ_F32X2], (float*)nullptr);
 }
 
 void free_clover(Lattice& lat) {
-    for (int p = 0; p < 3; p++) {
+    for (int p = 0; p < 4; p++) {
         dev_free(&lat, lat.clovC[p], rec_bytes(p, 72, lat.vh));
         lat.clovC[p] = nullptr;
     }
     dev_free(&lat, lat.clovC_norm, sizeof(float) * 2 * lat.vh);
     lat.clovC_norm = nullptr;
     for (auto& kv : lat.ainv) {
-        for (int p = 0; p < 3; p++) dev_free(&lat, kv.second.data[p], rec_bytes(p, 144, lat.vh));
+        for (int p = 0; p < 4; p++) dev_free(&lat, kv.second.data[p], rec_bytes(p, 144, lat.vh));
         dev_free(&lat, kv.second.norm, sizeof(float) * 2 * lat.vh);
     }
     lat.ainv.clear();

@@ -20,13 +20,79 @@
 
 namespace lq {
 
-enum Prec { P64 = 0, P32 = 1, P16 = 2 };
+// P64: IEEE double. P32: float. P16: 16-bit fixed point with FP32 arithmetic.
+// PDF: "double-float", a real stored and computed as an unevaluated sum of two
+// floats hi + lo (about 48 significant bits). B300 runs FP64 at 1/64 of its
+// FP32 rate, so the FP64-accuracy work of the mixed-precision solvers (reliable
+// updates, source preparation, reconstruction, true residual) uses PDF and
+// runs on the FP32 pipes.
+enum Prec { P64 = 0, P32 = 1, P16 = 2, PDF = 3 };
 
 // site-local epilogues fused into the hopping kernels (see wilson.cuh, hisq.cuh)
 enum Epi { EPI_HOP = 0, EPI_AINV = 1, EPI_XPAY = 2 };
 
+// ------------------------------------------------------------ double-float
+// Error-free transformations of Knuth (two-sum) and Dekker/FMA (two-product);
+// every step uses the _rn intrinsics so the compiler cannot contract or
+// reassociate them. Relative error of one operation is about 2^-44.
+struct df {
+    float hi, lo;
+    __host__ __device__ df() {}
+    __host__ __device__ df(float h) : hi(h), lo(0.f) {}
+    __host__ __device__ df(float h, float l) : hi(h), lo(l) {}
+    __device__ explicit df(int i) : hi((float)i), lo(0.f) {}
+    __device__ explicit df(double d) {
+        hi = __double2float_rn(d);
+        lo = __double2float_rn(d - (double)hi);
+    }
+    __device__ explicit operator double() const { return (double)hi + (double)lo; }
+    __device__ explicit operator float() const { return __fadd_rn(hi, lo); }
+};
+
+__device__ __forceinline__ df df_fast_two_sum(float a, float b) {  // |a| >= |b|
+    float s = __fadd_rn(a, b);
+    float e = __fsub_rn(b, __fsub_rn(s, a));
+    return df(s, e);
+}
+__device__ __forceinline__ df operator+(df x, df y) {
+    float s = __fadd_rn(x.hi, y.hi);
+    float bb = __fsub_rn(s, x.hi);
+    float e = __fadd_rn(__fsub_rn(x.hi, __fsub_rn(s, bb)), __fsub_rn(y.hi, bb));
+    e = __fadd_rn(e, __fadd_rn(x.lo, y.lo));
+    return df_fast_two_sum(s, e);
+}
+__device__ __forceinline__ df operator-(df x) { return df(-x.hi, -x.lo); }
+__device__ __forceinline__ df operator-(df x, df y) { return x + (-y); }
+__device__ __forceinline__ df operator*(df x, df y) {
+    float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fmaf_rn(x.hi, y.lo, e);
+    e = __fmaf_rn(x.lo, y.hi, e);
+    return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ df operator/(df x, df y) {
+    float q1 = __fdiv_rn(x.hi, y.hi);
+    df r = x - df(q1) * y;
+    float q2 = __fdiv_rn(r.hi, y.hi);
+    return df_fast_two_sum(q1, q2);
+}
+__device__ __forceinline__ df& operator+=(df& x, df y) { x = x + y; return x; }
+__device__ __forceinline__ df& operator-=(df& x, df y) { x = x - y; return x; }
+__device__ __forceinline__ df fma(df a, df b, df c) { return a * b + c; }
+using ::fma;
+
+// conversions between the arithmetic types of the kernels
+template <typename T> __device__ __forceinline__ T from_df(df d);
+template <> __device__ __forceinline__ df from_df<df>(df d) { return d; }
+template <> __device__ __forceinline__ double from_df<double>(df d) { return (double)d.hi + (double)d.lo; }
+template <> __device__ __forceinline__ float from_df<float>(df d) { return __fadd_rn(d.hi, d.lo); }
+__device__ __forceinline__ df to_df(df v) { return v; }
+__device__ __forceinline__ df to_df(double v) { return df(v); }
+__device__ __forceinline__ df to_df(float v) { return df(v); }
+
 template <int P> struct RealT { typedef float T; };
 template <> struct RealT<P64> { typedef double T; };
+template <> struct RealT<PDF> { typedef df T; };
 
 // ------------------------------------------------------------------ complex
 template <typename T> struct cx {
@@ -95,6 +161,7 @@ __device__ __forceinline__ int cb_hop(const Geo& g, const int c[4], int mu, int 
 // ----------------------------------------------------------------- storage
 template <int P, int NR> struct Chunk;
 template <int NR> struct Chunk<P64, NR> { typedef double2 C; enum { RPC = 2 }; };
+template <int NR> struct Chunk<PDF, NR> { typedef float4 C; enum { RPC = 2 }; };  // (hi, lo) x 2
 template <int NR> struct Chunk<P32, NR> {
     typedef typename std::conditional<NR % 4 == 0, float4, float2>::type C;
     enum { RPC = (NR % 4 == 0) ? 4 : 2 };
@@ -128,6 +195,9 @@ __device__ __forceinline__ void unpack_chunk(const typename Layout<P, NR>::C& c,
     typedef Layout<P, NR> Lay;
     if constexpr (P == P64) {
         v[0] = (T)c.x; v[1] = (T)c.y;
+    } else if constexpr (P == PDF) {
+        v[0] = from_df<T>(df(c.x, c.y));
+        v[1] = from_df<T>(df(c.z, c.w));
     } else if constexpr (P == P32) {
         if constexpr (Lay::RPC == 4) {
             v[0] = (T)c.x; v[1] = (T)c.y; v[2] = (T)c.z; v[3] = (T)c.w;
@@ -246,6 +316,9 @@ __device__ __forceinline__ void store_reals(void* base, int stride, int s, float
             typename Lay::C c;
             if constexpr (P == P64) {
                 c.x = (double)v[2 * k]; c.y = (double)v[2 * k + 1];
+            } else if constexpr (P == PDF) {
+                const df a0 = to_df(v[2 * k]), a1 = to_df(v[2 * k + 1]);
+                c.x = a0.hi; c.y = a0.lo; c.z = a1.hi; c.w = a1.lo;
             } else if constexpr (Lay::RPC == 4) {
                 c.x = (float)v[4 * k]; c.y = (float)v[4 * k + 1]; c.z = (float)v[4 * k + 2]; c.w = (float)v[4 * k + 3];
             } else {

@@ -24,7 +24,7 @@ static void wl(const char* name, WilsonArgs a, int block, cudaStream_t st) {
 
 template <int P, int R, int EPI>
 static void wl_nb(const char* name, WilsonArgs a, int nb, int block, cudaStream_t st) {
-    if constexpr (P == P64) {
+    if constexpr (P == P64 || P == PDF) {
         wl<P, R, EPI, 1>(name, a, block, st);
     } else {
         if (nb == 4) wl<P, R, EPI, 4>(name, a, block, st);
@@ -41,10 +41,11 @@ static void wl_epi(const char* name, WilsonArgs a, int epi, int nb, int block, c
 }
 
 static const char* wname(int prec, int epi) {
-    static const char* n[3][3] = {
+    static const char* n[4][3] = {
         {"wilson_dslash_f64_hop", "wilson_dslash_f64_ainv", "wilson_dslash_f64_xpay"},
         {"wilson_dslash_f32_hop", "wilson_dslash_f32_ainv", "wilson_dslash_f32_xpay"},
-        {"wilson_dslash_f16_hop", "wilson_dslash_f16_ainv", "wilson_dslash_f16_xpay"}};
+        {"wilson_dslash_f16_hop", "wilson_dslash_f16_ainv", "wilson_dslash_f16_xpay"},
+        {"wilson_dslash_f32x2_hop", "wilson_dslash_f32x2_ainv", "wilson_dslash_f32x2_xpay"}};
     return n[prec][epi];
 }
 
@@ -78,6 +79,8 @@ int wilson_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int ep
         if (op.prec == LQ_F64) {
             if (op.recon == 18) wl_epi<P64, 18>(name, a, epi, nb, block, st);
             else wl_epi<P64, 12>(name, a, epi, nb, block, st);
+        } else if (op.prec == LQ_F32X2) {
+            wl_epi<PDF, 18>(name, a, epi, nb, block, st);
         } else if (op.prec == LQ_F32) {
             if (op.recon == 18) wl_epi<P32, 18>(name, a, epi, nb, block, st);
             else wl_epi<P32, 12>(name, a, epi, nb, block, st);
@@ -115,6 +118,7 @@ void wilson_ainv_site(Lattice& lat, const OpDesc& op, int parity, int dagger, co
     if (a.has_clover) a.clov = ainv_block(lat, op.m, op.mu, in.prec, parity, &a.clov_norm, st);
     dim3 grid((lat.vh + 127) / 128, in.nrhs);
     if (in.prec == LQ_F64) launch("wilson_ainv_site", wilson_ainv_site_kernel<P64>, grid, dim3(128), st, a);
+    else if (in.prec == LQ_F32X2) launch("wilson_ainv_site", wilson_ainv_site_kernel<PDF>, grid, dim3(128), st, a);
     else if (in.prec == LQ_F32) launch("wilson_ainv_site", wilson_ainv_site_kernel<P32>, grid, dim3(128), st, a);
     else launch("wilson_ainv_site", wilson_ainv_site_kernel<P16>, grid, dim3(128), st, a);
 }
@@ -128,7 +132,7 @@ static void hl(const char* name, HisqArgs a, int block, cudaStream_t st) {
 
 template <int P, int RL, int EPI>
 static void hl_nb(const char* name, HisqArgs a, int nb, int block, cudaStream_t st) {
-    if constexpr (P == P64) {
+    if constexpr (P == P64 || P == PDF) {
         hl<P, RL, EPI, 1>(name, a, block, st);
     } else {
         if (nb == 4) hl<P, RL, EPI, 4>(name, a, block, st);
@@ -144,9 +148,10 @@ static void hl_epi(const char* name, HisqArgs a, int epi, int nb, int block, cud
 }
 
 static const char* hname(int prec, int epi) {
-    static const char* n[3][2] = {{"hisq_dslash_f64_hop", "hisq_dslash_f64_xpay"},
+    static const char* n[4][2] = {{"hisq_dslash_f64_hop", "hisq_dslash_f64_xpay"},
                                   {"hisq_dslash_f32_hop", "hisq_dslash_f32_xpay"},
-                                  {"hisq_dslash_f16_hop", "hisq_dslash_f16_xpay"}};
+                                  {"hisq_dslash_f16_hop", "hisq_dslash_f16_xpay"},
+                                  {"hisq_dslash_f32x2_hop", "hisq_dslash_f32x2_xpay"}};
     return n[prec][epi == EPI_XPAY ? 1 : 0];
 }
 
@@ -174,6 +179,8 @@ int hisq_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int epi,
         if (op.prec == LQ_F64) {
             if (op.recon == 18) hl_epi<P64, 18>(name, a, epi, nb, block, st);
             else hl_epi<P64, 12>(name, a, epi, nb, block, st);
+        } else if (op.prec == LQ_F32X2) {
+            hl_epi<PDF, 18>(name, a, epi, nb, block, st);
         } else if (op.prec == LQ_F32) {
             if (op.recon == 18) hl_epi<P32, 18>(name, a, epi, nb, block, st);
             else hl_epi<P32, 12>(name, a, epi, nb, block, st);

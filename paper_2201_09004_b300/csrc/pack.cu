@@ -37,12 +37,15 @@ static void pack_gauge_t(Lattice& lat, const double* canon, void* out, float sca
 void pack_gauge(Lattice& lat, int kind, int prec, int recon, PackedGauge& out, cudaStream_t st) {
     const double* canon = lat.canon[kind];
     if (!canon) fail(LQ_EINVAL, "gauge field of this kind is not loaded");
-    out.bytes = (size_t)2 * 4 * recon * (prec == LQ_F64 ? 8 : (prec == LQ_F32 ? 4 : 2)) * lat.vh;
+    out.bytes = (size_t)2 * 4 * recon * prec_bytes(prec) * lat.vh;
     out.data = dev_alloc(&lat, out.bytes);
     out.scale = prec == LQ_F16 ? lat.maxabs[kind] : 1.f;
     if (prec == LQ_F64) {
         if (recon == 18) pack_gauge_t<P64, 18>(lat, canon, out.data, out.scale, st);
         else pack_gauge_t<P64, 12>(lat, canon, out.data, out.scale, st);
+    } else if (prec == LQ_F32X2) {
+        if (recon == 18) pack_gauge_t<PDF, 18>(lat, canon, out.data, out.scale, st);
+        else pack_gauge_t<PDF, 12>(lat, canon, out.data, out.scale, st);
     } else if (prec == LQ_F32) {
         if (recon == 18) pack_gauge_t<P32, 18>(lat, canon, out.data, out.scale, st);
         else pack_gauge_t<P32, 12>(lat, canon, out.data, out.scale, st);
@@ -120,11 +123,13 @@ __global__ void export_kernel(double* canon, Geo g, int parity, FieldV f) {
     do {                                                                                                   \
         dim3 grid_((lat.vh + 127) / 128);                                                                  \
         if (f.kind == LQ_WILSON_FIELD) {                                                                   \
-            if (f.prec == LQ_F64) launch(NAME, KERNEL<P64, 24>, grid_, dim3(128), st, __VA_ARGS__);        \
+            if (f.prec == LQ_F32X2) launch(NAME, KERNEL<PDF, 24>, grid_, dim3(128), st, __VA_ARGS__);      \
+            else if (f.prec == LQ_F64) launch(NAME, KERNEL<P64, 24>, grid_, dim3(128), st, __VA_ARGS__);   \
             else if (f.prec == LQ_F32) launch(NAME, KERNEL<P32, 24>, grid_, dim3(128), st, __VA_ARGS__);   \
             else launch(NAME, KERNEL<P16, 24>, grid_, dim3(128), st, __VA_ARGS__);                         \
         } else {                                                                                           \
-            if (f.prec == LQ_F64) launch(NAME, KERNEL<P64, 6>, grid_, dim3(128), st, __VA_ARGS__);         \
+            if (f.prec == LQ_F32X2) launch(NAME, KERNEL<PDF, 6>, grid_, dim3(128), st, __VA_ARGS__);       \
+            else if (f.prec == LQ_F64) launch(NAME, KERNEL<P64, 6>, grid_, dim3(128), st, __VA_ARGS__);    \
             else if (f.prec == LQ_F32) launch(NAME, KERNEL<P32, 6>, grid_, dim3(128), st, __VA_ARGS__);    \
             else launch(NAME, KERNEL<P16, 6>, grid_, dim3(128), st, __VA_ARGS__);                          \
         }                                                                                                  \

@@ -160,7 +160,7 @@ static size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
 
 static size_t rhs_bytes_of(int kind, int prec, int vh) {
     int nr = kind == LQ_WILSON_FIELD ? 24 : 6;
-    return align256((size_t)nr * (prec == LQ_F64 ? 8 : (prec == LQ_F32 ? 4 : 2)) * vh);
+    return align256((size_t)nr * prec_bytes(prec) * vh);
 }
 
 size_t field_bytes(int kind, int prec, int nrhs, int vh) {

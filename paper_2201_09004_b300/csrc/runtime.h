@@ -17,6 +17,10 @@
 
 namespace lq {
 
+// bytes per real of a storage precision (lq_prec values)
+inline int prec_bytes(int prec) { return prec == LQ_F32 ? 4 : (prec == LQ_F16 ? 2 : 8); }
+inline bool valid_prec(int prec) { return prec >= LQ_F64 && prec <= LQ_F32X2; }
+
 // ------------------------------------------------------------------ errors
 struct Error {
     int code;
@@ -123,10 +127,10 @@ struct Lattice {
     std::map<std::tuple<int, int, int>, PackedGauge> packed;  // (kind, prec, recon)
     bool has_clover = false;
     double c_sw = 0.0;
-    void* clovC[3] = {nullptr, nullptr, nullptr};  // clover C per precision, [2 parities][72 reals][vh]
+    void* clovC[4] = {nullptr, nullptr, nullptr, nullptr};  // clover C per precision, [2][72 reals][vh]
     float* clovC_norm = nullptr;                     // FP16 norms [2][vh]
     struct Ainv {
-        void* data[3] = {nullptr, nullptr, nullptr};
+        void* data[4] = {nullptr, nullptr, nullptr, nullptr};
         float* norm = nullptr;
     };
     std::map<std::pair<double, double>, Ainv> ainv;  // (m, mu) -> A^{-1} per precision

@@ -108,8 +108,9 @@ static CgResult cgnr_mixed(Lattice& lat, const OpDesc& ops, const OpDesc& op64, 
     const int ps = ops.prec;
     const int px = ps == LQ_F16 ? LQ_F32 : ps;  // the sloppy solution accumulates in at least FP32
     Pool pool(lat.vh);
-    Field s_hi = pool.get(LQ_WILSON_FIELD, LQ_F64, n), q64 = pool.get(LQ_WILSON_FIELD, LQ_F64, n);
-    Field t64 = pool.get(LQ_WILSON_FIELD, LQ_F64, n), x_lo = pool.get(LQ_WILSON_FIELD, px, n);
+    const int ph = op64.prec;  // FP64, or double-float for the mixed solvers
+    Field s_hi = pool.get(LQ_WILSON_FIELD, ph, n), q64 = pool.get(LQ_WILSON_FIELD, ph, n);
+    Field t64 = pool.get(LQ_WILSON_FIELD, ph, n), x_lo = pool.get(LQ_WILSON_FIELD, px, n);
     Field s_lo = pool.get(LQ_WILSON_FIELD, ps, n), r = pool.get(LQ_WILSON_FIELD, ps, n);
     Field p = pool.get(LQ_WILSON_FIELD, ps, n), q = pool.get(LQ_WILSON_FIELD, ps, n);
     Field t = pool.get(LQ_WILSON_FIELD, ps, n);
@@ -201,7 +202,10 @@ int solve_wilson(Lattice& lat, const lq_op_params& opp, const lq_solve_params& s
     if (sp.solver != LQ_CGNR && sp.solver != LQ_MIXED_CGNR) fail(LQ_EINVAL, "solver kind for a Wilson action");
     if (!(sp.tol > 0)) fail(LQ_EINVAL, "tol must be positive");
     const int recon = sp.recon_sloppy == 12 ? 12 : 18;
-    const OpDesc op64 = wilson_desc(opp, LQ_F64, 18);
+    // the FP64-accuracy steps: native FP64 for the plain FP64 solver, double-float
+    // (FP32 pipes) when the iterations run in FP32 / FP16
+    const int ph = ps == LQ_F64 ? LQ_F64 : LQ_F32X2;
+    const OpDesc op64 = wilson_desc(opp, ph, 18);
     const OpDesc ops = wilson_desc(opp, ps, recon);
     double delta = sp.solver == LQ_MIXED_CGNR ? (sp.delta > 0 ? sp.delta : 0.1) : 0.0;
     if (ps == LQ_F64) delta = 0.0;
@@ -212,10 +216,10 @@ int solve_wilson(Lattice& lat, const lq_op_params& opp, const lq_solve_params& s
     LQ_CUDA(cudaEventCreate(&e1));
     LQ_CUDA(cudaEventRecord(e0, st));
     Pool pool(lat.vh);
-    Field be = pool.get(LQ_WILSON_FIELD, LQ_F64, nrhs), bo = pool.get(LQ_WILSON_FIELD, LQ_F64, nrhs);
-    Field bhat = pool.get(LQ_WILSON_FIELD, LQ_F64, nrhs), xe = pool.get(LQ_WILSON_FIELD, LQ_F64, nrhs);
-    Field xo = pool.get(LQ_WILSON_FIELD, LQ_F64, nrhs), te = pool.get(LQ_WILSON_FIELD, LQ_F64, nrhs);
-    Field to = pool.get(LQ_WILSON_FIELD, LQ_F64, nrhs);
+    Field be = pool.get(LQ_WILSON_FIELD, ph, nrhs), bo = pool.get(LQ_WILSON_FIELD, ph, nrhs);
+    Field bhat = pool.get(LQ_WILSON_FIELD, ph, nrhs), xe = pool.get(LQ_WILSON_FIELD, ph, nrhs);
+    Field xo = pool.get(LQ_WILSON_FIELD, ph, nrhs), te = pool.get(LQ_WILSON_FIELD, ph, nrhs);
+    Field to = pool.get(LQ_WILSON_FIELD, ph, nrhs);
     Scalars sc;
     sc.init(nrhs, lat.vh);
     std::vector<double> ones(nrhs, 1.0);
@@ -317,8 +321,9 @@ static CgResult cg_hisq(Lattice& lat, const OpDesc& ops, const OpDesc& op64, dou
     const int n = b.nrhs;
     const int ps = ops.prec, px = ps == LQ_F16 ? LQ_F32 : ps;
     Pool pool(lat.vh);
-    Field r_hi = pool.get(LQ_STAGGERED_FIELD, LQ_F64, n), q64 = pool.get(LQ_STAGGERED_FIELD, LQ_F64, n);
-    Field t64 = pool.get(LQ_STAGGERED_FIELD, LQ_F64, n), x_lo = pool.get(LQ_STAGGERED_FIELD, px, n);
+    const int ph = op64.prec;
+    Field r_hi = pool.get(LQ_STAGGERED_FIELD, ph, n), q64 = pool.get(LQ_STAGGERED_FIELD, ph, n);
+    Field t64 = pool.get(LQ_STAGGERED_FIELD, ph, n), x_lo = pool.get(LQ_STAGGERED_FIELD, px, n);
     Field r = pool.get(LQ_STAGGERED_FIELD, ps, n), p = pool.get(LQ_STAGGERED_FIELD, ps, n);
     Field q = pool.get(LQ_STAGGERED_FIELD, ps, n), t = pool.get(LQ_STAGGERED_FIELD, ps, n);
     Scalars sc;
@@ -508,7 +513,8 @@ int solve_hisq(Lattice& lat, const lq_op_params& opp, const lq_solve_params& sp,
     if (ps < LQ_F64 || ps > LQ_F16) fail(LQ_EINVAL, "prec_sloppy");
     if (!(sp.tol > 0)) fail(LQ_EINVAL, "tol must be positive");
     const int recon = sp.recon_sloppy == 12 ? 12 : 18;
-    const OpDesc op64 = hisq_desc(opp, LQ_F64, 18);
+    const int ph = ps == LQ_F64 ? LQ_F64 : LQ_F32X2;
+    const OpDesc op64 = hisq_desc(opp, ph, 18);
     const OpDesc ops = hisq_desc(opp, ps, recon);
     const double delta = (ps == LQ_F64) ? 0.0 : (sp.delta > 0 ? sp.delta : 0.1);
     const int maxiter = sp.maxiter > 0 ? sp.maxiter : 100000;
@@ -531,9 +537,9 @@ int solve_hisq(Lattice& lat, const lq_op_params& opp, const lq_solve_params& sp,
     LQ_CUDA(cudaEventRecord(e0, st));
     Pool pool(lat.vh);
     const int SF = LQ_STAGGERED_FIELD;
-    Field be = pool.get(SF, LQ_F64, nrhs), bo = pool.get(SF, LQ_F64, nrhs), c = pool.get(SF, LQ_F64, nrhs);
-    Field bh = pool.get(SF, LQ_F64, nrhs), xe = pool.get(SF, LQ_F64, nrhs), xo = pool.get(SF, LQ_F64, nrhs);
-    Field te = pool.get(SF, LQ_F64, nrhs), to = pool.get(SF, LQ_F64, nrhs);
+    Field be = pool.get(SF, ph, nrhs), bo = pool.get(SF, ph, nrhs), c = pool.get(SF, ph, nrhs);
+    Field bh = pool.get(SF, ph, nrhs), xe = pool.get(SF, ph, nrhs), xo = pool.get(SF, ph, nrhs);
+    Field te = pool.get(SF, ph, nrhs), to = pool.get(SF, ph, nrhs);
     Scalars sc;
     sc.init(nrhs, lat.vh);
     int ret = LQ_OK;

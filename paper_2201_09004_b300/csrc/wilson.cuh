@@ -351,7 +351,7 @@ __device__ __forceinline__ void hops_pipelined(const WilsonArgs& a, const int c[
 // (clover record or A^{-1} record, the y spinor, and their FP16 norms).
 template <int P, int EPI>
 __host__ __device__ constexpr int epi_smem_per_thread() {
-    return P == P64 ? 0
+    return (P == P64 || P == PDF) ? 0
          : EPI == EPI_AINV ? (int)(sizeof(typename Layout<P, 144>::C) * Layout<P, 144>::NC) + 8
          : EPI == EPI_XPAY ? (int)(sizeof(typename Layout<P, 72>::C) * Layout<P, 72>::NC +
                                    sizeof(typename Layout<P, 24>::C) * Layout<P, 24>::NC) + 8
@@ -399,7 +399,7 @@ __global__ void __launch_bounds__(256) wilson_dslash_kernel(WilsonArgs a) {
 #pragma unroll
                 for (int cc = 0; cc < 3; cc++) acc[b][sp][cc] = mk((T)0, (T)0);
         const T sf = a.dagger ? (T)-1 : (T)1;
-        if constexpr (NB == 1) {
+        if constexpr (NB == 1 && (P == P32 || P == P16)) {
             hops_pipelined<P, R, T>(a, c, s, kb, sf, acc[0]);
         } else {
             hop_dir<0, P, R, NB, T>(a, c, s, kb, sf, acc);

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "liblq.so")
 
 # enums of lq.h
 LQ_OK, LQ_EINVAL, LQ_ENOMEM, LQ_ENOTCONV, LQ_EBREAKDOWN, LQ_ENAN, LQ_EAGAIN, LQ_ETIMEOUT, LQ_ECUDA, LQ_EBUSY = range(10)
-F64, F32, F16 = 0, 1, 2
+F64, F32, F16, F32X2 = 0, 1, 2, 3
 R18, R12 = 18, 12
 THIN, FAT, LONG = 0, 1, 2
 HOST, DEVICE = 0, 1

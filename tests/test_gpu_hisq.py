@@ -31,7 +31,7 @@ DIMS = [(6, 6, 6, 6), (4, 4, 4, 6), (2, 2, 2, 2), (8, 6, 4, 10)]
 
 
 @pytest.mark.parametrize("dims", DIMS)
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 def test_hisq_hopping_term(L, orc, dims, prec):
     lat, V, W = make(L, dims, 41)
     psi = synth.gaussian_field(dims, 42, ncomp=3).numpy()
@@ -47,7 +47,7 @@ def test_hisq_hopping_term(L, orc, dims, prec):
             assert rel_err(got[sel], ref[sel]) < TOL[prec], (dims, prec, dagger, p)
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 def test_hisq_full_and_schur_operator(L, orc, prec):
     dims = (4, 4, 6, 6)
     lat, V, W = make(L, dims, 43)

@@ -38,7 +38,7 @@ DIMS = [(4, 4, 4, 8), (6, 4, 4, 6), (2, 2, 2, 2)]
 
 
 @pytest.mark.parametrize("dims", DIMS)
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 def test_hopping_term_each_parity_and_adjoint(L, orc, dims, prec):
     lat, U = make(L, dims, 11)
     psi = synth.gaussian_field(dims, 12).numpy()
@@ -55,7 +55,7 @@ def test_hopping_term_each_parity_and_adjoint(L, orc, dims, prec):
             assert rel_err(got[sel], ref[sel]) < TOL[prec], (dims, prec, dagger, p)
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 @pytest.mark.parametrize("clover", [False, True])
 def test_full_operator_twisted_clover(L, orc, prec, clover):
     dims = (4, 4, 4, 6)
@@ -108,7 +108,7 @@ def schur_reference(orc, dims, U, C, m, mu, v_even, dagger=False):
     return np.where((mask == 0)[..., None, None], out, 0)
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 def test_schur_operator(L, orc, prec):
     dims = (4, 4, 4, 6)
     lat, U = make(L, dims, 31, c_sw=1.05)
