@@ -271,6 +271,228 @@ def gpu_arm(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------- other workloads
+def _events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def _kernel_table(names, vh, bytes_per_site):
+    from paper_2201_09004_b300 import lib
+    out = {}
+    for name in names:
+        n, tot = lib.profile_query(name)
+        if n:
+            us = tot / n * 1e3
+            out[name] = {"launches": n, "ms": round(tot, 3), "avg_us": round(us, 2)}
+            if name in bytes_per_site:
+                out[name]["gbs"] = round(bytes_per_site[name] * vh / (us * 1e-6) / 1e9, 1)
+    return out
+
+
+def run_multirhs(args):
+    """32^3x96 twisted-mass clover (c_sw 1.04, m 0.04): 12 spin-colour point sources at a
+    seeded site x 3 twisted masses = 36 right-hand sides, solved 12 at a time (one mass
+    per call) through the fused multi-right-hand-side kernels, mixed precision to 1e-10.
+    Compared with the plain FP64 single-right-hand-side solver (timed on one source
+    and scaled to 36)."""
+    import torch
+    from paper_2201_09004_b300 import lib, synth
+    dims, csw, m, mus = (32, 32, 32, 96), 1.04, 0.04, [0.004, 0.008, 0.016]
+    torch.cuda.set_device(0)
+    U = synth.thin_links(dims, 103, device="cuda")
+    lat = lib.Lattice(dims)
+    lat.load_gauge(lib.THIN, U)
+    lat.load_clover(csw)
+    del U
+    site = synth.seeded_site(dims, 303)
+    srcs = [synth.point_source(dims, site, sp, c, device="cuda") for sp in range(4) for c in range(3)]
+    xs = [torch.empty_like(srcs[0]) for _ in srcs]
+    sp = lib.solve_params(solver=lib.MIXED_CGNR, tol=TOL, prec_sloppy=args.prec, recon_sloppy=lib.R12)
+    ops = [lib.op_params(lib.WILSON_TM_CLOVER, m, mu, c_sw=csw) for mu in mus]
+    for op in ops:  # warm-up: clover inverses per mass, tuning of the NB = 4 kernels
+        lat.solve(op, sp, srcs[:4], out=xs[:4])
+    torch.cuda.synchronize()
+    lib.profile_reset()
+    lib.profile_enable(True)
+    e0, e1 = _events()
+    e0.record()
+    infos = []
+    for op in ops:
+        _, inf = lat.solve(op, sp, srcs, out=xs)
+        infos += inf
+    e1.record()
+    torch.cuda.synchronize()
+    lib.profile_enable(False)
+    tts = e0.elapsed_time(e1) * 1e-3
+    vh = int(np.prod(dims)) // 2
+    # bytes per site of one multi-RHS launch with NB = 4 right-hand sides per thread
+    bps = {"wilson_dslash_f16_ainv": 4 * 52 + 8 * 24 + (144 * 2 + 4) + 4 * 52,
+           "wilson_dslash_f16_xpay": 4 * 52 + 8 * 24 + (72 * 2 + 4) + 4 * 52 + 4 * 52}
+    kern = _kernel_table(list(bps) + ["wilson_dslash_f32x2_ainv", "wilson_dslash_f32x2_xpay"], vh, bps)
+    sp64 = lib.solve_params(solver=lib.CGNR, tol=TOL, prec_sloppy=lib.F64)
+    e0, e1 = _events()
+    e0.record()
+    _, i64 = lat.solve(ops[1], sp64, [srcs[0]], out=[xs[0]])
+    e1.record()
+    torch.cuda.synchronize()
+    t64 = e0.elapsed_time(e1) * 1e-3
+    line = {"workload": "multirhs", "metric": "time to solution of 36 right-hand sides at true residual 1e-10",
+            "value": round(tts, 3), "unit": "s", "higher_is_better": False,
+            "config": {"dims": list(dims), "c_sw": csw, "m": m, "mus": mus, "nrhs": 36, "site": list(site),
+                       "sloppy_precision": args.prec, "rhs_per_call": 12},
+            "iters_max": max(i["iters"] for i in infos),
+            "true_rel_residual_max": max(i["true_rel_residual"] for i in infos),
+            "all_converged": all(i["status"] == 0 for i in infos),
+            "fp64_single_rhs": {"seconds_per_solve": round(t64, 3), "iters": i64[0]["iters"],
+                                "seconds_for_36_extrapolated": round(36 * t64, 3)},
+            "speedup_vs_fp64_single_rhs": round(36 * t64 / tts, 2), "kernels": kern}
+    print(json.dumps(line), flush=True)
+
+
+def run_hisq(args):
+    """48^3x144 HISQ (fat + long links), multi-shift CG over m in {0.002, 0.01, 0.02, 0.05},
+    one Z2 source, mixed precision with double-float refinement to 1e-10 for every mass."""
+    import torch
+    from paper_2201_09004_b300 import lib, synth
+    dims, masses = (48, 48, 48, 144), [0.002, 0.01, 0.02, 0.05]
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    lat = lib.Lattice(dims)
+    V = synth.fat_links(dims, 104, device="cuda")
+    lat.load_gauge(lib.FAT, V)
+    del V
+    W = synth.long_links(dims, 105, device="cuda")
+    lat.load_gauge(lib.LONG, W)
+    del W
+    torch.cuda.empty_cache()
+    b = synth.z2_source(dims, 204, ncomp=3, device="cuda")
+    gen_s = time.perf_counter() - t0
+    xs = [torch.empty_like(b) for _ in masses]
+    op = lib.op_params(lib.HISQ, masses[0])
+    sp = lib.solve_params(solver=lib.MULTISHIFT_CG, tol=TOL, prec_sloppy=args.prec, recon_sloppy=lib.R12,
+                          masses=masses)
+    # warm-up on a lattice of the same volume is the solve itself; tune with a short solve
+    lat.solve(op, lib.solve_params(solver=lib.MULTISHIFT_CG, tol=1e-3, prec_sloppy=args.prec,
+                                   recon_sloppy=lib.R12, masses=masses), [b], out=xs, check=False)
+    torch.cuda.synchronize()
+    lib.profile_reset()
+    lib.profile_enable(True)
+    e0, e1 = _events()
+    e0.record()
+    _, info = lat.solve(op, sp, [b], out=xs)
+    e1.record()
+    torch.cuda.synchronize()
+    lib.profile_enable(False)
+    tts = e0.elapsed_time(e1) * 1e-3
+    vh = int(np.prod(dims)) // 2
+    # FP16: fat R18 (36 B), long R12 (24 B), colour vector 12 B + 4 B norm
+    bps = {"hisq_dslash_f16_hop": 16 + 8 * 36 + 8 * 24 + 16, "hisq_dslash_f16_xpay": 16 + 8 * 36 + 8 * 24 + 16 + 16,
+           "hisq_dslash_f32_hop": 24 + 8 * 72 + 8 * 48 + 24, "hisq_dslash_f32_xpay": 24 + 8 * 72 + 8 * 48 + 24 + 24}
+    kern = _kernel_table(list(bps) + ["hisq_dslash_f32x2_hop", "hisq_dslash_f32x2_xpay"], vh, bps)
+    line = {"workload": "hisq", "metric": "time to solution, multi-shift over 4 masses at true residual 1e-10",
+            "value": round(tts, 3), "unit": "s", "higher_is_better": False,
+            "config": {"dims": list(dims), "masses": masses, "c_naik": -1.0 / 24.0, "sloppy_precision": args.prec},
+            "iters": info[0]["iters"], "reliable_updates": info[0]["reliable_updates"],
+            "true_rel_residual_max_over_shifts": info[0]["true_rel_residual"], "status": info[0]["status"],
+            "setup_seconds": round(gen_s, 1), "kernels": kern}
+    print(json.dumps(line), flush=True)
+
+
+def run_serving(args):
+    """Poisson stream of solve requests (sizes 8^3x16, 16^3x32, 24^3x64, 32^3x64; twisted-mass
+    clover with 12 point sources, or HISQ with one Z2 source; masses drawn from [0.005, 0.05];
+    two gauge seeds per size cached on the device) through the continuous-batching server
+    (mixed precision, 4 slots, HBM-budget admission), and the same trace through a FIFO
+    one-at-a-time FP64 server. Rate = 0.8 x the mixed server's measured capacity."""
+    import torch
+    from paper_2201_09004_b300 import lib, synth
+    torch.cuda.set_device(0)
+    sizes = [(8, 8, 8, 16), (16, 16, 16, 32), (24, 24, 24, 64), (32, 32, 32, 64)]
+    rng = np.random.default_rng(505)
+    lats, srcs = {}, {}
+    for si, d in enumerate(sizes):
+        for g in range(2):
+            lat = lib.Lattice(d)
+            lat.load_gauge(lib.THIN, synth.thin_links(d, 600 + 10 * si + g, device="cuda"))
+            lat.load_clover(1.05)
+            lat.load_gauge(lib.FAT, synth.fat_links(d, 700 + 10 * si + g, device="cuda"))
+            lat.load_gauge(lib.LONG, synth.long_links(d, 800 + 10 * si + g, device="cuda"))
+            lats[(si, g)] = lat
+        site = synth.seeded_site(d, 303)
+        srcs[(si, "tmc")] = [synth.point_source(d, site, sp, c).numpy() for sp in range(4) for c in range(3)]
+        srcs[(si, "hisq")] = [synth.z2_source(d, 204, ncomp=3).numpy()]
+    torch.cuda.empty_cache()
+
+    def make_requests(n):
+        reqs = []
+        for _ in range(n):
+            si = int(rng.integers(0, len(sizes)))
+            g = int(rng.integers(0, 2))
+            kind = "tmc" if rng.random() < 0.5 else "hisq"
+            mass = float(rng.uniform(0.005, 0.05))
+            reqs.append((si, g, kind, mass))
+        return reqs
+
+    def params(kind, mass, fp64):
+        if kind == "tmc":
+            op = lib.op_params(lib.WILSON_TM_CLOVER, 0.05, mass, c_sw=1.05)
+        else:
+            op = lib.op_params(lib.HISQ, mass)
+        if fp64:
+            sp = lib.solve_params(solver=lib.CGNR, tol=TOL, prec_sloppy=lib.F64)
+        else:
+            sp = lib.solve_params(solver=lib.MIXED_CGNR, tol=TOL, prec_sloppy=lib.F16, recon_sloppy=lib.R12)
+        return op, sp
+
+    def serve(reqs, arrivals, fp64, slots):
+        srv = lib.Server(200 << 30, slots)
+        t_start = time.perf_counter()
+        tickets = []
+        for (si, g, kind, mass), ta in zip(reqs, arrivals):
+            while time.perf_counter() - t_start < ta:
+                time.sleep(0.0005)
+            op, sp = params(kind, mass, fp64)
+            tickets.append(srv.submit(lats[(si, g)], op, sp, srcs[(si, kind)]))
+        lat_s, statuses = [], []
+        for t in tickets:
+            srv.wait(t, 3600 * 1000)
+            res = srv.poll(t)
+            _, info, times, code = res
+            lat_s.append(times["finished"] - times["submitted"])
+            statuses.append(code)
+        wall = time.perf_counter() - t_start
+        srv.close()
+        return np.array(lat_s), wall, statuses
+
+    # warm-up (tuning, clover inverses) on one request of every (size, kind)
+    warm = [(si, 0, k, 0.02) for si in range(len(sizes)) for k in ("tmc", "hisq")]
+    serve(warm, [0.0] * len(warm), False, 1)
+    serve(warm[:2], [0.0] * 2, True, 1)
+    # capacity of the mixed server: back-to-back service of a calibration batch
+    calib = make_requests(16)
+    _, wall_c, _ = serve(calib, [0.0] * len(calib), False, 4)
+    capacity = len(calib) / wall_c
+    rate = 0.8 * capacity
+    reqs = make_requests(args.requests)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))
+    arrivals -= arrivals[0]
+    lat_mixed, wall_mixed, st_mixed = serve(reqs, arrivals, False, 4)
+    lat_fifo, wall_fifo, st_fifo = serve(reqs, arrivals, True, 1)
+    ms = lambda a, q: round(float(np.percentile(a, q)) * 1e3, 1)
+    line = {"workload": "serving", "metric": "p50/p99 request latency and solves/s on a Poisson trace",
+            "requests": len(reqs), "rate_per_s": round(rate, 3), "capacity_calibration_per_s": round(capacity, 3),
+            "mixed_continuous_batching": {"p50_ms": ms(lat_mixed, 50), "p99_ms": ms(lat_mixed, 99),
+                                          "solves_per_s": round(len(reqs) / wall_mixed, 3),
+                                          "all_ok": all(c == 0 for c in st_mixed), "slots": 4},
+            "fifo_fp64_one_at_a_time": {"p50_ms": ms(lat_fifo, 50), "p99_ms": ms(lat_fifo, 99),
+                                        "solves_per_s": round(len(reqs) / wall_fifo, 3),
+                                        "all_ok": all(c == 0 for c in st_fifo)},
+            "config": {"sizes": [list(d) for d in sizes], "actions": ["wilson_tm_clover 12 rhs", "hisq 1 rhs"],
+                       "mass_range": [0.005, 0.05], "gauge_seeds_per_size": 2, "tol": TOL, "trace_seed": 505}}
+    print(json.dumps(line), flush=True)
+
+
 # ---------------------------------------------------------- oracle (CPU) arm
 def oracle_iterations():
     p = os.path.join(ROOT, "tests", "golden", "oracle_cgnr_24x24x24x64.json")
@@ -345,11 +567,21 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=8)
     ap.add_argument("--ref-iters", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="tmc", choices=["tmc", "multirhs", "hisq", "serving"],
+                    help="tmc: 24^3x64 twisted-mass clover (default, the headline); multirhs: 32^3x96, "
+                         "36 right-hand sides; hisq: 48^3x144 multi-shift; serving: Poisson request stream")
+    ap.add_argument("--requests", type=int, default=100, help="serving: number of requests")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         reference_arm(args)
+    elif args.workload == "multirhs":
+        run_multirhs(args)
+    elif args.workload == "hisq":
+        run_hisq(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         gpu_arm(args)
 

@@ -32,6 +32,7 @@ def main():
            "iterations": info["iters"], "true_rel_residual": info["true_rel_residual"],
            "status": info["status"], "seconds": time.time() - t, "threads": os.cpu_count()}
     path = os.path.join(os.path.dirname(HERE), "tests", "golden", "oracle_cgnr_24x24x24x64.json")
+    os.makedirs(os.path.dirname(path), exist_ok=True)
     with open(path, "w") as f:
         json.dump(out, f, indent=1)
     print(out)

@@ -318,6 +318,8 @@ static void make_precisions(Lattice& lat, void* d64, void* out[3], float** norm,
            out[LQ_F32X2], (float*)nullptr);
 }
 
+static void free_ainv_entry(Lattice& lat, Lattice::Ainv& a);
+
 void free_clover(Lattice& lat) {
     for (int p = 0; p < 4; p++) {
         dev_free(&lat, lat.clovC[p], rec_bytes(p, 72, lat.vh));
@@ -325,10 +327,7 @@ void free_clover(Lattice& lat) {
     }
     dev_free(&lat, lat.clovC_norm, sizeof(float) * 2 * lat.vh);
     lat.clovC_norm = nullptr;
-    for (auto& kv : lat.ainv) {
-        for (int p = 0; p < 4; p++) dev_free(&lat, kv.second.data[p], rec_bytes(p, 144, lat.vh));
-        dev_free(&lat, kv.second.norm, sizeof(float) * 2 * lat.vh);
-    }
+    for (auto& kv : lat.ainv) free_ainv_entry(lat, kv.second);
     lat.ainv.clear();
     lat.has_clover = false;
 }
@@ -357,12 +356,58 @@ void load_clover_canonical(Lattice& lat, const double* canon_dev, cudaStream_t s
     lat.has_clover = true;
 }
 
-void build_ainv(Lattice& lat, double m, double mu, Lattice::Ainv& out, cudaStream_t st) {
+// builds A^{-1} in precision prec only (through a temporary FP64 copy)
+void build_ainv(Lattice& lat, double m, double mu, int prec, Lattice::Ainv& out, cudaStream_t st) {
     void* d64 = dev_alloc(&lat, rec_bytes(LQ_F64, 144, lat.vh));
     dim3 grid((lat.vh + 63) / 64, 2);
     launch("clover_inverse", ainv_kernel, grid, dim3(64), st, (const void*)lat.clovC[LQ_F64], lat.geo, 4.0 + m, mu,
            d64);
-    make_precisions<144>(lat, d64, out.data, &out.norm, st);
+    if (prec == LQ_F64) {
+        out.data[LQ_F64] = d64;
+        return;
+    }
+    dim3 g2((lat.vh + 127) / 128, 2);
+    out.data[prec] = dev_alloc(&lat, rec_bytes(prec, 144, lat.vh));
+    if (prec == LQ_F32)
+        launch("convert_sites", convert_sites_kernel<P32, 144>, g2, dim3(128), st, (const void*)d64, lat.geo,
+               out.data[prec], (float*)nullptr);
+    else if (prec == LQ_F32X2)
+        launch("convert_sites", convert_sites_kernel<PDF, 144>, g2, dim3(128), st, (const void*)d64, lat.geo,
+               out.data[prec], (float*)nullptr);
+    else {
+        if (!out.norm) out.norm = (float*)dev_alloc(&lat, sizeof(float) * 2 * lat.vh);
+        launch("convert_sites", convert_sites_kernel<P16, 144>, g2, dim3(128), st, (const void*)d64, lat.geo,
+               out.data[prec], out.norm);
+    }
+    LQ_CUDA(cudaStreamSynchronize(st));
+    dev_free(&lat, d64, rec_bytes(LQ_F64, 144, lat.vh));
+}
+
+static void free_ainv_entry(Lattice& lat, Lattice::Ainv& a) {
+    for (int p = 0; p < 4; p++) dev_free(&lat, a.data[p], rec_bytes(p, 144, lat.vh));
+    dev_free(&lat, a.norm, sizeof(float) * 2 * lat.vh);
+}
+
+// drop least-recently-used unpinned entries beyond the cache size, never `keep` (lat.mu held)
+static void trim_ainv(Lattice& lat, const std::pair<double, double>* keep) {
+    while (lat.ainv.size() > kAinvCache) {
+        auto victim = lat.ainv.end();
+        for (auto it = lat.ainv.begin(); it != lat.ainv.end(); ++it)
+            if (it->second.pins == 0 && !(keep && it->first == *keep) &&
+                (victim == lat.ainv.end() || it->second.last_use < victim->second.last_use))
+                victim = it;
+        if (victim == lat.ainv.end()) return;
+        free_ainv_entry(lat, victim->second);
+        lat.ainv.erase(victim);
+    }
+}
+
+void pin_ainv(Lattice& lat, double m, double mu, bool pin) {
+    std::lock_guard<std::mutex> lk(lat.mu);
+    auto& e = lat.ainv[std::make_pair(m, mu)];
+    e.last_use = ++lat.ainv_clock;
+    e.pins += pin ? 1 : -1;
+    if (!pin) trim_ainv(lat, nullptr);
 }
 
 const void* clover_block(Lattice& lat, int prec, int parity, const float** norm) {
@@ -375,18 +420,17 @@ const void* clover_block(Lattice& lat, int prec, int parity, const float** norm)
 const void* ainv_block(Lattice& lat, double m, double mu, int prec, int parity, const float** norm, cudaStream_t st) {
     std::lock_guard<std::mutex> lk(lat.mu);
     if (!lat.has_clover) fail(LQ_EINVAL, "clover term not loaded");
-    auto key = std::make_pair(m, mu);
-    auto it = lat.ainv.find(key);
-    if (it == lat.ainv.end()) {
+    const auto key = std::make_pair(m, mu);
+    auto& e = lat.ainv[key];
+    e.last_use = ++lat.ainv_clock;
+    if (!e.data[prec]) {
         if (stream_capturing(st)) fail(LQ_EINVAL, "clover inverse for a new (m, mu) requested during capture");
-        Lattice::Ainv a;
-        build_ainv(lat, m, mu, a, st);
-        LQ_CUDA(cudaStreamSynchronize(st));
-        it = lat.ainv.emplace(key, a).first;
+        build_ainv(lat, m, mu, prec, e, st);
     }
-    size_t per = rec_bytes(prec, 144, lat.vh) / 2;
-    *norm = prec == LQ_F16 ? it->second.norm + (size_t)parity * lat.vh : nullptr;
-    return (const char*)it->second.data[prec] + per * parity;
+    const void* ptr = (const char*)e.data[prec] + rec_bytes(prec, 144, lat.vh) / 2 * parity;
+    *norm = prec == LQ_F16 ? e.norm + (size_t)parity * lat.vh : nullptr;
+    if (lat.ainv.size() > kAinvCache) trim_ainv(lat, &key);
+    return ptr;
 }
 
 }  // namespace lq

@@ -130,10 +130,13 @@ struct Lattice {
     void* clovC[4] = {nullptr, nullptr, nullptr, nullptr};  // clover C per precision, [2][72 reals][vh]
     float* clovC_norm = nullptr;                     // FP16 norms [2][vh]
     struct Ainv {
-        void* data[4] = {nullptr, nullptr, nullptr, nullptr};
+        void* data[4] = {nullptr, nullptr, nullptr, nullptr};  // per precision, built on first use
         float* norm = nullptr;
+        int pins = 0;           // solves currently using this entry
+        uint64_t last_use = 0;  // for least-recently-used eviction
     };
-    std::map<std::pair<double, double>, Ainv> ainv;  // (m, mu) -> A^{-1} per precision
+    std::map<std::pair<double, double>, Ainv> ainv;  // (m, mu) -> A^{-1}, at most kAinvCache unpinned
+    uint64_t ainv_clock = 0;
     size_t bytes = 0;                                // device bytes held
     std::mutex mu;  // guards the lazily filled caches when several streams share the lattice
 };
@@ -143,6 +146,9 @@ GaugeV gauge_view(Lattice& lat, int kind, int prec, int recon);
 const void* clover_block(Lattice& lat, int prec, int parity, const float** norm);
 const void* ainv_block(Lattice& lat, double m, double mu, int prec, int parity, const float** norm, cudaStream_t st);
 void free_clover(Lattice& lat);
+// keep the clover inverse of (m, mu) resident while a solve runs
+void pin_ainv(Lattice& lat, double m, double mu, bool pin);
+enum { kAinvCache = 8 };
 
 void* dev_alloc(Lattice* lat, size_t bytes);
 void dev_free(Lattice* lat, void* p, size_t bytes);
@@ -157,7 +163,7 @@ void gauge_maxabs(const double* canon, int V, float* out, cudaStream_t st);
 // ------------------------------------------------------------------ clover
 void build_clover(Lattice& lat, double c_sw, cudaStream_t st);
 void load_clover_canonical(Lattice& lat, const double* canon_dev, cudaStream_t st);
-void build_ainv(Lattice& lat, double m, double mu, Lattice::Ainv& out, cudaStream_t st);
+void build_ainv(Lattice& lat, double m, double mu, int prec, Lattice::Ainv& out, cudaStream_t st);
 
 // ------------------------------------------------------------------ dslash
 struct OpDesc {

@@ -79,6 +79,9 @@ size_t solve_workspace_bytes(const Lattice& lat, const lq_op_params& op, const l
         b = 8 * f64 + 3 * f64 + fx + 4 * fs;
         if (ns > 1) b += (size_t)(3 + 2 * ns) * field_bytes(kind, ps, 2 * nrhs, lat.vh);
     }
+    // a twisted-clover request may need a new clover inverse (sloppy + double-float
+    // copies, and a temporary FP64 one while it is built)
+    if (op.action == LQ_WILSON_TM_CLOVER) b += (size_t)144 * 2 * lat.vh * (prec_bytes(ps) + 8 + 8);
     return b + canon + (16u << 20);
 }
 

@@ -211,6 +211,12 @@ int solve_wilson(Lattice& lat, const lq_op_params& opp, const lq_solve_params& s
     if (ps == LQ_F64) delta = 0.0;
     const int maxiter = sp.maxiter > 0 ? sp.maxiter : 100000;
 
+    // the clover inverse of this (m, mu) stays resident for the whole solve
+    struct Pin {
+        Lattice& l; double m, mu; bool on;
+        Pin(Lattice& l_, double m_, double mu_, bool on_) : l(l_), m(m_), mu(mu_), on(on_) { if (on) pin_ainv(l, m, mu, true); }
+        ~Pin() { if (on) pin_ainv(l, m, mu, false); }
+    } pin(lat, opp.m, opp.mu, opp.action == LQ_WILSON_TM_CLOVER);
     cudaEvent_t e0, e1;
     LQ_CUDA(cudaEventCreate(&e0));
     LQ_CUDA(cudaEventCreate(&e1));

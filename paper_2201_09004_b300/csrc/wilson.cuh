@@ -253,6 +253,137 @@ __device__ __forceinline__ void reduce_norms(const double nrm[NB], double* norm_
 }
 
 // ---------------------------------------------------------------------------
+// Compact hop loop for the double-float precision: one copy of the hop body
+// runs for all eight hops (no unrolling), with the spin projection driven by a
+// small table, because the fully unrolled double-float code does not fit in the
+// instruction cache. (1 +- g_mu) in the DeGrand-Rossi basis couples spin 0 with
+// spin a and spin 1 with spin b through a unit coefficient (+-1 or +-i), and the
+// lower spins are rebuilt from the rotated half spinor the same way.
+
+// v * (sgn * (i if isi else 1))
+template <typename T>
+__device__ __forceinline__ cx<T> cunit(cx<T> v, bool neg, bool isi) {
+    cx<T> w = isi ? mk(-v.i, v.r) : v;
+    return neg ? mk(-w.r, -w.i) : w;
+}
+
+template <int P, int R, typename T>
+__device__ void hop_compact(const WilsonArgs& a, const int c[4], int s, int k0, int h, T sf, cx<T> acc[4][3]) {
+    const int mu = h >> 1;
+    const bool fwd = (h & 1) == 0;
+    float bs;
+    const int n = cb_hop(a.g, c, mu, fwd ? 1 : -1, bs);
+    cx<T> U[3][3];
+    load_link<P, R, T>(a.U, fwd ? a.parity : 1 - a.parity, mu, fwd ? s : n, U);
+    T v[24];
+    fload<P, 24, T>(a.in, k0, n, v);
+    cx<T> ps[4][3];
+    to_spinor(v, ps);
+    // projector (1 + sp g_mu): sp = sf forward, -sf backward; `neg` flips the sign of sp
+    const bool neg_sp = fwd ? (a.dagger != 0) : (a.dagger == 0);
+    (void)sf;
+    // table per mu: spin a / b coupled to 0 / 1, coefficients c0, c1 (as sign, is-i),
+    // and the rebuild of spins 2 and 3 from (r0, r1)
+    const int ia = (mu < 2) ? 3 : 2, ib = (mu < 2) ? 2 : 3;
+    const bool c0i = (mu == 0 || mu == 2), c1i = c0i;
+    const bool c0n = (mu == 1), c1n = (mu == 2);
+    cx<T> h0[3], h1[3], r0[3], r1[3];
+#pragma unroll
+    for (int q = 0; q < 3; q++) {
+        const cx<T> pa = ia == 3 ? ps[3][q] : ps[2][q];
+        const cx<T> pb = ib == 3 ? ps[3][q] : ps[2][q];
+        h0[q] = ps[0][q] + cunit(pa, c0n != neg_sp, c0i);
+        h1[q] = ps[1][q] + cunit(pb, c1n != neg_sp, c1i);
+    }
+    if (fwd) {
+        su3_mv(U, h0, r0);
+        su3_mv(U, h1, r1);
+    } else {
+        su3_dmv(U, h0, r0);
+        su3_dmv(U, h1, r1);
+    }
+    const bool flip = bs < 0.f;  // time boundary
+    // spin 2 gets e2 * r_{j2}, spin 3 gets e3 * r_{j3}:
+    //   mu0: -i r1, -i r0;  mu1: +r1, -r0;  mu2: -i r0, +i r1;  mu3: +r0, +r1  (times sp)
+    const bool j2is1 = mu < 2, j3is1 = mu >= 2;
+    const bool e2i = (mu == 0 || mu == 2), e3i = e2i;
+    const bool e2n = (mu == 0 || mu == 2), e3n = (mu == 0 || mu == 1);
+#pragma unroll
+    for (int q = 0; q < 3; q++) {
+        cx<T> a0 = flip ? mk(-r0[q].r, -r0[q].i) : r0[q];
+        cx<T> a1 = flip ? mk(-r1[q].r, -r1[q].i) : r1[q];
+        acc[0][q] = acc[0][q] + a0;
+        acc[1][q] = acc[1][q] + a1;
+        acc[2][q] = acc[2][q] + cunit(j2is1 ? a1 : a0, e2n != neg_sp, e2i);
+        acc[3][q] = acc[3][q] + cunit(j3is1 ? a1 : a0, e3n != neg_sp, e3i);
+    }
+}
+
+// Compact site-local epilogues for double-float (one right-hand side): a loop
+// over the twelve output rows with only the six-term row product unrolled.
+template <typename T>
+__device__ __forceinline__ cx<T> wsel(cx<T> w[4][3], int bl, int j) {
+    return bl ? blk(w, 1, j) : blk(w, 0, j);
+}
+
+// out = A^{-1} w (dagger: (A^{-1})^+ w); A^{-1}: 36 complex per block, row-major
+template <int P, typename T>
+__device__ void ainv_apply_rows(const WilsonArgs& a, int s, cx<T> w[4][3], cx<T> out[4][3]) {
+    typedef Layout<P, 144> Lay;
+    static_assert(Lay::RPC == 2, "one complex entry per chunk");
+    const typename Lay::C* base = (const typename Lay::C*)a.clov;
+    cx<T> o[12];
+#pragma unroll 1
+    for (int r = 0; r < 12; r++) {
+        const int bl = r / 6, i = r - 6 * bl;
+        cx<T> acc = mk((T)0, (T)0);
+#pragma unroll
+        for (int j = 0; j < 6; j++) {
+            const int e = a.dagger ? bl * 36 + j * 6 + i : bl * 36 + i * 6 + j;
+            T m[2];
+            unpack_chunk<P, 144, T>(__ldg(&base[(size_t)e * a.g.vh + s]), 1.f, m);
+            const cx<T> me = mk(m[0], m[1]);
+            if (a.dagger) cjmac(acc, me, wsel(w, bl, j));
+            else cmac(acc, me, wsel(w, bl, j));
+        }
+        o[r] = acc;
+    }
+#pragma unroll
+    for (int r = 0; r < 12; r++) blk(out, r / 6, r % 6) = o[r];
+}
+
+// out += C w; C per block: 6 real diagonal entries then 15 upper entries (row-major, i<j)
+template <int P, typename T>
+__device__ void clover_apply_rows(const WilsonArgs& a, int s, cx<T> w[4][3], cx<T> out[4][3]) {
+    typedef Layout<P, 72> Lay;
+    static_assert(Lay::RPC == 2, "two reals per chunk");
+    const typename Lay::C* base = (const typename Lay::C*)a.clov;
+    cx<T> o[12];
+#pragma unroll 1
+    for (int r = 0; r < 12; r++) {
+        const int bl = r / 6, i = r - 6 * bl;
+        T d[2];
+        unpack_chunk<P, 72, T>(__ldg(&base[(size_t)(18 * bl + i / 2) * a.g.vh + s]), 1.f, d);
+        const T di = (i & 1) ? d[1] : d[0];
+        cx<T> acc = di * wsel(w, bl, i);
+#pragma unroll
+        for (int j = 0; j < 6; j++) {
+            if (j == i) continue;
+            const int lo = j < i ? j : i, hi = j < i ? i : j;
+            const int q = lo * 5 - lo * (lo - 1) / 2 + (hi - lo - 1);
+            T m[2];
+            unpack_chunk<P, 72, T>(__ldg(&base[(size_t)(18 * bl + 3 + q) * a.g.vh + s]), 1.f, m);
+            const cx<T> me = mk(m[0], m[1]);
+            if (i < j) cmac(acc, me, wsel(w, bl, j));
+            else cjmac(acc, me, wsel(w, bl, j));
+        }
+        o[r] = acc;
+    }
+#pragma unroll
+    for (int r = 0; r < 12; r++) blk(out, r / 6, r % 6) = blk(out, r / 6, r % 6) + o[r];
+}
+
+// ---------------------------------------------------------------------------
 // Single right-hand side: the eight hops are software-pipelined. The raw
 // (still encoded) spinor and link chunks of hop h+1 are loaded before hop h is
 // decoded and computed, so every thread keeps one hop of gathers in flight
@@ -401,6 +532,9 @@ __global__ void __launch_bounds__(256) wilson_dslash_kernel(WilsonArgs a) {
         const T sf = a.dagger ? (T)-1 : (T)1;
         if constexpr (NB == 1 && (P == P32 || P == P16)) {
             hops_pipelined<P, R, T>(a, c, s, kb, sf, acc[0]);
+        } else if constexpr (P == PDF) {
+#pragma unroll 1
+            for (int h = 0; h < 8; h++) hop_compact<P, R, T>(a, c, s, kb, h, sf, acc[0]);
         } else {
             hop_dir<0, P, R, NB, T>(a, c, s, kb, sf, acc);
             hop_dir<1, P, R, NB, T>(a, c, s, kb, sf, acc);
@@ -434,6 +568,8 @@ __global__ void __launch_bounds__(256) wilson_dslash_kernel(WilsonArgs a) {
                 if constexpr (PF)
                     ainv_apply_src<P, NB, T, true>(sm_rec, blockDim.x, threadIdx.x,
                                                    P == P16 ? sm_norm[threadIdx.x] : 1.f, a.dagger, acc, res);
+                else if constexpr (P == PDF && NB == 1)
+                    ainv_apply_rows<P, T>(a, s, acc[0], res[0]);
                 else
                     ainv_apply<P, NB, T>(a, s, acc, res);
             } else {
@@ -483,6 +619,8 @@ __global__ void __launch_bounds__(256) wilson_dslash_kernel(WilsonArgs a) {
                 if constexpr (PF)
                     clover_apply_src<P, NB, T, true>(sm_rec, blockDim.x, threadIdx.x,
                                                      P == P16 ? sm_norm[threadIdx.x] : 1.f, yv, res);
+                else if constexpr (P == PDF && NB == 1)
+                    clover_apply_rows<P, T>(a, s, yv[0], res[0]);
                 else
                     clover_apply<P, NB, T>(a, s, yv, res);
             }
@@ -527,7 +665,8 @@ __global__ void __launch_bounds__(256) wilson_ainv_site_kernel(WilsonArgs a) {
         for (int sp = 0; sp < 4; sp++)
 #pragma unroll
             for (int cc = 0; cc < 3; cc++) res[0][sp][cc] = mk((T)0, (T)0);
-        ainv_apply<P, 1, T>(a, s, w, res);
+        if constexpr (P == PDF) ainv_apply_rows<P, T>(a, s, w[0], res[0]);
+        else ainv_apply<P, 1, T>(a, s, w, res);
     } else {
         const T m4 = (T)a.m4, mu = (T)a.mu;
         const T inv = (T)1 / (m4 * m4 + mu * mu);
