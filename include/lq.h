@@ -283,6 +283,9 @@ int lq_submit(lq_server s, const lq_request* req, const double* const* rhs, uint
 int lq_poll(lq_server s, uint64_t ticket, double* const* x, lq_solve_info* info, lq_request_times* times);
 /* blocks up to timeout_ms for the ticket to finish; LQ_ETIMEOUT otherwise */
 int lq_wait(lq_server s, uint64_t ticket, int timeout_ms);
+/* device bytes the server reserves for this request while it runs (its solver
+ * work fields and staging, not counting the resident lattice) */
+int lq_request_bytes(const lq_request* req, size_t* bytes);
 /* requests queued, running, and device bytes currently reserved by running requests */
 int lq_server_stats(lq_server s, int* queued, int* running, size_t* reserved_bytes);
 

@@ -8,27 +8,35 @@
 
 namespace lq {
 
-static int pick_nb(int nrhs) {
+// right-hand sides per site group, spread over consecutive threads
+static int pick_rg(int nrhs) {
     if (nrhs >= 4) return 4;
     if (nrhs >= 2) return 2;
     return 1;
 }
 
+// site blocks of a launch with `block` threads and rg threads per site
+static int site_blocks(int vh, int block, int rg) {
+    const int spb = block / rg;
+    return (vh + spb - 1) / spb;
+}
+
 // ------------------------------------------------------------------ Wilson
-template <int P, int R, int EPI, int NB>
+template <int P, int R, int EPI, int RG>
 static void wl(const char* name, WilsonArgs a, int block, cudaStream_t st) {
-    dim3 grid((a.g.vh + block - 1) / block, (a.nrhs + NB - 1) / NB);
-    const size_t smem = NB == 1 ? (size_t)epi_smem_per_thread<P, EPI>() * block : 0;
-    launch_smem(name, wilson_dslash_kernel<P, R, EPI, NB>, grid, dim3(block), smem, st, a);
+    const int ngroups = (a.nrhs + RG - 1) / RG;
+    dim3 grid(site_blocks(a.g.vh, block, RG) * ngroups);
+    const size_t smem = RG == 1 ? (size_t)epi_smem_per_thread<P, EPI>() * block : 0;
+    launch_smem(name, wilson_dslash_kernel<P, R, EPI, 1, RG>, grid, dim3(block), smem, st, a);
 }
 
 template <int P, int R, int EPI>
-static void wl_nb(const char* name, WilsonArgs a, int nb, int block, cudaStream_t st) {
+static void wl_nb(const char* name, WilsonArgs a, int rg, int block, cudaStream_t st) {
     if constexpr (P == P64 || P == PDF) {
         wl<P, R, EPI, 1>(name, a, block, st);
     } else {
-        if (nb == 4) wl<P, R, EPI, 4>(name, a, block, st);
-        else if (nb == 2) wl<P, R, EPI, 2>(name, a, block, st);
+        if (rg == 4) wl<P, R, EPI, 4>(name, a, block, st);
+        else if (rg == 2) wl<P, R, EPI, 2>(name, a, block, st);
         else wl<P, R, EPI, 1>(name, a, block, st);
     }
 }
@@ -73,7 +81,7 @@ int wilson_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int ep
         if (epi == EPI_XPAY) a.clov = clover_block(lat, op.prec, parity, &a.clov_norm);
         else if (epi == EPI_AINV) a.clov = ainv_block(lat, op.m, op.mu, op.prec, parity, &a.clov_norm, st);
     }
-    const int nb = pick_nb(a.nrhs);
+    const int nb = (op.prec == LQ_F32 || op.prec == LQ_F16) ? pick_rg(a.nrhs) : 1;
     const char* name = wname(op.prec, epi);
     auto run = [&](int block) {
         if (op.prec == LQ_F64) {
@@ -94,7 +102,7 @@ int wilson_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int ep
                       std::to_string(norm_out != nullptr);
     int block = tuned_block(key, st, run);
     run(block);
-    return (lat.vh + block - 1) / block;
+    return site_blocks(lat.vh, block, nb);
 }
 
 void wilson_ainv_site(Lattice& lat, const OpDesc& op, int parity, int dagger, const Field& in, Field& out,
@@ -124,19 +132,20 @@ void wilson_ainv_site(Lattice& lat, const OpDesc& op, int parity, int dagger, co
 }
 
 // ------------------------------------------------------------------- HISQ
-template <int P, int RL, int EPI, int NB>
+template <int P, int RL, int EPI, int RG>
 static void hl(const char* name, HisqArgs a, int block, cudaStream_t st) {
-    dim3 grid((a.g.vh + block - 1) / block, (a.nrhs + NB - 1) / NB);
-    launch(name, hisq_dslash_kernel<P, RL, EPI, NB>, grid, dim3(block), st, a);
+    const int ngroups = (a.nrhs + RG - 1) / RG;
+    dim3 grid(site_blocks(a.g.vh, block, RG) * ngroups);
+    launch(name, hisq_dslash_kernel<P, RL, EPI, 1, RG>, grid, dim3(block), st, a);
 }
 
 template <int P, int RL, int EPI>
-static void hl_nb(const char* name, HisqArgs a, int nb, int block, cudaStream_t st) {
+static void hl_nb(const char* name, HisqArgs a, int rg, int block, cudaStream_t st) {
     if constexpr (P == P64 || P == PDF) {
         hl<P, RL, EPI, 1>(name, a, block, st);
     } else {
-        if (nb == 4) hl<P, RL, EPI, 4>(name, a, block, st);
-        else if (nb == 2) hl<P, RL, EPI, 2>(name, a, block, st);
+        if (rg == 4) hl<P, RL, EPI, 4>(name, a, block, st);
+        else if (rg == 2) hl<P, RL, EPI, 2>(name, a, block, st);
         else hl<P, RL, EPI, 1>(name, a, block, st);
     }
 }
@@ -173,7 +182,7 @@ int hisq_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int epi,
     a.a = aa;
     a.nrhs = in.nrhs;
     a.norm_out = norm_out;
-    const int nb = pick_nb(a.nrhs);
+    const int nb = (op.prec == LQ_F32 || op.prec == LQ_F16) ? pick_rg(a.nrhs) : 1;
     const char* name = hname(op.prec, epi);
     auto run = [&](int block) {
         if (op.prec == LQ_F64) {
@@ -193,7 +202,7 @@ int hisq_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int epi,
                       std::to_string(lat.vh) + "/n" + std::to_string(norm_out != nullptr);
     int block = tuned_block(key, st, run);
     run(block);
-    return (lat.vh + block - 1) / block;
+    return site_blocks(lat.vh, block, nb);
 }
 
 }  // namespace lq

@@ -79,15 +79,20 @@ __device__ __forceinline__ void stag_dir(const HisqArgs& a, const int c[4], int 
     stag_hop<MU, 3, P, RL, NB, T>(a, a.lng, c, s, kb, eta * cn, acc);
 }
 
-template <int P, int RL, int EPI, int NB>
+// thread / block mapping as in wilson_dslash_kernel (RG threads per site)
+template <int P, int RL, int EPI, int NB, int RG = 1>
 __global__ void __launch_bounds__(256) hisq_dslash_kernel(HisqArgs a) {
     typedef typename RealT<P>::T T;
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    const int kb = blockIdx.y * NB;
+    const int spb = blockDim.x / RG;
+    const int ngroups = (a.nrhs + RG * NB - 1) / (RG * NB);
+    const int sb = blockIdx.x / ngroups, grp = blockIdx.x - sb * ngroups;
+    const int nsb = gridDim.x / ngroups;
+    const int s = sb * spb + threadIdx.x / RG;
+    const int kb = (grp * RG + threadIdx.x % RG) * NB;
     double nrm[NB];
 #pragma unroll
     for (int b = 0; b < NB; b++) nrm[b] = 0.0;
-    if (s < a.g.vh) {
+    if (s < a.g.vh && kb < a.nrhs) {
         int c[4];
         cb_coords(a.g, s, a.parity, c);
         cx<T> acc[NB][3];
@@ -127,7 +132,7 @@ __global__ void __launch_bounds__(256) hisq_dslash_kernel(HisqArgs a) {
             fstore<P, 6, T>(a.out, kb + b, s, v);
         }
     }
-    if (a.norm_out) reduce_norms<NB>(nrm, a.norm_out, kb, a.nrhs);
+    if (a.norm_out) reduce_norms_rg<NB, RG>(nrm, a.norm_out, grp, sb, nsb, a.nrhs);
 }
 
 }  // namespace lq

@@ -278,6 +278,14 @@ extern "C" int lq_wait(lq_server s, uint64_t ticket, int timeout_ms) {
     LQ_CATCH
 }
 
+extern "C" int lq_request_bytes(const lq_request* req, size_t* bytes) {
+    LQ_TRY
+    if (!req || !req->lat || !bytes) fail(LQ_EINVAL, "null argument");
+    *bytes = solve_workspace_bytes(req->lat->lat, req->op, req->solve, req->nrhs);
+    return LQ_OK;
+    LQ_CATCH
+}
+
 extern "C" int lq_server_stats(lq_server s, int* queued, int* running, size_t* reserved_bytes) {
     LQ_TRY
     if (!s) fail(LQ_EINVAL, "null server");

@@ -31,7 +31,8 @@ struct Scalars {
     int nrhs = 0;
     void init(int n, int vh) {
         nrhs = n;
-        size_t per = std::max<size_t>((size_t)(vh + 63) / 64, (size_t)RED_BLOCKS);
+        // hopping kernels write one partial per site block: at least 8 sites per block
+        size_t per = std::max<size_t>((size_t)(vh + 7) / 8, (size_t)RED_BLOCKS);
         LQ_CUDA(cudaMalloc(&dev, sizeof(double) * SC_N * n));
         LQ_CUDA(cudaMemset(dev, 0, sizeof(double) * SC_N * n));
         LQ_CUDA(cudaMalloc(&part, sizeof(double) * per * n));

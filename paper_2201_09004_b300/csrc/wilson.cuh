@@ -252,6 +252,37 @@ __device__ __forceinline__ void reduce_norms(const double nrm[NB], double* norm_
     }
 }
 
+// Block reduction when RG consecutive threads share a site, one right-hand side
+// each (NB = 1), or one thread carries NB right-hand sides (RG = 1). The
+// per-block partial of right-hand side k goes to norm_out[k * nsb + sb], sb the
+// site block and nsb the number of site blocks.
+template <int NB, int RG>
+__device__ __forceinline__ void reduce_norms_rg(const double nrm[NB], double* norm_out, int grp, int sb, int nsb,
+                                                int nrhs) {
+    static_assert(NB == 1 || RG == 1, "right-hand sides are spread over threads or registers, not both");
+    __shared__ double red[NB * RG][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int b = 0; b < NB; b++) {
+        double v = nrm[b];
+#pragma unroll
+        for (int o = 16; o >= RG; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane < RG) red[b * RG + lane][wid] = v;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+#pragma unroll
+        for (int q = 0; q < NB * RG; q++) {
+            double v = lane < nw ? red[q][lane] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            const int k = (grp * RG + (q % RG)) * NB + q / RG;
+            if (lane == 0 && k < nrhs) norm_out[(size_t)k * nsb + sb] = v;
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Compact hop loop for the double-float precision: one copy of the hop body
 // runs for all eight hops (no unrolling), with the spin projection driven by a
@@ -489,16 +520,25 @@ __host__ __device__ constexpr int epi_smem_per_thread() {
          : 0;
 }
 
-template <int P, int R, int EPI, int NB>
+// Grid: blocks are ordered site block major, right-hand-side group minor, so that
+// the groups of one site block run together and share links and clover records
+// through L2. Within a block, RG consecutive threads take one site and one
+// right-hand side each (their link and clover loads are the same addresses and
+// are served once); NB > 1 keeps NB right-hand sides in one thread's registers.
+template <int P, int R, int EPI, int NB, int RG = 1>
 __global__ void __launch_bounds__(256) wilson_dslash_kernel(WilsonArgs a) {
     typedef typename RealT<P>::T T;
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    const int kb = blockIdx.y * NB;
+    const int spb = blockDim.x / RG;                       // sites per block
+    const int ngroups = (a.nrhs + RG * NB - 1) / (RG * NB);
+    const int sb = blockIdx.x / ngroups, grp = blockIdx.x - sb * ngroups;
+    const int nsb = gridDim.x / ngroups;
+    const int s = sb * spb + threadIdx.x / RG;
+    const int kb = (grp * RG + threadIdx.x % RG) * NB;
     double nrm[NB];
 #pragma unroll
     for (int b = 0; b < NB; b++) nrm[b] = 0.0;
     // shared-memory copies of the epilogue operands (single right-hand side, FP32/FP16)
-    constexpr bool PF = (NB == 1) && (epi_smem_per_thread<P, EPI>() > 0);
+    constexpr bool PF = (NB == 1) && (RG == 1) && (epi_smem_per_thread<P, EPI>() > 0);
     extern __shared__ __align__(16) unsigned char lq_smem[];
     typedef typename Layout<P, 144>::C CA;
     typedef typename Layout<P, 72>::C CC;
@@ -506,7 +546,7 @@ __global__ void __launch_bounds__(256) wilson_dslash_kernel(WilsonArgs a) {
     unsigned char* sm_rec = lq_smem;  // clover / inverse record, chunk-major
     unsigned char* sm_y = lq_smem + (EPI == EPI_AINV ? sizeof(CA) * Layout<P, 144>::NC : sizeof(CC) * Layout<P, 72>::NC) * blockDim.x;
     float* sm_norm = (float*)(sm_y + (EPI == EPI_XPAY ? sizeof(CY) * Layout<P, 24>::NC * blockDim.x : 0));
-    if (s < a.g.vh) {
+    if (s < a.g.vh && kb < a.nrhs) {
         int c[4];
         cb_coords(a.g, s, a.parity, c);
         if constexpr (PF) {
@@ -646,7 +686,7 @@ __global__ void __launch_bounds__(256) wilson_dslash_kernel(WilsonArgs a) {
             fstore<P, 24, T>(a.out, kb + b, s, v);
         }
     }
-    if (a.norm_out) reduce_norms<NB>(nrm, a.norm_out, kb, a.nrhs);
+    if (a.norm_out) reduce_norms_rg<NB, RG>(nrm, a.norm_out, grp, sb, nsb, a.nrhs);
 }
 
 // site-local out = A^{-1} in (dagger: (A^{-1})^+ in) on fields of parity a.parity

@@ -39,7 +39,7 @@ EXPORTS = [
     "lq_load_clover", "lq_dslash_apply", "lq_operator_apply", "lq_solve", "lq_field_create",
     "lq_field_destroy", "lq_field_import", "lq_field_export", "lq_dslash_field", "lq_schur_field",
     "lq_profile_enable", "lq_profile_reset", "lq_profile_query", "lq_launch_count", "lq_server_create",
-    "lq_server_destroy", "lq_submit", "lq_poll", "lq_wait", "lq_server_stats", "lq_dslash_apply_noalloc",
+    "lq_server_destroy", "lq_submit", "lq_poll", "lq_wait", "lq_server_stats", "lq_dslash_apply_noalloc", "lq_request_bytes",
 ]
 
 
@@ -346,8 +346,17 @@ class Server:
         self._pending[t.value] = (nsol, rhs[0].shape, len(rhs))
         return t.value
 
+    def request_bytes(self, lat: Lattice, op, params, nrhs):
+        """Device bytes the server reserves for such a request while it runs."""
+        req = Request(lat.h.value, op, params, int(nrhs))
+        b = ctypes.c_size_t()
+        _check(lib().lq_request_bytes(ctypes.byref(req), ctypes.byref(b)))
+        return b.value
+
     def poll(self, ticket):
         """None while running; then (x list, info list, times dict, status)."""
+        if ticket not in self._pending:
+            _check(lib().lq_poll(self.h, ctypes.c_uint64(ticket), None, None, None))
         nsol, shape, nrhs = self._pending[ticket]
         xs = [np.empty(shape, dtype=np.complex128) for _ in range(nsol)]
         xp = (ctypes.c_void_p * nsol)(*[x.ctypes.data for x in xs])

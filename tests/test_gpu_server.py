@@ -99,7 +99,10 @@ def test_budget_admission_and_rejection(L, world):
     assert e.value.code == L.LQ_ENOMEM
     srv.close()
     # a budget that fits one request at a time serialises admissions
-    srv = L.Server(lat.device_bytes() + (200 << 20), 4)
+    probe = L.Server(1 << 40, 1)
+    need = probe.request_bytes(lat, op, sp, len(rhs))
+    probe.close()
+    srv = L.Server(lat.device_bytes() + int(1.5 * need), 4)
     ts = [srv.submit(lat, op, sp, rhs) for _ in range(3)]
     ends = []
     for t in ts:
