@@ -209,6 +209,15 @@ def gpu_arm(args):
                 "share_of_kernel_time": round(tot / all_t, 4), "traffic": NCU_TRAFFIC.get(dom)}
     per_kernel = {k: {"launches": v[0], "ms": round(v[1], 3),
                       "gbs": round(BYTES_PER_SITE[k] * vh / (v[1] / v[0] * 1e-3) / 1e9, 1)} for k, v in kernels.items()}
+    # device time per solve of every kernel family in the timed region
+    breakdown = {}
+    for name in ["wilson_dslash_f16", "wilson_dslash_f32x2", "wilson_dslash_f32_", "wilson_ainv_site", "blas_cg_xs",
+                 "blas_cg_p", "blas_finalize", "blas_norm2", "blas_copy", "blas_axpy", "blas_xmy_norm", "blas_zero",
+                 "import_field", "export_field"]:
+        n_, t_ = lib.profile_query(name)
+        if n_:
+            breakdown[name] = {"launches_per_solve": round(n_ / args.steps, 1), "ms_per_solve": round(t_ / args.steps, 3)}
+    breakdown["all_kernels_ms_per_solve"] = round(all_t / args.steps, 3)
 
     # plain FP64 CGNR on the same system (the comparator of the mixed solver)
     sp64 = lib.solve_params(solver=lib.CGNR, tol=TOL, prec_sloppy=lib.F64)
@@ -260,7 +269,7 @@ def gpu_arm(args):
             "true_rel_residual_max": res,
             "latency_ms": {"p50": round(float(np.percentile(lat_ms, 50)), 3),
                            "p99": round(float(np.percentile(lat_ms, 99)), 3)},
-            "roofline": roofline, "kernels": per_kernel, "fp64": fp64, "e2e": e2e,
+            "roofline": roofline, "kernels": per_kernel, "time_breakdown": breakdown, "fp64": fp64, "e2e": e2e,
             "gpu_launches": int(launches), "clocks": clocks,
         }
         if not args.no_cpu_baseline:

@@ -26,7 +26,7 @@ template <int P, int R, int EPI, int RG>
 static void wl(const char* name, WilsonArgs a, int block, cudaStream_t st) {
     const int ngroups = (a.nrhs + RG - 1) / RG;
     dim3 grid(site_blocks(a.g.vh, block, RG) * ngroups);
-    const size_t smem = RG == 1 ? (size_t)epi_smem_per_thread<P, EPI>() * block : 0;
+    const size_t smem = epi_smem_bytes<P, EPI>(block, RG);
     launch_smem(name, wilson_dslash_kernel<P, R, EPI, 1, RG>, grid, dim3(block), smem, st, a);
 }
 

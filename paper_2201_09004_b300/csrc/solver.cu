@@ -145,7 +145,23 @@ static CgResult cgnr_mixed(Lattice& lat, const OpDesc& ops, const OpDesc& op64, 
             if (!done[k]) return false;
         return true;
     };
-    int it = 0;
+    // The host reads the residual norms of iteration i while iteration i+1 runs:
+    // each iteration ends with an asynchronous copy of the scalars into one of
+    // two pinned slots and an event, and the host waits on the previous one.
+    // A reliable update or convergence is therefore decided one iteration late,
+    // which costs at most one extra iteration and keeps the GPU busy.
+    double* ring = nullptr;
+    LQ_CUDA(cudaMallocHost(&ring, sizeof(double) * SC_N * n * 2));
+    cudaEvent_t ev[2];
+    LQ_CUDA(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+    LQ_CUDA(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+    struct Cleanup {
+        double* r; cudaEvent_t* e;
+        ~Cleanup() { cudaFreeHost(r); cudaEventDestroy(e[0]); cudaEventDestroy(e[1]); }
+    } cleanup{ring, ev};
+    auto slot = [&](int i) { return ring + (size_t)(i & 1) * SC_N * n; };
+    int it = 0, pending = -1;  // iteration whose scalars are in flight
+    std::vector<char> counted(n, 0);
     while (!all_done() && it < maxiter) {
         nb = schur_wilson(lat, ops, 0, p, q, t, sc.part, st);
         blas_finalize(sc.part, nb, n, sc.dev, 0, FIN_ALPHA, st);
@@ -154,18 +170,29 @@ static CgResult cgnr_mixed(Lattice& lat, const OpDesc& ops, const OpDesc& op64, 
         nb = schur_wilson(lat, ops, 1, s_lo, r, t, sc.part, st);
         blas_finalize(sc.part, nb, n, sc.dev, 0, FIN_BETA, st);
         blas_cg_p(p, r, sc.dev, st);
+        LQ_CUDA(cudaMemcpyAsync(slot(it), sc.dev, sizeof(double) * SC_N * n, cudaMemcpyDeviceToHost, st));
+        LQ_CUDA(cudaEventRecord(ev[it & 1], st));
+        for (int k = 0; k < n; k++)
+            if (!done[k]) {
+                res.iters[k]++;
+                res.applications[k] += 2;
+            }
+        const int prev = pending;
+        pending = it;
         it++;
-        sc.pull(st);
         bool update = it == maxiter;
-        for (int k = 0; k < n; k++) {
-            if (done[k]) continue;
-            res.iters[k]++;
-            res.applications[k] += 2;
-            double ss = sqrt(sc.h(k, SC_SS));
-            check_finite(ss, "iterated residual");
-            if (ss < delta * rmax[k] || ss <= tol_abs[k]) update = true;
+        if (prev >= 0) {
+            LQ_CUDA(cudaEventSynchronize(ev[prev & 1]));
+            const double* hs = slot(prev);
+            for (int k = 0; k < n; k++) {
+                if (done[k]) continue;
+                double ss = sqrt(hs[(size_t)k * SC_N + SC_SS]);
+                check_finite(ss, "iterated residual");
+                if (ss < delta * rmax[k] || ss <= tol_abs[k]) update = true;
+            }
         }
         if (!update) continue;
+        pending = -1;
         // reliable update: fold the sloppy solution into FP64 and recompute the true residual
         blas_axpy_h(x_hi, ones.data(), x_lo, st);
         blas_zero(x_lo, st);

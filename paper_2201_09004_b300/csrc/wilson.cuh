@@ -509,15 +509,30 @@ __device__ __forceinline__ void hops_pipelined(const WilsonArgs& a, const int c[
     process_hop<7>(a, B, sf, acc);
 }
 
-// Shared-memory bytes per thread of the prefetched epilogue operands
-// (clover record or A^{-1} record, the y spinor, and their FP16 norms).
+// Prefetched epilogue operands in shared memory: one clover / A^{-1} record per
+// site (copied by the first of its RG threads), one y spinor per thread (XPAY),
+// and their FP16 norms.
 template <int P, int EPI>
-__host__ __device__ constexpr int epi_smem_per_thread() {
+__host__ __device__ constexpr int epi_rec_bytes() {
     return (P == P64 || P == PDF) ? 0
-         : EPI == EPI_AINV ? (int)(sizeof(typename Layout<P, 144>::C) * Layout<P, 144>::NC) + 8
-         : EPI == EPI_XPAY ? (int)(sizeof(typename Layout<P, 72>::C) * Layout<P, 72>::NC +
-                                   sizeof(typename Layout<P, 24>::C) * Layout<P, 24>::NC) + 8
+         : EPI == EPI_AINV ? (int)(sizeof(typename Layout<P, 144>::C) * Layout<P, 144>::NC)
+         : EPI == EPI_XPAY ? (int)(sizeof(typename Layout<P, 72>::C) * Layout<P, 72>::NC)
          : 0;
+}
+template <int P, int EPI>
+__host__ __device__ constexpr int epi_y_bytes() {
+    return (P == P64 || P == PDF || EPI != EPI_XPAY) ? 0 : (int)(sizeof(typename Layout<P, 24>::C) * Layout<P, 24>::NC);
+}
+template <int P, int EPI>
+__host__ __device__ constexpr int epi_smem_per_thread() {  // non-zero when the epilogue is prefetched
+    return epi_rec_bytes<P, EPI>() + epi_y_bytes<P, EPI>() + (epi_rec_bytes<P, EPI>() ? 8 : 0);
+}
+template <int P, int EPI>
+__host__ __device__ constexpr size_t epi_smem_bytes(int block, int rg) {
+    return epi_smem_per_thread<P, EPI>() == 0
+               ? 0
+               : (size_t)epi_rec_bytes<P, EPI>() * (block / rg) + (size_t)epi_y_bytes<P, EPI>() * block +
+                     4 * ((size_t)(block / rg) + block);
 }
 
 // Grid: blocks are ordered site block major, right-hand-side group minor, so that
@@ -537,28 +552,39 @@ __global__ void __launch_bounds__(256) wilson_dslash_kernel(WilsonArgs a) {
     double nrm[NB];
 #pragma unroll
     for (int b = 0; b < NB; b++) nrm[b] = 0.0;
-    // shared-memory copies of the epilogue operands (single right-hand side, FP32/FP16)
-    constexpr bool PF = (NB == 1) && (RG == 1) && (epi_smem_per_thread<P, EPI>() > 0);
+    // shared-memory copies of the epilogue operands (FP32/FP16, one RHS per thread)
+    constexpr bool PF = (NB == 1) && (epi_smem_per_thread<P, EPI>() > 0);
     extern __shared__ __align__(16) unsigned char lq_smem[];
     typedef typename Layout<P, 144>::C CA;
     typedef typename Layout<P, 72>::C CC;
     typedef typename Layout<P, 24>::C CY;
-    unsigned char* sm_rec = lq_smem;  // clover / inverse record, chunk-major
-    unsigned char* sm_y = lq_smem + (EPI == EPI_AINV ? sizeof(CA) * Layout<P, 144>::NC : sizeof(CC) * Layout<P, 72>::NC) * blockDim.x;
-    float* sm_norm = (float*)(sm_y + (EPI == EPI_XPAY ? sizeof(CY) * Layout<P, 24>::NC * blockDim.x : 0));
+    const int g = threadIdx.x / RG;   // site slot within the block
+    unsigned char* sm_rec = lq_smem;  // clover / inverse record per site slot, chunk-major
+    unsigned char* sm_y = lq_smem + (size_t)epi_rec_bytes<P, EPI>() * spb;
+    float* sm_norm = (float*)(sm_y + (size_t)epi_y_bytes<P, EPI>() * blockDim.x);  // [spb] record, [blockDim] y
     if (s < a.g.vh && kb < a.nrhs) {
         int c[4];
         cb_coords(a.g, s, a.parity, c);
         if constexpr (PF) {
-            if (a.has_clover) {
-                if constexpr (EPI == EPI_AINV) prefetch_record<P, 144>(sm_rec, a.clov, a.g.vh, s);
-                else prefetch_record<P, 72>(sm_rec, a.clov, a.g.vh, s);
-                if constexpr (P == P16) cp_async4(&sm_norm[threadIdx.x], a.clov_norm + s);
+            if (a.has_clover && threadIdx.x % RG == 0) {
+                // one copy per site: chunk k of slot g at k * spb + g
+                if constexpr (EPI == EPI_AINV) {
+                    CA* d = (CA*)sm_rec;
+                    const CA* gsrc = (const CA*)a.clov;
+#pragma unroll
+                    for (int k = 0; k < Layout<P, 144>::NC; k++) cp_async16(&d[k * spb + g], &gsrc[(size_t)k * a.g.vh + s]);
+                } else {
+                    CC* d = (CC*)sm_rec;
+                    const CC* gsrc = (const CC*)a.clov;
+#pragma unroll
+                    for (int k = 0; k < Layout<P, 72>::NC; k++) cp_async16(&d[k * spb + g], &gsrc[(size_t)k * a.g.vh + s]);
+                }
+                if constexpr (P == P16) cp_async4(&sm_norm[g], a.clov_norm + s);
             }
             if constexpr (EPI == EPI_XPAY) {
                 prefetch_record<P, 24>(sm_y, (const char*)a.y.data + (size_t)kb * a.y.rhs_bytes, a.g.vh, s);
                 if constexpr (P == P16)
-                    cp_async4(&sm_norm[blockDim.x + threadIdx.x], a.y.norm + (size_t)kb * a.g.vh + s);
+                    cp_async4(&sm_norm[spb + threadIdx.x], a.y.norm + (size_t)kb * a.g.vh + s);
             }
             cp_async_commit();
         }
@@ -581,7 +607,11 @@ __global__ void __launch_bounds__(256) wilson_dslash_kernel(WilsonArgs a) {
             hop_dir<2, P, R, NB, T>(a, c, s, kb, sf, acc);
             hop_dir<3, P, R, NB, T>(a, c, s, kb, sf, acc);
         }
-        if constexpr (PF) cp_async_wait_all();
+        if constexpr (PF) {
+            cp_async_wait_all();
+            // the site's record was copied by its first thread: make it visible to the others
+            if constexpr (RG > 1) __syncwarp(__activemask());
+        }
 #pragma unroll
         for (int b = 0; b < NB; b++)
 #pragma unroll
@@ -606,8 +636,7 @@ __global__ void __launch_bounds__(256) wilson_dslash_kernel(WilsonArgs a) {
 #pragma unroll
                         for (int cc = 0; cc < 3; cc++) res[b][sp][cc] = mk((T)0, (T)0);
                 if constexpr (PF)
-                    ainv_apply_src<P, NB, T, true>(sm_rec, blockDim.x, threadIdx.x,
-                                                   P == P16 ? sm_norm[threadIdx.x] : 1.f, a.dagger, acc, res);
+                    ainv_apply_src<P, NB, T, true>(sm_rec, spb, g, P == P16 ? sm_norm[g] : 1.f, a.dagger, acc, res);
                 else if constexpr (P == PDF && NB == 1)
                     ainv_apply_rows<P, T>(a, s, acc[0], res[0]);
                 else
@@ -632,7 +661,7 @@ __global__ void __launch_bounds__(256) wilson_dslash_kernel(WilsonArgs a) {
             for (int b = 0; b < NB; b++) {
                 T v[24];
                 if constexpr (PF) {
-                    const float fy = (P == P16) ? sm_norm[blockDim.x + threadIdx.x] * (1.f / 32767.f) : 1.f;
+                    const float fy = (P == P16) ? sm_norm[spb + threadIdx.x] * (1.f / 32767.f) : 1.f;
 #pragma unroll
                     for (int k = 0; k < Layout<P, 24>::NC; k++)
                         unpack_chunk<P, 24, T>(((const CY*)sm_y)[k * blockDim.x + threadIdx.x], fy,
@@ -657,8 +686,7 @@ __global__ void __launch_bounds__(256) wilson_dslash_kernel(WilsonArgs a) {
                 }
             if (a.has_clover) {
                 if constexpr (PF)
-                    clover_apply_src<P, NB, T, true>(sm_rec, blockDim.x, threadIdx.x,
-                                                     P == P16 ? sm_norm[threadIdx.x] : 1.f, yv, res);
+                    clover_apply_src<P, NB, T, true>(sm_rec, spb, g, P == P16 ? sm_norm[g] : 1.f, yv, res);
                 else if constexpr (P == PDF && NB == 1)
                     clover_apply_rows<P, T>(a, s, yv[0], res[0]);
                 else
