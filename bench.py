@@ -133,6 +133,19 @@ def setup_gpu(dev):
     return lat, b
 
 
+def job_rate(local_seconds, units_per_rank, world, device="cpu"):
+    """Whole-job throughput of `world` replicas: every rank processed
+    units_per_rank units; the job took the slowest rank's time (max over ranks).
+    Returns (units per second, max seconds)."""
+    import torch
+    t = torch.tensor([float(local_seconds)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    s = float(t.item())
+    return world * units_per_rank / s, s
+
+
 def gpu_arm(args):
     import torch
     import torch.distributed as dist
@@ -147,7 +160,8 @@ def gpu_arm(args):
     dev = f"cuda:{local}"
     lat, b = setup_gpu(dev)
     op = lib.op_params(lib.WILSON_TM_CLOVER, MASS, MU, c_sw=C_SW)
-    sp = lib.solve_params(solver=lib.MIXED_CGNR, tol=TOL, delta=0.1, prec_sloppy=args.prec, recon_sloppy=lib.R12)
+    sp = lib.solve_params(solver=lib.MIXED_CGNR, tol=TOL, delta=0.1, prec_sloppy=args.prec, recon_sloppy=lib.R12,
+                          graph_iters=args.graph_iters)
     stream = torch.cuda.current_stream()
     x = torch.empty_like(b)
 
@@ -180,12 +194,8 @@ def gpu_arm(args):
     launches = lib.launch_count() - launches0
     lib.profile_enable(False)
     clocks = sampler.stop() if rank == 0 else None
-    ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * args.steps / (ms_max * 1e-3)
+    value, s_max = job_rate(ev0.elapsed_time(ev1) * 1e-3, args.steps, world, dev)
+    ms_max = s_max * 1e3
 
     # dominant kernel and its roofline, from the events recorded in the timed region
     kernels = {}
@@ -245,11 +255,8 @@ def gpu_arm(args):
     t0 = time.perf_counter()
     for _ in range(args.steps):
         lat.solve(op, sp, [bh], out=[xh])
-    e2e_s = time.perf_counter() - t0
-    tt = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-    e2e = {"value": round(world * args.steps / float(tt.item()), 3), "unit": "solves/s",
+    e2e_rate, _ = job_rate(time.perf_counter() - t0, args.steps, world, dev)
+    e2e = {"value": round(e2e_rate, 3), "unit": "solves/s",
            "h2d_bytes_per_step": int(bh.numel() * 16), "d2h_bytes_per_step": int(xh.numel() * 16)}
 
     if rank == 0:
@@ -263,6 +270,7 @@ def gpu_arm(args):
             "config": {"workload": WORKLOAD, "dims": list(DIMS), "action": "wilson twisted-mass clover",
                        "c_sw": C_SW, "m": MASS, "mu": MU, "gauge_seed": GAUGE_SEED, "source_seed": SOURCE_SEED,
                        "tol": TOL, "sloppy_precision": args.prec, "recon": 12, "delta": 0.1,
+                       "graph_iters": args.graph_iters,
                        "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (clover inverse, clover and links ~0.3 GB per step)"},
             "iters": int(np.median(iters)), "reliable_updates": infos[-1]["reliable_updates"],
@@ -580,6 +588,8 @@ def main():
                     help="tmc: 24^3x64 twisted-mass clover (default, the headline); multirhs: 32^3x96, "
                          "36 right-hand sides; hisq: 48^3x144 multi-shift; serving: Poisson request stream")
     ap.add_argument("--requests", type=int, default=100, help="serving: number of requests")
+    ap.add_argument("--graph-iters", type=int, default=0,
+                    help="CG iterations per CUDA graph (0: library default, -1: no graphs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -123,6 +123,8 @@ typedef struct {
     int recon_sloppy; /* lq_recon for thin/long links in the sloppy operator */
     int nshift;
     const double* masses;
+    int graph_iters;  /* Krylov iterations captured per CUDA graph and replayed with one
+                         launch: 0 = the library's choice (1), < 0 = no graphs */
 } lq_solve_params;
 
 typedef struct {
@@ -150,8 +152,16 @@ int lq_create_lattice(const int dims[4], int t_boundary, lq_lattice* out);
 /* Frees every device buffer of the lattice. Accepts NULL. */
 int lq_destroy_lattice(lq_lattice lat);
 
-/* Device bytes the lattice currently holds (links, clover, caches). */
+/* Device bytes the lattice currently holds (links, clover, caches, and the
+ * solver work buffers it keeps between solves). */
 int lq_lattice_bytes(lq_lattice lat, size_t* bytes);
+
+/* Frees the solver work buffers the lattice keeps between solves (device
+ * fields, staging buffers, pinned host scalars) that no running solve uses.
+ * *freed (may be NULL) receives the device bytes released. A later solve
+ * allocates them again. Not part of the paper's method: a memory-management
+ * call of this library. */
+int lq_lattice_release_workspace(lq_lattice lat, size_t* freed);
 
 /* Loads links in the canonical gauge layout (host or device, FP64). kind
  * selects the thin links of the Wilson actions, or the fat / long links of

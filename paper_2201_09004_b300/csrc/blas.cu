@@ -1,8 +1,9 @@
 // blas.cu -- Krylov vector operations on even-odd fields: updates with device
-// or host scalars, precision conversion, and FP64 reductions. Reductions are
-// deterministic: each thread sums its sites in a fixed order, blocks reduce by
-// warp shuffles, and one block per right-hand side adds the per-block partials
-// in index order with Neumaier-compensated summation.
+// or host scalars, precision conversion, and reductions. Reductions are
+// deterministic and carried in double-float arithmetic (about 2^-44 relative
+// per step, on the FP32 pipes): each thread sums its sites in a fixed order,
+// blocks reduce by warp shuffles, and one block per right-hand side adds the
+// per-block partials in a fixed order.
 #include <type_traits>
 
 #include "runtime.h"
@@ -21,39 +22,40 @@ struct HostScalars {
     double b[64];
 };
 
-__device__ __forceinline__ double block_sum(double v) {
-    __shared__ double red[32];
+// block-wide double-float sum (valid in thread 0)
+__device__ __forceinline__ df block_sum_df(df v) {
+    __shared__ float2 red[32];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    for (int o = 16; o > 0; o >>= 1) v = v + shfl_down_df(v, o);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     __syncthreads();
-    if (lane == 0) red[wid] = v;
+    if (lane == 0) red[wid] = make_float2(v.hi, v.lo);
     __syncthreads();
-    v = 0.0;
+    v = df(0.f);
     if (wid == 0) {
-        v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+        if (lane < (int)(blockDim.x >> 5)) v = df(red[lane].x, red[lane].y);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        for (int o = 16; o > 0; o >>= 1) v = v + shfl_down_df(v, o);
     }
-    return v;  // valid in thread 0
+    return v;
 }
 
 #define SITE_LOOP(vh) for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < (vh); s += gridDim.x * blockDim.x)
 
 template <int P, int NR>
-__global__ void norm2_kernel(FieldV x, double* part) {
+__global__ void norm2_kernel(FieldV x, df* part) {
     typedef typename RealT<P>::T T;
     const int k = blockIdx.y;
-    double acc = 0.0;
+    df acc(0.f);
     SITE_LOOP(x.vh) {
         T v[NR];
         fload<P, NR, T>(x, k, s, v);
         T t = (T)0;
 #pragma unroll
         for (int q = 0; q < NR; q++) t = fma(v[q], v[q], t);
-        acc += (double)t;
+        acc = acc + df_of(t);
     }
-    double r = block_sum(acc);
+    df r = block_sum_df(acc);
     if (threadIdx.x == 0) part[(size_t)k * gridDim.x + blockIdx.x] = r;
 }
 
@@ -98,11 +100,11 @@ __global__ void axpy_h_kernel(FieldV y, FieldV x, HostScalars h) {
 
 // y = a_k x + b_k y, optional partial |y|^2 (host scalars)
 template <int P, int NR>
-__global__ void axpby_h_kernel(FieldV y, FieldV x, HostScalars h, double* part) {
+__global__ void axpby_h_kernel(FieldV y, FieldV x, HostScalars h, df* part) {
     typedef typename RealT<P>::T T;
     const int k = blockIdx.y;
     const T a = (T)h.a[k], b = (T)h.b[k];
-    double acc = 0.0;
+    df acc(0.f);
     SITE_LOOP(y.vh) {
         T vy[NR], vx[NR];
         fload<P, NR, T>(y, k, s, vy);
@@ -113,21 +115,21 @@ __global__ void axpby_h_kernel(FieldV y, FieldV x, HostScalars h, double* part) 
             vy[q] = fma(b, vy[q], a * vx[q]);
             t = fma(vy[q], vy[q], t);
         }
-        acc += (double)t;
+        acc = acc + df_of(t);
         fstore<P, NR, T>(y, k, s, vy);
     }
     if (part) {
-        double r = block_sum(acc);
+        df r = block_sum_df(acc);
         if (threadIdx.x == 0) part[(size_t)k * gridDim.x + blockIdx.x] = r;
     }
 }
 
 // s = b - q, partial |s|^2
 template <int P, int NR>
-__global__ void xmy_norm_kernel(FieldV sf, FieldV b, FieldV qf, double* part) {
+__global__ void xmy_norm_kernel(FieldV sf, FieldV b, FieldV qf, df* part) {
     typedef typename RealT<P>::T T;
     const int k = blockIdx.y;
-    double acc = 0.0;
+    df acc(0.f);
     SITE_LOOP(sf.vh) {
         T vb[NR], vq[NR];
         fload<P, NR, T>(b, k, s, vb);
@@ -138,23 +140,23 @@ __global__ void xmy_norm_kernel(FieldV sf, FieldV b, FieldV qf, double* part) {
             vb[q] -= vq[q];
             t = fma(vb[q], vb[q], t);
         }
-        acc += (double)t;
+        acc = acc + df_of(t);
         fstore<P, NR, T>(sf, k, s, vb);
     }
-    double r = block_sum(acc);
+    df r = block_sum_df(acc);
     if (threadIdx.x == 0) part[(size_t)k * gridDim.x + blockIdx.x] = r;
 }
 
 // x += alpha p; s -= alpha q; partial |s|^2; alpha_k = sc[k*SC_N + SC_ALPHA]
 template <int PX, int P, int NR>
-__global__ void cg_xs_kernel(FieldV x, FieldV p, FieldV sf, FieldV qf, const double* sc, double* part) {
+__global__ void cg_xs_kernel(FieldV x, FieldV p, FieldV sf, FieldV qf, const double* sc, df* part) {
     typedef typename RealT<P>::T T;
     typedef typename MathT<PX, P>::T TX;
     const int k = blockIdx.y;
     const double al = sc[(size_t)k * SC_N + SC_ALPHA];
     const T a = (T)al;
     const TX ax = (TX)al;
-    double acc = 0.0;
+    df acc(0.f);
     SITE_LOOP(x.vh) {
         T vp[NR], vs[NR], vq[NR];
         TX vx[NR];
@@ -169,11 +171,11 @@ __global__ void cg_xs_kernel(FieldV x, FieldV p, FieldV sf, FieldV qf, const dou
             vs[q] = fma(-a, vq[q], vs[q]);
             t = fma(vs[q], vs[q], t);
         }
-        acc += (double)t;
+        acc = acc + df_of(t);
         fstore<PX, NR, TX>(x, k, s, vx);
         fstore<P, NR, T>(sf, k, s, vs);
     }
-    double r = block_sum(acc);
+    df r = block_sum_df(acc);
     if (threadIdx.x == 0) part[(size_t)k * gridDim.x + blockIdx.x] = r;
 }
 
@@ -193,22 +195,16 @@ __global__ void cg_p_kernel(FieldV p, FieldV r, const double* sc) {
     }
 }
 
-// sum the partials of right-hand side blockIdx.x, then apply the scalar step
-__global__ void finalize_kernel(const double* part, int nblocks, double* sc, int slot, int op) {
+// sum the partials of right-hand side blockIdx.x (double-float, fixed order),
+// then apply the scalar step in FP64
+__global__ void finalize_kernel(const df* part, int nblocks, double* sc, int slot, int op) {
     const int k = blockIdx.x;
-    const double* pk = part + (size_t)k * nblocks;
-    double sum = 0.0, comp = 0.0;  // Neumaier summation of this thread's strided partials
-    for (int i = threadIdx.x; i < nblocks; i += blockDim.x) {
-        double v = pk[i];
-        double t = sum + v;
-        if (fabs(sum) >= fabs(v)) comp += (sum - t) + v;
-        else comp += (v - t) + sum;
-        sum = t;
-    }
-    double s = block_sum(sum);
-    double c = block_sum(comp);
+    const df* pk = part + (size_t)k * nblocks;
+    df sum(0.f);
+    for (int i = threadIdx.x; i < nblocks; i += blockDim.x) sum = sum + pk[i];
+    sum = block_sum_df(sum);
     if (threadIdx.x == 0) {
-        double tot = s + c;
+        const double tot = df_to_double(sum);
         double* S = sc + (size_t)k * SC_N;
         if (op == FIN_SET) {
             S[slot] = tot;
@@ -245,7 +241,7 @@ static dim3 upd_grid(int vh, int nrhs) {
         else launch(NAME, KERNEL(6), GRID, dim3(RED_THREADS), st, __VA_ARGS__);                  \
     } while (0)
 
-void blas_norm2(const Field& x, double* part, cudaStream_t st) {
+void blas_norm2(const Field& x, df* part, cudaStream_t st) {
 #define K(NR) norm2_kernel<P_, NR>
 #define L(P) { constexpr int P_ = P; BY_KIND(x, "blas_norm2", K, red_grid(x.nrhs), x.view(), part); }
     DISPATCH_P(x.prec, L);
@@ -309,7 +305,7 @@ void blas_axpy_h(Field& y, const double* a, const Field& x, cudaStream_t st) {
     else axpy_h_from<PDF>(y, h, x, st);
 }
 
-void blas_axpby_h(Field& y, const double* a, const Field& x, const double* b, double* part, cudaStream_t st) {
+void blas_axpby_h(Field& y, const double* a, const Field& x, const double* b, df* part, cudaStream_t st) {
     if (y.prec != x.prec || y.kind != x.kind || y.nrhs != x.nrhs) fail(LQ_EINVAL, "blas_axpby: field mismatch");
     HostScalars h = hs(a, b, y.nrhs);
     dim3 g = part ? red_grid(y.nrhs) : upd_grid(y.vh, y.nrhs);
@@ -320,7 +316,7 @@ void blas_axpby_h(Field& y, const double* a, const Field& x, const double* b, do
 #undef K
 }
 
-void blas_xmy_norm(Field& s, const Field& b, const Field& q, double* part, cudaStream_t st) {
+void blas_xmy_norm(Field& s, const Field& b, const Field& q, df* part, cudaStream_t st) {
     if (s.prec != b.prec || s.prec != q.prec) fail(LQ_EINVAL, "blas_xmy_norm: precision mismatch");
 #define K(NR) xmy_norm_kernel<P_, NR>
 #define L(P) { constexpr int P_ = P; BY_KIND(s, "blas_xmy_norm", K, red_grid(s.nrhs), s.view(), b.view(), q.view(), part); }
@@ -330,7 +326,7 @@ void blas_xmy_norm(Field& s, const Field& b, const Field& q, double* part, cudaS
 }
 
 template <int PX>
-static void cg_xs_from(Field& x, const Field& p, Field& s, const Field& q, const double* sc, double* part,
+static void cg_xs_from(Field& x, const Field& p, Field& s, const Field& q, const double* sc, df* part,
                        cudaStream_t st) {
 #define K(NR) cg_xs_kernel<PX, P_, NR>
 #define L(P) { constexpr int P_ = P; BY_KIND(x, "blas_cg_xs", K, red_grid(x.nrhs), x.view(), p.view(), s.view(), q.view(), sc, part); }
@@ -339,7 +335,7 @@ static void cg_xs_from(Field& x, const Field& p, Field& s, const Field& q, const
 #undef K
 }
 
-void blas_cg_xs(Field& x, const Field& p, Field& s, const Field& q, const double* sc, double* part,
+void blas_cg_xs(Field& x, const Field& p, Field& s, const Field& q, const double* sc, df* part,
                 cudaStream_t st) {
     if (p.prec != s.prec || p.prec != q.prec) fail(LQ_EINVAL, "blas_cg_xs: precision mismatch");
     if (x.prec == LQ_F64) cg_xs_from<P64>(x, p, s, q, sc, part, st);
@@ -358,7 +354,7 @@ void blas_cg_p(Field& p, const Field& r, const double* sc, cudaStream_t st) {
 #undef K
 }
 
-void blas_finalize(const double* part, int nblocks, int nrhs, double* sc, int slot, int op, cudaStream_t st) {
+void blas_finalize(const df* part, int nblocks, int nrhs, double* sc, int slot, int op, cudaStream_t st) {
     launch("blas_finalize", finalize_kernel, dim3(nrhs), dim3(256), st, part, nblocks, sc, slot, op);
 }
 

@@ -33,21 +33,29 @@ struct lq_field_s {
 
 static cudaStream_t as_stream(void* s) { return (cudaStream_t)s; }
 
-// device staging buffer, freed on scope exit
+// device staging buffer, released on scope exit: plain, or taken from the
+// lattice's workspace cache (kept for the next call)
 struct DevBuf {
     void* p = nullptr;
     size_t n = 0;
-    explicit DevBuf(size_t bytes) : n(bytes) {
-        if (bytes) {
-            cudaError_t e = cudaMalloc(&p, bytes);
-            if (e != cudaSuccess) {
-                cudaGetLastError();
-                fail(LQ_ENOMEM, "staging allocation failed");
-            }
+    Lattice* lat = nullptr;
+    cudaStream_t st = nullptr;
+    explicit DevBuf(size_t bytes, Lattice* l = nullptr, cudaStream_t s = nullptr) : n(bytes), lat(l), st(s) {
+        if (!bytes) return;
+        if (lat) {
+            p = ws_get(*lat, bytes, false, st);
+            return;
+        }
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            fail(LQ_ENOMEM, "staging allocation failed");
         }
     }
     ~DevBuf() {
-        if (p) cudaFree(p);
+        if (!p) return;
+        if (lat) ws_put(*lat, p, st);
+        else cudaFree(p);
     }
 };
 
@@ -99,6 +107,8 @@ extern "C" int lq_destroy_lattice(lq_lattice h) {
     if (!h) return LQ_OK;
     Lattice& L = h->lat;
     cudaDeviceSynchronize();
+    ws_release(L);
+    if (L.own_stream) cudaStreamDestroy(L.own_stream);
     free_clover(L);
     for (auto& kv : L.packed) dev_free(&L, kv.second.data, kv.second.bytes);
     for (int k = 0; k < 3; k++) dev_free(&L, L.canon[k], (size_t)L.V * 4 * 18 * sizeof(double));
@@ -110,7 +120,23 @@ extern "C" int lq_destroy_lattice(lq_lattice h) {
 extern "C" int lq_lattice_bytes(lq_lattice h, size_t* bytes) {
     LQ_TRY
     check_lattice(h);
-    if (bytes) *bytes = h->lat.bytes;
+    if (bytes) {
+        Lattice& L = h->lat;
+        std::lock_guard<std::mutex> lk(L.mu);
+        size_t ws = 0;
+        for (auto& b : L.ws)
+            if (!b.host) ws += b.bytes;
+        *bytes = L.bytes + ws;
+    }
+    return LQ_OK;
+    LQ_CATCH
+}
+
+extern "C" int lq_lattice_release_workspace(lq_lattice h, size_t* freed) {
+    LQ_TRY
+    check_lattice(h);
+    size_t n = ws_release(h->lat);
+    if (freed) *freed = n;
     return LQ_OK;
     LQ_CATCH
 }
@@ -278,6 +304,16 @@ extern "C" int lq_solve(lq_lattice h, const lq_op_params* op, const lq_solve_par
     if (nrhs < 1) fail(LQ_EINVAL, "nrhs must be positive");
     Lattice& L = h->lat;
     cudaStream_t st = as_stream(stream);
+    if (st == nullptr || st == cudaStreamLegacy) {
+        // run on the lattice's own stream, ordered after the caller's earlier default-stream work
+        if (!L.own_stream) LQ_CUDA(cudaStreamCreateWithFlags(&L.own_stream, cudaStreamNonBlocking));
+        cudaEvent_t fork;
+        LQ_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        cudaEventRecord(fork, st);
+        cudaStreamWaitEvent(L.own_stream, fork, 0);
+        cudaEventDestroy(fork);
+        st = L.own_stream;
+    }
     const size_t bytes = field_canon_bytes(L, op->action);
     const int nsol = nrhs * ((op->action == LQ_HISQ && sp->solver == LQ_MULTISHIFT_CG) ? std::max(1, sp->nshift) : 1);
     for (int k = 0; k < nrhs; k++)
@@ -286,7 +322,7 @@ extern "C" int lq_solve(lq_lattice h, const lq_op_params* op, const lq_solve_par
         if (!x[k]) fail(LQ_EINVAL, "null solution pointer");
     std::vector<const double*> db(nrhs);
     std::vector<double*> dx(nsol);
-    DevBuf stage(loc == LQ_HOST ? bytes * (nrhs + nsol) : 0);
+    DevBuf stage(loc == LQ_HOST ? bytes * (nrhs + nsol) : 0, &L, st);
     if (loc == LQ_HOST) {
         for (int k = 0; k < nrhs; k++) {
             double* d = (double*)stage.p + (size_t)k * (bytes / sizeof(double));

@@ -81,6 +81,17 @@ __device__ __forceinline__ df& operator-=(df& x, df y) { x = x - y; return x; }
 __device__ __forceinline__ df fma(df a, df b, df c) { return a * b + c; }
 using ::fma;
 
+// Reductions carry their partial sums as double-float values: B300 runs FP64
+// at 1/64 of its FP32 rate, and even a block-level FP64 tree reduction on one
+// SM costs microseconds. Every sum is formed in a fixed order (deterministic).
+__device__ __forceinline__ df df_of(float v) { return df(v); }
+__device__ __forceinline__ df df_of(double v) { return df(v); }
+__device__ __forceinline__ df df_of(df v) { return v; }
+__device__ __forceinline__ df shfl_down_df(df v, int o) {
+    return df(__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o));
+}
+__device__ __forceinline__ double df_to_double(df v) { return (double)v.hi + (double)v.lo; }
+
 // conversions between the arithmetic types of the kernels
 template <typename T> __device__ __forceinline__ T from_df(df d);
 template <> __device__ __forceinline__ df from_df<df>(df d) { return d; }

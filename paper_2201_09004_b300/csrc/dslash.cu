@@ -4,6 +4,7 @@
 #include <string>
 
 #include "hisq.cuh"
+#include "wilson_df.cuh"
 #include "runtime.h"
 
 namespace lq {
@@ -48,6 +49,13 @@ static void wl_epi(const char* name, WilsonArgs a, int epi, int nb, int block, c
     else wl_nb<P, R, EPI_XPAY>(name, a, nb, block, st);
 }
 
+// double-float: two threads per site, one right-hand side per grid row
+template <int EPI, bool SITE>
+static void wl_df(const char* name, WilsonArgs a, int block, cudaStream_t st) {
+    dim3 grid(site_blocks(a.g.vh, block, 2), a.nrhs);
+    launch(name, wilson_dslash_df2_kernel<EPI, SITE>, grid, dim3(block), st, a);
+}
+
 static const char* wname(int prec, int epi) {
     static const char* n[4][3] = {
         {"wilson_dslash_f64_hop", "wilson_dslash_f64_ainv", "wilson_dslash_f64_xpay"},
@@ -58,7 +66,7 @@ static const char* wname(int prec, int epi) {
 }
 
 int wilson_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int epi, const Field& in, Field& out,
-                  const Field* y, double* norm_out, cudaStream_t st) {
+                  const Field* y, df* norm_out, cudaStream_t st) {
     if (in.prec != op.prec || out.prec != op.prec || (y && y->prec != op.prec))
         fail(LQ_EINVAL, "wilson_dslash: field precision does not match the operator");
     if (in.kind != LQ_WILSON_FIELD || out.nrhs != in.nrhs) fail(LQ_EINVAL, "wilson_dslash: field shape");
@@ -88,7 +96,9 @@ int wilson_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int ep
             if (op.recon == 18) wl_epi<P64, 18>(name, a, epi, nb, block, st);
             else wl_epi<P64, 12>(name, a, epi, nb, block, st);
         } else if (op.prec == LQ_F32X2) {
-            wl_epi<PDF, 18>(name, a, epi, nb, block, st);
+            if (epi == EPI_HOP) wl_df<EPI_HOP, false>(name, a, block, st);
+            else if (epi == EPI_AINV) wl_df<EPI_AINV, false>(name, a, block, st);
+            else wl_df<EPI_XPAY, false>(name, a, block, st);
         } else if (op.prec == LQ_F32) {
             if (op.recon == 18) wl_epi<P32, 18>(name, a, epi, nb, block, st);
             else wl_epi<P32, 12>(name, a, epi, nb, block, st);
@@ -102,7 +112,7 @@ int wilson_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int ep
                       std::to_string(norm_out != nullptr);
     int block = tuned_block(key, st, run);
     run(block);
-    return site_blocks(lat.vh, block, nb);
+    return site_blocks(lat.vh, block, op.prec == LQ_F32X2 ? 2 : nb);
 }
 
 void wilson_ainv_site(Lattice& lat, const OpDesc& op, int parity, int dagger, const Field& in, Field& out,
@@ -126,7 +136,9 @@ void wilson_ainv_site(Lattice& lat, const OpDesc& op, int parity, int dagger, co
     if (a.has_clover) a.clov = ainv_block(lat, op.m, op.mu, in.prec, parity, &a.clov_norm, st);
     dim3 grid((lat.vh + 127) / 128, in.nrhs);
     if (in.prec == LQ_F64) launch("wilson_ainv_site", wilson_ainv_site_kernel<P64>, grid, dim3(128), st, a);
-    else if (in.prec == LQ_F32X2) launch("wilson_ainv_site", wilson_ainv_site_kernel<PDF>, grid, dim3(128), st, a);
+    else if (in.prec == LQ_F32X2)
+        launch("wilson_ainv_site", wilson_dslash_df2_kernel<EPI_AINV, true>, dim3((lat.vh + 63) / 64, in.nrhs),
+               dim3(128), st, a);
     else if (in.prec == LQ_F32) launch("wilson_ainv_site", wilson_ainv_site_kernel<P32>, grid, dim3(128), st, a);
     else launch("wilson_ainv_site", wilson_ainv_site_kernel<P16>, grid, dim3(128), st, a);
 }
@@ -165,7 +177,7 @@ static const char* hname(int prec, int epi) {
 }
 
 int hisq_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int epi, double aa, const Field& in,
-                Field& out, const Field* y, double* norm_out, cudaStream_t st) {
+                Field& out, const Field* y, df* norm_out, cudaStream_t st) {
     if (in.prec != op.prec || out.prec != op.prec || (y && y->prec != op.prec))
         fail(LQ_EINVAL, "hisq_dslash: field precision does not match the operator");
     if (in.kind != LQ_STAGGERED_FIELD || out.nrhs != in.nrhs) fail(LQ_EINVAL, "hisq_dslash: field shape");
@@ -202,7 +214,7 @@ int hisq_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int epi,
                       std::to_string(lat.vh) + "/n" + std::to_string(norm_out != nullptr);
     int block = tuned_block(key, st, run);
     run(block);
-    return site_blocks(lat.vh, block, nb);
+    return site_blocks(lat.vh, block, op.prec == LQ_F32X2 ? 2 : nb);
 }
 
 }  // namespace lq

@@ -23,7 +23,7 @@ struct HisqArgs {
     double c_naik;
     double a;       // XPAY scale
     int nrhs;
-    double* norm_out;
+    df* norm_out;
 };
 
 template <int MU, int STEP, int P, int R, int NB, typename T>
@@ -89,9 +89,9 @@ __global__ void __launch_bounds__(256) hisq_dslash_kernel(HisqArgs a) {
     const int nsb = gridDim.x / ngroups;
     const int s = sb * spb + threadIdx.x / RG;
     const int kb = (grp * RG + threadIdx.x % RG) * NB;
-    double nrm[NB];
+    df nrm[NB];
 #pragma unroll
-    for (int b = 0; b < NB; b++) nrm[b] = 0.0;
+    for (int b = 0; b < NB; b++) nrm[b] = df(0.f);
     if (s < a.g.vh && kb < a.nrhs) {
         int c[4];
         cb_coords(a.g, s, a.parity, c);
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(256) hisq_dslash_kernel(HisqArgs a) {
                 T t = (T)0;
 #pragma unroll
                 for (int q = 0; q < 6; q++) t = fma(v[q], v[q], t);
-                nrm[b] = (double)t;
+                nrm[b] = df_of(t);
             }
             fstore<P, 6, T>(a.out, kb + b, s, v);
         }

@@ -18,7 +18,17 @@ void fail(int code, const std::string& msg) { throw Error{code, msg}; }
 
 // ----------------------------------------------------------------- launches
 static std::atomic<int64_t> g_launches{0};
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+// while this thread captures a graph: its launch count and profile records
+static thread_local int64_t* t_cap_kernels = nullptr;
+static thread_local std::vector<GraphProf>* t_cap_prof = nullptr;
+
+void count_launch() {
+    if (t_cap_kernels) {
+        (*t_cap_kernels)++;  // counted once per replay instead
+        return;
+    }
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+}
 
 struct ProfRec {
     std::string name;
@@ -27,7 +37,20 @@ struct ProfRec {
 static std::mutex g_prof_mu;
 static std::atomic<bool> g_prof_on{false};
 static std::vector<ProfRec> g_prof;                                   // recorded launches since reset
+static std::vector<std::pair<std::string, float>> g_prof_done;       // timed graph-replayed launches
 static std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_prof_free;  // reusable event pairs
+
+static std::pair<cudaEvent_t, cudaEvent_t> take_pair() {  // g_prof_mu held
+    std::pair<cudaEvent_t, cudaEvent_t> ev;
+    if (!g_prof_free.empty()) {
+        ev = g_prof_free.back();
+        g_prof_free.pop_back();
+    } else {
+        cudaEventCreate(&ev.first);
+        cudaEventCreate(&ev.second);
+    }
+    return ev;
+}
 
 bool stream_capturing(cudaStream_t st) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -38,27 +61,105 @@ bool stream_capturing(cudaStream_t st) {
     return cs != cudaStreamCaptureStatusNone;
 }
 
+// slots: -1 none, >= 0 an eager record, <= -2 a record of the graph being captured
 int prof_begin(const char* name, cudaStream_t st) {
     if (!g_prof_on.load()) return -1;
+    if (t_cap_prof) {
+        std::pair<cudaEvent_t, cudaEvent_t> ev;
+        {
+            std::lock_guard<std::mutex> lk(g_prof_mu);
+            ev = take_pair();
+        }
+        cudaEventRecordWithFlags(ev.first, st, cudaEventRecordExternal);
+        t_cap_prof->push_back(GraphProf{name, ev.first, ev.second});
+        return -2 - (int)(t_cap_prof->size() - 1);
+    }
     if (stream_capturing(st)) return -1;
     std::lock_guard<std::mutex> lk(g_prof_mu);
-    std::pair<cudaEvent_t, cudaEvent_t> ev;
-    if (!g_prof_free.empty()) {
-        ev = g_prof_free.back();
-        g_prof_free.pop_back();
-    } else {
-        cudaEventCreate(&ev.first);
-        cudaEventCreate(&ev.second);
-    }
+    std::pair<cudaEvent_t, cudaEvent_t> ev = take_pair();
     cudaEventRecord(ev.first, st);
     g_prof.push_back(ProfRec{name, ev.first, ev.second});
     return (int)g_prof.size() - 1;
 }
 
 void prof_end(int slot, cudaStream_t st) {
-    if (slot < 0) return;
+    if (slot == -1) return;
+    if (slot <= -2) {
+        cudaEventRecordWithFlags((*t_cap_prof)[-2 - slot].b, st, cudaEventRecordExternal);
+        return;
+    }
     std::lock_guard<std::mutex> lk(g_prof_mu);
     cudaEventRecord(g_prof[slot].b, st);
+}
+
+// ------------------------------------------------------------- CUDA graphs
+bool graph_capture_begin(cudaStream_t st) {
+    // the legacy default stream cannot be captured
+    if (st == nullptr || st == cudaStreamLegacy) return false;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    static thread_local int64_t kernels;
+    static thread_local std::vector<GraphProf> prof;
+    kernels = 0;
+    prof.clear();
+    t_cap_kernels = &kernels;
+    t_cap_prof = &prof;
+    return true;
+}
+
+bool graph_capture_end(cudaStream_t st, Graph& g) {
+    std::vector<GraphProf> prof = *t_cap_prof;
+    const int64_t kernels = *t_cap_kernels;
+    t_cap_kernels = nullptr;
+    t_cap_prof = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(st, &graph);
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess && graph) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess || !exec) {
+        cudaGetLastError();
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        for (auto& r : prof) g_prof_free.push_back({r.a, r.b});
+        return false;
+    }
+    g.exec = exec;
+    g.prof.swap(prof);
+    g.kernels = kernels;
+    g.uncollected = false;
+    return true;
+}
+
+void graph_launch(Graph& g, cudaStream_t st) {
+    LQ_CUDA(cudaGraphLaunch(g.exec, st));
+    g_launches.fetch_add(g.kernels, std::memory_order_relaxed);
+    g.uncollected = !g.prof.empty();
+}
+
+void graph_collect(Graph& g) {
+    if (!g.uncollected) return;
+    g.uncollected = false;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto& r : g.prof) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess)
+            g_prof_done.push_back({r.name, ms});
+        else
+            cudaGetLastError();
+    }
+}
+
+void graph_destroy(Graph& g) {
+    if (g.exec) {
+        graph_collect(g);
+        cudaGraphExecDestroy(g.exec);
+    }
+    g.exec = nullptr;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto& r : g.prof) g_prof_free.push_back({r.a, r.b});
+    g.prof.clear();
 }
 
 static std::mutex g_smem_mu;
@@ -181,6 +282,113 @@ Field field_alloc(int kind, int prec, int nrhs, int vh) {
     return f;
 }
 
+// ---------------------------------------------------------- workspace cache
+void* ws_get(Lattice& lat, size_t bytes, bool host, cudaStream_t st) {
+    bytes = bytes ? bytes : 16;
+    {
+        std::lock_guard<std::mutex> lk(lat.mu);
+        // best fit among the idle buffers of the same kind, wasting at most a quarter
+        int best = -1;
+        for (size_t i = 0; i < lat.ws.size(); i++) {
+            const auto& b = lat.ws[i];
+            if (b.busy || b.host != host || b.bytes < bytes || b.bytes > bytes + bytes / 4) continue;
+            if (best < 0 || b.bytes < lat.ws[best].bytes) best = (int)i;
+        }
+        if (best >= 0) {
+            auto& b = lat.ws[best];
+            b.busy = true;
+            if (host) {
+                // the host reads and writes it directly: the last user's copies must be done
+                if (b.ev) LQ_CUDA(cudaEventSynchronize(b.ev));
+            } else if (b.ev && b.st != st) {
+                LQ_CUDA(cudaStreamWaitEvent(st, b.ev, 0));
+            }
+            return b.p;
+        }
+    }
+    Lattice::WsBlock b;
+    b.bytes = bytes;
+    b.host = host;
+    b.busy = true;
+    cudaError_t e = host ? cudaMallocHost(&b.p, bytes) : cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        // idle buffers of other sizes may be what is in the way
+        ws_release(lat);
+        e = host ? cudaMallocHost(&b.p, bytes) : cudaMalloc(&b.p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            fail(LQ_ENOMEM, std::string("workspace allocation of ") + std::to_string(bytes) +
+                                " bytes failed: " + cudaGetErrorString(e));
+        }
+    }
+    LQ_CUDA(cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming));
+    std::lock_guard<std::mutex> lk(lat.mu);
+    lat.ws.push_back(b);
+    return b.p;
+}
+
+static void ws_free_block(Lattice::WsBlock& b) {
+    if (b.host) cudaFreeHost(b.p);
+    else cudaFree(b.p);
+    if (b.ev) cudaEventDestroy(b.ev);
+    b.p = nullptr;
+}
+
+void ws_put(Lattice& lat, void* p, cudaStream_t st) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(lat.mu);
+    for (size_t i = 0; i < lat.ws.size(); i++) {
+        auto& b = lat.ws[i];
+        if (b.p != p) continue;
+        if (!lat.ws_keep) {
+            ws_free_block(b);
+            lat.ws.erase(lat.ws.begin() + i);
+            return;
+        }
+        cudaEventRecord(b.ev, st);
+        b.st = st;
+        b.busy = false;
+        return;
+    }
+}
+
+size_t ws_release(Lattice& lat) {
+    std::lock_guard<std::mutex> lk(lat.mu);
+    size_t freed = 0;
+    std::vector<Lattice::WsBlock> keep;
+    for (auto& b : lat.ws) {
+        if (b.busy) {
+            keep.push_back(b);
+            continue;
+        }
+        if (!b.host) freed += b.bytes;
+        ws_free_block(b);
+    }
+    lat.ws.swap(keep);
+    return freed;
+}
+
+size_t ws_idle_bytes(Lattice& lat) {
+    std::lock_guard<std::mutex> lk(lat.mu);
+    size_t n = 0;
+    for (auto& b : lat.ws)
+        if (!b.busy && !b.host) n += b.bytes;
+    return n;
+}
+
+Field ws_field(Lattice& lat, int kind, int prec, int nrhs, cudaStream_t st) {
+    Field f;
+    f.kind = kind;
+    f.prec = prec;
+    f.nrhs = nrhs;
+    f.vh = lat.vh;
+    f.rhs_bytes = rhs_bytes_of(kind, prec, lat.vh);
+    f.data = ws_get(lat, field_bytes(kind, prec, nrhs, lat.vh), false, st);
+    if (prec == LQ_F16) f.norm = (float*)((char*)f.data + f.rhs_bytes * nrhs);
+    return f;
+}
+
 void field_free(Field& f) {
     if (f.data) cudaFree(f.data);
     f.data = nullptr;
@@ -203,6 +411,7 @@ extern "C" int lq_profile_reset(void) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
     for (auto& r : g_prof) g_prof_free.push_back({r.a, r.b});
     g_prof.clear();
+    g_prof_done.clear();
     g_launches.store(0);
     return LQ_OK;
 }
@@ -222,6 +431,11 @@ extern "C" int lq_profile_query(const char* name, int64_t* launches, double* tot
             t += ms;
             n++;
         }
+    }
+    for (auto& r : g_prof_done) {
+        if (name && *name && r.first.find(name) == std::string::npos) continue;
+        t += r.second;
+        n++;
     }
     if (launches) *launches = n;
     if (total_ms) *total_ms = t;

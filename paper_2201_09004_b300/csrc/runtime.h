@@ -73,6 +73,29 @@ inline void launch(const char* name, void (*kernel)(KArgs...), dim3 grid, dim3 b
     count_launch();
 }
 
+// ------------------------------------------------------------- CUDA graphs
+// A captured sequence of launches (solver iterations) replayed by one
+// cudaGraphLaunch. If profiling is on while it is captured, every kernel is
+// bracketed by event-record nodes; collect() adds the times of the last replay
+// to the profile and must run after that replay has finished.
+struct GraphProf {
+    std::string name;
+    cudaEvent_t a, b;
+};
+struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<GraphProf> prof;
+    int64_t kernels = 0;       // kernel launches per replay
+    bool uncollected = false;  // a replay whose profile is not yet collected
+};
+// false (nothing captured) where the stream cannot be captured
+bool graph_capture_begin(cudaStream_t st);
+// ends the capture; false (and the stream back to normal) if it failed
+bool graph_capture_end(cudaStream_t st, Graph& g);
+void graph_launch(Graph& g, cudaStream_t st);
+void graph_collect(Graph& g);
+void graph_destroy(Graph& g);
+
 // Block-size autotuner: the first call for a key times each candidate block
 // size on the real arguments (the launch must be idempotent) and caches the
 // fastest; later calls reuse it. While a stream is capturing, an untuned key
@@ -137,6 +160,21 @@ struct Lattice {
     };
     std::map<std::pair<double, double>, Ainv> ainv;  // (m, mu) -> A^{-1}, at most kAinvCache unpinned
     uint64_t ainv_clock = 0;
+    // Work buffers of the solvers (device fields, pinned host scalars), kept
+    // between solves so that a solve allocates nothing once the lattice is warm.
+    struct WsBlock {
+        void* p = nullptr;
+        size_t bytes = 0;
+        bool host = false;
+        bool busy = false;
+        cudaEvent_t ev = nullptr;   // recorded on the last user's stream when returned
+        cudaStream_t st = nullptr;  // that stream
+    };
+    std::vector<WsBlock> ws;
+    bool ws_keep = true;  // false: a returned buffer is freed at once
+    // solves issued on the legacy default stream run on this stream (created on
+    // first use), which CUDA graphs can capture
+    cudaStream_t own_stream = nullptr;
     size_t bytes = 0;                                // device bytes held
     std::mutex mu;  // guards the lazily filled caches when several streams share the lattice
 };
@@ -152,6 +190,15 @@ enum { kAinvCache = 8 };
 
 void* dev_alloc(Lattice* lat, size_t bytes);
 void dev_free(Lattice* lat, void* p, size_t bytes);
+
+// workspace cache of the lattice: a buffer of at least `bytes` (device, or
+// pinned host), ordered after the previous user's work when that ran on
+// another stream; put() returns it (the caller's work on `st` may still run).
+void* ws_get(Lattice& lat, size_t bytes, bool host, cudaStream_t st);
+void ws_put(Lattice& lat, void* p, cudaStream_t st);
+size_t ws_release(Lattice& lat);           // frees the idle buffers; returns the device bytes freed
+size_t ws_idle_bytes(Lattice& lat);        // device bytes held by idle buffers
+Field ws_field(Lattice& lat, int kind, int prec, int nrhs, cudaStream_t st);
 
 // ------------------------------------------------------------ pack / unpack
 void pack_gauge(Lattice& lat, int kind, int prec, int recon, PackedGauge& out, cudaStream_t st);
@@ -177,9 +224,9 @@ struct OpDesc {
 // norm_out: optional per-block partials of |out|^2 (nrhs * blocks).
 // Returns the number of thread blocks per right-hand side (the partial-sum stride).
 int wilson_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int epi, const Field& in,
-                  Field& out, const Field* y, double* norm_out, cudaStream_t st);
+                  Field& out, const Field* y, df* norm_out, cudaStream_t st);
 int hisq_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int epi, double a, const Field& in,
-                Field& out, const Field* y, double* norm_out, cudaStream_t st);
+                Field& out, const Field* y, df* norm_out, cudaStream_t st);
 // site-local out = A_pp^{-1} in (Wilson twisted mass / clover), parity of both fields
 void wilson_ainv_site(Lattice& lat, const OpDesc& op, int parity, int dagger, const Field& in, Field& out,
                       cudaStream_t st);
@@ -188,16 +235,16 @@ void wilson_ainv_site(Lattice& lat, const OpDesc& op, int parity, int dagger, co
 // All BLAS kernels work on whole fields of one parity, per right-hand side.
 // Reductions write per-block partials to `part`, then finalize into dev scalars.
 enum { RED_BLOCKS = 148 * 4, RED_THREADS = 256 };
-void blas_norm2(const Field& x, double* part, cudaStream_t st);          // part[k*RED_BLOCKS + b]
+void blas_norm2(const Field& x, df* part, cudaStream_t st);          // part[k*RED_BLOCKS + b]
 void blas_copy(Field& dst, const Field& src, cudaStream_t st);           // with precision conversion
 void blas_zero(Field& x, cudaStream_t st);
 void blas_axpy_h(Field& y, const double* a_host, const Field& x, cudaStream_t st);  // y += a_k x (host scalars)
 // y = a_k x + b_k y per right-hand side k (host scalars), optional partial |y|^2
-void blas_axpby_h(Field& y, const double* a, const Field& x, const double* b, double* part, cudaStream_t st);
+void blas_axpby_h(Field& y, const double* a, const Field& x, const double* b, df* part, cudaStream_t st);
 // s = b - q, with partial |s|^2
-void blas_xmy_norm(Field& s, const Field& b, const Field& q, double* part, cudaStream_t st);
+void blas_xmy_norm(Field& s, const Field& b, const Field& q, df* part, cudaStream_t st);
 // CG update: alpha_k = sc[k*SC_N + SC_ALPHA]; x += alpha p; s -= alpha q; partial |s|^2
-void blas_cg_xs(Field& x, const Field& p, Field& s, const Field& q, const double* sc, double* part,
+void blas_cg_xs(Field& x, const Field& p, Field& s, const Field& q, const double* sc, df* part,
                 cudaStream_t st);
 // p = r + beta p, beta_k = sc[k*SC_N + SC_BETA]
 void blas_cg_p(Field& p, const Field& r, const double* sc, cudaStream_t st);
@@ -206,13 +253,13 @@ void blas_cg_p(Field& p, const Field& r, const double* sc, cudaStream_t st);
 enum { SC_RR = 0, SC_QQ, SC_SS, SC_RRN, SC_ALPHA, SC_BETA, SC_B2, SC_FROZEN, SC_PP, SC_N };
 enum { FIN_SET = 0, FIN_ALPHA = 1, FIN_BETA = 2 };
 // sum part[k*nblocks ...] (compensated, fixed order) into sc[k*SC_N + slot], or apply `op`
-void blas_finalize(const double* part, int nblocks, int nrhs, double* sc, int slot, int op, cudaStream_t st);
+void blas_finalize(const df* part, int nblocks, int nrhs, double* sc, int slot, int op, cudaStream_t st);
 
 // ----------------------------------------------------------------- solvers
 // Schur operators on resident fields (see solver.cu)
-int schur_wilson(Lattice& lat, const OpDesc& op, int dagger, const Field& in, Field& out, Field& tmp, double* part,
+int schur_wilson(Lattice& lat, const OpDesc& op, int dagger, const Field& in, Field& out, Field& tmp, df* part,
                  cudaStream_t st);
-int schur_hisq(Lattice& lat, const OpDesc& op, double sigma, const Field& in, Field& out, Field& t, double* part_t,
+int schur_hisq(Lattice& lat, const OpDesc& op, double sigma, const Field& in, Field& out, Field& t, df* part_t,
                cudaStream_t st);
 // estimated device bytes of a solve's work fields
 size_t solve_workspace_bytes(const Lattice& lat, const lq_op_params& op, const lq_solve_params& sp, int nrhs);

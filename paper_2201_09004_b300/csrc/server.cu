@@ -129,6 +129,8 @@ void lq_server_s::worker() {
             sp.masses = r->masses.empty() ? nullptr : r->masses.data();
             status = lq_solve(r->req.lat, &r->req.op, &sp, r->req.nrhs, b.data(), x.data(), LQ_HOST,
                               r->info.data(), st);
+            // the admission ledger counts a request's work buffers only while it runs
+            ws_release(r->req.lat->lat);
         }
         {
             std::lock_guard<std::mutex> lk(mu);

@@ -23,20 +23,25 @@
 
 namespace lq {
 
-// device scalars, their pinned host copy and the partial-sum buffer of one solve
+// device scalars, their pinned host copy and the partial-sum buffer of one
+// solve, taken from the lattice's workspace cache
 struct Scalars {
+    Lattice* lat = nullptr;
+    cudaStream_t st = nullptr;
     double* dev = nullptr;
     double* host = nullptr;
-    double* part = nullptr;
+    df* part = nullptr;
     int nrhs = 0;
-    void init(int n, int vh) {
+    void init(Lattice& l, int n, cudaStream_t s) {
+        lat = &l;
+        st = s;
         nrhs = n;
         // hopping kernels write one partial per site block: at least 8 sites per block
-        size_t per = std::max<size_t>((size_t)(vh + 7) / 8, (size_t)RED_BLOCKS);
-        LQ_CUDA(cudaMalloc(&dev, sizeof(double) * SC_N * n));
-        LQ_CUDA(cudaMemset(dev, 0, sizeof(double) * SC_N * n));
-        LQ_CUDA(cudaMalloc(&part, sizeof(double) * per * n));
-        LQ_CUDA(cudaMallocHost(&host, sizeof(double) * SC_N * n));
+        size_t per = std::max<size_t>((size_t)(l.vh + 7) / 8, (size_t)RED_BLOCKS);
+        dev = (double*)ws_get(l, sizeof(double) * SC_N * n, false, s);
+        LQ_CUDA(cudaMemsetAsync(dev, 0, sizeof(double) * SC_N * n, s));
+        part = (df*)ws_get(l, sizeof(df) * per * n, false, s);
+        host = (double*)ws_get(l, sizeof(double) * SC_N * n, true, s);
     }
     void pull(cudaStream_t st) {
         LQ_CUDA(cudaMemcpyAsync(host, dev, sizeof(double) * SC_N * nrhs, cudaMemcpyDeviceToHost, st));
@@ -51,23 +56,25 @@ struct Scalars {
     }
     void fin(int nb, int slot, cudaStream_t st) { blas_finalize(part, nb, nrhs, dev, slot, FIN_SET, st); }
     ~Scalars() {
-        if (dev) cudaFree(dev);
-        if (part) cudaFree(part);
-        if (host) cudaFreeHost(host);
+        if (!lat) return;
+        ws_put(*lat, dev, st);
+        ws_put(*lat, part, st);
+        ws_put(*lat, host, st);
     }
 };
 
-// fields of one solve, freed together
+// fields of one solve, returned together to the lattice's workspace cache
 struct Pool {
     std::vector<Field> owned;
-    int vh;
-    explicit Pool(int v) : vh(v) {}
+    Lattice& lat;
+    cudaStream_t st;
+    Pool(Lattice& l, cudaStream_t s) : lat(l), st(s) {}
     Field get(int kind, int prec, int n) {
-        owned.push_back(field_alloc(kind, prec, n, vh));
+        owned.push_back(ws_field(lat, kind, prec, n, st));
         return owned.back();
     }
     ~Pool() {
-        for (auto& f : owned) field_free(f);
+        for (auto& f : owned) ws_put(lat, f.data, st);
     }
 };
 
@@ -93,7 +100,7 @@ static OpDesc wilson_desc(const lq_op_params& op, int prec, int recon) {
 }
 
 // out = Mhat in (dagger: Mhat^+); tmp holds the odd sites. Returns the blocks of the |out|^2 partials.
-int schur_wilson(Lattice& lat, const OpDesc& op, int dagger, const Field& in, Field& out, Field& tmp, double* part,
+int schur_wilson(Lattice& lat, const OpDesc& op, int dagger, const Field& in, Field& out, Field& tmp, df* part,
                  cudaStream_t st) {
     wilson_dslash(lat, op, 1, dagger, EPI_AINV, in, tmp, nullptr, nullptr, st);
     return wilson_dslash(lat, op, 0, dagger, EPI_XPAY, tmp, out, &in, part, st);
@@ -104,11 +111,12 @@ int schur_wilson(Lattice& lat, const OpDesc& op, int dagger, const Field& in, Fi
 // The iteration keeps alpha and beta on the device; the host reads |s|^2 once
 // per iteration to decide on reliable updates and convergence.
 static CgResult cgnr_mixed(Lattice& lat, const OpDesc& ops, const OpDesc& op64, Field& bhat, Field& x_hi,
-                           const std::vector<double>& tol_abs, double delta, int maxiter, cudaStream_t st) {
+                           const std::vector<double>& tol_abs, double delta, int maxiter, int graph_iters,
+                           cudaStream_t st) {
     const int n = bhat.nrhs;
     const int ps = ops.prec;
     const int px = ps == LQ_F16 ? LQ_F32 : ps;  // the sloppy solution accumulates in at least FP32
-    Pool pool(lat.vh);
+    Pool pool(lat, st);
     const int ph = op64.prec;  // FP64, or double-float for the mixed solvers
     Field s_hi = pool.get(LQ_WILSON_FIELD, ph, n), q64 = pool.get(LQ_WILSON_FIELD, ph, n);
     Field t64 = pool.get(LQ_WILSON_FIELD, ph, n), x_lo = pool.get(LQ_WILSON_FIELD, px, n);
@@ -116,7 +124,7 @@ static CgResult cgnr_mixed(Lattice& lat, const OpDesc& ops, const OpDesc& op64, 
     Field p = pool.get(LQ_WILSON_FIELD, ps, n), q = pool.get(LQ_WILSON_FIELD, ps, n);
     Field t = pool.get(LQ_WILSON_FIELD, ps, n);
     Scalars sc;
-    sc.init(n, lat.vh);
+    sc.init(lat, n, st);
     CgResult res(n);
     std::vector<double> rmax(n, 0.0), ones(n, 1.0);
     std::vector<char> done(n, 0);
@@ -150,37 +158,75 @@ static CgResult cgnr_mixed(Lattice& lat, const OpDesc& ops, const OpDesc& op64, 
     // two pinned slots and an event, and the host waits on the previous one.
     // A reliable update or convergence is therefore decided one iteration late,
     // which costs at most one extra iteration and keeps the GPU busy.
-    double* ring = nullptr;
-    LQ_CUDA(cudaMallocHost(&ring, sizeof(double) * SC_N * n * 2));
+    double* ring = (double*)ws_get(lat, sizeof(double) * SC_N * n * 2, true, st);
     cudaEvent_t ev[2];
     LQ_CUDA(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
     LQ_CUDA(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
     struct Cleanup {
-        double* r; cudaEvent_t* e;
-        ~Cleanup() { cudaFreeHost(r); cudaEventDestroy(e[0]); cudaEventDestroy(e[1]); }
-    } cleanup{ring, ev};
+        Lattice& l; double* r; cudaEvent_t* e; cudaStream_t s;
+        ~Cleanup() { ws_put(l, r, s); cudaEventDestroy(e[0]); cudaEventDestroy(e[1]); }
+    } cleanup{lat, ring, ev, st};
     auto slot = [&](int i) { return ring + (size_t)(i & 1) * SC_N * n; };
-    int it = 0, pending = -1;  // iteration whose scalars are in flight
-    std::vector<char> counted(n, 0);
-    while (!all_done() && it < maxiter) {
-        nb = schur_wilson(lat, ops, 0, p, q, t, sc.part, st);
-        blas_finalize(sc.part, nb, n, sc.dev, 0, FIN_ALPHA, st);
+    // One CG iteration on the device; `dst` (or null) receives the scalars.
+    auto iteration = [&](double* dst) {
+        int nb2 = schur_wilson(lat, ops, 0, p, q, t, sc.part, st);
+        blas_finalize(sc.part, nb2, n, sc.dev, 0, FIN_ALPHA, st);
         blas_cg_xs(x_lo, p, s_lo, q, sc.dev, sc.part, st);
         sc.fin(RED_BLOCKS, SC_SS, st);
-        nb = schur_wilson(lat, ops, 1, s_lo, r, t, sc.part, st);
-        blas_finalize(sc.part, nb, n, sc.dev, 0, FIN_BETA, st);
+        nb2 = schur_wilson(lat, ops, 1, s_lo, r, t, sc.part, st);
+        blas_finalize(sc.part, nb2, n, sc.dev, 0, FIN_BETA, st);
         blas_cg_p(p, r, sc.dev, st);
-        LQ_CUDA(cudaMemcpyAsync(slot(it), sc.dev, sizeof(double) * SC_N * n, cudaMemcpyDeviceToHost, st));
-        LQ_CUDA(cudaEventRecord(ev[it & 1], st));
+        if (dst) LQ_CUDA(cudaMemcpyAsync(dst, sc.dev, sizeof(double) * SC_N * n, cudaMemcpyDeviceToHost, st));
+    };
+    // After the first (eager, autotuning) iteration, blocks of gk iterations
+    // are captured into two CUDA graphs, one per ring slot, and replayed.
+    const int gk = graph_iters < 0 ? 0 : (graph_iters == 0 ? 1 : graph_iters);
+    Graph graphs[2];
+    struct GraphCleanup {
+        Graph* g;
+        ~GraphCleanup() { graph_destroy(g[0]); graph_destroy(g[1]); }
+    } graph_cleanup{graphs};
+    bool use_graphs = gk > 0;
+    int it = 0, launch_no = 0, pending = -1;  // launch whose scalars are in flight
+    while (!all_done() && it < maxiter) {
+        const int gi = launch_no & 1;
+        int steps = 1;
+        if (use_graphs && it > 0 && it + gk <= maxiter) {
+            Graph& g = graphs[gi];
+            if (!g.exec) {
+                bool ok = graph_capture_begin(st);
+                if (ok) {
+                    try {
+                        for (int j = 0; j < gk; j++) iteration(j == gk - 1 ? slot(gi) : nullptr);
+                    } catch (...) {
+                        ok = false;
+                    }
+                    ok = graph_capture_end(st, g) && ok;
+                }
+                if (!ok) use_graphs = false;  // run eagerly from here on
+            } else {
+                graph_collect(g);  // its previous replay finished before the host check of it
+            }
+            if (g.exec) {
+                graph_launch(g, st);
+                steps = gk;
+            } else {
+                iteration(slot(gi));
+            }
+        } else {
+            iteration(slot(gi));
+        }
+        LQ_CUDA(cudaEventRecord(ev[gi], st));
         for (int k = 0; k < n; k++)
             if (!done[k]) {
-                res.iters[k]++;
-                res.applications[k] += 2;
+                res.iters[k] += steps;
+                res.applications[k] += 2 * steps;
             }
         const int prev = pending;
-        pending = it;
-        it++;
-        bool update = it == maxiter;
+        pending = launch_no;
+        launch_no++;
+        it += steps;
+        bool update = it >= maxiter;
         if (prev >= 0) {
             LQ_CUDA(cudaEventSynchronize(ev[prev & 1]));
             const double* hs = slot(prev);
@@ -249,13 +295,13 @@ int solve_wilson(Lattice& lat, const lq_op_params& opp, const lq_solve_params& s
     LQ_CUDA(cudaEventCreate(&e0));
     LQ_CUDA(cudaEventCreate(&e1));
     LQ_CUDA(cudaEventRecord(e0, st));
-    Pool pool(lat.vh);
+    Pool pool(lat, st);
     Field be = pool.get(LQ_WILSON_FIELD, ph, nrhs), bo = pool.get(LQ_WILSON_FIELD, ph, nrhs);
     Field bhat = pool.get(LQ_WILSON_FIELD, ph, nrhs), xe = pool.get(LQ_WILSON_FIELD, ph, nrhs);
     Field xo = pool.get(LQ_WILSON_FIELD, ph, nrhs), te = pool.get(LQ_WILSON_FIELD, ph, nrhs);
     Field to = pool.get(LQ_WILSON_FIELD, ph, nrhs);
     Scalars sc;
-    sc.init(nrhs, lat.vh);
+    sc.init(lat, nrhs, st);
     std::vector<double> ones(nrhs, 1.0);
     int ret = LQ_OK;
     try {
@@ -281,7 +327,7 @@ int solve_wilson(Lattice& lat, const lq_op_params& opp, const lq_solve_params& s
         blas_copy(bhat, be, st);
         blas_axpy_h(bhat, ones.data(), te, st);
 
-        CgResult cr = cgnr_mixed(lat, ops, op64, bhat, xe, tol_abs, delta, maxiter, st);
+        CgResult cr = cgnr_mixed(lat, ops, op64, bhat, xe, tol_abs, delta, maxiter, sp.graph_iters, st);
 
         // x_o = A_oo^{-1} (b_o + H_oe x_e)
         wilson_dslash(lat, op64, 1, 0, EPI_HOP, xe, to, nullptr, nullptr, st);
@@ -342,7 +388,7 @@ static OpDesc hisq_desc(const lq_op_params& op, int prec, int recon) {
 
 // out = sigma in - H_eo H_oe in; t = H_oe in (odd). part_t receives |t|^2 partials,
 // so that (in, out) = sigma |in|^2 + |t|^2 (since -H_eo = H_oe^+).
-int schur_hisq(Lattice& lat, const OpDesc& op, double sigma, const Field& in, Field& out, Field& t, double* part_t,
+int schur_hisq(Lattice& lat, const OpDesc& op, double sigma, const Field& in, Field& out, Field& t, df* part_t,
                cudaStream_t st) {
     int nb = hisq_dslash(lat, op, 1, 0, EPI_HOP, 0.0, in, t, nullptr, part_t, st);
     hisq_dslash(lat, op, 0, 0, EPI_XPAY, sigma, t, out, &in, nullptr, st);
@@ -354,14 +400,14 @@ static CgResult cg_hisq(Lattice& lat, const OpDesc& ops, const OpDesc& op64, dou
                         Field& x_hi, const std::vector<double>& tol_abs, double delta, int maxiter, cudaStream_t st) {
     const int n = b.nrhs;
     const int ps = ops.prec, px = ps == LQ_F16 ? LQ_F32 : ps;
-    Pool pool(lat.vh);
+    Pool pool(lat, st);
     const int ph = op64.prec;
     Field r_hi = pool.get(LQ_STAGGERED_FIELD, ph, n), q64 = pool.get(LQ_STAGGERED_FIELD, ph, n);
     Field t64 = pool.get(LQ_STAGGERED_FIELD, ph, n), x_lo = pool.get(LQ_STAGGERED_FIELD, px, n);
     Field r = pool.get(LQ_STAGGERED_FIELD, ps, n), p = pool.get(LQ_STAGGERED_FIELD, ps, n);
     Field q = pool.get(LQ_STAGGERED_FIELD, ps, n), t = pool.get(LQ_STAGGERED_FIELD, ps, n);
     Scalars sc;
-    sc.init(n, lat.vh);
+    sc.init(lat, n, st);
     CgResult res(n);
     std::vector<double> rr(n), pp(n), rmax(n), a(n), bb(n), ones(n, 1.0);
     std::vector<char> done(n, 0);
@@ -447,13 +493,13 @@ static CgResult cg_hisq(Lattice& lat, const OpDesc& ops, const OpDesc& op64, dou
 static int multishift_hisq(Lattice& lat, const OpDesc& op, const std::vector<double>& sigma, const Field& b,
                            std::vector<Field>& y, double tol_rel, int maxiter, cudaStream_t st) {
     const int n = b.nrhs, ns = (int)sigma.size();
-    Pool pool(lat.vh);
+    Pool pool(lat, st);
     Field r = pool.get(LQ_STAGGERED_FIELD, op.prec, n), q = pool.get(LQ_STAGGERED_FIELD, op.prec, n);
     Field t = pool.get(LQ_STAGGERED_FIELD, op.prec, n);
     std::vector<Field> p;
     for (int i = 0; i < ns; i++) p.push_back(pool.get(LQ_STAGGERED_FIELD, op.prec, n));
     Scalars sc;
-    sc.init(n, lat.vh);
+    sc.init(lat, n, st);
     blas_copy(r, b, st);
     for (int i = 0; i < ns; i++) {
         blas_copy(p[i], b, st);
@@ -569,13 +615,13 @@ int solve_hisq(Lattice& lat, const lq_op_params& opp, const lq_solve_params& sp,
     LQ_CUDA(cudaEventCreate(&e0));
     LQ_CUDA(cudaEventCreate(&e1));
     LQ_CUDA(cudaEventRecord(e0, st));
-    Pool pool(lat.vh);
+    Pool pool(lat, st);
     const int SF = LQ_STAGGERED_FIELD;
     Field be = pool.get(SF, ph, nrhs), bo = pool.get(SF, ph, nrhs), c = pool.get(SF, ph, nrhs);
     Field bh = pool.get(SF, ph, nrhs), xe = pool.get(SF, ph, nrhs), xo = pool.get(SF, ph, nrhs);
     Field te = pool.get(SF, ph, nrhs), to = pool.get(SF, ph, nrhs);
     Scalars sc;
-    sc.init(nrhs, lat.vh);
+    sc.init(lat, nrhs, st);
     int ret = LQ_OK;
     try {
         for (int k = 0; k < nrhs; k++) {

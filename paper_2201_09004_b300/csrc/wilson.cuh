@@ -33,7 +33,7 @@ struct WilsonArgs {
     double m4;              // 4 + m
     double mu;              // twisted mass, already negated for the adjoint
     int nrhs;
-    double* norm_out;       // if non-null: per-block partial sums of |out|^2, per rhs
+    df* norm_out;       // if non-null: per-block partial sums of |out|^2, per rhs
 };
 
 // spin projection h = top two spins of (1 + s g_mu) psi, for psi as cx[4][3]
@@ -226,57 +226,31 @@ __device__ __forceinline__ void ainv_apply(const WilsonArgs& a, int s, cx<T> w[N
     ainv_apply_src<P, NB, T, false>(a.clov, a.g.vh, s, sc, a.dagger, w, out);
 }
 
-// block reduction of per-thread |out|^2 (one value per rhs) into
-// norm_out[(kb+b) * gridDim.x + blockIdx.x]
-template <int NB>
-__device__ __forceinline__ void reduce_norms(const double nrm[NB], double* norm_out, int kb, int nrhs) {
-    __shared__ double red[NB][32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int b = 0; b < NB; b++) {
-        double v = nrm[b];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) red[b][wid] = v;
-    }
-    __syncthreads();
-    if (wid == 0) {
-        const int nw = blockDim.x >> 5;
-#pragma unroll
-        for (int b = 0; b < NB; b++) {
-            double v = lane < nw ? red[b][lane] : 0.0;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if (lane == 0 && kb + b < nrhs) norm_out[(size_t)(kb + b) * gridDim.x + blockIdx.x] = v;
-        }
-    }
-}
-
-// Block reduction when RG consecutive threads share a site, one right-hand side
-// each (NB = 1), or one thread carries NB right-hand sides (RG = 1). The
-// per-block partial of right-hand side k goes to norm_out[k * nsb + sb], sb the
-// site block and nsb the number of site blocks.
+// Block reduction of the per-thread |out|^2 (double-float) when RG consecutive
+// threads share a site, one right-hand side each (NB = 1), or one thread
+// carries NB right-hand sides (RG = 1). The per-block partial of right-hand
+// side k goes to norm_out[k * nsb + sb], sb the site block and nsb the number
+// of site blocks.
 template <int NB, int RG>
-__device__ __forceinline__ void reduce_norms_rg(const double nrm[NB], double* norm_out, int grp, int sb, int nsb,
-                                                int nrhs) {
+__device__ __forceinline__ void reduce_norms_rg(const df nrm[NB], df* norm_out, int grp, int sb, int nsb, int nrhs) {
     static_assert(NB == 1 || RG == 1, "right-hand sides are spread over threads or registers, not both");
-    __shared__ double red[NB * RG][32];
+    __shared__ float2 red[NB * RG][32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int b = 0; b < NB; b++) {
-        double v = nrm[b];
+        df v = nrm[b];
 #pragma unroll
-        for (int o = 16; o >= RG; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane < RG) red[b * RG + lane][wid] = v;
+        for (int o = 16; o >= RG; o >>= 1) v = v + shfl_down_df(v, o);
+        if (lane < RG) red[b * RG + lane][wid] = make_float2(v.hi, v.lo);
     }
     __syncthreads();
     if (wid == 0) {
         const int nw = blockDim.x >> 5;
 #pragma unroll
         for (int q = 0; q < NB * RG; q++) {
-            double v = lane < nw ? red[q][lane] : 0.0;
+            df v = lane < nw ? df(red[q][lane].x, red[q][lane].y) : df(0.f);
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            for (int o = 16; o > 0; o >>= 1) v = v + shfl_down_df(v, o);
             const int k = (grp * RG + (q % RG)) * NB + q / RG;
             if (lane == 0 && k < nrhs) norm_out[(size_t)k * nsb + sb] = v;
         }
@@ -549,9 +523,9 @@ __global__ void __launch_bounds__(256) wilson_dslash_kernel(WilsonArgs a) {
     const int nsb = gridDim.x / ngroups;
     const int s = sb * spb + threadIdx.x / RG;
     const int kb = (grp * RG + threadIdx.x % RG) * NB;
-    double nrm[NB];
+    df nrm[NB];
 #pragma unroll
-    for (int b = 0; b < NB; b++) nrm[b] = 0.0;
+    for (int b = 0; b < NB; b++) nrm[b] = df(0.f);
     // shared-memory copies of the epilogue operands (FP32/FP16, one RHS per thread)
     constexpr bool PF = (NB == 1) && (epi_smem_per_thread<P, EPI>() > 0);
     extern __shared__ __align__(16) unsigned char lq_smem[];
@@ -709,7 +683,7 @@ __global__ void __launch_bounds__(256) wilson_dslash_kernel(WilsonArgs a) {
                 T t = (T)0;
 #pragma unroll
                 for (int q = 0; q < 24; q++) t = fma(v[q], v[q], t);
-                nrm[b] = (double)t;
+                nrm[b] = df_of(t);
             }
             fstore<P, 24, T>(a.out, kb + b, s, v);
         }

@@ -1,0 +1,193 @@
+// wilson_df.cuh -- the Wilson hopping kernel in double-float precision, two
+// threads per site.
+//
+// The FP64-accuracy steps of the mixed solvers (reliable updates, source
+// preparation, reconstruction of the odd sites, the final true residual) run
+// in double-float arithmetic on the FP32 pipes. With one thread per site the
+// kernel holds about 180 registers (a full 4x3 accumulator, a link and a
+// spinor, each real as a hi/lo pair) and only eight warps fit on an SM to hide
+// the neighbour gathers. Here the two threads of a site split the work by
+// half-spinor component (Sec. 2.1: (1 +- g_mu) has rank two): thread h loads
+// spin h of each neighbour and the spin that (1 +- g_mu) couples to it, forms
+// half-spinor component h, multiplies it by the link and accumulates into
+// upper spin h and one lower spin. After the eight hops the pair exchanges
+// partial sums with two-lane shuffles so that thread h holds chiral block h
+// (spins 2h and 2h+1), and applies the site-local epilogue to that 6-vector:
+// block h of A^{-1}, or A y - D psi with block h of the clover term. Each
+// output row is written as soon as it is formed.
+#pragma once
+#include "wilson.cuh"
+
+namespace lq {
+
+typedef cx<df> cd;
+
+__device__ __forceinline__ cd ld_cd(const float4* base, size_t idx) {
+    const float4 c = __ldg(base + idx);
+    return mk(df(c.x, c.y), df(c.z, c.w));
+}
+__device__ __forceinline__ void st_cd(float4* base, size_t idx, cd v) {
+    base[idx] = make_float4(v.r.hi, v.r.lo, v.i.hi, v.i.lo);
+}
+// value of the other thread of the pair (lanes 2g, 2g+1)
+__device__ __forceinline__ cd pair_swap(cd v) {
+    cd o;
+    o.r.hi = __shfl_xor_sync(0xffffffffu, v.r.hi, 1);
+    o.r.lo = __shfl_xor_sync(0xffffffffu, v.r.lo, 1);
+    o.i.hi = __shfl_xor_sync(0xffffffffu, v.i.hi, 1);
+    o.i.lo = __shfl_xor_sync(0xffffffffu, v.i.lo, 1);
+    return o;
+}
+__device__ __forceinline__ df cnorm2(cd v) { return v.r * v.r + v.i * v.i; }
+
+// SITE = true: no hops, w = block h of `in` at the site (out = A^{-1} in).
+template <int EPI, bool SITE>
+__global__ void __launch_bounds__(256, 2) wilson_dslash_df2_kernel(WilsonArgs a) {
+    const int h = threadIdx.x & 1;
+    const int k = blockIdx.y;
+    const int spb = blockDim.x >> 1;
+    const int s_raw = blockIdx.x * spb + (threadIdx.x >> 1);
+    const bool live = s_raw < a.g.vh;
+    const int s = live ? s_raw : a.g.vh - 1;  // a pair past the end computes a valid site, stores nothing
+    const size_t vh = (size_t)a.g.vh;
+    const bool dag = a.dagger != 0;
+    const float4* in = (const float4*)((const char*)a.in.data + (size_t)k * a.in.rhs_bytes);
+
+    cd w[6];  // chiral block h: spins 2h, 2h+1 (index 3 * spin' + colour)
+    if constexpr (SITE) {
+#pragma unroll
+        for (int j = 0; j < 6; j++) w[j] = ld_cd(in, (size_t)(6 * h + j) * vh + s);
+    } else {
+        int c[4];
+        cb_coords(a.g, s, a.parity, c);
+        cd up[3], lo2[3], lo3[3];  // upper spin h, lower spins 2 and 3
+#pragma unroll
+        for (int q = 0; q < 3; q++) up[q] = lo2[q] = lo3[q] = mk(df(0.f), df(0.f));
+#pragma unroll 1
+        for (int hop = 0; hop < 8; hop++) {
+            const int mu = hop >> 1;
+            const bool fwd = (hop & 1) == 0;
+            float bs;
+            const int n = cb_hop(a.g, c, mu, fwd ? 1 : -1, bs);
+            cx<df> U[3][3];
+            load_link<PDF, 18, df>(a.U, fwd ? a.parity : 1 - a.parity, mu, fwd ? s : n, U);
+            // projector (1 + sp g_mu): sp = +-1 forward / backward, flipped for the adjoint
+            const bool neg_sp = fwd ? dag : !dag;
+            // component h couples spin h with spin pb through +-1 or +-i (DeGrand-Rossi)
+            const int pb = mu < 2 ? 3 - h : 2 + h;
+            const bool ci = (mu == 0 || mu == 2);
+            const bool cn = (mu == 1 && h == 0) || (mu == 2 && h == 1);
+            cd hv[3];
+#pragma unroll
+            for (int q = 0; q < 3; q++) {
+                const cd pa = ld_cd(in, (size_t)(h * 3 + q) * vh + n);
+                const cd pp = ld_cd(in, (size_t)(pb * 3 + q) * vh + n);
+                hv[q] = pa + cunit(pp, cn != neg_sp, ci);
+            }
+            cd r[3];
+            if (fwd) su3_mv(U, hv, r);
+            else su3_dmv(U, hv, r);
+            // rebuild: upper spin h gets r; lower spin (3 if to3 else 2) gets +-r or +-i r
+            const bool flip = bs < 0.f;  // time boundary
+            const bool to3 = mu < 2 ? (h == 0) : (h == 1);
+            const bool ei = (mu == 0 || mu == 2);
+            const bool en = mu == 0 || (mu == 1 && h == 0) || (mu == 2 && h == 0);
+#pragma unroll
+            for (int q = 0; q < 3; q++) {
+                const cd rq = flip ? mk(-r[q].r, -r[q].i) : r[q];
+                up[q] = up[q] + rq;
+                const cd e = cunit(rq, en != neg_sp, ei);
+                if (to3) lo3[q] = lo3[q] + e;
+                else lo2[q] = lo2[q] + e;
+            }
+        }
+        // thread 0 takes the partner's upper spin (spin 1); thread 1 the partner's lower spins
+        const df half(0.5f);
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            const cd ra = pair_swap(h ? up[q] : lo2[q]);
+            const cd rb = pair_swap(lo3[q]);
+            const cd w0 = h ? lo2[q] + ra : up[q];
+            const cd w1 = h ? lo3[q] + rb : ra;
+            w[q] = mk(half * w0.r, half * w0.i);
+            w[3 + q] = mk(half * w1.r, half * w1.i);
+        }
+    }
+
+    float4* out = (float4*)((char*)a.out.data + (size_t)k * a.out.rhs_bytes);
+    df nrm(0.f);
+    if constexpr (EPI == EPI_HOP) {
+#pragma unroll
+        for (int i = 0; i < 6; i++) {
+            if (live) st_cd(out, (size_t)(6 * h + i) * vh + s, w[i]);
+            nrm = nrm + cnorm2(w[i]);
+        }
+    } else if constexpr (EPI == EPI_AINV) {
+        if (a.has_clover) {
+            // rows of block h of A^{-1} (36 complex, row-major); the adjoint reads the transpose, conjugated
+            const float4* A = (const float4*)a.clov;
+#pragma unroll 1
+            for (int i = 0; i < 6; i++) {
+                cd acc = mk(df(0.f), df(0.f));
+#pragma unroll
+                for (int j = 0; j < 6; j++) {
+                    const int e = dag ? h * 36 + j * 6 + i : h * 36 + i * 6 + j;
+                    const cd m = ld_cd(A, (size_t)e * vh + s);
+                    if (dag) cjmac(acc, m, w[j]);
+                    else cmac(acc, m, w[j]);
+                }
+                if (live) st_cd(out, (size_t)(6 * h + i) * vh + s, acc);
+                nrm = nrm + cnorm2(acc);
+            }
+        } else {
+            // A^{-1} = ((4+m) - i chi mu) / ((4+m)^2 + mu^2), chi = +1 on block 0, -1 on block 1
+            const double inv = 1.0 / (a.m4 * a.m4 + a.mu * a.mu);
+            const cd f = mk(df(a.m4 * inv), df((h ? 1.0 : -1.0) * a.mu * inv));
+#pragma unroll
+            for (int i = 0; i < 6; i++) {
+                const cd o = f * w[i];
+                if (live) st_cd(out, (size_t)(6 * h + i) * vh + s, o);
+                nrm = nrm + cnorm2(o);
+            }
+        }
+    } else {  // EPI_XPAY: out = ((4+m) + i chi mu + C) y - w on block h
+        const float4* yb = (const float4*)((const char*)a.y.data + (size_t)k * a.y.rhs_bytes);
+        cd yv[6];
+#pragma unroll
+        for (int j = 0; j < 6; j++) yv[j] = ld_cd(yb, (size_t)(6 * h + j) * vh + s);
+        const cd f = mk(df(a.m4), df((h ? -1.0 : 1.0) * a.mu));
+        // C block h: 6 real diagonal entries (3 chunks) then the 15 upper entries (row-major, i < j)
+        const float4* C = (const float4*)a.clov;
+        const bool clov = a.has_clover != 0;
+#pragma unroll 1
+        for (int i = 0; i < 6; i++) {
+            df di(0.f);
+            if (clov) {
+                const float4 dc = __ldg(C + (size_t)(18 * h + i / 2) * vh + s);
+                di = (i & 1) ? df(dc.z, dc.w) : df(dc.x, dc.y);
+            }
+            cd acc = mk(df(0.f), df(0.f));
+#pragma unroll
+            for (int j = 0; j < 6; j++) {
+                if (j == i) {
+                    cmac(acc, mk(f.r + di, f.i), yv[j]);
+                    acc = acc - w[j];
+                } else if (clov) {
+                    const int lo = j < i ? j : i, hi = j < i ? i : j;
+                    const int q = lo * 5 - lo * (lo - 1) / 2 + (hi - lo - 1);
+                    const cd m = ld_cd(C, (size_t)(18 * h + 3 + q) * vh + s);
+                    if (i < j) cmac(acc, m, yv[j]);
+                    else cjmac(acc, m, yv[j]);
+                }
+            }
+            if (live) st_cd(out, (size_t)(6 * h + i) * vh + s, acc);
+            nrm = nrm + cnorm2(acc);
+        }
+    }
+    if (a.norm_out) {
+        const df v[1] = {live ? nrm : df(0.f)};
+        reduce_norms_rg<1, 1>(v, a.norm_out, k, blockIdx.x, gridDim.x, a.nrhs);
+    }
+}
+
+}  // namespace lq

@@ -35,7 +35,7 @@ STATUS_NAMES = {0: "LQ_OK", 1: "LQ_EINVAL", 2: "LQ_ENOMEM", 3: "LQ_ENOTCONV", 4:
 
 # every function lq.h declares (checked by the CPU test of the boundary)
 EXPORTS = [
-    "lq_last_error", "lq_create_lattice", "lq_destroy_lattice", "lq_lattice_bytes", "lq_load_gauge",
+    "lq_last_error", "lq_create_lattice", "lq_destroy_lattice", "lq_lattice_bytes", "lq_lattice_release_workspace", "lq_load_gauge",
     "lq_load_clover", "lq_dslash_apply", "lq_operator_apply", "lq_solve", "lq_field_create",
     "lq_field_destroy", "lq_field_import", "lq_field_export", "lq_dslash_field", "lq_schur_field",
     "lq_profile_enable", "lq_profile_reset", "lq_profile_query", "lq_launch_count", "lq_server_create",
@@ -57,7 +57,8 @@ class OpParams(ctypes.Structure):
 class SolveParams(ctypes.Structure):
     _fields_ = [("solver", ctypes.c_int), ("tol", ctypes.c_double), ("delta", ctypes.c_double),
                 ("maxiter", ctypes.c_int), ("prec_sloppy", ctypes.c_int), ("recon_sloppy", ctypes.c_int),
-                ("nshift", ctypes.c_int), ("masses", ctypes.POINTER(ctypes.c_double))]
+                ("nshift", ctypes.c_int), ("masses", ctypes.POINTER(ctypes.c_double)),
+                ("graph_iters", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -132,8 +133,9 @@ def op_params(action, m, mu=0.0, c_sw=0.0, c_naik=-1.0 / 24.0):
 
 
 def solve_params(solver=MIXED_CGNR, tol=1e-10, delta=0.1, maxiter=100000, prec_sloppy=F32, recon_sloppy=R12,
-                 masses=None):
-    sp = SolveParams(int(solver), float(tol), float(delta), int(maxiter), int(prec_sloppy), int(recon_sloppy), 0, None)
+                 masses=None, graph_iters=0):
+    sp = SolveParams(int(solver), float(tol), float(delta), int(maxiter), int(prec_sloppy), int(recon_sloppy), 0, None,
+                     int(graph_iters))
     if masses is not None:
         arr = (ctypes.c_double * len(masses))(*[float(m) for m in masses])
         sp.nshift = len(masses)
@@ -173,6 +175,12 @@ class Lattice:
     def device_bytes(self):
         b = ctypes.c_size_t()
         _check(lib().lq_lattice_bytes(self.h, ctypes.byref(b)))
+        return b.value
+
+    def release_workspace(self):
+        """Frees the idle solver work buffers kept between solves; returns the device bytes freed."""
+        b = ctypes.c_size_t()
+        _check(lib().lq_lattice_release_workspace(self.h, ctypes.byref(b)))
         return b.value
 
     def load_gauge(self, kind, links):

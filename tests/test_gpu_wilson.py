@@ -164,6 +164,60 @@ def test_solve_clover_mixed_multi_rhs(L, orc, prec):
     assert rel_err(x1[0], xs[1]) < 1e-8
 
 
+def test_workspace_kept_between_solves(L, orc):
+    """The work buffers a solve takes stay with the lattice: a second solve
+    allocates nothing more and returns bit-identical solutions (the reductions
+    run in a fixed order), on the same stream and on another one; releasing
+    them frees device memory and the next solve is unchanged."""
+    import torch
+    dims = (4, 4, 6, 8)
+    lat, U = make(L, dims, 106, c_sw=1.05)
+    op = L.op_params(L.WILSON_TM_CLOVER, 0.05, 0.01, c_sw=1.05)
+    b = synth.z2_source(dims, 206).numpy()
+    sp = L.solve_params(solver=L.MIXED_CGNR, tol=1e-10, prec_sloppy=L.F16)
+    x1, _ = lat.solve(op, sp, [b])
+    held = lat.device_bytes()
+    x2, _ = lat.solve(op, sp, [b])
+    assert lat.device_bytes() == held
+    assert np.array_equal(x1[0], x2[0])
+    side = torch.cuda.Stream()
+    x3, _ = lat.solve(op, sp, [b], stream=side)
+    torch.cuda.synchronize()
+    assert lat.device_bytes() == held
+    assert np.array_equal(x1[0], x3[0])
+    freed = lat.release_workspace()
+    assert freed > 0 and lat.device_bytes() == held - freed
+    x4, _ = lat.solve(op, sp, [b])
+    assert np.array_equal(x1[0], x4[0])
+    C = orc.clover(dims, U, 1.05)
+    assert true_residual(orc, dims, U, C, 0.05, 0.01, b, x4[0]) <= 1e-10
+
+
+def test_graph_replay_matches_eager_launches(L, orc):
+    """CG iterations replayed from CUDA graphs give the same solution, bit for
+    bit, as eager launches (same kernels, same order), and the launch counter
+    counts every replayed kernel. Several iterations per graph converge too."""
+    dims = (4, 4, 6, 8)
+    lat, U = make(L, dims, 107, c_sw=1.05)
+    C = orc.clover(dims, U, 1.05)
+    op = L.op_params(L.WILSON_TM_CLOVER, 0.05, 0.01, c_sw=1.05)
+    b = synth.z2_source(dims, 207).numpy()
+    res = {}
+    for gk in (-1, 0, 3):
+        sp = L.solve_params(solver=L.MIXED_CGNR, tol=1e-10, prec_sloppy=L.F16, graph_iters=gk)
+        lat.solve(op, sp, [b])  # tunes
+        n0 = L.launch_count()
+        xs, info = lat.solve(op, sp, [b])
+        res[gk] = (xs[0], info[0], L.launch_count() - n0)
+    x_e, i_e, n_e = res[-1]
+    x_g, i_g, n_g = res[0]
+    assert np.array_equal(x_e, x_g)
+    assert i_e["iters"] == i_g["iters"] and n_e == n_g
+    x_3, i_3, _ = res[3]
+    assert i_3["status"] == 0 and i_3["iters"] <= i_e["iters"] + 8
+    assert true_residual(orc, dims, U, C, 0.05, 0.01, b, x_3) <= 1e-10
+
+
 def test_solve_device_arrays_and_2x4(L, orc):
     import torch
     dims = (2, 2, 2, 2)
@@ -235,7 +289,7 @@ def test_full_size_hopping_term_sampled_sites(L, orc):
             assert rel_err(got[sites], ref) < TOL[prec], (prec, p)
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 @pytest.mark.parametrize("nrhs", [2, 3, 4, 5])
 def test_multi_rhs_operator_equals_single(L, prec, nrhs):
     """The fused multi-right-hand-side kernels (NB = 2 / 4 per thread, ragged
