@@ -54,8 +54,9 @@ BYTES_PER_SITE = {
 }
 FLOPS_PER_SITE = {"hop": 1320, "ainv": 1320 + 2 * 6 * 6 * 8, "xpay": 1320 + 2 * 36 * 8 + 48}
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of the
-# benchmark configuration (profiles/); None until captured for the current kernel.
-NCU_TRAFFIC = {}
+# benchmark configuration (profiles/wilson_dslash_f16_ainv_24x24x24x64.md); set back to
+# None whenever the kernel changes after the capture.
+NCU_TRAFFIC = {"wilson_dslash_f16_ainv": 255_320_000}
 
 REASONS = {
     0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap", 0x8: "hw_slowdown",
@@ -343,9 +344,11 @@ def run_multirhs(args):
     lib.profile_enable(False)
     tts = e0.elapsed_time(e1) * 1e-3
     vh = int(np.prod(dims)) // 2
-    # bytes per site of one multi-RHS launch with NB = 4 right-hand sides per thread
-    bps = {"wilson_dslash_f16_ainv": 4 * 52 + 8 * 24 + (144 * 2 + 4) + 4 * 52,
-           "wilson_dslash_f16_xpay": 4 * 52 + 8 * 24 + (72 * 2 + 4) + 4 * 52 + 4 * 52}
+    # algorithmic bytes per site of one launch over the 12 right-hand sides of a call:
+    # links and the clover (inverse) block once, spinors per right-hand side
+    n = len(srcs)
+    bps = {"wilson_dslash_f16_ainv": n * 52 + 8 * 24 + (144 * 2 + 4) + n * 52,
+           "wilson_dslash_f16_xpay": n * 52 + 8 * 24 + (72 * 2 + 4) + n * 52 + n * 52}
     kern = _kernel_table(list(bps) + ["wilson_dslash_f32x2_ainv", "wilson_dslash_f32x2_xpay"], vh, bps)
     sp64 = lib.solve_params(solver=lib.CGNR, tol=TOL, prec_sloppy=lib.F64)
     e0, e1 = _events()
