@@ -259,6 +259,17 @@ int lq_profile_query(const char* name, int64_t* launches, double* total_ms);
 /* number of kernel launches the library issued since the last reset */
 int64_t lq_launch_count(void);
 
+/* Autotuner controls (the tuner times each candidate launch configuration of a
+ * kernel on its first call for a given shape and keeps the fastest).
+ * lq_tune_reset forgets every tuned choice. lq_tune_force(code) restricts later
+ * tuning to the candidate with that code where a kernel offers it (code = block
+ * size; 1000 + block size for the FP32/FP16 Wilson kernel built with its
+ * registers capped at 85 per thread; 2000 + block size for its single-RHS build
+ * with two hops of gathers in flight); 0 lifts the restriction. For tests and diagnostics;
+ * not part of the paper's method. */
+int lq_tune_reset(void);
+int lq_tune_force(int code);
+
 /* ----------------------------------------------------------------- serving */
 
 /* A request server for continuous batching of solves: requests are queued,

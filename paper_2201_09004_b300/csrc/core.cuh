@@ -243,15 +243,31 @@ __device__ __forceinline__ void load_reals(const void* base, int stride, int s, 
     }
 }
 
-// load the reals of chunk k only (RPC of them); SMEM: base is a shared-memory copy
-template <int P, int NR, typename T, bool SMEM = false>
+// FP16 chunk to its integer codes (the caller applies the scale)
+template <int NR, typename T>
+__device__ __forceinline__ void unpack_codes16(const typename Layout<P16, NR>::C& c, T* v) {
+    typedef Layout<P16, NR> Lay;
+    if constexpr (Lay::RPC == 8) {
+        v[0] = (T)s16lo(c.x); v[1] = (T)s16hi(c.x); v[2] = (T)s16lo(c.y); v[3] = (T)s16hi(c.y);
+        v[4] = (T)s16lo(c.z); v[5] = (T)s16hi(c.z); v[6] = (T)s16lo(c.w); v[7] = (T)s16hi(c.w);
+    } else if constexpr (Lay::RPC == 4) {
+        v[0] = (T)s16lo(c.x); v[1] = (T)s16hi(c.x); v[2] = (T)s16lo(c.y); v[3] = (T)s16hi(c.y);
+    } else {
+        v[0] = (T)s16lo(c); v[1] = (T)s16hi(c);
+    }
+}
+
+// load the reals of chunk k only (RPC of them); SMEM: base is a shared-memory copy;
+// CODES: FP16 entries come back as integer codes, unscaled
+template <int P, int NR, typename T, bool SMEM = false, bool CODES = false>
 __device__ __forceinline__ void load_chunk(const void* base, int stride, int s, int k, float scale, T* v) {
     typedef Layout<P, NR> Lay;
     const typename Lay::C* b = (const typename Lay::C*)base;
     typename Lay::C c;
     if constexpr (SMEM) c = b[(size_t)k * stride + s];
     else c = __ldg(&b[(size_t)k * stride + s]);
-    unpack_chunk<P, NR, T>(c, scale * (1.f / 32767.f), v);
+    if constexpr (P == P16 && CODES) unpack_codes16<NR, T>(c, v);
+    else unpack_chunk<P, NR, T>(c, scale * (1.f / 32767.f), v);
 }
 
 // ------------------------------------------------------- async copies (cp.async)

@@ -23,22 +23,35 @@ static int site_blocks(int vh, int block, int rg) {
 }
 
 // ------------------------------------------------------------------ Wilson
-template <int P, int R, int EPI, int RG>
+template <int P, int R, int EPI, int RG, int MINB = 1, bool DEEP = false>
 static void wl(const char* name, WilsonArgs a, int block, cudaStream_t st) {
     const int ngroups = (a.nrhs + RG - 1) / RG;
     dim3 grid(site_blocks(a.g.vh, block, RG) * ngroups);
     const size_t smem = epi_smem_bytes<P, EPI>(block, RG);
-    launch_smem(name, wilson_dslash_kernel<P, R, EPI, 1, RG>, grid, dim3(block), smem, st, a);
+    launch_smem(name, wilson_dslash_kernel<P, R, EPI, 1, RG, MINB, DEEP>, grid, dim3(block), smem, st, a);
 }
 
+// tuning codes of the FP32/FP16 kernels: a block size; kCapped + block size for
+// the build whose registers are capped at 85 per thread; kDeep + block size for
+// the single-RHS build with two hops of gathers in flight (at most 128 registers)
+enum { kCapped = 1000, kDeep = 2000 };
+
 template <int P, int R, int EPI>
-static void wl_nb(const char* name, WilsonArgs a, int rg, int block, cudaStream_t st) {
+static void wl_nb(const char* name, WilsonArgs a, int rg, int cfg, cudaStream_t st) {
     if constexpr (P == P64 || P == PDF) {
-        wl<P, R, EPI, 1>(name, a, block, st);
+        wl<P, R, EPI, 1>(name, a, cfg, st);
     } else {
-        if (rg == 4) wl<P, R, EPI, 4>(name, a, block, st);
-        else if (rg == 2) wl<P, R, EPI, 2>(name, a, block, st);
-        else wl<P, R, EPI, 1>(name, a, block, st);
+        const int variant = cfg / 1000, block = cfg % 1000;
+        if (rg == 4) {
+            if (variant == 1) wl<P, R, EPI, 4, 3>(name, a, block, st);
+            else wl<P, R, EPI, 4>(name, a, block, st);
+        } else if (rg == 2) {
+            wl<P, R, EPI, 2>(name, a, block, st);
+        } else {
+            if (variant == 1) wl<P, R, EPI, 1, 3>(name, a, block, st);
+            else if (variant == 2) wl<P, R, EPI, 1, 2, true>(name, a, block, st);
+            else wl<P, R, EPI, 1>(name, a, block, st);
+        }
     }
 }
 
@@ -91,7 +104,7 @@ int wilson_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int ep
     }
     const int nb = (op.prec == LQ_F32 || op.prec == LQ_F16) ? pick_rg(a.nrhs) : 1;
     const char* name = wname(op.prec, epi);
-    auto run = [&](int block) {
+    auto run = [&](int block) {  // block: a tuning code (see wl_nb)
         if (op.prec == LQ_F64) {
             if (op.recon == 18) wl_epi<P64, 18>(name, a, epi, nb, block, st);
             else wl_epi<P64, 12>(name, a, epi, nb, block, st);
@@ -110,8 +123,14 @@ int wilson_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int ep
     std::string key = std::string(name) + "/r" + std::to_string(op.recon) + "/nb" + std::to_string(nb) + "/v" +
                       std::to_string(lat.vh) + "/c" + std::to_string(a.has_clover) + "/n" +
                       std::to_string(norm_out != nullptr);
-    int block = tuned_block(key, st, run);
-    run(block);
+    std::vector<int> cand = {64, 128, 256};
+    if ((op.prec == LQ_F32 || op.prec == LQ_F16) && nb != 2)
+        for (int b : {64, 128, 256}) cand.push_back(kCapped + b);
+    if ((op.prec == LQ_F32 || op.prec == LQ_F16) && nb == 1)
+        for (int b : {64, 128}) cand.push_back(kDeep + b);
+    int cfg = tuned_block(key, st, run, cand);
+    run(cfg);
+    const int block = cfg % 1000;
     return site_blocks(lat.vh, block, op.prec == LQ_F32X2 ? 2 : nb);
 }
 
@@ -214,7 +233,7 @@ int hisq_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int epi,
                       std::to_string(lat.vh) + "/n" + std::to_string(norm_out != nullptr);
     int block = tuned_block(key, st, run);
     run(block);
-    return site_blocks(lat.vh, block, op.prec == LQ_F32X2 ? 2 : nb);
+    return site_blocks(lat.vh, block, nb);
 }
 
 }  // namespace lq

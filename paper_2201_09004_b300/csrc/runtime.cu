@@ -1,7 +1,10 @@
 // runtime.cu -- errors, launch bookkeeping, profiling events, autotuner, device
 // memory and fields.
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <mutex>
 #include <unordered_map>
@@ -180,6 +183,7 @@ void opt_in_smem(const void* kernel, size_t bytes) {
 // ------------------------------------------------------------------- tuner
 static std::mutex g_tune_mu;
 static std::unordered_map<std::string, int> g_tuned;
+static std::atomic<int> g_tune_force{0};
 
 int num_sms() {
     static int n = 0;
@@ -192,14 +196,17 @@ int num_sms() {
     return n;
 }
 
-int tuned_block(const std::string& key, cudaStream_t st, const std::function<void(int)>& run) {
+int tuned_block(const std::string& key, cudaStream_t st, const std::function<void(int)>& run,
+                const std::vector<int>& candidates) {
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tuned.find(key);
         if (it != g_tuned.end()) return it->second;
     }
     if (stream_capturing(st)) return 128;
-    static const int cand[] = {64, 128, 256};
+    std::vector<int> cand = candidates;
+    const int forced = g_tune_force.load();
+    if (forced && std::find(cand.begin(), cand.end(), forced) != cand.end()) cand = {forced};
     cudaEvent_t a, b;
     LQ_CUDA(cudaEventCreate(&a));
     LQ_CUDA(cudaEventCreate(&b));
@@ -220,6 +227,8 @@ int tuned_block(const std::string& key, cudaStream_t st, const std::function<voi
             LQ_CUDA(cudaEventSynchronize(b));
             float ms = 0.f;
             LQ_CUDA(cudaEventElapsedTime(&ms, a, b));
+            static const bool log = getenv("LQ_TUNE_LOG") != nullptr;  // diagnostics: every candidate's time
+            if (log) fprintf(stderr, "lq tune %s candidate %d: %.2f us\n", key.c_str(), bs, ms * 1e3f / 3.f);
             if (ms < best_ms) {
                 best_ms = ms;
                 best = bs;
@@ -443,3 +452,15 @@ extern "C" int lq_profile_query(const char* name, int64_t* launches, double* tot
 }
 
 extern "C" int64_t lq_launch_count(void) { return g_launches.load(); }
+
+extern "C" int lq_tune_reset(void) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned.clear();
+    return LQ_OK;
+}
+
+extern "C" int lq_tune_force(int code) {
+    if (code < 0) return LQ_EINVAL;
+    g_tune_force.store(code);
+    return LQ_OK;
+}

@@ -96,11 +96,12 @@ void graph_launch(Graph& g, cudaStream_t st);
 void graph_collect(Graph& g);
 void graph_destroy(Graph& g);
 
-// Block-size autotuner: the first call for a key times each candidate block
-// size on the real arguments (the launch must be idempotent) and caches the
-// fastest; later calls reuse it. While a stream is capturing, an untuned key
-// falls back to 128 threads.
-int tuned_block(const std::string& key, cudaStream_t st, const std::function<void(int)>& run);
+// Launch autotuner: the first call for a key times each candidate (a block
+// size, or a code of the caller's for block size and kernel variant) on the real
+// arguments (the launch must be idempotent) and caches the fastest; later calls
+// reuse it. While a stream is capturing, an untuned key falls back to 128.
+int tuned_block(const std::string& key, cudaStream_t st, const std::function<void(int)>& run,
+                const std::vector<int>& candidates = {64, 128, 256});
 int num_sms();
 
 // ------------------------------------------------------------------- fields

@@ -154,14 +154,31 @@ __host__ __device__ constexpr int offd_col(int q) {
 // out_b += C_b w_b for both chiral blocks, C packed per block as 6 real
 // diagonal entries then the 15 upper off-diagonal entries (row-major, i<j).
 // The record is read from base[k * stride + s] (global, or a shared-memory copy).
+// FP16: the entries are decoded to their integer codes and the site's scale
+// (norm / 32767) multiplies the 24 reals of w once instead of every entry
+// (w is scaled in place: callers pass an operand they no longer need).
+template <int P, int NB, typename T>
+__device__ __forceinline__ void scale_codes16(float sc, cx<T> w[NB][4][3]) {
+    if constexpr (P == P16) {
+        const T f = (T)(sc * (1.f / 32767.f));
+#pragma unroll
+        for (int b = 0; b < NB; b++)
+#pragma unroll
+            for (int sp = 0; sp < 4; sp++)
+#pragma unroll
+                for (int q = 0; q < 3; q++) w[b][sp][q] = f * w[b][sp][q];
+    }
+}
+
 template <int P, int NB, typename T, bool SMEM = false>
 __device__ __forceinline__ void clover_apply_src(const void* base, int stride, int s, float sc, cx<T> w[NB][4][3],
                                                  cx<T> out[NB][4][3]) {
     typedef Layout<P, 72> Lay;
+    scale_codes16<P, NB, T>(sc, w);
 #pragma unroll
     for (int k = 0; k < Lay::NC; k++) {
         T v[Lay::RPC];
-        load_chunk<P, 72, T, SMEM>(base, stride, s, k, sc, v);
+        load_chunk<P, 72, T, SMEM, true>(base, stride, s, k, sc, v);
 #pragma unroll
         for (int u = 0; u < Lay::RPC / 2; u++) {
             const int r = k * Lay::RPC + 2 * u;  // real index of this pair
@@ -198,10 +215,11 @@ template <int P, int NB, typename T, bool SMEM = false>
 __device__ __forceinline__ void ainv_apply_src(const void* base, int stride, int s, float sc, int dagger,
                                                cx<T> w[NB][4][3], cx<T> out[NB][4][3]) {
     typedef Layout<P, 144> Lay;
+    scale_codes16<P, NB, T>(sc, w);  // w scaled in place, entries as integer codes
 #pragma unroll
     for (int k = 0; k < Lay::NC; k++) {
         T v[Lay::RPC];
-        load_chunk<P, 144, T, SMEM>(base, stride, s, k, sc, v);
+        load_chunk<P, 144, T, SMEM, true>(base, stride, s, k, sc, v);
 #pragma unroll
         for (int u = 0; u < Lay::RPC / 2; u++) {
             const int e = (k * Lay::RPC) / 2 + u;
@@ -427,14 +445,21 @@ __device__ __forceinline__ void process_hop(const WilsonArgs& a, const HopRaw<P,
     constexpr bool FWD = (H & 1) == 0;
     typedef Layout<P, 24> LS;
     typedef Layout<P, R> LU;
+    // FP16: spinor and link stay in integer codes (value / scale); the two scales
+    // and the boundary sign multiply the 12 reals of the rotated half spinor once
     T v[24];
-    const float fs = (P == P16) ? h.n * (1.f / 32767.f) : 1.f;
 #pragma unroll
-    for (int k = 0; k < LS::NC; k++) unpack_chunk<P, 24, T>(h.sp[k], fs, v + k * LS::RPC);
+    for (int k = 0; k < LS::NC; k++) {
+        if constexpr (P == P16) unpack_codes16<24, T>(h.sp[k], v + k * LS::RPC);
+        else unpack_chunk<P, 24, T>(h.sp[k], 1.f, v + k * LS::RPC);
+    }
     T lv[R];
     const float fu = a.U.scale * (1.f / 32767.f);
 #pragma unroll
-    for (int k = 0; k < LU::NC; k++) unpack_chunk<P, R, T>(h.u[k], fu, lv + k * LU::RPC);
+    for (int k = 0; k < LU::NC; k++) {
+        if constexpr (P == P16) unpack_codes16<R, T>(h.u[k], lv + k * LU::RPC);
+        else unpack_chunk<P, R, T>(h.u[k], 1.f, lv + k * LU::RPC);
+    }
     cx<T> U[3][3];
 #pragma unroll
     for (int r = 0; r < 2; r++)
@@ -447,6 +472,10 @@ __device__ __forceinline__ void process_hop(const WilsonArgs& a, const HopRaw<P,
         U[2][0] = cj(U[0][1] * U[1][2] - U[0][2] * U[1][1]);
         U[2][1] = cj(U[0][2] * U[1][0] - U[0][0] * U[1][2]);
         U[2][2] = cj(U[0][0] * U[1][1] - U[0][1] * U[1][0]);
+        if constexpr (P == P16) {  // conj(row0 x row1) of codes carries the scale twice
+#pragma unroll
+            for (int q = 0; q < 3; q++) U[2][q] = (T)fu * U[2][q];
+        }
     }
     cx<T> ps[4][3], h0[3], h1[3], r0[3], r1[3];
     to_spinor(v, ps);
@@ -459,7 +488,11 @@ __device__ __forceinline__ void process_hop(const WilsonArgs& a, const HopRaw<P,
         su3_dmv(U, h0, r0);
         su3_dmv(U, h1, r1);
     }
-    if constexpr (MU == 3) {
+    if constexpr (P == P16) {
+        const T sg = (T)(h.n * (1.f / 32767.f) * fu * (MU == 3 ? h.bs : 1.f));
+#pragma unroll
+        for (int k = 0; k < 3; k++) { r0[k] = sg * r0[k]; r1[k] = sg * r1[k]; }
+    } else if constexpr (MU == 3) {
         const T sg = (T)h.bs;
 #pragma unroll
         for (int k = 0; k < 3; k++) { r0[k] = sg * r0[k]; r1[k] = sg * r1[k]; }
@@ -480,6 +513,23 @@ __device__ __forceinline__ void hops_pipelined(const WilsonArgs& a, const int c[
     fetch_hop<5>(a, c, s, k0, B); process_hop<4>(a, A, sf, acc);
     fetch_hop<6>(a, c, s, k0, A); process_hop<5>(a, B, sf, acc);
     fetch_hop<7>(a, c, s, k0, B); process_hop<6>(a, A, sf, acc);
+    process_hop<7>(a, B, sf, acc);
+}
+
+// the same with the gathers of two hops ahead in flight (three raw buffers)
+template <int P, int R, typename T>
+__device__ __forceinline__ void hops_pipelined2(const WilsonArgs& a, const int c[4], int s, int k0, T sf,
+                                                cx<T> acc[4][3]) {
+    HopRaw<P, R> A, B, C;
+    fetch_hop<0>(a, c, s, k0, A);
+    fetch_hop<1>(a, c, s, k0, B);
+    fetch_hop<2>(a, c, s, k0, C); process_hop<0>(a, A, sf, acc);
+    fetch_hop<3>(a, c, s, k0, A); process_hop<1>(a, B, sf, acc);
+    fetch_hop<4>(a, c, s, k0, B); process_hop<2>(a, C, sf, acc);
+    fetch_hop<5>(a, c, s, k0, C); process_hop<3>(a, A, sf, acc);
+    fetch_hop<6>(a, c, s, k0, A); process_hop<4>(a, B, sf, acc);
+    fetch_hop<7>(a, c, s, k0, B); process_hop<5>(a, C, sf, acc);
+    process_hop<6>(a, A, sf, acc);
     process_hop<7>(a, B, sf, acc);
 }
 
@@ -509,13 +559,17 @@ __host__ __device__ constexpr size_t epi_smem_bytes(int block, int rg) {
                      4 * ((size_t)(block / rg) + block);
 }
 
+
 // Grid: blocks are ordered site block major, right-hand-side group minor, so that
 // the groups of one site block run together and share links and clover records
 // through L2. Within a block, RG consecutive threads take one site and one
 // right-hand side each (their link and clover loads are the same addresses and
 // are served once); NB > 1 keeps NB right-hand sides in one thread's registers.
-template <int P, int R, int EPI, int NB, int RG = 1>
-__global__ void __launch_bounds__(256) wilson_dslash_kernel(WilsonArgs a) {
+// MINB: minimum resident blocks of 256 threads the compiler must allow (1, or 3
+// to cap the registers at 85 per thread for more warps in flight). DEEP: the
+// single-RHS FP32/FP16 hops keep two hops of gathers in flight instead of one.
+template <int P, int R, int EPI, int NB, int RG = 1, int MINB = 1, bool DEEP = false>
+__global__ void __launch_bounds__(256, MINB) wilson_dslash_kernel(WilsonArgs a) {
     typedef typename RealT<P>::T T;
     const int spb = blockDim.x / RG;                       // sites per block
     const int ngroups = (a.nrhs + RG * NB - 1) / (RG * NB);
@@ -534,7 +588,7 @@ __global__ void __launch_bounds__(256) wilson_dslash_kernel(WilsonArgs a) {
     typedef typename Layout<P, 24>::C CY;
     const int g = threadIdx.x / RG;   // site slot within the block
     unsigned char* sm_rec = lq_smem;  // clover / inverse record per site slot, chunk-major
-    unsigned char* sm_y = lq_smem + (size_t)epi_rec_bytes<P, EPI>() * spb;
+    unsigned char* sm_y = sm_rec + (size_t)epi_rec_bytes<P, EPI>() * spb;
     float* sm_norm = (float*)(sm_y + (size_t)epi_y_bytes<P, EPI>() * blockDim.x);  // [spb] record, [blockDim] y
     if (s < a.g.vh && kb < a.nrhs) {
         int c[4];
@@ -570,7 +624,9 @@ __global__ void __launch_bounds__(256) wilson_dslash_kernel(WilsonArgs a) {
 #pragma unroll
                 for (int cc = 0; cc < 3; cc++) acc[b][sp][cc] = mk((T)0, (T)0);
         const T sf = a.dagger ? (T)-1 : (T)1;
-        if constexpr (NB == 1 && (P == P32 || P == P16)) {
+        if constexpr (NB == 1 && (P == P32 || P == P16) && DEEP) {
+            hops_pipelined2<P, R, T>(a, c, s, kb, sf, acc[0]);
+        } else if constexpr (NB == 1 && (P == P32 || P == P16)) {
             hops_pipelined<P, R, T>(a, c, s, kb, sf, acc[0]);
         } else if constexpr (P == PDF) {
 #pragma unroll 1

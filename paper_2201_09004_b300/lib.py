@@ -38,7 +38,7 @@ EXPORTS = [
     "lq_last_error", "lq_create_lattice", "lq_destroy_lattice", "lq_lattice_bytes", "lq_lattice_release_workspace", "lq_load_gauge",
     "lq_load_clover", "lq_dslash_apply", "lq_operator_apply", "lq_solve", "lq_field_create",
     "lq_field_destroy", "lq_field_import", "lq_field_export", "lq_dslash_field", "lq_schur_field",
-    "lq_profile_enable", "lq_profile_reset", "lq_profile_query", "lq_launch_count", "lq_server_create",
+    "lq_profile_enable", "lq_profile_reset", "lq_profile_query", "lq_launch_count", "lq_tune_reset", "lq_tune_force", "lq_server_create",
     "lq_server_destroy", "lq_submit", "lq_poll", "lq_wait", "lq_server_stats", "lq_dslash_apply_noalloc", "lq_request_bytes",
 ]
 
@@ -321,6 +321,17 @@ def profile_query(name=""):
 
 def launch_count():
     return int(lib().lq_launch_count())
+
+
+def tune_reset():
+    """Forgets every autotuned launch configuration."""
+    _check(lib().lq_tune_reset())
+
+
+def tune_force(code):
+    """Restricts later tuning to one candidate code (block size, or 1000 + block size
+    for the register-capped FP32/FP16 Wilson kernel); 0 lifts the restriction."""
+    _check(lib().lq_tune_force(ctypes.c_int(code)))
 
 
 class Server:

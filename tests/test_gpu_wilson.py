@@ -123,6 +123,36 @@ def test_schur_operator(L, orc, prec):
         assert rel_err(got, ref) < 10 * TOL[prec], (prec, dagger)
 
 
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("code", [64, 128, 256, 1064, 1128, 1256, 2064, 2128])
+def test_each_tuning_candidate(L, orc, prec, code):
+    """Every launch configuration the autotuner may pick (block sizes; the
+    register-capped build; two hops of gathers in flight) gives the oracle's hopping term and Schur operator,
+    on a lattice with a ragged last block."""
+    dims = (6, 4, 4, 6)
+    lat, U = make(L, dims, 33, c_sw=1.05)
+    C = orc.clover(dims, U, 1.05)
+    op = L.op_params(L.WILSON_TM_CLOVER, 0.05, 0.1, c_sw=1.05)
+    v = synth.gaussian_field(dims, 34).numpy()
+    mask = parity_mask(dims)
+    W = orc.Wilson(dims, U, 0.0, 0.0)
+    try:
+        L.tune_reset()
+        L.tune_force(code)
+        for dagger in (False, True):
+            ref = W.hop(v, dagger=dagger)
+            for p in (0, 1):
+                src = np.where((mask == 1 - p)[..., None, None], v, 0)
+                got = lat.dslash_apply(op, p, src, dagger=dagger, prec=prec)
+                assert rel_err(got[mask == p], ref[mask == p]) < TOL[prec], (code, prec, dagger, p)
+            ref = schur_reference(orc, dims, U, C, 0.05, 0.1, v, dagger=dagger)
+            got = lat.operator_apply(op, v, form=L.OP_SCHUR, dagger=dagger, prec=prec)
+            assert rel_err(got, ref) < 10 * TOL[prec], (code, prec, dagger)
+    finally:
+        L.tune_force(0)
+        L.tune_reset()
+
+
 def true_residual(orc, dims, U, C, m, mu, b, x):
     r = b - orc.Wilson(dims, U, m, mu, clover=C).apply(x)
     return np.linalg.norm(r) / np.linalg.norm(b)
