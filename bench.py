@@ -56,7 +56,7 @@ FLOPS_PER_SITE = {"hop": 1320, "ainv": 1320 + 2 * 6 * 6 * 8, "xpay": 1320 + 2 * 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of the
 # benchmark configuration (profiles/wilson_dslash_f16_ainv_24x24x24x64.md); set back to
 # None whenever the kernel changes after the capture.
-NCU_TRAFFIC = {"wilson_dslash_f16_ainv": 255_320_000}
+NCU_TRAFFIC = {}
 
 REASONS = {
     0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap", 0x8: "hw_slowdown",

@@ -66,7 +66,7 @@ static void wl_epi(const char* name, WilsonArgs a, int epi, int nb, int block, c
 template <int EPI, bool SITE>
 static void wl_df(const char* name, WilsonArgs a, int block, cudaStream_t st) {
     dim3 grid(site_blocks(a.g.vh, block, 2), a.nrhs);
-    launch(name, wilson_dslash_df2_kernel<EPI, SITE>, grid, dim3(block), st, a);
+    launch_smem(name, wilson_dslash_df2_kernel<EPI, SITE>, grid, dim3(block), SITE ? 0 : df2_smem_bytes(block), st, a);
 }
 
 static const char* wname(int prec, int epi) {

@@ -196,10 +196,37 @@ int num_sms() {
     return n;
 }
 
+// With LQ_TUNE_CACHE=<file>, tuned choices are read from the file on first use
+// and every new choice is appended ("key code" per line), so that separate
+// processes (a profiler run after a plain run) launch the same configurations.
+static void tune_cache_load() {  // g_tune_mu held
+    static bool loaded = false;
+    if (loaded) return;
+    loaded = true;
+    const char* path = getenv("LQ_TUNE_CACHE");
+    if (!path) return;
+    FILE* f = fopen(path, "r");
+    if (!f) return;
+    char key[512];
+    int code;
+    while (fscanf(f, "%511s %d", key, &code) == 2) g_tuned[key] = code;
+    fclose(f);
+}
+
+static void tune_cache_store(const std::string& key, int code) {  // g_tune_mu held
+    const char* path = getenv("LQ_TUNE_CACHE");
+    if (!path) return;
+    FILE* f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%s %d\n", key.c_str(), code);
+    fclose(f);
+}
+
 int tuned_block(const std::string& key, cudaStream_t st, const std::function<void(int)>& run,
                 const std::vector<int>& candidates) {
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_cache_load();
         auto it = g_tuned.find(key);
         if (it != g_tuned.end()) return it->second;
     }
@@ -245,6 +272,7 @@ int tuned_block(const std::string& key, cudaStream_t st, const std::function<voi
     cudaEventDestroy(b);
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tuned[key] = best;
+    if (!forced) tune_cache_store(key, best);
     return best;
 }
 

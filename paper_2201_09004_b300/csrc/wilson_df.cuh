@@ -40,6 +40,58 @@ __device__ __forceinline__ cd pair_swap(cd v) {
 }
 __device__ __forceinline__ df cnorm2(cd v) { return v.r * v.r + v.i * v.i; }
 
+// Dot-product accumulator: the running sum keeps its high part exact with a
+// two-sum per term and collects every rounding and product error in a plain
+// FP32 low part, normalised once at the end (12 FP32 instructions per real
+// multiply-add instead of 17 for a normalised double-float multiply and add).
+struct dfacc {
+    float hi, lo;
+};
+__device__ __forceinline__ void acc_prod(dfacc& a, df x, df y) {  // a += x y
+    const float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fmaf_rn(x.hi, y.lo, e);
+    e = __fmaf_rn(x.lo, y.hi, e);
+    const float s = __fadd_rn(a.hi, p);
+    const float bb = __fsub_rn(s, a.hi);
+    const float t = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    a.hi = s;
+    a.lo = __fadd_rn(a.lo, __fadd_rn(t, e));
+}
+__device__ __forceinline__ void acc_add(dfacc& a, df x) {  // a += x
+    const float s = __fadd_rn(a.hi, x.hi);
+    const float bb = __fsub_rn(s, a.hi);
+    const float t = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(x.hi, bb));
+    a.hi = s;
+    a.lo = __fadd_rn(a.lo, __fadd_rn(t, x.lo));
+}
+__device__ __forceinline__ df acc_done(dfacc a) { return df_fast_two_sum(a.hi, a.lo); }
+
+struct cacc {
+    dfacc r, i;
+};
+__device__ __forceinline__ cacc cacc_zero() { return cacc{{0.f, 0.f}, {0.f, 0.f}}; }
+__device__ __forceinline__ void cacc_mac(cacc& a, cd x, cd y) {  // a += x y
+    acc_prod(a.r, x.r, y.r);
+    acc_prod(a.r, -x.i, y.i);
+    acc_prod(a.i, x.r, y.i);
+    acc_prod(a.i, x.i, y.r);
+}
+__device__ __forceinline__ void cacc_cjmac(cacc& a, cd x, cd y) {  // a += conj(x) y
+    acc_prod(a.r, x.r, y.r);
+    acc_prod(a.r, x.i, y.i);
+    acc_prod(a.i, x.r, y.i);
+    acc_prod(a.i, -x.i, y.r);
+}
+__device__ __forceinline__ void cacc_add(cacc& a, cd x) {
+    acc_add(a.r, x.r);
+    acc_add(a.i, x.i);
+}
+__device__ __forceinline__ cd cacc_done(cacc a) { return mk(acc_done(a.r), acc_done(a.i)); }
+
+// dynamic shared memory of the hop staging (two slots of 21 chunks per site)
+__host__ __device__ constexpr size_t df2_smem_bytes(int block) { return (size_t)2 * 21 * 16 * (block / 2); }
+
 // SITE = true: no hops, w = block h of `in` at the site (out = A^{-1} in).
 template <int EPI, bool SITE>
 __global__ void __launch_bounds__(256, 2) wilson_dslash_df2_kernel(WilsonArgs a) {
@@ -60,17 +112,51 @@ __global__ void __launch_bounds__(256, 2) wilson_dslash_df2_kernel(WilsonArgs a)
     } else {
         int c[4];
         cb_coords(a.g, s, a.parity, c);
-        cd up[3], lo2[3], lo3[3];  // upper spin h, lower spins 2 and 3
-#pragma unroll
-        for (int q = 0; q < 3; q++) up[q] = lo2[q] = lo3[q] = mk(df(0.f), df(0.f));
-#pragma unroll 1
-        for (int hop = 0; hop < 8; hop++) {
+        // The link (9 chunks) and neighbour spinor (12 chunks) of hop i+1 are copied
+        // into shared memory with cp.async while hop i computes: stage[slot][chunk][site],
+        // the two threads of a site copying alternate chunks.
+        extern __shared__ __align__(16) unsigned char lq_smem[];
+        float4* stage = (float4*)lq_smem;
+        const int g = threadIdx.x >> 1;
+        auto issue = [&](int hop, int slot) -> float {
             const int mu = hop >> 1;
             const bool fwd = (hop & 1) == 0;
             float bs;
             const int n = cb_hop(a.g, c, mu, fwd ? 1 : -1, bs);
+            const float4* ub = (const float4*)a.U.data + (size_t)((fwd ? a.parity : 1 - a.parity) * 4 + mu) * 9 * vh;
+            const size_t ls = (size_t)(fwd ? s : n);
+#pragma unroll
+            for (int k = h; k < 21; k += 2) {
+                const float4* src = k < 9 ? ub + (size_t)k * vh + ls : in + (size_t)(k - 9) * vh + n;
+                cp_async16(&stage[(slot * 21 + k) * spb + g], src);
+            }
+            cp_async_commit();
+            return bs;
+        };
+        cd up[3], lo2[3], lo3[3];  // upper spin h, lower spins 2 and 3
+#pragma unroll
+        for (int q = 0; q < 3; q++) up[q] = lo2[q] = lo3[q] = mk(df(0.f), df(0.f));
+        float bs_next = issue(0, 0);
+#pragma unroll 1
+        for (int hop = 0; hop < 8; hop++) {
+            const int mu = hop >> 1;
+            const bool fwd = (hop & 1) == 0;
+            const float bs = bs_next;
+            if (hop < 7) {
+                __syncwarp();  // both threads of the pair are done with the slot about to be refilled
+                bs_next = issue(hop + 1, (hop + 1) & 1);
+                asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+            } else {
+                cp_async_wait_all();
+            }
+            __syncwarp();  // the partner's copies of this hop are visible
+            const float4* sl = stage + (size_t)((hop & 1) * 21) * spb + g;
             cx<df> U[3][3];
-            load_link<PDF, 18, df>(a.U, fwd ? a.parity : 1 - a.parity, mu, fwd ? s : n, U);
+#pragma unroll
+            for (int k = 0; k < 9; k++) {
+                const float4 v = sl[k * spb];
+                U[k / 3][k % 3] = mk(df(v.x, v.y), df(v.z, v.w));
+            }
             // projector (1 + sp g_mu): sp = +-1 forward / backward, flipped for the adjoint
             const bool neg_sp = fwd ? dag : !dag;
             // component h couples spin h with spin pb through +-1 or +-i (DeGrand-Rossi)
@@ -80,13 +166,23 @@ __global__ void __launch_bounds__(256, 2) wilson_dslash_df2_kernel(WilsonArgs a)
             cd hv[3];
 #pragma unroll
             for (int q = 0; q < 3; q++) {
-                const cd pa = ld_cd(in, (size_t)(h * 3 + q) * vh + n);
-                const cd pp = ld_cd(in, (size_t)(pb * 3 + q) * vh + n);
+                const float4 va = sl[(9 + h * 3 + q) * spb];
+                const float4 vp = sl[(9 + pb * 3 + q) * spb];
+                const cd pa = mk(df(va.x, va.y), df(va.z, va.w));
+                const cd pp = mk(df(vp.x, vp.y), df(vp.z, vp.w));
                 hv[q] = pa + cunit(pp, cn != neg_sp, ci);
             }
             cd r[3];
-            if (fwd) su3_mv(U, hv, r);
-            else su3_dmv(U, hv, r);
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                cacc t = cacc_zero();
+#pragma unroll
+                for (int j = 0; j < 3; j++) {
+                    if (fwd) cacc_mac(t, U[i][j], hv[j]);
+                    else cacc_cjmac(t, U[j][i], hv[j]);
+                }
+                r[i] = cacc_done(t);
+            }
             // rebuild: upper spin h gets r; lower spin (3 if to3 else 2) gets +-r or +-i r
             const bool flip = bs < 0.f;  // time boundary
             const bool to3 = mu < 2 ? (h == 0) : (h == 1);
@@ -128,14 +224,15 @@ __global__ void __launch_bounds__(256, 2) wilson_dslash_df2_kernel(WilsonArgs a)
             const float4* A = (const float4*)a.clov;
 #pragma unroll 1
             for (int i = 0; i < 6; i++) {
-                cd acc = mk(df(0.f), df(0.f));
+                cacc t = cacc_zero();
 #pragma unroll
                 for (int j = 0; j < 6; j++) {
                     const int e = dag ? h * 36 + j * 6 + i : h * 36 + i * 6 + j;
                     const cd m = ld_cd(A, (size_t)e * vh + s);
-                    if (dag) cjmac(acc, m, w[j]);
-                    else cmac(acc, m, w[j]);
+                    if (dag) cacc_cjmac(t, m, w[j]);
+                    else cacc_mac(t, m, w[j]);
                 }
+                const cd acc = cacc_done(t);
                 if (live) st_cd(out, (size_t)(6 * h + i) * vh + s, acc);
                 nrm = nrm + cnorm2(acc);
             }
@@ -166,20 +263,21 @@ __global__ void __launch_bounds__(256, 2) wilson_dslash_df2_kernel(WilsonArgs a)
                 const float4 dc = __ldg(C + (size_t)(18 * h + i / 2) * vh + s);
                 di = (i & 1) ? df(dc.z, dc.w) : df(dc.x, dc.y);
             }
-            cd acc = mk(df(0.f), df(0.f));
+            cacc t = cacc_zero();
 #pragma unroll
             for (int j = 0; j < 6; j++) {
                 if (j == i) {
-                    cmac(acc, mk(f.r + di, f.i), yv[j]);
-                    acc = acc - w[j];
+                    cacc_mac(t, mk(f.r + di, f.i), yv[j]);
+                    cacc_add(t, mk(-w[j].r, -w[j].i));
                 } else if (clov) {
                     const int lo = j < i ? j : i, hi = j < i ? i : j;
                     const int q = lo * 5 - lo * (lo - 1) / 2 + (hi - lo - 1);
                     const cd m = ld_cd(C, (size_t)(18 * h + 3 + q) * vh + s);
-                    if (i < j) cmac(acc, m, yv[j]);
-                    else cjmac(acc, m, yv[j]);
+                    if (i < j) cacc_mac(t, m, yv[j]);
+                    else cacc_cjmac(t, m, yv[j]);
                 }
             }
+            const cd acc = cacc_done(t);
             if (live) st_cd(out, (size_t)(6 * h + i) * vh + s, acc);
             nrm = nrm + cnorm2(acc);
         }
