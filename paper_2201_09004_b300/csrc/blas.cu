@@ -22,28 +22,10 @@ struct HostScalars {
     double b[64];
 };
 
-// block-wide double-float sum (valid in thread 0)
-__device__ __forceinline__ df block_sum_df(df v) {
-    __shared__ float2 red[32];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = v + shfl_down_df(v, o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) red[wid] = make_float2(v.hi, v.lo);
-    __syncthreads();
-    v = df(0.f);
-    if (wid == 0) {
-        if (lane < (int)(blockDim.x >> 5)) v = df(red[lane].x, red[lane].y);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v = v + shfl_down_df(v, o);
-    }
-    return v;
-}
-
 #define SITE_LOOP(vh) for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < (vh); s += gridDim.x * blockDim.x)
 
 template <int P, int NR>
-__global__ void norm2_kernel(FieldV x, df* part) {
+__global__ void norm2_kernel(FieldV x, df* part, FinArgs fin) {
     typedef typename RealT<P>::T T;
     const int k = blockIdx.y;
     df acc(0.f);
@@ -57,6 +39,7 @@ __global__ void norm2_kernel(FieldV x, df* part) {
     }
     df r = block_sum_df(acc);
     if (threadIdx.x == 0) part[(size_t)k * gridDim.x + blockIdx.x] = r;
+    fin_tail(part, gridDim.x, gridDim.y, fin);
 }
 
 template <int PD, int PS, int NR>
@@ -126,7 +109,7 @@ __global__ void axpby_h_kernel(FieldV y, FieldV x, HostScalars h, df* part) {
 
 // s = b - q, partial |s|^2
 template <int P, int NR>
-__global__ void xmy_norm_kernel(FieldV sf, FieldV b, FieldV qf, df* part) {
+__global__ void xmy_norm_kernel(FieldV sf, FieldV b, FieldV qf, df* part, FinArgs fin) {
     typedef typename RealT<P>::T T;
     const int k = blockIdx.y;
     df acc(0.f);
@@ -145,11 +128,12 @@ __global__ void xmy_norm_kernel(FieldV sf, FieldV b, FieldV qf, df* part) {
     }
     df r = block_sum_df(acc);
     if (threadIdx.x == 0) part[(size_t)k * gridDim.x + blockIdx.x] = r;
+    fin_tail(part, gridDim.x, gridDim.y, fin);
 }
 
 // x += alpha p; s -= alpha q; partial |s|^2; alpha_k = sc[k*SC_N + SC_ALPHA]
 template <int PX, int P, int NR>
-__global__ void cg_xs_kernel(FieldV x, FieldV p, FieldV sf, FieldV qf, const double* sc, df* part) {
+__global__ void cg_xs_kernel(FieldV x, FieldV p, FieldV sf, FieldV qf, const double* sc, df* part, FinArgs fin) {
     typedef typename RealT<P>::T T;
     typedef typename MathT<PX, P>::T TX;
     const int k = blockIdx.y;
@@ -177,6 +161,7 @@ __global__ void cg_xs_kernel(FieldV x, FieldV p, FieldV sf, FieldV qf, const dou
     }
     df r = block_sum_df(acc);
     if (threadIdx.x == 0) part[(size_t)k * gridDim.x + blockIdx.x] = r;
+    fin_tail(part, gridDim.x, gridDim.y, fin);
 }
 
 // p = r + beta p
@@ -203,20 +188,7 @@ __global__ void finalize_kernel(const df* part, int nblocks, double* sc, int slo
     df sum(0.f);
     for (int i = threadIdx.x; i < nblocks; i += blockDim.x) sum = sum + pk[i];
     sum = block_sum_df(sum);
-    if (threadIdx.x == 0) {
-        const double tot = df_to_double(sum);
-        double* S = sc + (size_t)k * SC_N;
-        if (op == FIN_SET) {
-            S[slot] = tot;
-        } else if (op == FIN_ALPHA) {  // tot = |q|^2: alpha = rr / qq
-            S[SC_QQ] = tot;
-            S[SC_ALPHA] = (tot > 0.0 && S[SC_FROZEN] == 0.0) ? S[SC_RR] / tot : 0.0;
-        } else if (op == FIN_BETA) {   // tot = |r'|^2: beta = rr'/rr, rr = rr'
-            S[SC_RRN] = tot;
-            S[SC_BETA] = (S[SC_RR] > 0.0 && S[SC_FROZEN] == 0.0) ? tot / S[SC_RR] : 0.0;
-            S[SC_RR] = tot;
-        }
-    }
+    if (threadIdx.x == 0) fin_apply(sc + (size_t)k * SC_N, df_to_double(sum), slot, op);
 }
 
 // ---------------------------------------------------------------- launchers
@@ -241,9 +213,9 @@ static dim3 upd_grid(int vh, int nrhs) {
         else launch(NAME, KERNEL(6), GRID, dim3(RED_THREADS), st, __VA_ARGS__);                  \
     } while (0)
 
-void blas_norm2(const Field& x, df* part, cudaStream_t st) {
+void blas_norm2(const Field& x, df* part, cudaStream_t st, const FinArgs& fin) {
 #define K(NR) norm2_kernel<P_, NR>
-#define L(P) { constexpr int P_ = P; BY_KIND(x, "blas_norm2", K, red_grid(x.nrhs), x.view(), part); }
+#define L(P) { constexpr int P_ = P; BY_KIND(x, "blas_norm2", K, red_grid(x.nrhs), x.view(), part, fin); }
     DISPATCH_P(x.prec, L);
 #undef L
 #undef K
@@ -316,10 +288,10 @@ void blas_axpby_h(Field& y, const double* a, const Field& x, const double* b, df
 #undef K
 }
 
-void blas_xmy_norm(Field& s, const Field& b, const Field& q, df* part, cudaStream_t st) {
+void blas_xmy_norm(Field& s, const Field& b, const Field& q, df* part, cudaStream_t st, const FinArgs& fin) {
     if (s.prec != b.prec || s.prec != q.prec) fail(LQ_EINVAL, "blas_xmy_norm: precision mismatch");
 #define K(NR) xmy_norm_kernel<P_, NR>
-#define L(P) { constexpr int P_ = P; BY_KIND(s, "blas_xmy_norm", K, red_grid(s.nrhs), s.view(), b.view(), q.view(), part); }
+#define L(P) { constexpr int P_ = P; BY_KIND(s, "blas_xmy_norm", K, red_grid(s.nrhs), s.view(), b.view(), q.view(), part, fin); }
     DISPATCH_P(s.prec, L);
 #undef L
 #undef K
@@ -327,21 +299,21 @@ void blas_xmy_norm(Field& s, const Field& b, const Field& q, df* part, cudaStrea
 
 template <int PX>
 static void cg_xs_from(Field& x, const Field& p, Field& s, const Field& q, const double* sc, df* part,
-                       cudaStream_t st) {
+                       cudaStream_t st, const FinArgs& fin) {
 #define K(NR) cg_xs_kernel<PX, P_, NR>
-#define L(P) { constexpr int P_ = P; BY_KIND(x, "blas_cg_xs", K, red_grid(x.nrhs), x.view(), p.view(), s.view(), q.view(), sc, part); }
+#define L(P) { constexpr int P_ = P; BY_KIND(x, "blas_cg_xs", K, red_grid(x.nrhs), x.view(), p.view(), s.view(), q.view(), sc, part, fin); }
     DISPATCH_P(p.prec, L);
 #undef L
 #undef K
 }
 
 void blas_cg_xs(Field& x, const Field& p, Field& s, const Field& q, const double* sc, df* part,
-                cudaStream_t st) {
+                cudaStream_t st, const FinArgs& fin) {
     if (p.prec != s.prec || p.prec != q.prec) fail(LQ_EINVAL, "blas_cg_xs: precision mismatch");
-    if (x.prec == LQ_F64) cg_xs_from<P64>(x, p, s, q, sc, part, st);
-    else if (x.prec == LQ_F32) cg_xs_from<P32>(x, p, s, q, sc, part, st);
-    else if (x.prec == LQ_F16) cg_xs_from<P16>(x, p, s, q, sc, part, st);
-    else cg_xs_from<PDF>(x, p, s, q, sc, part, st);
+    if (x.prec == LQ_F64) cg_xs_from<P64>(x, p, s, q, sc, part, st, fin);
+    else if (x.prec == LQ_F32) cg_xs_from<P32>(x, p, s, q, sc, part, st, fin);
+    else if (x.prec == LQ_F16) cg_xs_from<P16>(x, p, s, q, sc, part, st, fin);
+    else cg_xs_from<PDF>(x, p, s, q, sc, part, st, fin);
 }
 
 void blas_cg_p(Field& p, const Field& r, const double* sc, cudaStream_t st) {

@@ -92,6 +92,78 @@ __device__ __forceinline__ df shfl_down_df(df v, int o) {
 }
 __device__ __forceinline__ double df_to_double(df v) { return (double)v.hi + (double)v.lo; }
 
+// block-wide double-float sum (valid in thread 0)
+__device__ __forceinline__ df block_sum_df(df v) {
+    __shared__ float2 red[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = v + shfl_down_df(v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = make_float2(v.hi, v.lo);
+    __syncthreads();
+    v = df(0.f);
+    if (wid == 0) {
+        if (lane < (int)(blockDim.x >> 5)) v = df(red[lane].x, red[lane].y);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = v + shfl_down_df(v, o);
+    }
+    return v;
+}
+
+// ------------------------------------------------------- scalar steps of CG
+// scalar slots per right-hand side in the solver scalar block
+enum { SC_RR = 0, SC_QQ, SC_SS, SC_RRN, SC_ALPHA, SC_BETA, SC_B2, SC_FROZEN, SC_PP, SC_N };
+enum { FIN_SET = 0, FIN_ALPHA = 1, FIN_BETA = 2 };
+
+// apply the scalar step to the total of a reduction (S: the rhs's scalar block)
+__device__ __forceinline__ void fin_apply(double* S, double tot, int slot, int op) {
+    if (op == FIN_SET) {
+        S[slot] = tot;
+    } else if (op == FIN_ALPHA) {  // tot = |q|^2: alpha = rr / qq
+        S[SC_QQ] = tot;
+        S[SC_ALPHA] = (tot > 0.0 && S[SC_FROZEN] == 0.0) ? S[SC_RR] / tot : 0.0;
+    } else if (op == FIN_BETA) {   // tot = |r'|^2: beta = rr'/rr, rr = rr'
+        S[SC_RRN] = tot;
+        S[SC_BETA] = (S[SC_RR] > 0.0 && S[SC_FROZEN] == 0.0) ? tot / S[SC_RR] : 0.0;
+        S[SC_RR] = tot;
+    }
+}
+
+// A reduction finalised inside the kernel that produces its partials: the last
+// block to finish (atomic ticket) sums every rhs's partials in index order and
+// applies the scalar step, then re-arms the ticket. sc == nullptr: no fusion.
+struct FinArgs {
+    double* sc = nullptr;
+    int slot = 0;
+    int op = 0;
+    unsigned* count = nullptr;
+};
+
+// called by every thread of every block after thread 0 wrote the block's partials
+__device__ __forceinline__ void fin_tail(const df* part, int nparts, int nrhs, const FinArgs& f) {
+    if (!f.sc) return;
+    __shared__ int last;
+    if (threadIdx.x == 0) {
+        __threadfence();  // this block's partials before its ticket
+        const unsigned total = gridDim.x * gridDim.y * gridDim.z;
+        last = atomicAdd(f.count, 1u) == total - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int k = 0; k < nrhs; k++) {
+        const df* pk = part + (size_t)k * nparts;
+        df sum(0.f);
+        for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+            const float2 v = __ldcg((const float2*)(pk + i));
+            sum = sum + df(v.x, v.y);
+        }
+        sum = block_sum_df(sum);
+        if (threadIdx.x == 0) fin_apply(f.sc + (size_t)k * SC_N, df_to_double(sum), f.slot, f.op);
+    }
+    if (threadIdx.x == 0) *f.count = 0u;
+}
+
 // conversions between the arithmetic types of the kernels
 template <typename T> __device__ __forceinline__ T from_df(df d);
 template <> __device__ __forceinline__ df from_df<df>(df d) { return d; }

@@ -79,7 +79,7 @@ static const char* wname(int prec, int epi) {
 }
 
 int wilson_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int epi, const Field& in, Field& out,
-                  const Field* y, df* norm_out, cudaStream_t st) {
+                  const Field* y, df* norm_out, cudaStream_t st, const FinArgs& fin) {
     if (in.prec != op.prec || out.prec != op.prec || (y && y->prec != op.prec))
         fail(LQ_EINVAL, "wilson_dslash: field precision does not match the operator");
     if (in.kind != LQ_WILSON_FIELD || out.nrhs != in.nrhs) fail(LQ_EINVAL, "wilson_dslash: field shape");
@@ -96,6 +96,7 @@ int wilson_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int ep
     a.mu = dagger ? -op.mu : op.mu;
     a.nrhs = in.nrhs;
     a.norm_out = norm_out;
+    a.fin = FinArgs();  // the tuner's trial launches never finalise
     a.clov = nullptr;
     a.clov_norm = nullptr;
     if (a.has_clover) {
@@ -129,6 +130,7 @@ int wilson_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int ep
     if ((op.prec == LQ_F32 || op.prec == LQ_F16) && nb == 1)
         for (int b : {64, 128}) cand.push_back(kDeep + b);
     int cfg = tuned_block(key, st, run, cand);
+    a.fin = norm_out ? fin : FinArgs();
     run(cfg);
     const int block = cfg % 1000;
     return site_blocks(lat.vh, block, op.prec == LQ_F32X2 ? 2 : nb);

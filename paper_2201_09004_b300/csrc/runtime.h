@@ -225,7 +225,7 @@ struct OpDesc {
 // norm_out: optional per-block partials of |out|^2 (nrhs * blocks).
 // Returns the number of thread blocks per right-hand side (the partial-sum stride).
 int wilson_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int epi, const Field& in,
-                  Field& out, const Field* y, df* norm_out, cudaStream_t st);
+                  Field& out, const Field* y, df* norm_out, cudaStream_t st, const FinArgs& fin = FinArgs());
 int hisq_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int epi, double a, const Field& in,
                 Field& out, const Field* y, df* norm_out, cudaStream_t st);
 // site-local out = A_pp^{-1} in (Wilson twisted mass / clover), parity of both fields
@@ -236,30 +236,28 @@ void wilson_ainv_site(Lattice& lat, const OpDesc& op, int parity, int dagger, co
 // All BLAS kernels work on whole fields of one parity, per right-hand side.
 // Reductions write per-block partials to `part`, then finalize into dev scalars.
 enum { RED_BLOCKS = 148 * 4, RED_THREADS = 256 };
-void blas_norm2(const Field& x, df* part, cudaStream_t st);          // part[k*RED_BLOCKS + b]
+void blas_norm2(const Field& x, df* part, cudaStream_t st, const FinArgs& fin = FinArgs());          // part[k*RED_BLOCKS + b]
 void blas_copy(Field& dst, const Field& src, cudaStream_t st);           // with precision conversion
 void blas_zero(Field& x, cudaStream_t st);
 void blas_axpy_h(Field& y, const double* a_host, const Field& x, cudaStream_t st);  // y += a_k x (host scalars)
 // y = a_k x + b_k y per right-hand side k (host scalars), optional partial |y|^2
 void blas_axpby_h(Field& y, const double* a, const Field& x, const double* b, df* part, cudaStream_t st);
 // s = b - q, with partial |s|^2
-void blas_xmy_norm(Field& s, const Field& b, const Field& q, df* part, cudaStream_t st);
+void blas_xmy_norm(Field& s, const Field& b, const Field& q, df* part, cudaStream_t st,
+                   const FinArgs& fin = FinArgs());
 // CG update: alpha_k = sc[k*SC_N + SC_ALPHA]; x += alpha p; s -= alpha q; partial |s|^2
 void blas_cg_xs(Field& x, const Field& p, Field& s, const Field& q, const double* sc, df* part,
-                cudaStream_t st);
+                cudaStream_t st, const FinArgs& fin = FinArgs());
 // p = r + beta p, beta_k = sc[k*SC_N + SC_BETA]
 void blas_cg_p(Field& p, const Field& r, const double* sc, cudaStream_t st);
 
-// scalar slots per right-hand side in the solver scalar block
-enum { SC_RR = 0, SC_QQ, SC_SS, SC_RRN, SC_ALPHA, SC_BETA, SC_B2, SC_FROZEN, SC_PP, SC_N };
-enum { FIN_SET = 0, FIN_ALPHA = 1, FIN_BETA = 2 };
 // sum part[k*nblocks ...] (compensated, fixed order) into sc[k*SC_N + slot], or apply `op`
 void blas_finalize(const df* part, int nblocks, int nrhs, double* sc, int slot, int op, cudaStream_t st);
 
 // ----------------------------------------------------------------- solvers
 // Schur operators on resident fields (see solver.cu)
 int schur_wilson(Lattice& lat, const OpDesc& op, int dagger, const Field& in, Field& out, Field& tmp, df* part,
-                 cudaStream_t st);
+                 cudaStream_t st, const FinArgs& fin = FinArgs());
 int schur_hisq(Lattice& lat, const OpDesc& op, double sigma, const Field& in, Field& out, Field& t, df* part_t,
                cudaStream_t st);
 // estimated device bytes of a solve's work fields

@@ -31,6 +31,7 @@ struct Scalars {
     double* dev = nullptr;
     double* host = nullptr;
     df* part = nullptr;
+    unsigned* count = nullptr;  // ticket of the reductions finalised in their producing kernel
     int nrhs = 0;
     void init(Lattice& l, int n, cudaStream_t s) {
         lat = &l;
@@ -42,6 +43,17 @@ struct Scalars {
         LQ_CUDA(cudaMemsetAsync(dev, 0, sizeof(double) * SC_N * n, s));
         part = (df*)ws_get(l, sizeof(df) * per * n, false, s);
         host = (double*)ws_get(l, sizeof(double) * SC_N * n, true, s);
+        count = (unsigned*)ws_get(l, 16, false, s);
+        LQ_CUDA(cudaMemsetAsync(count, 0, 16, s));
+    }
+    // finalise a reduction into `slot` (or apply `op`) inside the kernel producing its partials
+    FinArgs f(int slot, int op) const {
+        FinArgs a;
+        a.sc = dev;
+        a.slot = slot;
+        a.op = op;
+        a.count = count;
+        return a;
     }
     void pull(cudaStream_t st) {
         LQ_CUDA(cudaMemcpyAsync(host, dev, sizeof(double) * SC_N * nrhs, cudaMemcpyDeviceToHost, st));
@@ -60,6 +72,7 @@ struct Scalars {
         ws_put(*lat, dev, st);
         ws_put(*lat, part, st);
         ws_put(*lat, host, st);
+        ws_put(*lat, count, st);
     }
 };
 
@@ -101,9 +114,9 @@ static OpDesc wilson_desc(const lq_op_params& op, int prec, int recon) {
 
 // out = Mhat in (dagger: Mhat^+); tmp holds the odd sites. Returns the blocks of the |out|^2 partials.
 int schur_wilson(Lattice& lat, const OpDesc& op, int dagger, const Field& in, Field& out, Field& tmp, df* part,
-                 cudaStream_t st) {
+                 cudaStream_t st, const FinArgs& fin) {
     wilson_dslash(lat, op, 1, dagger, EPI_AINV, in, tmp, nullptr, nullptr, st);
-    return wilson_dslash(lat, op, 0, dagger, EPI_XPAY, tmp, out, &in, part, st);
+    return wilson_dslash(lat, op, 0, dagger, EPI_XPAY, tmp, out, &in, part, st, fin);
 }
 
 // CGNR on Mhat for all right-hand sides of bhat at once (FP64, even sites).
@@ -168,13 +181,11 @@ static CgResult cgnr_mixed(Lattice& lat, const OpDesc& ops, const OpDesc& op64, 
     } cleanup{lat, ring, ev, st};
     auto slot = [&](int i) { return ring + (size_t)(i & 1) * SC_N * n; };
     // One CG iteration on the device; `dst` (or null) receives the scalars.
+    // Each reduction is finalised by the last block of the kernel producing it.
     auto iteration = [&](double* dst) {
-        int nb2 = schur_wilson(lat, ops, 0, p, q, t, sc.part, st);
-        blas_finalize(sc.part, nb2, n, sc.dev, 0, FIN_ALPHA, st);
-        blas_cg_xs(x_lo, p, s_lo, q, sc.dev, sc.part, st);
-        sc.fin(RED_BLOCKS, SC_SS, st);
-        nb2 = schur_wilson(lat, ops, 1, s_lo, r, t, sc.part, st);
-        blas_finalize(sc.part, nb2, n, sc.dev, 0, FIN_BETA, st);
+        schur_wilson(lat, ops, 0, p, q, t, sc.part, st, sc.f(0, FIN_ALPHA));
+        blas_cg_xs(x_lo, p, s_lo, q, sc.dev, sc.part, st, sc.f(SC_SS, FIN_SET));
+        schur_wilson(lat, ops, 1, s_lo, r, t, sc.part, st, sc.f(0, FIN_BETA));
         blas_cg_p(p, r, sc.dev, st);
         if (dst) LQ_CUDA(cudaMemcpyAsync(dst, sc.dev, sizeof(double) * SC_N * n, cudaMemcpyDeviceToHost, st));
     };
@@ -243,11 +254,10 @@ static CgResult cgnr_mixed(Lattice& lat, const OpDesc& ops, const OpDesc& op64, 
         blas_axpy_h(x_hi, ones.data(), x_lo, st);
         blas_zero(x_lo, st);
         schur_wilson(lat, op64, 0, x_hi, q64, t64, nullptr, st);
-        blas_xmy_norm(s_hi, bhat, q64, sc.part, st);
-        sc.fin(RED_BLOCKS, SC_SS, st);
+        blas_xmy_norm(s_hi, bhat, q64, sc.part, st, sc.f(SC_SS, FIN_SET));
         blas_copy(s_lo, s_hi, st);
-        nb = schur_wilson(lat, ops, 1, s_lo, r, t, sc.part, st);
-        sc.fin(nb, SC_RR, st);  // keep p, restart the norm recurrence from the new r
+        // keep p, restart the norm recurrence from the new r
+        schur_wilson(lat, ops, 1, s_lo, r, t, sc.part, st, sc.f(SC_RR, FIN_SET));
         sc.pull(st);
         for (int k = 0; k < n; k++) {
             if (done[k]) continue;

@@ -34,6 +34,7 @@ struct WilsonArgs {
     double mu;              // twisted mass, already negated for the adjoint
     int nrhs;
     df* norm_out;       // if non-null: per-block partial sums of |out|^2, per rhs
+    FinArgs fin;        // with norm_out: the last block finalises the sums
 };
 
 // spin projection h = top two spins of (1 + s g_mu) psi, for psi as cx[4][3]
@@ -744,7 +745,10 @@ __global__ void __launch_bounds__(256, MINB) wilson_dslash_kernel(WilsonArgs a) 
             fstore<P, 24, T>(a.out, kb + b, s, v);
         }
     }
-    if (a.norm_out) reduce_norms_rg<NB, RG>(nrm, a.norm_out, grp, sb, nsb, a.nrhs);
+    if (a.norm_out) {
+        reduce_norms_rg<NB, RG>(nrm, a.norm_out, grp, sb, nsb, a.nrhs);
+        fin_tail(a.norm_out, nsb, a.nrhs, a.fin);
+    }
 }
 
 // site-local out = A^{-1} in (dagger: (A^{-1})^+ in) on fields of parity a.parity

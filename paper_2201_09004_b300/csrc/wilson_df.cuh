@@ -105,7 +105,8 @@ __global__ void __launch_bounds__(256, 2) wilson_dslash_df2_kernel(WilsonArgs a)
     const bool dag = a.dagger != 0;
     const float4* in = (const float4*)((const char*)a.in.data + (size_t)k * a.in.rhs_bytes);
 
-    cd w[6];  // chiral block h: spins 2h, 2h+1 (index 3 * spin' + colour)
+    cd w[6];   // chiral block h: spins 2h, 2h+1 (index 3 * spin' + colour)
+    cd yv[6];  // EPI_XPAY: block h of y, loaded while the pair exchanges its sums
     if constexpr (SITE) {
 #pragma unroll
         for (int j = 0; j < 6; j++) w[j] = ld_cd(in, (size_t)(6 * h + j) * vh + s);
@@ -197,6 +198,11 @@ __global__ void __launch_bounds__(256, 2) wilson_dslash_df2_kernel(WilsonArgs a)
                 else lo2[q] = lo2[q] + e;
             }
         }
+        if constexpr (EPI == EPI_XPAY) {
+            const float4* yb = (const float4*)((const char*)a.y.data + (size_t)k * a.y.rhs_bytes);
+#pragma unroll
+            for (int j = 0; j < 6; j++) yv[j] = ld_cd(yb, (size_t)(6 * h + j) * vh + s);
+        }
         // thread 0 takes the partner's upper spin (spin 1); thread 1 the partner's lower spins
         const df half(0.5f);
 #pragma unroll
@@ -220,18 +226,28 @@ __global__ void __launch_bounds__(256, 2) wilson_dslash_df2_kernel(WilsonArgs a)
         }
     } else if constexpr (EPI == EPI_AINV) {
         if (a.has_clover) {
-            // rows of block h of A^{-1} (36 complex, row-major); the adjoint reads the transpose, conjugated
+            // rows of block h of A^{-1} (36 complex, row-major); the adjoint reads the transpose,
+            // conjugated. The entries of row i+1 are in flight while row i is computed.
             const float4* A = (const float4*)a.clov;
+            auto entry = [&](int i, int j) { return (size_t)(dag ? h * 36 + j * 6 + i : h * 36 + i * 6 + j) * vh + s; };
+            float4 cur[6], nxt[6];
+#pragma unroll
+            for (int j = 0; j < 6; j++) cur[j] = __ldg(A + entry(0, j));
 #pragma unroll 1
             for (int i = 0; i < 6; i++) {
+                if (i < 5) {
+#pragma unroll
+                    for (int j = 0; j < 6; j++) nxt[j] = __ldg(A + entry(i + 1, j));
+                }
                 cacc t = cacc_zero();
 #pragma unroll
                 for (int j = 0; j < 6; j++) {
-                    const int e = dag ? h * 36 + j * 6 + i : h * 36 + i * 6 + j;
-                    const cd m = ld_cd(A, (size_t)e * vh + s);
+                    const cd m = mk(df(cur[j].x, cur[j].y), df(cur[j].z, cur[j].w));
                     if (dag) cacc_cjmac(t, m, w[j]);
                     else cacc_mac(t, m, w[j]);
                 }
+#pragma unroll
+                for (int j = 0; j < 6; j++) cur[j] = nxt[j];
                 const cd acc = cacc_done(t);
                 if (live) st_cd(out, (size_t)(6 * h + i) * vh + s, acc);
                 nrm = nrm + cnorm2(acc);
@@ -248,35 +264,43 @@ __global__ void __launch_bounds__(256, 2) wilson_dslash_df2_kernel(WilsonArgs a)
             }
         }
     } else {  // EPI_XPAY: out = ((4+m) + i chi mu + C) y - w on block h
-        const float4* yb = (const float4*)((const char*)a.y.data + (size_t)k * a.y.rhs_bytes);
-        cd yv[6];
-#pragma unroll
-        for (int j = 0; j < 6; j++) yv[j] = ld_cd(yb, (size_t)(6 * h + j) * vh + s);
         const cd f = mk(df(a.m4), df((h ? -1.0 : 1.0) * a.mu));
-        // C block h: 6 real diagonal entries (3 chunks) then the 15 upper entries (row-major, i < j)
+        // C block h: 6 real diagonal entries (3 chunks) then the 15 upper entries
+        // (row-major, i < j); chunk (i, j) of row i is the diagonal pair for j == i.
+        // The chunks of row i+1 are in flight while row i is computed.
         const float4* C = (const float4*)a.clov;
         const bool clov = a.has_clover != 0;
+        auto chunk = [&](int i, int j) {
+            const int lo = j < i ? j : i, hi = j < i ? i : j;
+            const int q = lo * 5 - lo * (lo - 1) / 2 + (hi - lo - 1);
+            return (size_t)(18 * h + (j == i ? i / 2 : 3 + q)) * vh + s;
+        };
+        float4 cur[6], nxt[6];
+        if (clov) {
+#pragma unroll
+            for (int j = 0; j < 6; j++) cur[j] = __ldg(C + chunk(0, j));
+        }
 #pragma unroll 1
         for (int i = 0; i < 6; i++) {
-            df di(0.f);
-            if (clov) {
-                const float4 dc = __ldg(C + (size_t)(18 * h + i / 2) * vh + s);
-                di = (i & 1) ? df(dc.z, dc.w) : df(dc.x, dc.y);
+            if (clov && i < 5) {
+#pragma unroll
+                for (int j = 0; j < 6; j++) nxt[j] = __ldg(C + chunk(i + 1, j));
             }
             cacc t = cacc_zero();
 #pragma unroll
             for (int j = 0; j < 6; j++) {
                 if (j == i) {
+                    const df di = !clov ? df(0.f) : (i & 1) ? df(cur[j].z, cur[j].w) : df(cur[j].x, cur[j].y);
                     cacc_mac(t, mk(f.r + di, f.i), yv[j]);
                     cacc_add(t, mk(-w[j].r, -w[j].i));
                 } else if (clov) {
-                    const int lo = j < i ? j : i, hi = j < i ? i : j;
-                    const int q = lo * 5 - lo * (lo - 1) / 2 + (hi - lo - 1);
-                    const cd m = ld_cd(C, (size_t)(18 * h + 3 + q) * vh + s);
+                    const cd m = mk(df(cur[j].x, cur[j].y), df(cur[j].z, cur[j].w));
                     if (i < j) cacc_mac(t, m, yv[j]);
                     else cacc_cjmac(t, m, yv[j]);
                 }
             }
+#pragma unroll
+            for (int j = 0; j < 6; j++) cur[j] = nxt[j];
             const cd acc = cacc_done(t);
             if (live) st_cd(out, (size_t)(6 * h + i) * vh + s, acc);
             nrm = nrm + cnorm2(acc);
@@ -285,6 +309,7 @@ __global__ void __launch_bounds__(256, 2) wilson_dslash_df2_kernel(WilsonArgs a)
     if (a.norm_out) {
         const df v[1] = {live ? nrm : df(0.f)};
         reduce_norms_rg<1, 1>(v, a.norm_out, k, blockIdx.x, gridDim.x, a.nrhs);
+        fin_tail(a.norm_out, gridDim.x, a.nrhs, a.fin);
     }
 }
 
