@@ -267,9 +267,13 @@ __device__ __forceinline__ float s16lo(int w) {
 __device__ __forceinline__ float s16hi(int w) {
     return __int_as_float((int)__byte_perm((unsigned)w, 0x4B000000u, 0x7632)) - LQ_F16_MAGIC;
 }
-__device__ __forceinline__ int pack16(float a, float b) {
-    unsigned qa = (unsigned)(__float2int_rn(a) + 32768), qb = (unsigned)(__float2int_rn(b) + 32768);
-    return (int)((qa & 0xffffu) | (qb << 16));
+// two reals times f, each in [-32767, 32767] after scaling, to offset-binary codes:
+// adding 2^23 + 32768 rounds to the nearest integer (ties to even) and leaves
+// code + 32768 in the low 16 bits of the float, so no float-to-int conversion is needed
+__device__ __forceinline__ int pack16f(float a, float b, float f) {
+    const unsigned ua = __float_as_uint(__fmaf_rn(a, f, LQ_F16_MAGIC));
+    const unsigned ub = __float_as_uint(__fmaf_rn(b, f, LQ_F16_MAGIC));
+    return (int)__byte_perm(ua, ub, 0x5410);
 }
 
 // unpack one chunk c into RPC reals (FP16: times f = scale/32767)
@@ -392,20 +396,21 @@ __device__ __forceinline__ void store_reals(void* base, int stride, int s, float
             nrm = m;
             norm[s] = m;
         }
-        const float f = nrm > 0.f ? 32767.f / nrm : 0.f;
+        // |v| f <= 32767 (1 + 2^-22) rounds to at most 32767
+        const float f = nrm > 0.f ? __fdividef(32767.f, nrm) : 0.f;
 #pragma unroll
         for (int k = 0; k < Lay::NC; k++) {
             typename Lay::C c;
             if constexpr (Lay::RPC == 8) {
-                c.x = pack16((float)v[8 * k + 0] * f, (float)v[8 * k + 1] * f);
-                c.y = pack16((float)v[8 * k + 2] * f, (float)v[8 * k + 3] * f);
-                c.z = pack16((float)v[8 * k + 4] * f, (float)v[8 * k + 5] * f);
-                c.w = pack16((float)v[8 * k + 6] * f, (float)v[8 * k + 7] * f);
+                c.x = pack16f((float)v[8 * k + 0], (float)v[8 * k + 1], f);
+                c.y = pack16f((float)v[8 * k + 2], (float)v[8 * k + 3], f);
+                c.z = pack16f((float)v[8 * k + 4], (float)v[8 * k + 5], f);
+                c.w = pack16f((float)v[8 * k + 6], (float)v[8 * k + 7], f);
             } else if constexpr (Lay::RPC == 4) {
-                c.x = pack16((float)v[4 * k + 0] * f, (float)v[4 * k + 1] * f);
-                c.y = pack16((float)v[4 * k + 2] * f, (float)v[4 * k + 3] * f);
+                c.x = pack16f((float)v[4 * k + 0], (float)v[4 * k + 1], f);
+                c.y = pack16f((float)v[4 * k + 2], (float)v[4 * k + 3], f);
             } else {
-                c = pack16((float)v[2 * k + 0] * f, (float)v[2 * k + 1] * f);
+                c = pack16f((float)v[2 * k + 0], (float)v[2 * k + 1], f);
             }
             b[(size_t)k * stride + s] = c;
         }
