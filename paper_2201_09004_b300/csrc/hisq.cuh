@@ -9,6 +9,8 @@
 // Epilogues: EPI_HOP out = D psi; EPI_XPAY out = a*y - D psi (the even-odd
 // Schur operator m^2 - H_eo H_oe as two launches, and its shifted versions).
 #pragma once
+#include <utility>
+
 #include "wilson.cuh"
 
 namespace lq {
@@ -79,6 +81,109 @@ __device__ __forceinline__ void stag_dir(const HisqArgs& a, const int c[4], int 
     stag_hop<MU, 3, P, RL, NB, T>(a, a.lng, c, s, kb, eta * cn, acc);
 }
 
+// ---------------------------------------------------------------------------
+// One right-hand side per thread: the 16 hops (per direction: fat forward,
+// fat backward, long forward, long backward) are software-pipelined, the raw
+// (still encoded) vector and link chunks of hop j+1 being loaded before hop j
+// is decoded and applied.
+template <int P, int R> struct StagRaw {
+    typename Layout<P, 6>::C sp[Layout<P, 6>::NC];
+    typename Layout<P, R>::C u[Layout<P, R>::NC];
+    float n;   // FP16 vector norm
+    float bs;  // boundary sign of the hop
+};
+
+template <int J, int P, int R>
+__device__ __forceinline__ void stag_fetch(const HisqArgs& a, const GaugeV& G, const int c[4], int s, int k0,
+                                           StagRaw<P, R>& r) {
+    constexpr int MU = J >> 2;
+    constexpr int STEP = ((J >> 1) & 1) ? 3 : 1;
+    constexpr bool FWD = (J & 1) == 0;
+    typedef typename Layout<P, 6>::C CS;
+    typedef typename Layout<P, R>::C CU;
+    float bs;
+    const int n = cb_hop(a.g, c, MU, FWD ? STEP : -STEP, bs);
+    r.bs = bs;
+    const CS* sb = (const CS*)((const char*)a.in.data + (size_t)k0 * a.in.rhs_bytes);
+#pragma unroll
+    for (int k = 0; k < Layout<P, 6>::NC; k++) r.sp[k] = __ldg(&sb[(size_t)k * a.g.vh + n]);
+    if constexpr (P == P16) r.n = __ldg(a.in.norm + (size_t)k0 * a.g.vh + n);
+    const int lp = FWD ? a.parity : 1 - a.parity;
+    const CU* ub = (const CU*)G.data + (size_t)(lp * 4 + MU) * Layout<P, R>::NC * a.g.vh;
+    const int ls = FWD ? s : n;
+#pragma unroll
+    for (int k = 0; k < Layout<P, R>::NC; k++) r.u[k] = __ldg(&ub[(size_t)k * a.g.vh + ls]);
+}
+
+template <int J, int P, int R, typename T>
+__device__ __forceinline__ void stag_apply(const GaugeV& G, const StagRaw<P, R>& r, T coef, cx<T> acc[3]) {
+    constexpr bool FWD = (J & 1) == 0;
+    typedef Layout<P, 6> LS;
+    typedef Layout<P, R> LU;
+    T v[6], lv[R];
+#pragma unroll
+    for (int k = 0; k < LS::NC; k++) {
+        if constexpr (P == P16) unpack_codes16<6, T>(r.sp[k], v + k * LS::RPC);
+        else unpack_chunk<P, 6, T>(r.sp[k], 1.f, v + k * LS::RPC);
+    }
+#pragma unroll
+    for (int k = 0; k < LU::NC; k++) {
+        if constexpr (P == P16) unpack_codes16<R, T>(r.u[k], lv + k * LU::RPC);
+        else unpack_chunk<P, R, T>(r.u[k], 1.f, lv + k * LU::RPC);
+    }
+    const float fu = G.scale * (1.f / 32767.f);
+    cx<T> U[3][3];
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int q = 0; q < 3; q++) U[i][q] = mk(lv[(i * 3 + q) * 2], lv[(i * 3 + q) * 2 + 1]);
+    if constexpr (R == 18) {
+#pragma unroll
+        for (int q = 0; q < 3; q++) U[2][q] = mk(lv[(6 + q) * 2], lv[(6 + q) * 2 + 1]);
+    } else {
+        U[2][0] = cj(U[0][1] * U[1][2] - U[0][2] * U[1][1]);
+        U[2][1] = cj(U[0][2] * U[1][0] - U[0][0] * U[1][2]);
+        U[2][2] = cj(U[0][0] * U[1][1] - U[0][1] * U[1][0]);
+        if constexpr (P == P16) {  // conj(row0 x row1) of codes carries the scale twice
+#pragma unroll
+            for (int q = 0; q < 3; q++) U[2][q] = (T)fu * U[2][q];
+        }
+    }
+    const cx<T> ps[3] = {mk(v[0], v[1]), mk(v[2], v[3]), mk(v[4], v[5])};
+    cx<T> o[3];
+    if constexpr (FWD) su3_mv(U, ps, o);
+    else su3_dmv(U, ps, o);
+    // forward hops add, backward hops subtract; FP16 scales and the boundary sign fold in here
+    T f = coef * (T)r.bs * (FWD ? (T)1 : (T)-1);
+    if constexpr (P == P16) f = f * (T)(r.n * (1.f / 32767.f) * fu);
+#pragma unroll
+    for (int q = 0; q < 3; q++) acc[q] = acc[q] + f * o[q];
+}
+
+template <int P, int RL, typename T, int... J>
+__device__ __forceinline__ void stag_hops_pipelined(const HisqArgs& a, const int c[4], int s, int k0, T cn,
+                                                    cx<T> acc[3], std::integer_sequence<int, J...>) {
+    StagRaw<P, 18> F[2];
+    StagRaw<P, RL> L[2];
+    // eta_mu(x), MILC ordering
+    const T eta[4] = {(c[3] & 1) ? (T)-1 : (T)1, ((c[3] + c[0]) & 1) ? (T)-1 : (T)1,
+                      ((c[3] + c[0] + c[1]) & 1) ? (T)-1 : (T)1, (T)1};
+    auto fetch = [&](auto jc) {
+        constexpr int j = decltype(jc)::value;
+        if constexpr (j < 16) {
+            if constexpr ((j >> 1) & 1) stag_fetch<j, P, RL>(a, a.lng, c, s, k0, L[j & 1]);
+            else stag_fetch<j, P, 18>(a, a.fat, c, s, k0, F[j & 1]);
+        }
+    };
+    auto apply = [&](auto jc) {
+        constexpr int j = decltype(jc)::value;
+        if constexpr ((j >> 1) & 1) stag_apply<j, P, RL, T>(a.lng, L[j & 1], eta[j >> 2] * cn, acc);
+        else stag_apply<j, P, 18, T>(a.fat, F[j & 1], eta[j >> 2], acc);
+    };
+    fetch(std::integral_constant<int, 0>());
+    ((fetch(std::integral_constant<int, J + 1>()), apply(std::integral_constant<int, J>())), ...);
+}
+
 // thread / block mapping as in wilson_dslash_kernel (RG threads per site)
 template <int P, int RL, int EPI, int NB, int RG = 1>
 __global__ void __launch_bounds__(256) hisq_dslash_kernel(HisqArgs a) {
@@ -101,10 +206,14 @@ __global__ void __launch_bounds__(256) hisq_dslash_kernel(HisqArgs a) {
 #pragma unroll
             for (int k = 0; k < 3; k++) acc[b][k] = mk((T)0, (T)0);
         const T cn = (T)a.c_naik;
-        stag_dir<0, P, RL, NB, T>(a, c, s, kb, cn, acc);
-        stag_dir<1, P, RL, NB, T>(a, c, s, kb, cn, acc);
-        stag_dir<2, P, RL, NB, T>(a, c, s, kb, cn, acc);
-        stag_dir<3, P, RL, NB, T>(a, c, s, kb, cn, acc);
+        if constexpr (NB == 1 && (P == P16 || P == P32)) {
+            stag_hops_pipelined<P, RL, T>(a, c, s, kb, cn, acc[0], std::make_integer_sequence<int, 16>());
+        } else {
+            stag_dir<0, P, RL, NB, T>(a, c, s, kb, cn, acc);
+            stag_dir<1, P, RL, NB, T>(a, c, s, kb, cn, acc);
+            stag_dir<2, P, RL, NB, T>(a, c, s, kb, cn, acc);
+            stag_dir<3, P, RL, NB, T>(a, c, s, kb, cn, acc);
+        }
         const T half = a.dagger ? (T)-0.5 : (T)0.5;
 #pragma unroll
         for (int b = 0; b < NB; b++) {
