@@ -248,6 +248,26 @@ def gpu_arm(args):
         fp64 = {"solves_per_s": round(1.0 / s64, 3), "iters": i64[0]["iters"],
                 "true_rel_residual": i64[0]["true_rel_residual"], "speedup_mixed_over_fp64": round(value / world * s64, 2)}
 
+    # mixed-precision BiCGStab directly on the Schur operator (the same system and tolerance)
+    bicg = None
+    if args.bicgstab_steps > 0:
+        spb = lib.solve_params(solver=lib.BICGSTAB, tol=TOL, delta=0.1, prec_sloppy=args.prec,
+                               recon_sloppy=lib.R12, graph_iters=args.graph_iters)
+        lat.solve(op, spb, [b], stream=stream, out=[x])  # tunes the BiCGStab kernels
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ib = None
+        for _ in range(args.bicgstab_steps):
+            _, ib = lat.solve(op, spb, [b], stream=stream, out=[x])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sb = e0.elapsed_time(e1) * 1e-3 / args.bicgstab_steps
+        bicg = {"solves_per_s": round(1.0 / sb, 3), "iters": ib[0]["iters"],
+                "reliable_updates": ib[0]["reliable_updates"], "operator_applications": ib[0]["operator_applications"],
+                "true_rel_residual": ib[0]["true_rel_residual"], "speedup_over_mixed_cgnr": round(1.0 / (sb * value / world), 2)}
+
     # end to end through the C ABI with pinned host buffers
     bh = b.cpu().pin_memory()
     xh = torch.empty_like(bh).pin_memory()
@@ -278,7 +298,8 @@ def gpu_arm(args):
             "true_rel_residual_max": res,
             "latency_ms": {"p50": round(float(np.percentile(lat_ms, 50)), 3),
                            "p99": round(float(np.percentile(lat_ms, 99)), 3)},
-            "roofline": roofline, "kernels": per_kernel, "time_breakdown": breakdown, "fp64": fp64, "e2e": e2e,
+            "roofline": roofline, "kernels": per_kernel, "time_breakdown": breakdown, "fp64": fp64,
+            "bicgstab": bicg, "e2e": e2e,
             "gpu_launches": int(launches), "clocks": clocks,
         }
         if not args.no_cpu_baseline:
@@ -585,6 +606,8 @@ def main():
     ap.add_argument("--prec", type=int, default=2, help="sloppy precision: 1 = FP32, 2 = FP16 storage")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--cpu-iters", type=int, default=8)
+    ap.add_argument("--bicgstab-steps", type=int, default=3,
+                    help="also time the mixed-precision BiCGStab solve of the same system")
     ap.add_argument("--ref-iters", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="tmc", choices=["tmc", "multirhs", "hisq", "serving"],

@@ -84,7 +84,7 @@ typedef enum { LQ_R18 = 18, LQ_R12 = 12 } lq_recon;            /* link compressi
 typedef enum { LQ_THIN = 0, LQ_FAT = 1, LQ_LONG = 2 } lq_gauge_kind;
 typedef enum { LQ_HOST = 0, LQ_DEVICE = 1 } lq_loc;
 typedef enum { LQ_WILSON_TM = 0, LQ_WILSON_TM_CLOVER = 1, LQ_HISQ = 2 } lq_action;
-typedef enum { LQ_CGNR = 0, LQ_MIXED_CGNR = 1, LQ_MULTISHIFT_CG = 2 } lq_solver;
+typedef enum { LQ_CGNR = 0, LQ_MIXED_CGNR = 1, LQ_MULTISHIFT_CG = 2, LQ_BICGSTAB = 3 } lq_solver;
 typedef enum { LQ_OP_FULL = 0, LQ_OP_SCHUR = 1 } lq_op_form;
 typedef enum { LQ_WILSON_FIELD = 0, LQ_STAGGERED_FIELD = 1 } lq_field_kind;
 typedef enum { LQ_EVEN = 0, LQ_ODD = 1 } lq_parity;
@@ -109,6 +109,12 @@ typedef struct {
  *   LQ_MIXED_CGNR:    same, with the Krylov vectors and operator in prec_sloppy
  *                     and reliable updates in FP64 whenever the iterated residual
  *                     falls below delta times its maximum since the last update.
+ *   LQ_BICGSTAB:      Wilson actions; BiCGStab (van der Vorst) directly on the
+ *                     even-odd Schur operator (no normal equations; the CPU
+ *                     solver of the paper's Table 2), in prec_sloppy with the same
+ *                     FP64 reliable updates as LQ_MIXED_CGNR (delta; none for
+ *                     prec_sloppy = LQ_F64). A vanishing BiCGStab denominator ends
+ *                     that right-hand side with LQ_EBREAKDOWN.
  *   LQ_MULTISHIFT_CG: HISQ only; one Krylov space for all nshift masses
  *                     masses[0..nshift-1] (ascending) in prec_sloppy, then each
  *                     mass refined by the mixed-precision CG; x gets nrhs*nshift

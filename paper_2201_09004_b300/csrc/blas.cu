@@ -191,6 +191,189 @@ __global__ void finalize_kernel(const df* part, int nblocks, double* sc, int slo
     if (threadIdx.x == 0) fin_apply(sc + (size_t)k * SC_N, df_to_double(sum), slot, op);
 }
 
+// ------------------------------------------------------------- BiCGStab
+// complex scalar (re, im) of rhs k from the solver scalar block
+template <typename T>
+__device__ __forceinline__ cx<T> sc_cx(const double* sc, int k, int slot) {
+    return mk((T)sc[(size_t)k * SC_N + slot], (T)sc[(size_t)k * SC_N + slot + 1]);
+}
+template <typename T>
+__device__ __forceinline__ cx<T> ld_c(const T* v, int j) { return mk(v[2 * j], v[2 * j + 1]); }
+
+// write W block partials (thread 0) and finalise in the last block
+template <int W>
+__device__ __forceinline__ void partials_w(const df (&acc)[W], df* part, int k, const FinArgs& fin) {
+#pragma unroll
+    for (int w = 0; w < W; w++) {
+        const df r = block_sum_df(acc[w]);
+        if (threadIdx.x == 0) part[(size_t)(k * W + w) * gridDim.x + blockIdx.x] = r;
+    }
+    fin_tail_w<W>(part, gridDim.x, gridDim.y, fin);
+}
+
+// (a, b) = sum conj(a) b: W = 2 totals (re, im), then FIN_BICG_ALPHA
+template <int P, int NR>
+__global__ void cdot_kernel(FieldV a, FieldV b, df* part, FinArgs fin) {
+    typedef typename RealT<P>::T T;
+    const int k = blockIdx.y;
+    df acc[2] = {df(0.f), df(0.f)};
+    SITE_LOOP(a.vh) {
+        T va[NR], vb[NR];
+        fload<P, NR, T>(a, k, s, va);
+        fload<P, NR, T>(b, k, s, vb);
+        T re = (T)0, im = (T)0;
+#pragma unroll
+        for (int j = 0; j < NR / 2; j++) {
+            re = fma(va[2 * j], vb[2 * j], re);
+            re = fma(va[2 * j + 1], vb[2 * j + 1], re);
+            im = fma(va[2 * j], vb[2 * j + 1], im);
+            im = fma(-va[2 * j + 1], vb[2 * j], im);
+        }
+        acc[0] = acc[0] + df_of(re);
+        acc[1] = acc[1] + df_of(im);
+    }
+    partials_w<2>(acc, part, k, fin);
+}
+
+// s = r - alpha v (in place in r)
+template <int P, int NR>
+__global__ void bicg_s_kernel(FieldV r, FieldV v, const double* sc) {
+    typedef typename RealT<P>::T T;
+    const int k = blockIdx.y;
+    const cx<T> al = sc_cx<T>(sc, k, SC_AL_R);
+    SITE_LOOP(r.vh) {
+        T vr[NR], vv[NR];
+        fload<P, NR, T>(r, k, s, vr);
+        fload<P, NR, T>(v, k, s, vv);
+#pragma unroll
+        for (int j = 0; j < NR / 2; j++) {
+            const cx<T> o = ld_c(vr, j) - al * ld_c(vv, j);
+            vr[2 * j] = o.r;
+            vr[2 * j + 1] = o.i;
+        }
+        fstore<P, NR, T>(r, k, s, vr);
+    }
+}
+
+// (t, s) and |t|^2: W = 3 totals, then FIN_BICG_OMEGA
+template <int P, int NR>
+__global__ void tdot_kernel(FieldV t, FieldV sf, df* part, FinArgs fin) {
+    typedef typename RealT<P>::T T;
+    const int k = blockIdx.y;
+    df acc[3] = {df(0.f), df(0.f), df(0.f)};
+    SITE_LOOP(t.vh) {
+        T vt[NR], vs[NR];
+        fload<P, NR, T>(t, k, s, vt);
+        fload<P, NR, T>(sf, k, s, vs);
+        T re = (T)0, im = (T)0, tt = (T)0;
+#pragma unroll
+        for (int j = 0; j < NR / 2; j++) {
+            re = fma(vt[2 * j], vs[2 * j], re);
+            re = fma(vt[2 * j + 1], vs[2 * j + 1], re);
+            im = fma(vt[2 * j], vs[2 * j + 1], im);
+            im = fma(-vt[2 * j + 1], vs[2 * j], im);
+            tt = fma(vt[2 * j], vt[2 * j], tt);
+            tt = fma(vt[2 * j + 1], vt[2 * j + 1], tt);
+        }
+        acc[0] = acc[0] + df_of(re);
+        acc[1] = acc[1] + df_of(im);
+        acc[2] = acc[2] + df_of(tt);
+    }
+    partials_w<3>(acc, part, k, fin);
+}
+
+// x += alpha p + omega s; r = s - omega t (s held in r); |r|^2, (r0, r): W = 3, then FIN_BICG_BETA
+template <int PX, int P, int NR>
+__global__ void bicg_xr_kernel(FieldV x, FieldV p, FieldV r, FieldV t, FieldV r0, const double* sc, df* part,
+                               FinArgs fin) {
+    typedef typename RealT<P>::T T;
+    typedef typename MathT<PX, P>::T TX;
+    const int k = blockIdx.y;
+    const cx<TX> al = sc_cx<TX>(sc, k, SC_AL_R), om = sc_cx<TX>(sc, k, SC_OM_R);
+    const cx<T> omt = sc_cx<T>(sc, k, SC_OM_R);
+    df acc[3] = {df(0.f), df(0.f), df(0.f)};
+    SITE_LOOP(x.vh) {
+        T vp[NR], vs[NR], vt[NR], v0[NR];
+        TX vx[NR];
+        fload<P, NR, T>(p, k, s, vp);
+        fload<P, NR, T>(r, k, s, vs);
+        fload<P, NR, T>(t, k, s, vt);
+        fload<P, NR, T>(r0, k, s, v0);
+        fload<PX, NR, TX>(x, k, s, vx);
+        T rr = (T)0, re = (T)0, im = (T)0;
+#pragma unroll
+        for (int j = 0; j < NR / 2; j++) {
+            const cx<TX> pj = mk((TX)vp[2 * j], (TX)vp[2 * j + 1]), sj = mk((TX)vs[2 * j], (TX)vs[2 * j + 1]);
+            const cx<TX> xn = ld_c(vx, j) + al * pj + om * sj;
+            vx[2 * j] = xn.r;
+            vx[2 * j + 1] = xn.i;
+            const cx<T> rn = ld_c(vs, j) - omt * ld_c(vt, j);
+            vs[2 * j] = rn.r;
+            vs[2 * j + 1] = rn.i;
+            rr = fma(rn.r, rn.r, rr);
+            rr = fma(rn.i, rn.i, rr);
+            re = fma(v0[2 * j], rn.r, re);
+            re = fma(v0[2 * j + 1], rn.i, re);
+            im = fma(v0[2 * j], rn.i, im);
+            im = fma(-v0[2 * j + 1], rn.r, im);
+        }
+        acc[0] = acc[0] + df_of(rr);
+        acc[1] = acc[1] + df_of(re);
+        acc[2] = acc[2] + df_of(im);
+        fstore<PX, NR, TX>(x, k, s, vx);
+        fstore<P, NR, T>(r, k, s, vs);
+    }
+    partials_w<3>(acc, part, k, fin);
+}
+
+// p = r + beta (p - omega v)
+template <int P, int NR>
+__global__ void bicg_p_kernel(FieldV p, FieldV r, FieldV v, const double* sc) {
+    typedef typename RealT<P>::T T;
+    const int k = blockIdx.y;
+    const cx<T> be = sc_cx<T>(sc, k, SC_BE_R), om = sc_cx<T>(sc, k, SC_OM_R);
+    SITE_LOOP(p.vh) {
+        T vp[NR], vr[NR], vv[NR];
+        fload<P, NR, T>(p, k, s, vp);
+        fload<P, NR, T>(r, k, s, vr);
+        fload<P, NR, T>(v, k, s, vv);
+#pragma unroll
+        for (int j = 0; j < NR / 2; j++) {
+            const cx<T> o = ld_c(vr, j) + be * (ld_c(vp, j) - om * ld_c(vv, j));
+            vp[2 * j] = o.r;
+            vp[2 * j + 1] = o.i;
+        }
+        fstore<P, NR, T>(p, k, s, vp);
+    }
+}
+
+// |r|^2 and (r0, r): W = 3, then FIN_BICG_RHO
+template <int P, int NR>
+__global__ void rho_kernel(FieldV r, FieldV r0, df* part, FinArgs fin) {
+    typedef typename RealT<P>::T T;
+    const int k = blockIdx.y;
+    df acc[3] = {df(0.f), df(0.f), df(0.f)};
+    SITE_LOOP(r.vh) {
+        T vr[NR], v0[NR];
+        fload<P, NR, T>(r, k, s, vr);
+        fload<P, NR, T>(r0, k, s, v0);
+        T rr = (T)0, re = (T)0, im = (T)0;
+#pragma unroll
+        for (int j = 0; j < NR / 2; j++) {
+            rr = fma(vr[2 * j], vr[2 * j], rr);
+            rr = fma(vr[2 * j + 1], vr[2 * j + 1], rr);
+            re = fma(v0[2 * j], vr[2 * j], re);
+            re = fma(v0[2 * j + 1], vr[2 * j + 1], re);
+            im = fma(v0[2 * j], vr[2 * j + 1], im);
+            im = fma(-v0[2 * j + 1], vr[2 * j], im);
+        }
+        acc[0] = acc[0] + df_of(rr);
+        acc[1] = acc[1] + df_of(re);
+        acc[2] = acc[2] + df_of(im);
+    }
+    partials_w<3>(acc, part, k, fin);
+}
+
 // ---------------------------------------------------------------- launchers
 static dim3 red_grid(int nrhs) { return dim3(RED_BLOCKS, nrhs); }
 static dim3 upd_grid(int vh, int nrhs) {
@@ -314,6 +497,72 @@ void blas_cg_xs(Field& x, const Field& p, Field& s, const Field& q, const double
     else if (x.prec == LQ_F32) cg_xs_from<P32>(x, p, s, q, sc, part, st, fin);
     else if (x.prec == LQ_F16) cg_xs_from<P16>(x, p, s, q, sc, part, st, fin);
     else cg_xs_from<PDF>(x, p, s, q, sc, part, st, fin);
+}
+
+void blas_bicg_cdot(const Field& a, const Field& b, df* part, cudaStream_t st, const FinArgs& fin) {
+    if (a.prec != b.prec) fail(LQ_EINVAL, "blas_bicg_cdot: precision mismatch");
+#define K(NR) cdot_kernel<P_, NR>
+#define L(P) { constexpr int P_ = P; BY_KIND(a, "blas_bicg_cdot", K, red_grid(a.nrhs), a.view(), b.view(), part, fin); }
+    DISPATCH_P(a.prec, L);
+#undef L
+#undef K
+}
+
+void blas_bicg_s(Field& r, const Field& v, const double* sc, cudaStream_t st) {
+    if (r.prec != v.prec) fail(LQ_EINVAL, "blas_bicg_s: precision mismatch");
+    dim3 g = upd_grid(r.vh, r.nrhs);
+#define K(NR) bicg_s_kernel<P_, NR>
+#define L(P) { constexpr int P_ = P; BY_KIND(r, "blas_bicg_s", K, g, r.view(), v.view(), sc); }
+    DISPATCH_P(r.prec, L);
+#undef L
+#undef K
+}
+
+void blas_bicg_tdot(const Field& t, const Field& s, df* part, cudaStream_t st, const FinArgs& fin) {
+    if (t.prec != s.prec) fail(LQ_EINVAL, "blas_bicg_tdot: precision mismatch");
+#define K(NR) tdot_kernel<P_, NR>
+#define L(P) { constexpr int P_ = P; BY_KIND(t, "blas_bicg_tdot", K, red_grid(t.nrhs), t.view(), s.view(), part, fin); }
+    DISPATCH_P(t.prec, L);
+#undef L
+#undef K
+}
+
+template <int PX>
+static void bicg_xr_from(Field& x, const Field& p, Field& r, const Field& t, const Field& r0, const double* sc,
+                         df* part, cudaStream_t st, const FinArgs& fin) {
+#define K(NR) bicg_xr_kernel<PX, P_, NR>
+#define L(P) { constexpr int P_ = P; BY_KIND(x, "blas_bicg_xr", K, red_grid(x.nrhs), x.view(), p.view(), r.view(), t.view(), r0.view(), sc, part, fin); }
+    DISPATCH_P(p.prec, L);
+#undef L
+#undef K
+}
+
+void blas_bicg_xr(Field& x, const Field& p, Field& r, const Field& t, const Field& r0, const double* sc, df* part,
+                  cudaStream_t st, const FinArgs& fin) {
+    if (p.prec != r.prec || p.prec != t.prec || p.prec != r0.prec) fail(LQ_EINVAL, "blas_bicg_xr: precision mismatch");
+    if (x.prec == LQ_F64) bicg_xr_from<P64>(x, p, r, t, r0, sc, part, st, fin);
+    else if (x.prec == LQ_F32) bicg_xr_from<P32>(x, p, r, t, r0, sc, part, st, fin);
+    else if (x.prec == LQ_F16) bicg_xr_from<P16>(x, p, r, t, r0, sc, part, st, fin);
+    else bicg_xr_from<PDF>(x, p, r, t, r0, sc, part, st, fin);
+}
+
+void blas_bicg_p(Field& p, const Field& r, const Field& v, const double* sc, cudaStream_t st) {
+    if (p.prec != r.prec || p.prec != v.prec) fail(LQ_EINVAL, "blas_bicg_p: precision mismatch");
+    dim3 g = upd_grid(p.vh, p.nrhs);
+#define K(NR) bicg_p_kernel<P_, NR>
+#define L(P) { constexpr int P_ = P; BY_KIND(p, "blas_bicg_p", K, g, p.view(), r.view(), v.view(), sc); }
+    DISPATCH_P(p.prec, L);
+#undef L
+#undef K
+}
+
+void blas_bicg_rho(const Field& r, const Field& r0, df* part, cudaStream_t st, const FinArgs& fin) {
+    if (r.prec != r0.prec) fail(LQ_EINVAL, "blas_bicg_rho: precision mismatch");
+#define K(NR) rho_kernel<P_, NR>
+#define L(P) { constexpr int P_ = P; BY_KIND(r, "blas_bicg_rho", K, red_grid(r.nrhs), r.view(), r0.view(), part, fin); }
+    DISPATCH_P(r.prec, L);
+#undef L
+#undef K
 }
 
 void blas_cg_p(Field& p, const Field& r, const double* sc, cudaStream_t st) {

@@ -112,8 +112,14 @@ __device__ __forceinline__ df block_sum_df(df v) {
 
 // ------------------------------------------------------- scalar steps of CG
 // scalar slots per right-hand side in the solver scalar block
-enum { SC_RR = 0, SC_QQ, SC_SS, SC_RRN, SC_ALPHA, SC_BETA, SC_B2, SC_FROZEN, SC_PP, SC_N };
-enum { FIN_SET = 0, FIN_ALPHA = 1, FIN_BETA = 2 };
+// (the BiCGStab scalars are complex: rho = (r0, r), alpha, omega, beta as re/im pairs;
+// SC_BREAK is set when a BiCGStab denominator vanishes)
+enum {
+    SC_RR = 0, SC_QQ, SC_SS, SC_RRN, SC_ALPHA, SC_BETA, SC_B2, SC_FROZEN, SC_PP,
+    SC_RHO_R, SC_RHO_I, SC_AL_R, SC_AL_I, SC_OM_R, SC_OM_I, SC_BE_R, SC_BE_I, SC_BREAK, SC_N
+};
+enum { FIN_SET = 0, FIN_ALPHA = 1, FIN_BETA = 2, FIN_BICG_ALPHA = 3, FIN_BICG_OMEGA = 4, FIN_BICG_BETA = 5,
+       FIN_BICG_RHO = 6 };
 
 // apply the scalar step to the total of a reduction (S: the rhs's scalar block)
 __device__ __forceinline__ void fin_apply(double* S, double tot, int slot, int op) {
@@ -129,6 +135,56 @@ __device__ __forceinline__ void fin_apply(double* S, double tot, int slot, int o
     }
 }
 
+// BiCGStab steps (van der Vorst) on W = 2 or 3 totals of one right-hand side:
+//   FIN_BICG_ALPHA  t = (r0, v):          alpha = rho / (r0, v)
+//   FIN_BICG_OMEGA  t = (t, s), |t|^2:    omega = (t, s) / |t|^2
+//   FIN_BICG_BETA   t = |r|^2, (r0, r):   beta = (rho' / rho)(alpha / omega), rho = rho'
+//   FIN_BICG_RHO    t = |r|^2, (r0, r):   rho = (r0, r) (start, after a reliable update or restart)
+// A frozen right-hand side gets zero steps; a vanishing denominator freezes it and sets SC_BREAK.
+__device__ __forceinline__ void cdiv(double ar, double ai, double br, double bi, double& cr, double& ci) {
+    const double d = br * br + bi * bi;
+    cr = (ar * br + ai * bi) / d;
+    ci = (ai * br - ar * bi) / d;
+}
+__device__ __forceinline__ void fin_apply_bicg(double* S, const double* t, int op) {
+    const bool frozen = S[SC_FROZEN] != 0.0;
+    if (op == FIN_BICG_ALPHA) {
+        if (frozen || (t[0] == 0.0 && t[1] == 0.0)) {
+            if (!frozen) { S[SC_BREAK] = 1.0; S[SC_FROZEN] = 1.0; }
+            S[SC_AL_R] = S[SC_AL_I] = 0.0;
+        } else {
+            cdiv(S[SC_RHO_R], S[SC_RHO_I], t[0], t[1], S[SC_AL_R], S[SC_AL_I]);
+        }
+    } else if (op == FIN_BICG_OMEGA) {
+        if (frozen || !(t[2] > 0.0)) {
+            if (!frozen) { S[SC_BREAK] = 1.0; S[SC_FROZEN] = 1.0; }
+            S[SC_OM_R] = S[SC_OM_I] = 0.0;
+        } else {
+            S[SC_OM_R] = t[0] / t[2];
+            S[SC_OM_I] = t[1] / t[2];
+        }
+    } else if (op == FIN_BICG_BETA) {
+        S[SC_SS] = t[0];
+        double qr = 0.0, qi = 0.0, br = 0.0, bi = 0.0;
+        const bool ok = !frozen && (S[SC_RHO_R] != 0.0 || S[SC_RHO_I] != 0.0) && (S[SC_OM_R] != 0.0 || S[SC_OM_I] != 0.0);
+        if (ok) {
+            cdiv(t[1], t[2], S[SC_RHO_R], S[SC_RHO_I], qr, qi);  // rho' / rho
+            double ar, ai;
+            cdiv(S[SC_AL_R], S[SC_AL_I], S[SC_OM_R], S[SC_OM_I], ar, ai);  // alpha / omega
+            br = qr * ar - qi * ai;
+            bi = qr * ai + qi * ar;
+        }
+        S[SC_BE_R] = br;
+        S[SC_BE_I] = bi;
+        S[SC_RHO_R] = t[1];
+        S[SC_RHO_I] = t[2];
+    } else if (op == FIN_BICG_RHO) {  // |r|^2 of the sloppy copy goes to SC_RRN
+        S[SC_RRN] = t[0];
+        S[SC_RHO_R] = t[1];
+        S[SC_RHO_I] = t[2];
+    }
+}
+
 // A reduction finalised inside the kernel that produces its partials: the last
 // block to finish (atomic ticket) sums every rhs's partials in index order and
 // applies the scalar step, then re-arms the ticket. sc == nullptr: no fusion.
@@ -138,6 +194,36 @@ struct FinArgs {
     int op = 0;
     unsigned* count = nullptr;
 };
+
+// W totals per right-hand side: partial w of rhs k from block b at part[(k * W + w) * nparts + b]
+template <int W>
+__device__ __forceinline__ void fin_tail_w(const df* part, int nparts, int nrhs, const FinArgs& f) {
+    if (!f.sc) return;
+    __shared__ int last_w;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned total = gridDim.x * gridDim.y * gridDim.z;
+        last_w = atomicAdd(f.count, 1u) == total - 1;
+    }
+    __syncthreads();
+    if (!last_w) return;
+    __threadfence();
+    for (int k = 0; k < nrhs; k++) {
+        double tot[W];
+#pragma unroll
+        for (int w = 0; w < W; w++) {
+            const df* pk = part + (size_t)(k * W + w) * nparts;
+            df sum(0.f);
+            for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+                const float2 v = __ldcg((const float2*)(pk + i));
+                sum = sum + df(v.x, v.y);
+            }
+            tot[w] = df_to_double(block_sum_df(sum));
+        }
+        if (threadIdx.x == 0) fin_apply_bicg(f.sc + (size_t)k * SC_N, tot, f.op);
+    }
+    if (threadIdx.x == 0) *f.count = 0u;
+}
 
 // called by every thread of every block after thread 0 wrote the block's partials
 __device__ __forceinline__ void fin_tail(const df* part, int nparts, int nrhs, const FinArgs& f) {

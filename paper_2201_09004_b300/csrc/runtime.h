@@ -248,6 +248,17 @@ void blas_xmy_norm(Field& s, const Field& b, const Field& q, df* part, cudaStrea
 // CG update: alpha_k = sc[k*SC_N + SC_ALPHA]; x += alpha p; s -= alpha q; partial |s|^2
 void blas_cg_xs(Field& x, const Field& p, Field& s, const Field& q, const double* sc, df* part,
                 cudaStream_t st, const FinArgs& fin = FinArgs());
+// BiCGStab vector steps (complex device scalars in the solver scalar block, see core.cuh):
+// (a, b) -> partials (2 per block), s = r - alpha v in place, (t, s) and |t|^2 (3),
+// x += alpha p + omega s with r = s - omega t and |r|^2, (r0, r) (3), p = r + beta (p - omega v),
+// |r|^2 and (r0, r) (3). Reductions are finalised by the last block (fin.sc non-null).
+void blas_bicg_cdot(const Field& a, const Field& b, df* part, cudaStream_t st, const FinArgs& fin);
+void blas_bicg_s(Field& r, const Field& v, const double* sc, cudaStream_t st);
+void blas_bicg_tdot(const Field& t, const Field& s, df* part, cudaStream_t st, const FinArgs& fin);
+void blas_bicg_xr(Field& x, const Field& p, Field& r, const Field& t, const Field& r0, const double* sc, df* part,
+                  cudaStream_t st, const FinArgs& fin);
+void blas_bicg_p(Field& p, const Field& r, const Field& v, const double* sc, cudaStream_t st);
+void blas_bicg_rho(const Field& r, const Field& r0, df* part, cudaStream_t st, const FinArgs& fin);
 // p = r + beta p, beta_k = sc[k*SC_N + SC_BETA]
 void blas_cg_p(Field& p, const Field& r, const double* sc, cudaStream_t st);
 

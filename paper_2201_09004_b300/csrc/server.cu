@@ -74,7 +74,7 @@ size_t solve_workspace_bytes(const Lattice& lat, const lq_op_params& op, const l
     size_t canon = (size_t)lat.V * (hisq ? 6 : 24) * sizeof(double) * (size_t)(nrhs + nrhs * ns);
     size_t b;
     if (!hisq) {
-        b = 7 * f64 + 3 * f64 + fx + 5 * fs;
+        b = 7 * f64 + 3 * f64 + fx + (sp.solver == LQ_BICGSTAB ? 6 : 5) * fs;
     } else {
         b = 8 * f64 + 3 * f64 + fx + 4 * fs;
         if (ns > 1) b += (size_t)(3 + 2 * ns) * field_bytes(kind, ps, 2 * nrhs, lat.vh);

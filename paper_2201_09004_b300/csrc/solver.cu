@@ -38,7 +38,8 @@ struct Scalars {
         st = s;
         nrhs = n;
         // hopping kernels write one partial per site block: at least 8 sites per block
-        size_t per = std::max<size_t>((size_t)(l.vh + 7) / 8, (size_t)RED_BLOCKS);
+        // (BiCGStab reductions write 3 partials per BLAS block)
+        size_t per = std::max<size_t>((size_t)(l.vh + 7) / 8, (size_t)3 * RED_BLOCKS);
         dev = (double*)ws_get(l, sizeof(double) * SC_N * n, false, s);
         LQ_CUDA(cudaMemsetAsync(dev, 0, sizeof(double) * SC_N * n, s));
         part = (df*)ws_get(l, sizeof(df) * per * n, false, s);
@@ -276,6 +277,172 @@ static CgResult cgnr_mixed(Lattice& lat, const OpDesc& ops, const OpDesc& op64, 
     return res;
 }
 
+// Mixed-precision BiCGStab (van der Vorst) on Mhat for all right-hand sides of
+// bhat: the iteration runs in the sloppy precision with complex device scalars;
+// the host reads |r|^2 one iteration late (as in cgnr_mixed). A reliable update
+// folds x_lo into x_hi, recomputes r = bhat - Mhat x_hi in FP64 accuracy and
+// rho = (r0, r), and keeps p and the shadow residual r0.
+static CgResult bicgstab_mixed(Lattice& lat, const OpDesc& ops, const OpDesc& op64, Field& bhat, Field& x_hi,
+                               const std::vector<double>& tol_abs, double delta, int maxiter, int graph_iters,
+                               cudaStream_t st) {
+    const int n = bhat.nrhs;
+    const int ps = ops.prec;
+    const int px = ps == LQ_F16 ? LQ_F32 : ps;
+    const int WF = LQ_WILSON_FIELD;
+    Pool pool(lat, st);
+    const int ph = op64.prec;
+    Field r_hi = pool.get(WF, ph, n), q64 = pool.get(WF, ph, n), t64 = pool.get(WF, ph, n);
+    Field x_lo = pool.get(WF, px, n);
+    Field r = pool.get(WF, ps, n), r0 = pool.get(WF, ps, n), p = pool.get(WF, ps, n);
+    Field v = pool.get(WF, ps, n), t = pool.get(WF, ps, n), tmp = pool.get(WF, ps, n);
+    Scalars sc;
+    sc.init(lat, n, st);
+    CgResult res(n);
+    std::vector<double> rmax(n, 0.0), ones(n, 1.0);
+    std::vector<char> done(n, 0);
+
+    blas_zero(x_hi, st);
+    blas_zero(x_lo, st);
+    blas_norm2(bhat, sc.part, st, sc.f(SC_SS, FIN_SET));
+    blas_copy(r, bhat, st);
+    blas_copy(r0, r, st);
+    blas_copy(p, r, st);
+    blas_bicg_rho(r, r0, sc.part, st, sc.f(0, FIN_BICG_RHO));  // rho = (r0, r)
+    sc.pull(st);
+    std::vector<int> restarts(n, 0);
+    for (int k = 0; k < n; k++) {
+        check_finite(sc.h(k, SC_SS), "source");
+        rmax[k] = sqrt(sc.h(k, SC_SS));
+        if (rmax[k] <= tol_abs[k]) {
+            done[k] = 1;
+            res.status[k] = LQ_OK;
+            sc.set(k, SC_FROZEN, 1.0, st);
+        }
+    }
+    auto all_done = [&]() {
+        for (int k = 0; k < n; k++)
+            if (!done[k]) return false;
+        return true;
+    };
+    double* ring = (double*)ws_get(lat, sizeof(double) * SC_N * n * 2, true, st);
+    cudaEvent_t ev[2];
+    LQ_CUDA(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+    LQ_CUDA(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+    struct Cleanup {
+        Lattice& l; double* r; cudaEvent_t* e; cudaStream_t s;
+        ~Cleanup() { ws_put(l, r, s); cudaEventDestroy(e[0]); cudaEventDestroy(e[1]); }
+    } cleanup{lat, ring, ev, st};
+    auto slot = [&](int i) { return ring + (size_t)(i & 1) * SC_N * n; };
+    auto iteration = [&](double* dst) {
+        schur_wilson(lat, ops, 0, p, v, tmp, nullptr, st);                     // v = Mhat p
+        blas_bicg_cdot(r0, v, sc.part, st, sc.f(0, FIN_BICG_ALPHA));            // alpha = rho / (r0, v)
+        blas_bicg_s(r, v, sc.dev, st);                                         // s = r - alpha v
+        schur_wilson(lat, ops, 0, r, t, tmp, nullptr, st);                     // t = Mhat s
+        blas_bicg_tdot(t, r, sc.part, st, sc.f(0, FIN_BICG_OMEGA));            // omega = (t, s) / |t|^2
+        blas_bicg_xr(x_lo, p, r, t, r0, sc.dev, sc.part, st, sc.f(0, FIN_BICG_BETA));  // x, r, rho', beta
+        blas_bicg_p(p, r, v, sc.dev, st);                                      // p = r + beta (p - omega v)
+        if (dst) LQ_CUDA(cudaMemcpyAsync(dst, sc.dev, sizeof(double) * SC_N * n, cudaMemcpyDeviceToHost, st));
+    };
+    const int gk = graph_iters < 0 ? 0 : (graph_iters == 0 ? 1 : graph_iters);
+    Graph graphs[2];
+    struct GraphCleanup {
+        Graph* g;
+        ~GraphCleanup() { graph_destroy(g[0]); graph_destroy(g[1]); }
+    } graph_cleanup{graphs};
+    bool use_graphs = gk > 0;
+    int it = 0, launch_no = 0, pending = -1;
+    while (!all_done() && it < maxiter) {
+        const int gi = launch_no & 1;
+        int steps = 1;
+        if (use_graphs && it > 0 && it + gk <= maxiter) {
+            Graph& g = graphs[gi];
+            if (!g.exec) {
+                bool ok = graph_capture_begin(st);
+                if (ok) {
+                    try {
+                        for (int j = 0; j < gk; j++) iteration(j == gk - 1 ? slot(gi) : nullptr);
+                    } catch (...) {
+                        ok = false;
+                    }
+                    ok = graph_capture_end(st, g) && ok;
+                }
+                if (!ok) use_graphs = false;
+            } else {
+                graph_collect(g);
+            }
+            if (g.exec) {
+                graph_launch(g, st);
+                steps = gk;
+            } else {
+                iteration(slot(gi));
+            }
+        } else {
+            iteration(slot(gi));
+        }
+        LQ_CUDA(cudaEventRecord(ev[gi], st));
+        for (int k = 0; k < n; k++)
+            if (!done[k]) {
+                res.iters[k] += steps;
+                res.applications[k] += 2 * steps;
+            }
+        const int prev = pending;
+        pending = launch_no;
+        launch_no++;
+        it += steps;
+        bool update = it >= maxiter;
+        if (prev >= 0) {
+            LQ_CUDA(cudaEventSynchronize(ev[prev & 1]));
+            const double* hs = slot(prev);
+            for (int k = 0; k < n; k++) {
+                if (done[k]) continue;
+                if (hs[(size_t)k * SC_N + SC_BREAK] != 0.0) update = true;
+                double ss = sqrt(hs[(size_t)k * SC_N + SC_SS]);
+                check_finite(ss, "iterated residual");
+                if (ss < delta * rmax[k] || ss <= tol_abs[k]) update = true;
+            }
+        }
+        if (!update) continue;
+        pending = -1;
+        // reliable update: fold x_lo into x_hi, recompute r in FP64 accuracy, rho = (r0, r)
+        blas_axpy_h(x_hi, ones.data(), x_lo, st);
+        blas_zero(x_lo, st);
+        schur_wilson(lat, op64, 0, x_hi, q64, t64, nullptr, st);
+        blas_xmy_norm(r_hi, bhat, q64, sc.part, st, sc.f(SC_SS, FIN_SET));
+        blas_copy(r, r_hi, st);
+        blas_bicg_rho(r, r0, sc.part, st, sc.f(0, FIN_BICG_RHO));
+        sc.pull(st);
+        for (int k = 0; k < n; k++) {
+            if (done[k]) continue;
+            res.updates[k]++;
+            res.applications[k] += 2;
+            double ss = sqrt(sc.h(k, SC_SS));
+            check_finite(ss, "true residual");
+            rmax[k] = ss;
+            if (ss <= tol_abs[k]) {
+                done[k] = 1;
+                res.status[k] = LQ_OK;
+                sc.set(k, SC_FROZEN, 1.0, st);
+            } else if (sc.h(k, SC_BREAK) != 0.0) {
+                // a vanishing denominator: restart this right-hand side from its true residual
+                if (++restarts[k] > 8) {
+                    done[k] = 1;
+                    res.status[k] = LQ_EBREAKDOWN;
+                    continue;
+                }
+                Field r0k = r0.sub(k, 1), pk = p.sub(k, 1), rk = r.sub(k, 1);
+                blas_copy(r0k, rk, st);
+                blas_copy(pk, rk, st);
+                sc.set(k, SC_BREAK, 0.0, st);
+                sc.set(k, SC_FROZEN, 0.0, st);
+                FinArgs fk = sc.f(0, FIN_BICG_RHO);
+                fk.sc += (size_t)k * SC_N;  // the sub-field's rhs 0 is rhs k
+                blas_bicg_rho(rk, r0k, sc.part, st, fk);
+            }
+        }
+    }
+    return res;
+}
+
 int solve_wilson(Lattice& lat, const lq_op_params& opp, const lq_solve_params& sp, int nrhs, const double* const* b,
                  double* const* x, lq_solve_info* info, cudaStream_t st) {
     if (opp.action == LQ_WILSON_TM_CLOVER && !lat.has_clover) fail(LQ_EINVAL, "clover action without clover term");
@@ -283,7 +450,8 @@ int solve_wilson(Lattice& lat, const lq_op_params& opp, const lq_solve_params& s
     if (nrhs < 1 || nrhs > 64) fail(LQ_EINVAL, "nrhs must be in [1, 64]");
     int ps = sp.prec_sloppy;
     if (ps < LQ_F64 || ps > LQ_F16) fail(LQ_EINVAL, "prec_sloppy");
-    if (sp.solver != LQ_CGNR && sp.solver != LQ_MIXED_CGNR) fail(LQ_EINVAL, "solver kind for a Wilson action");
+    if (sp.solver != LQ_CGNR && sp.solver != LQ_MIXED_CGNR && sp.solver != LQ_BICGSTAB)
+        fail(LQ_EINVAL, "solver kind for a Wilson action");
     if (!(sp.tol > 0)) fail(LQ_EINVAL, "tol must be positive");
     const int recon = sp.recon_sloppy == 12 ? 12 : 18;
     // the FP64-accuracy steps: native FP64 for the plain FP64 solver, double-float
@@ -291,7 +459,7 @@ int solve_wilson(Lattice& lat, const lq_op_params& opp, const lq_solve_params& s
     const int ph = ps == LQ_F64 ? LQ_F64 : LQ_F32X2;
     const OpDesc op64 = wilson_desc(opp, ph, 18);
     const OpDesc ops = wilson_desc(opp, ps, recon);
-    double delta = sp.solver == LQ_MIXED_CGNR ? (sp.delta > 0 ? sp.delta : 0.1) : 0.0;
+    double delta = sp.solver != LQ_CGNR ? (sp.delta > 0 ? sp.delta : 0.1) : 0.0;
     if (ps == LQ_F64) delta = 0.0;
     const int maxiter = sp.maxiter > 0 ? sp.maxiter : 100000;
 
@@ -337,7 +505,9 @@ int solve_wilson(Lattice& lat, const lq_op_params& opp, const lq_solve_params& s
         blas_copy(bhat, be, st);
         blas_axpy_h(bhat, ones.data(), te, st);
 
-        CgResult cr = cgnr_mixed(lat, ops, op64, bhat, xe, tol_abs, delta, maxiter, sp.graph_iters, st);
+        CgResult cr = sp.solver == LQ_BICGSTAB
+                          ? bicgstab_mixed(lat, ops, op64, bhat, xe, tol_abs, delta, maxiter, sp.graph_iters, st)
+                          : cgnr_mixed(lat, ops, op64, bhat, xe, tol_abs, delta, maxiter, sp.graph_iters, st);
 
         // x_o = A_oo^{-1} (b_o + H_oe x_e)
         wilson_dslash(lat, op64, 1, 0, EPI_HOP, xe, to, nullptr, nullptr, st);

@@ -26,7 +26,7 @@ R18, R12 = 18, 12
 THIN, FAT, LONG = 0, 1, 2
 HOST, DEVICE = 0, 1
 WILSON_TM, WILSON_TM_CLOVER, HISQ = 0, 1, 2
-CGNR, MIXED_CGNR, MULTISHIFT_CG = 0, 1, 2
+CGNR, MIXED_CGNR, MULTISHIFT_CG, BICGSTAB = 0, 1, 2, 3
 OP_FULL, OP_SCHUR = 0, 1
 WILSON_FIELD, STAGGERED_FIELD = 0, 1
 

@@ -194,6 +194,40 @@ def test_solve_clover_mixed_multi_rhs(L, orc, prec):
     assert rel_err(x1[0], xs[1]) < 1e-8
 
 
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_bicgstab_tiny(L, orc, prec):
+    """BiCGStab directly on the even-odd Schur operator (the paper's Table 2 CPU
+    solver), plain FP64 or mixed with reliable updates: the oracle's true
+    residual <= 1e-10 and the solution equals the oracle's."""
+    dims = (4, 4, 4, 8)
+    lat, U = make(L, dims, 101)
+    b = synth.z2_source(dims, 201).numpy()
+    op = L.op_params(L.WILSON_TM, 0.1, 0.05)
+    xs, info = lat.solve(op, L.solve_params(solver=L.BICGSTAB, tol=1e-10, prec_sloppy=prec), [b])
+    assert info[0]["status"] == 0
+    assert true_residual(orc, dims, U, None, 0.1, 0.05, b, xs[0]) <= 1e-10
+    x_ref, _ = orc.Wilson(dims, U, 0.1, 0.05).bicgstab(b, tol=1e-13)
+    assert rel_err(xs[0], x_ref) < 1e-8
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_bicgstab_clover_multi_rhs_equals_cgnr(L, orc, prec):
+    """Twisted clover, three right-hand sides at once: every BiCGStab solution
+    meets the oracle's true residual and agrees with the CGNR solution."""
+    dims = (4, 4, 6, 8)
+    lat, U = make(L, dims, 108, c_sw=1.05)
+    C = orc.clover(dims, U, 1.05)
+    op = L.op_params(L.WILSON_TM_CLOVER, 0.05, 0.01, c_sw=1.05)
+    bs = [synth.z2_source(dims, 208 + k).numpy() for k in range(2)]
+    bs.append(synth.point_source(dims, (1, 2, 3, 4), 2, 1).numpy())
+    xs, info = lat.solve(op, L.solve_params(solver=L.BICGSTAB, tol=1e-10, prec_sloppy=prec), bs)
+    xc, _ = lat.solve(op, L.solve_params(solver=L.MIXED_CGNR, tol=1e-10, prec_sloppy=prec), bs)
+    for b, x, y, inf in zip(bs, xs, xc, info):
+        assert inf["status"] == 0
+        assert true_residual(orc, dims, U, C, 0.05, 0.01, b, x) <= 1e-10
+        assert rel_err(x, y) < 1e-8
+
+
 def test_workspace_kept_between_solves(L, orc):
     """The work buffers a solve takes stay with the lattice: a second solve
     allocates nothing more and returns bit-identical solutions (the reductions
