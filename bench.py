@@ -56,7 +56,7 @@ FLOPS_PER_SITE = {"hop": 1320, "ainv": 1320 + 2 * 6 * 6 * 8, "xpay": 1320 + 2 * 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of the
 # benchmark configuration (profiles/wilson_dslash_f16_ainv_24x24x24x64.md); set back to
 # None whenever the kernel changes after the capture.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {"wilson_dslash_f16_ainv": 254_870_000}
 
 REASONS = {
     0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap", 0x8: "hw_slowdown",
@@ -177,8 +177,7 @@ def gpu_arm(args):
     sampler = ClockSampler()
     if rank == 0:
         sampler.start(local)
-    lib.profile_reset()
-    lib.profile_enable(True)
+    lib.profile_enable(False)
     launches0 = lib.launch_count()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -193,10 +192,24 @@ def gpu_arm(args):
     ev1.record(stream)
     barrier()
     launches = lib.launch_count() - launches0
-    lib.profile_enable(False)
     clocks = sampler.stop() if rank == 0 else None
     value, s_max = job_rate(ev0.elapsed_time(ev1) * 1e-3, args.steps, world, dev)
     ms_max = s_max * 1e3
+
+    # second timed pass over the same steps with a CUDA event pair around every
+    # launch of the library (on its stream): per-kernel times for the roofline
+    lib.profile_reset()
+    lib.profile_enable(True)
+    ep0 = torch.cuda.Event(enable_timing=True)
+    ep1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    ep0.record(stream)
+    for _ in range(args.steps):
+        lat.solve(op, sp, [b], stream=stream, out=[x])
+    ep1.record(stream)
+    barrier()
+    lib.profile_enable(False)
+    profiled_ms = ep0.elapsed_time(ep1) / args.steps
 
     # dominant kernel and its roofline, from the events recorded in the timed region
     kernels = {}
@@ -217,7 +230,9 @@ def gpu_arm(args):
                 "frac": round(achieved / peak, 4), "peak_source": peak_kind, "frac_of_nominal_8tbs": round(achieved / 8000.0, 4),
                 "algorithmic_bytes_per_launch": byts, "avg_launch_us": round(avg_s * 1e6, 2),
                 "gflops": round(FLOPS_PER_SITE[epi] * vh / avg_s / 1e9, 1),
-                "share_of_kernel_time": round(tot / all_t, 4), "traffic": NCU_TRAFFIC.get(dom)}
+                "share_of_kernel_time": round(tot / all_t, 4), "traffic": NCU_TRAFFIC.get(dom),
+                "pass": "second timed pass of the same steps with per-launch CUDA events",
+                "profiled_ms_per_step": round(profiled_ms, 3)}
     per_kernel = {k: {"launches": v[0], "ms": round(v[1], 3),
                       "gbs": round(BYTES_PER_SITE[k] * vh / (v[1] / v[0] * 1e-3) / 1e9, 1)} for k, v in kernels.items()}
     # device time per solve of every kernel family in the timed region
@@ -371,6 +386,19 @@ def run_multirhs(args):
     bps = {"wilson_dslash_f16_ainv": n * 52 + 8 * 24 + (144 * 2 + 4) + n * 52,
            "wilson_dslash_f16_xpay": n * 52 + 8 * 24 + (72 * 2 + 4) + n * 52 + n * 52}
     kern = _kernel_table(list(bps) + ["wilson_dslash_f32x2_ainv", "wilson_dslash_f32x2_xpay"], vh, bps)
+    # the same 36 right-hand sides with mixed-precision BiCGStab on the Schur operator
+    spb = lib.solve_params(solver=lib.BICGSTAB, tol=TOL, prec_sloppy=args.prec, recon_sloppy=lib.R12)
+    lat.solve(ops[0], spb, srcs[:4], out=xs[:4])
+    torch.cuda.synchronize()
+    e0, e1 = _events()
+    e0.record()
+    binfos = []
+    for op in ops:
+        _, inf = lat.solve(op, spb, srcs, out=xs)
+        binfos += inf
+    e1.record()
+    torch.cuda.synchronize()
+    tts_b = e0.elapsed_time(e1) * 1e-3
     sp64 = lib.solve_params(solver=lib.CGNR, tol=TOL, prec_sloppy=lib.F64)
     e0, e1 = _events()
     e0.record()
@@ -387,7 +415,12 @@ def run_multirhs(args):
             "all_converged": all(i["status"] == 0 for i in infos),
             "fp64_single_rhs": {"seconds_per_solve": round(t64, 3), "iters": i64[0]["iters"],
                                 "seconds_for_36_extrapolated": round(36 * t64, 3)},
-            "speedup_vs_fp64_single_rhs": round(36 * t64 / tts, 2), "kernels": kern}
+            "speedup_vs_fp64_single_rhs": round(36 * t64 / tts, 2),
+            "bicgstab": {"seconds": round(tts_b, 3), "iters_max": max(i["iters"] for i in binfos),
+                         "true_rel_residual_max": max(i["true_rel_residual"] for i in binfos),
+                         "all_converged": all(i["status"] == 0 for i in binfos),
+                         "speedup_vs_fp64_single_rhs": round(36 * t64 / tts_b, 2)},
+            "kernels": kern}
     print(json.dumps(line), flush=True)
 
 
