@@ -424,6 +424,87 @@ def run_multirhs(args):
     print(json.dumps(line), flush=True)
 
 
+def run_dslash(args):
+    """The operator kernels alone on resident fields (24^3x64, one output parity per
+    launch): FP16 / FP32 R12 hopping term, the FP16 A^-1 D and A y - D kernels of the
+    Schur operator, and the HISQ FP16 hopping term on the same volume. L2 is flushed
+    (a 256 MB write) before every timed launch; each launch is timed alone with CUDA
+    events on its stream. Reports algorithmic GB/s against the measured copy peak
+    and the nominal 8 TB/s."""
+    import torch
+    from paper_2201_09004_b300 import lib, synth
+    torch.cuda.set_device(0)
+    dims = DIMS
+    vh = int(np.prod(dims)) // 2
+    U = synth.thin_links(dims, GAUGE_SEED, device="cuda")
+    lat = lib.Lattice(dims)
+    lat.load_gauge(lib.THIN, U)
+    lat.load_clover(C_SW)
+    del U
+    V = synth.fat_links(dims, 104, device="cuda")
+    lat.load_gauge(lib.FAT, V)
+    del V
+    W = synth.long_links(dims, 105, device="cuda")
+    lat.load_gauge(lib.LONG, W)
+    del W
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    peak, peak_kind = measured_peaks()
+    stream = torch.cuda.current_stream()
+    reps = max(args.steps, 10)
+
+    def timed(fn):
+        fn()
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = _events()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e3)
+        return float(np.median(ts))
+
+    out = {}
+    opw = lib.op_params(lib.WILSON_TM_CLOVER, MASS, MU, c_sw=C_SW)
+    oph = lib.op_params(lib.HISQ, 0.01)
+    psi = synth.gaussian_field(dims, 206, device="cuda")
+    chi = synth.gaussian_field(dims, 207, ncomp=3, device="cuda")
+    cases = [("wilson_hop_f16_r12", lib.F16, 52 + 8 * 24 + 52, "hop"),
+             ("wilson_hop_f32_r12", lib.F32, 96 + 8 * 48 + 96, "hop"),
+             ("wilson_schur_f16_r12 (A^-1 D + A y - D)", lib.F16, (52 + 8 * 24 + 292 + 52) + (52 + 8 * 24 + 148 + 52 + 52), "schur"),
+             ("hisq_hop_f16", lib.F16, 16 + 8 * 36 + 8 * 24 + 16, "hisq")]
+    for name, prec, bps, kind in cases:
+        if kind == "hisq":
+            fi = lib.Field(lat, lib.STAGGERED_FIELD, prec)
+            fo = lib.Field(lat, lib.STAGGERED_FIELD, prec)
+            fi.load(0, 1, chi)
+            us = timed(lambda: lib.dslash_field(lat, oph, 0, fi, fo, stream=stream))
+            launches = 1
+        else:
+            fi = lib.Field(lat, lib.WILSON_FIELD, prec)
+            fo = lib.Field(lat, lib.WILSON_FIELD, prec)
+            if kind == "hop":
+                fi.load(0, 1, psi)
+                us = timed(lambda: lib.dslash_field(lat, opw, 0, fi, fo, stream=stream))
+                launches = 1
+            else:
+                ft = lib.Field(lat, lib.WILSON_FIELD, prec)
+                fi.load(0, 0, psi)
+                us = timed(lambda: lib.schur_field(lat, opw, fi, fo, ft, stream=stream))
+                launches = 2
+        gbs = bps * vh / (us * 1e-6) / 1e9
+        out[name] = {"us": round(us, 2), "launches": launches, "bytes_per_site": bps, "GB_s": round(gbs, 1),
+                     "frac_of_measured": round(gbs / peak, 4), "frac_of_nominal_8tbs": round(gbs / 8000.0, 4)}
+    line = {"workload": "dslash", "metric": "Dslash HBM GB/s vs roofline (algorithmic bytes, L2 flushed)",
+            "config": {"dims": list(dims), "sites_per_parity": vh, "peak_gbs": peak, "peak_source": peak_kind,
+                       "reps": reps, "l2": "flushed (256 MB write) before every timed launch"},
+            "kernels": out}
+    print(json.dumps(line), flush=True)
+
+
 def run_hisq(args):
     """48^3x144 HISQ (fat + long links), multi-shift CG over m in {0.002, 0.01, 0.02, 0.05},
     one Z2 source, mixed precision with double-float refinement to 1e-10 for every mass."""
@@ -643,9 +724,10 @@ def main():
                     help="also time the mixed-precision BiCGStab solve of the same system")
     ap.add_argument("--ref-iters", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="tmc", choices=["tmc", "multirhs", "hisq", "serving"],
+    ap.add_argument("--workload", default="tmc", choices=["tmc", "multirhs", "hisq", "serving", "dslash"],
                     help="tmc: 24^3x64 twisted-mass clover (default, the headline); multirhs: 32^3x96, "
-                         "36 right-hand sides; hisq: 48^3x144 multi-shift; serving: Poisson request stream")
+                         "36 right-hand sides; hisq: 48^3x144 multi-shift; serving: Poisson request stream; "
+                         "dslash: the operator kernels alone")
     ap.add_argument("--requests", type=int, default=100, help="serving: number of requests")
     ap.add_argument("--graph-iters", type=int, default=0,
                     help="CG iterations per CUDA graph (0: library default, -1: no graphs)")
@@ -658,6 +740,8 @@ def main():
         run_multirhs(args)
     elif args.workload == "hisq":
         run_hisq(args)
+    elif args.workload == "dslash":
+        run_dslash(args)
     elif args.workload == "serving":
         run_serving(args)
     else:

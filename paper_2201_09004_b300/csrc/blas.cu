@@ -164,6 +164,31 @@ __global__ void cg_xs_kernel(FieldV x, FieldV p, FieldV sf, FieldV qf, const dou
     fin_tail(part, gridDim.x, gridDim.y, fin);
 }
 
+// p = r + beta p with partial |p|^2
+template <int P, int NR>
+__global__ void cg_p_norm_kernel(FieldV p, FieldV r, const double* sc, df* part, FinArgs fin) {
+    typedef typename RealT<P>::T T;
+    const int k = blockIdx.y;
+    const T b = (T)sc[(size_t)k * SC_N + SC_BETA];
+    df acc(0.f);
+    SITE_LOOP(p.vh) {
+        T vp[NR], vr[NR];
+        fload<P, NR, T>(p, k, s, vp);
+        fload<P, NR, T>(r, k, s, vr);
+        T t = (T)0;
+#pragma unroll
+        for (int q = 0; q < NR; q++) {
+            vp[q] = fma(b, vp[q], vr[q]);
+            t = fma(vp[q], vp[q], t);
+        }
+        acc = acc + df_of(t);
+        fstore<P, NR, T>(p, k, s, vp);
+    }
+    df rr = block_sum_df(acc);
+    if (threadIdx.x == 0) part[(size_t)k * gridDim.x + blockIdx.x] = rr;
+    fin_tail(part, gridDim.x, gridDim.y, fin);
+}
+
 // p = r + beta p
 template <int P, int NR>
 __global__ void cg_p_kernel(FieldV p, FieldV r, const double* sc) {
@@ -188,7 +213,7 @@ __global__ void finalize_kernel(const df* part, int nblocks, double* sc, int slo
     df sum(0.f);
     for (int i = threadIdx.x; i < nblocks; i += blockDim.x) sum = sum + pk[i];
     sum = block_sum_df(sum);
-    if (threadIdx.x == 0) fin_apply(sc + (size_t)k * SC_N, df_to_double(sum), slot, op);
+    if (threadIdx.x == 0) fin_apply(sc + (size_t)k * SC_N, df_to_double(sum), slot, op, 0.0);
 }
 
 // ------------------------------------------------------------- BiCGStab
@@ -561,6 +586,15 @@ void blas_bicg_rho(const Field& r, const Field& r0, df* part, cudaStream_t st, c
 #define K(NR) rho_kernel<P_, NR>
 #define L(P) { constexpr int P_ = P; BY_KIND(r, "blas_bicg_rho", K, red_grid(r.nrhs), r.view(), r0.view(), part, fin); }
     DISPATCH_P(r.prec, L);
+#undef L
+#undef K
+}
+
+void blas_cg_p_norm(Field& p, const Field& r, const double* sc, df* part, cudaStream_t st, const FinArgs& fin) {
+    if (p.prec != r.prec) fail(LQ_EINVAL, "blas_cg_p_norm: precision mismatch");
+#define K(NR) cg_p_norm_kernel<P_, NR>
+#define L(P) { constexpr int P_ = P; BY_KIND(p, "blas_cg_p", K, red_grid(p.nrhs), p.view(), r.view(), sc, part, fin); }
+    DISPATCH_P(p.prec, L);
 #undef L
 #undef K
 }

@@ -198,7 +198,7 @@ static const char* hname(int prec, int epi) {
 }
 
 int hisq_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int epi, double aa, const Field& in,
-                Field& out, const Field* y, df* norm_out, cudaStream_t st) {
+                Field& out, const Field* y, df* norm_out, cudaStream_t st, const FinArgs& fin) {
     if (in.prec != op.prec || out.prec != op.prec || (y && y->prec != op.prec))
         fail(LQ_EINVAL, "hisq_dslash: field precision does not match the operator");
     if (in.kind != LQ_STAGGERED_FIELD || out.nrhs != in.nrhs) fail(LQ_EINVAL, "hisq_dslash: field shape");
@@ -215,6 +215,7 @@ int hisq_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int epi,
     a.a = aa;
     a.nrhs = in.nrhs;
     a.norm_out = norm_out;
+    a.fin = FinArgs();  // the tuner's trial launches never finalise
     const int nb = (op.prec == LQ_F32 || op.prec == LQ_F16) ? pick_rg(a.nrhs) : 1;
     const char* name = hname(op.prec, epi);
     auto run = [&](int block) {
@@ -234,6 +235,7 @@ int hisq_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int epi,
     std::string key = std::string(name) + "/r" + std::to_string(op.recon) + "/nb" + std::to_string(nb) + "/v" +
                       std::to_string(lat.vh) + "/n" + std::to_string(norm_out != nullptr);
     int block = tuned_block(key, st, run);
+    a.fin = norm_out ? fin : FinArgs();
     run(block);
     return site_blocks(lat.vh, block, nb);
 }

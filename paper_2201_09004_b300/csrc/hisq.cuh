@@ -26,6 +26,7 @@ struct HisqArgs {
     double a;       // XPAY scale
     int nrhs;
     df* norm_out;
+    FinArgs fin;  // with norm_out: the last block finalises the sums
 };
 
 template <int MU, int STEP, int P, int R, int NB, typename T>
@@ -241,7 +242,10 @@ __global__ void __launch_bounds__(256) hisq_dslash_kernel(HisqArgs a) {
             fstore<P, 6, T>(a.out, kb + b, s, v);
         }
     }
-    if (a.norm_out) reduce_norms_rg<NB, RG>(nrm, a.norm_out, grp, sb, nsb, a.nrhs);
+    if (a.norm_out) {
+        reduce_norms_rg<NB, RG>(nrm, a.norm_out, grp, sb, nsb, a.nrhs);
+        fin_tail(a.norm_out, nsb, a.nrhs, a.fin);
+    }
 }
 
 }  // namespace lq

@@ -227,7 +227,7 @@ struct OpDesc {
 int wilson_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int epi, const Field& in,
                   Field& out, const Field* y, df* norm_out, cudaStream_t st, const FinArgs& fin = FinArgs());
 int hisq_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int epi, double a, const Field& in,
-                Field& out, const Field* y, df* norm_out, cudaStream_t st);
+                Field& out, const Field* y, df* norm_out, cudaStream_t st, const FinArgs& fin = FinArgs());
 // site-local out = A_pp^{-1} in (Wilson twisted mass / clover), parity of both fields
 void wilson_ainv_site(Lattice& lat, const OpDesc& op, int parity, int dagger, const Field& in, Field& out,
                       cudaStream_t st);
@@ -259,6 +259,8 @@ void blas_bicg_xr(Field& x, const Field& p, Field& r, const Field& t, const Fiel
                   cudaStream_t st, const FinArgs& fin);
 void blas_bicg_p(Field& p, const Field& r, const Field& v, const double* sc, cudaStream_t st);
 void blas_bicg_rho(const Field& r, const Field& r0, df* part, cudaStream_t st, const FinArgs& fin);
+// p = r + beta p with partial |p|^2
+void blas_cg_p_norm(Field& p, const Field& r, const double* sc, df* part, cudaStream_t st, const FinArgs& fin);
 // p = r + beta p, beta_k = sc[k*SC_N + SC_BETA]
 void blas_cg_p(Field& p, const Field& r, const double* sc, cudaStream_t st);
 
@@ -270,7 +272,7 @@ void blas_finalize(const df* part, int nblocks, int nrhs, double* sc, int slot, 
 int schur_wilson(Lattice& lat, const OpDesc& op, int dagger, const Field& in, Field& out, Field& tmp, df* part,
                  cudaStream_t st, const FinArgs& fin = FinArgs());
 int schur_hisq(Lattice& lat, const OpDesc& op, double sigma, const Field& in, Field& out, Field& t, df* part_t,
-               cudaStream_t st);
+               cudaStream_t st, const FinArgs& fin = FinArgs());
 // estimated device bytes of a solve's work fields
 size_t solve_workspace_bytes(const Lattice& lat, const lq_op_params& op, const lq_solve_params& sp, int nrhs);
 int solve_wilson(Lattice& lat, const lq_op_params& op, const lq_solve_params& sp, int nrhs, const double* const* b,

@@ -120,58 +120,34 @@ int schur_wilson(Lattice& lat, const OpDesc& op, int dagger, const Field& in, Fi
     return wilson_dslash(lat, op, 0, dagger, EPI_XPAY, tmp, out, &in, part, st, fin);
 }
 
-// CGNR on Mhat for all right-hand sides of bhat at once (FP64, even sites).
-// x_hi receives the solution; tol_abs[k] is the target of |bhat - Mhat x|.
-// The iteration keeps alpha and beta on the device; the host reads |s|^2 once
-// per iteration to decide on reliable updates and convergence.
-static CgResult cgnr_mixed(Lattice& lat, const OpDesc& ops, const OpDesc& op64, Field& bhat, Field& x_hi,
-                           const std::vector<double>& tol_abs, double delta, int maxiter, int graph_iters,
-                           cudaStream_t st) {
-    const int n = bhat.nrhs;
-    const int ps = ops.prec;
-    const int px = ps == LQ_F16 ? LQ_F32 : ps;  // the sloppy solution accumulates in at least FP32
-    Pool pool(lat, st);
-    const int ph = op64.prec;  // FP64, or double-float for the mixed solvers
-    Field s_hi = pool.get(LQ_WILSON_FIELD, ph, n), q64 = pool.get(LQ_WILSON_FIELD, ph, n);
-    Field t64 = pool.get(LQ_WILSON_FIELD, ph, n), x_lo = pool.get(LQ_WILSON_FIELD, px, n);
-    Field s_lo = pool.get(LQ_WILSON_FIELD, ps, n), r = pool.get(LQ_WILSON_FIELD, ps, n);
-    Field p = pool.get(LQ_WILSON_FIELD, ps, n), q = pool.get(LQ_WILSON_FIELD, ps, n);
-    Field t = pool.get(LQ_WILSON_FIELD, ps, n);
-    Scalars sc;
-    sc.init(lat, n, st);
-    CgResult res(n);
-    std::vector<double> rmax(n, 0.0), ones(n, 1.0);
-    std::vector<char> done(n, 0);
+// ------------------------------------------------------------ Krylov driver
+// The loop shared by the mixed-precision solvers. The host reads the residual
+// norms of iteration i while iteration i+1 runs: each iteration ends with an
+// asynchronous copy of the device scalars into one of two pinned slots and an
+// event, and the host waits on the previous one, so the GPU queue never drains.
+// A reliable update (iterated |r| below delta times its value at the last
+// update), convergence or a breakdown flag is therefore acted on one iteration
+// late, which costs at most one extra iteration. After the first (autotuning)
+// iteration, graph_iters iterations are captured into two CUDA graphs (one per
+// slot) and replayed with one launch each.
+//   iteration(dst): the device work of one iteration; dst (or null) gets the scalars.
+//   update(): reliable update, ends with the true |r|^2 in SC_SS (not yet pulled).
+//   after_update(k): optional per-rhs fix-up after the pull (returns false to stop rhs k).
+struct KrylovState {
+    std::vector<double> rmax;
+    std::vector<char> done;
+};
 
-    blas_zero(x_hi, st);
-    blas_copy(s_hi, bhat, st);
-    blas_norm2(bhat, sc.part, st);
-    sc.fin(RED_BLOCKS, SC_SS, st);
-    blas_copy(s_lo, s_hi, st);
-    blas_zero(x_lo, st);
-    int nb = schur_wilson(lat, ops, 1, s_lo, r, t, sc.part, st);
-    sc.fin(nb, SC_RR, st);
-    blas_copy(p, r, st);
-    sc.pull(st);
-    for (int k = 0; k < n; k++) {
-        check_finite(sc.h(k, SC_SS), "source");
-        rmax[k] = sqrt(sc.h(k, SC_SS));
-        if (rmax[k] <= tol_abs[k]) {
-            done[k] = 1;
-            res.status[k] = LQ_OK;
-            sc.set(k, SC_FROZEN, 1.0, st);
-        }
-    }
+template <class Iter, class Update, class After>
+static void krylov_loop(Lattice& lat, Scalars& sc, CgResult& res, KrylovState& ks, const std::vector<double>& tol_abs,
+                        double delta, int maxiter, int graph_iters, int apps_per_iter, cudaStream_t st,
+                        Iter iteration, Update update, After after_update) {
+    const int n = sc.nrhs;
     auto all_done = [&]() {
         for (int k = 0; k < n; k++)
-            if (!done[k]) return false;
+            if (!ks.done[k]) return false;
         return true;
     };
-    // The host reads the residual norms of iteration i while iteration i+1 runs:
-    // each iteration ends with an asynchronous copy of the scalars into one of
-    // two pinned slots and an event, and the host waits on the previous one.
-    // A reliable update or convergence is therefore decided one iteration late,
-    // which costs at most one extra iteration and keeps the GPU busy.
     double* ring = (double*)ws_get(lat, sizeof(double) * SC_N * n * 2, true, st);
     cudaEvent_t ev[2];
     LQ_CUDA(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
@@ -181,17 +157,6 @@ static CgResult cgnr_mixed(Lattice& lat, const OpDesc& ops, const OpDesc& op64, 
         ~Cleanup() { ws_put(l, r, s); cudaEventDestroy(e[0]); cudaEventDestroy(e[1]); }
     } cleanup{lat, ring, ev, st};
     auto slot = [&](int i) { return ring + (size_t)(i & 1) * SC_N * n; };
-    // One CG iteration on the device; `dst` (or null) receives the scalars.
-    // Each reduction is finalised by the last block of the kernel producing it.
-    auto iteration = [&](double* dst) {
-        schur_wilson(lat, ops, 0, p, q, t, sc.part, st, sc.f(0, FIN_ALPHA));
-        blas_cg_xs(x_lo, p, s_lo, q, sc.dev, sc.part, st, sc.f(SC_SS, FIN_SET));
-        schur_wilson(lat, ops, 1, s_lo, r, t, sc.part, st, sc.f(0, FIN_BETA));
-        blas_cg_p(p, r, sc.dev, st);
-        if (dst) LQ_CUDA(cudaMemcpyAsync(dst, sc.dev, sizeof(double) * SC_N * n, cudaMemcpyDeviceToHost, st));
-    };
-    // After the first (eager, autotuning) iteration, blocks of gk iterations
-    // are captured into two CUDA graphs, one per ring slot, and replayed.
     const int gk = graph_iters < 0 ? 0 : (graph_iters == 0 ? 1 : graph_iters);
     Graph graphs[2];
     struct GraphCleanup {
@@ -230,58 +195,124 @@ static CgResult cgnr_mixed(Lattice& lat, const OpDesc& ops, const OpDesc& op64, 
         }
         LQ_CUDA(cudaEventRecord(ev[gi], st));
         for (int k = 0; k < n; k++)
-            if (!done[k]) {
+            if (!ks.done[k]) {
                 res.iters[k] += steps;
-                res.applications[k] += 2 * steps;
+                res.applications[k] += apps_per_iter * steps;
             }
         const int prev = pending;
         pending = launch_no;
         launch_no++;
         it += steps;
-        bool update = it >= maxiter;
+        bool upd = it >= maxiter;
         if (prev >= 0) {
             LQ_CUDA(cudaEventSynchronize(ev[prev & 1]));
             const double* hs = slot(prev);
             for (int k = 0; k < n; k++) {
-                if (done[k]) continue;
+                if (ks.done[k]) continue;
+                if (hs[(size_t)k * SC_N + SC_BREAK] != 0.0) upd = true;
                 double ss = sqrt(hs[(size_t)k * SC_N + SC_SS]);
                 check_finite(ss, "iterated residual");
-                if (ss < delta * rmax[k] || ss <= tol_abs[k]) update = true;
+                if (ss < delta * ks.rmax[k] || ss <= tol_abs[k]) upd = true;
             }
         }
-        if (!update) continue;
+        if (!upd) continue;
         pending = -1;
-        // reliable update: fold the sloppy solution into FP64 and recompute the true residual
+        update();
+        sc.pull(st);
+        for (int k = 0; k < n; k++) {
+            if (ks.done[k]) continue;
+            res.updates[k]++;
+            double ss = sqrt(sc.h(k, SC_SS));
+            check_finite(ss, "true residual");
+            ks.rmax[k] = ss;
+            if (ss <= tol_abs[k]) {
+                ks.done[k] = 1;
+                res.status[k] = LQ_OK;
+                sc.set(k, SC_FROZEN, 1.0, st);
+            } else if (!after_update(k)) {
+                ks.done[k] = 1;
+            }
+        }
+    }
+}
+
+// first check of the sources: |r|^2 in SC_SS (pulled)
+static KrylovState krylov_start(Scalars& sc, CgResult& res, const std::vector<double>& tol_abs, cudaStream_t st) {
+    KrylovState ks;
+    ks.rmax.assign(sc.nrhs, 0.0);
+    ks.done.assign(sc.nrhs, 0);
+    for (int k = 0; k < sc.nrhs; k++) {
+        check_finite(sc.h(k, SC_SS), "source");
+        ks.rmax[k] = sqrt(sc.h(k, SC_SS));
+        if (ks.rmax[k] <= tol_abs[k]) {
+            ks.done[k] = 1;
+            res.status[k] = LQ_OK;
+            sc.set(k, SC_FROZEN, 1.0, st);
+        }
+    }
+    return ks;
+}
+
+// CGNR on Mhat for all right-hand sides of bhat at once (FP64, even sites).
+// x_hi receives the solution; tol_abs[k] is the target of |bhat - Mhat x|.
+// Each reduction is finalised by the last block of the kernel producing it
+// (alpha and beta stay on the device). A reliable update folds the sloppy
+// solution into x_hi, recomputes s = bhat - Mhat x_hi in FP64 accuracy, keeps
+// p and restarts the norm recurrence from the new r = Mhat^+ s.
+static CgResult cgnr_mixed(Lattice& lat, const OpDesc& ops, const OpDesc& op64, Field& bhat, Field& x_hi,
+                           const std::vector<double>& tol_abs, double delta, int maxiter, int graph_iters,
+                           cudaStream_t st) {
+    const int n = bhat.nrhs;
+    const int ps = ops.prec;
+    const int px = ps == LQ_F16 ? LQ_F32 : ps;  // the sloppy solution accumulates in at least FP32
+    const int WF = LQ_WILSON_FIELD;
+    Pool pool(lat, st);
+    const int ph = op64.prec;  // FP64, or double-float for the mixed solvers
+    Field s_hi = pool.get(WF, ph, n), q64 = pool.get(WF, ph, n), t64 = pool.get(WF, ph, n);
+    Field x_lo = pool.get(WF, px, n);
+    Field s_lo = pool.get(WF, ps, n), r = pool.get(WF, ps, n), p = pool.get(WF, ps, n);
+    Field q = pool.get(WF, ps, n), t = pool.get(WF, ps, n);
+    Scalars sc;
+    sc.init(lat, n, st);
+    CgResult res(n);
+    std::vector<double> ones(n, 1.0);
+
+    blas_zero(x_hi, st);
+    blas_copy(s_hi, bhat, st);
+    blas_norm2(bhat, sc.part, st, sc.f(SC_SS, FIN_SET));
+    blas_copy(s_lo, s_hi, st);
+    blas_zero(x_lo, st);
+    schur_wilson(lat, ops, 1, s_lo, r, t, sc.part, st, sc.f(SC_RR, FIN_SET));
+    blas_copy(p, r, st);
+    sc.pull(st);
+    KrylovState ks = krylov_start(sc, res, tol_abs, st);
+    auto iteration = [&](double* dst) {
+        schur_wilson(lat, ops, 0, p, q, t, sc.part, st, sc.f(0, FIN_ALPHA));
+        blas_cg_xs(x_lo, p, s_lo, q, sc.dev, sc.part, st, sc.f(SC_SS, FIN_SET));
+        schur_wilson(lat, ops, 1, s_lo, r, t, sc.part, st, sc.f(0, FIN_BETA));
+        blas_cg_p(p, r, sc.dev, st);
+        if (dst) LQ_CUDA(cudaMemcpyAsync(dst, sc.dev, sizeof(double) * SC_N * n, cudaMemcpyDeviceToHost, st));
+    };
+    auto update = [&]() {
         blas_axpy_h(x_hi, ones.data(), x_lo, st);
         blas_zero(x_lo, st);
         schur_wilson(lat, op64, 0, x_hi, q64, t64, nullptr, st);
         blas_xmy_norm(s_hi, bhat, q64, sc.part, st, sc.f(SC_SS, FIN_SET));
         blas_copy(s_lo, s_hi, st);
-        // keep p, restart the norm recurrence from the new r
         schur_wilson(lat, ops, 1, s_lo, r, t, sc.part, st, sc.f(SC_RR, FIN_SET));
-        sc.pull(st);
-        for (int k = 0; k < n; k++) {
-            if (done[k]) continue;
-            res.updates[k]++;
-            res.applications[k] += 2;
-            double ss = sqrt(sc.h(k, SC_SS));
-            check_finite(ss, "true residual");
-            rmax[k] = ss;
-            if (ss <= tol_abs[k]) {
-                done[k] = 1;
-                res.status[k] = LQ_OK;
-                sc.set(k, SC_FROZEN, 1.0, st);
-            }
-        }
-    }
+        for (int k = 0; k < n; k++)
+            if (!ks.done[k]) res.applications[k] += 2;
+    };
+    krylov_loop(lat, sc, res, ks, tol_abs, delta, maxiter, graph_iters, 2, st, iteration, update,
+                [](int) { return true; });
     return res;
 }
 
 // Mixed-precision BiCGStab (van der Vorst) on Mhat for all right-hand sides of
-// bhat: the iteration runs in the sloppy precision with complex device scalars;
-// the host reads |r|^2 one iteration late (as in cgnr_mixed). A reliable update
-// folds x_lo into x_hi, recomputes r = bhat - Mhat x_hi in FP64 accuracy and
-// rho = (r0, r), and keeps p and the shadow residual r0.
+// bhat, with complex device scalars finalised in the producing kernels. A
+// reliable update folds x_lo into x_hi, recomputes r = bhat - Mhat x_hi in FP64
+// accuracy and rho = (r0, r), and keeps p and the shadow residual r0; a
+// vanishing denominator restarts that rhs from its true residual (r0 = p = r).
 static CgResult bicgstab_mixed(Lattice& lat, const OpDesc& ops, const OpDesc& op64, Field& bhat, Field& x_hi,
                                const std::vector<double>& tol_abs, double delta, int maxiter, int graph_iters,
                                cudaStream_t st) {
@@ -298,8 +329,8 @@ static CgResult bicgstab_mixed(Lattice& lat, const OpDesc& ops, const OpDesc& op
     Scalars sc;
     sc.init(lat, n, st);
     CgResult res(n);
-    std::vector<double> rmax(n, 0.0), ones(n, 1.0);
-    std::vector<char> done(n, 0);
+    std::vector<double> ones(n, 1.0);
+    std::vector<int> restarts(n, 0);
 
     blas_zero(x_hi, st);
     blas_zero(x_lo, st);
@@ -309,30 +340,7 @@ static CgResult bicgstab_mixed(Lattice& lat, const OpDesc& ops, const OpDesc& op
     blas_copy(p, r, st);
     blas_bicg_rho(r, r0, sc.part, st, sc.f(0, FIN_BICG_RHO));  // rho = (r0, r)
     sc.pull(st);
-    std::vector<int> restarts(n, 0);
-    for (int k = 0; k < n; k++) {
-        check_finite(sc.h(k, SC_SS), "source");
-        rmax[k] = sqrt(sc.h(k, SC_SS));
-        if (rmax[k] <= tol_abs[k]) {
-            done[k] = 1;
-            res.status[k] = LQ_OK;
-            sc.set(k, SC_FROZEN, 1.0, st);
-        }
-    }
-    auto all_done = [&]() {
-        for (int k = 0; k < n; k++)
-            if (!done[k]) return false;
-        return true;
-    };
-    double* ring = (double*)ws_get(lat, sizeof(double) * SC_N * n * 2, true, st);
-    cudaEvent_t ev[2];
-    LQ_CUDA(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
-    LQ_CUDA(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
-    struct Cleanup {
-        Lattice& l; double* r; cudaEvent_t* e; cudaStream_t s;
-        ~Cleanup() { ws_put(l, r, s); cudaEventDestroy(e[0]); cudaEventDestroy(e[1]); }
-    } cleanup{lat, ring, ev, st};
-    auto slot = [&](int i) { return ring + (size_t)(i & 1) * SC_N * n; };
+    KrylovState ks = krylov_start(sc, res, tol_abs, st);
     auto iteration = [&](double* dst) {
         schur_wilson(lat, ops, 0, p, v, tmp, nullptr, st);                     // v = Mhat p
         blas_bicg_cdot(r0, v, sc.part, st, sc.f(0, FIN_BICG_ALPHA));            // alpha = rho / (r0, v)
@@ -343,103 +351,34 @@ static CgResult bicgstab_mixed(Lattice& lat, const OpDesc& ops, const OpDesc& op
         blas_bicg_p(p, r, v, sc.dev, st);                                      // p = r + beta (p - omega v)
         if (dst) LQ_CUDA(cudaMemcpyAsync(dst, sc.dev, sizeof(double) * SC_N * n, cudaMemcpyDeviceToHost, st));
     };
-    const int gk = graph_iters < 0 ? 0 : (graph_iters == 0 ? 1 : graph_iters);
-    Graph graphs[2];
-    struct GraphCleanup {
-        Graph* g;
-        ~GraphCleanup() { graph_destroy(g[0]); graph_destroy(g[1]); }
-    } graph_cleanup{graphs};
-    bool use_graphs = gk > 0;
-    int it = 0, launch_no = 0, pending = -1;
-    while (!all_done() && it < maxiter) {
-        const int gi = launch_no & 1;
-        int steps = 1;
-        if (use_graphs && it > 0 && it + gk <= maxiter) {
-            Graph& g = graphs[gi];
-            if (!g.exec) {
-                bool ok = graph_capture_begin(st);
-                if (ok) {
-                    try {
-                        for (int j = 0; j < gk; j++) iteration(j == gk - 1 ? slot(gi) : nullptr);
-                    } catch (...) {
-                        ok = false;
-                    }
-                    ok = graph_capture_end(st, g) && ok;
-                }
-                if (!ok) use_graphs = false;
-            } else {
-                graph_collect(g);
-            }
-            if (g.exec) {
-                graph_launch(g, st);
-                steps = gk;
-            } else {
-                iteration(slot(gi));
-            }
-        } else {
-            iteration(slot(gi));
-        }
-        LQ_CUDA(cudaEventRecord(ev[gi], st));
-        for (int k = 0; k < n; k++)
-            if (!done[k]) {
-                res.iters[k] += steps;
-                res.applications[k] += 2 * steps;
-            }
-        const int prev = pending;
-        pending = launch_no;
-        launch_no++;
-        it += steps;
-        bool update = it >= maxiter;
-        if (prev >= 0) {
-            LQ_CUDA(cudaEventSynchronize(ev[prev & 1]));
-            const double* hs = slot(prev);
-            for (int k = 0; k < n; k++) {
-                if (done[k]) continue;
-                if (hs[(size_t)k * SC_N + SC_BREAK] != 0.0) update = true;
-                double ss = sqrt(hs[(size_t)k * SC_N + SC_SS]);
-                check_finite(ss, "iterated residual");
-                if (ss < delta * rmax[k] || ss <= tol_abs[k]) update = true;
-            }
-        }
-        if (!update) continue;
-        pending = -1;
-        // reliable update: fold x_lo into x_hi, recompute r in FP64 accuracy, rho = (r0, r)
+    auto update = [&]() {
         blas_axpy_h(x_hi, ones.data(), x_lo, st);
         blas_zero(x_lo, st);
         schur_wilson(lat, op64, 0, x_hi, q64, t64, nullptr, st);
         blas_xmy_norm(r_hi, bhat, q64, sc.part, st, sc.f(SC_SS, FIN_SET));
         blas_copy(r, r_hi, st);
         blas_bicg_rho(r, r0, sc.part, st, sc.f(0, FIN_BICG_RHO));
-        sc.pull(st);
-        for (int k = 0; k < n; k++) {
-            if (done[k]) continue;
-            res.updates[k]++;
-            res.applications[k] += 2;
-            double ss = sqrt(sc.h(k, SC_SS));
-            check_finite(ss, "true residual");
-            rmax[k] = ss;
-            if (ss <= tol_abs[k]) {
-                done[k] = 1;
-                res.status[k] = LQ_OK;
-                sc.set(k, SC_FROZEN, 1.0, st);
-            } else if (sc.h(k, SC_BREAK) != 0.0) {
-                // a vanishing denominator: restart this right-hand side from its true residual
-                if (++restarts[k] > 8) {
-                    done[k] = 1;
-                    res.status[k] = LQ_EBREAKDOWN;
-                    continue;
-                }
-                Field r0k = r0.sub(k, 1), pk = p.sub(k, 1), rk = r.sub(k, 1);
-                blas_copy(r0k, rk, st);
-                blas_copy(pk, rk, st);
-                sc.set(k, SC_BREAK, 0.0, st);
-                sc.set(k, SC_FROZEN, 0.0, st);
-                FinArgs fk = sc.f(0, FIN_BICG_RHO);
-                fk.sc += (size_t)k * SC_N;  // the sub-field's rhs 0 is rhs k
-                blas_bicg_rho(rk, r0k, sc.part, st, fk);
-            }
+        for (int k = 0; k < n; k++)
+            if (!ks.done[k]) res.applications[k] += 2;
+    };
+    auto after_update = [&](int k) {
+        if (sc.h(k, SC_BREAK) == 0.0) return true;
+        // a vanishing denominator: restart this right-hand side from its true residual
+        if (++restarts[k] > 8) {
+            res.status[k] = LQ_EBREAKDOWN;
+            return false;
         }
-    }
+        Field r0k = r0.sub(k, 1), pk = p.sub(k, 1), rk = r.sub(k, 1);
+        blas_copy(r0k, rk, st);
+        blas_copy(pk, rk, st);
+        sc.set(k, SC_BREAK, 0.0, st);
+        sc.set(k, SC_FROZEN, 0.0, st);
+        FinArgs fk = sc.f(0, FIN_BICG_RHO);
+        fk.sc += (size_t)k * SC_N;  // the sub-field's rhs 0 is rhs k
+        blas_bicg_rho(rk, r0k, sc.part, st, fk);
+        return true;
+    };
+    krylov_loop(lat, sc, res, ks, tol_abs, delta, maxiter, graph_iters, 2, st, iteration, update, after_update);
     return res;
 }
 
@@ -569,101 +508,67 @@ static OpDesc hisq_desc(const lq_op_params& op, int prec, int recon) {
 // out = sigma in - H_eo H_oe in; t = H_oe in (odd). part_t receives |t|^2 partials,
 // so that (in, out) = sigma |in|^2 + |t|^2 (since -H_eo = H_oe^+).
 int schur_hisq(Lattice& lat, const OpDesc& op, double sigma, const Field& in, Field& out, Field& t, df* part_t,
-               cudaStream_t st) {
-    int nb = hisq_dslash(lat, op, 1, 0, EPI_HOP, 0.0, in, t, nullptr, part_t, st);
+               cudaStream_t st, const FinArgs& fin) {
+    int nb = hisq_dslash(lat, op, 1, 0, EPI_HOP, 0.0, in, t, nullptr, part_t, st, fin);
     hisq_dslash(lat, op, 0, 0, EPI_XPAY, sigma, t, out, &in, nullptr, st);
     return nb;
 }
 
-// Mixed-precision CG for (sigma - H_eo H_oe) x = b from the initial guess in x_hi.
+// Mixed-precision CG for A x = b, A = sigma - H_eo H_oe = sigma + H_oe^+ H_oe
+// (hermitian positive definite), from the initial guess in x_hi, on the Krylov
+// driver: (p, A p) = sigma |p|^2 + |H_oe p|^2 with |H_oe p|^2 finalised in the
+// kernel that forms H_oe p, alpha and beta on the device; a reliable update
+// recomputes r = b - A x_hi in FP64 accuracy and keeps p.
 static CgResult cg_hisq(Lattice& lat, const OpDesc& ops, const OpDesc& op64, double sigma, const Field& b,
-                        Field& x_hi, const std::vector<double>& tol_abs, double delta, int maxiter, cudaStream_t st) {
+                        Field& x_hi, const std::vector<double>& tol_abs, double delta, int maxiter, int graph_iters,
+                        cudaStream_t st) {
     const int n = b.nrhs;
     const int ps = ops.prec, px = ps == LQ_F16 ? LQ_F32 : ps;
+    const int SF = LQ_STAGGERED_FIELD;
     Pool pool(lat, st);
     const int ph = op64.prec;
-    Field r_hi = pool.get(LQ_STAGGERED_FIELD, ph, n), q64 = pool.get(LQ_STAGGERED_FIELD, ph, n);
-    Field t64 = pool.get(LQ_STAGGERED_FIELD, ph, n), x_lo = pool.get(LQ_STAGGERED_FIELD, px, n);
-    Field r = pool.get(LQ_STAGGERED_FIELD, ps, n), p = pool.get(LQ_STAGGERED_FIELD, ps, n);
-    Field q = pool.get(LQ_STAGGERED_FIELD, ps, n), t = pool.get(LQ_STAGGERED_FIELD, ps, n);
+    Field r_hi = pool.get(SF, ph, n), q64 = pool.get(SF, ph, n), t64 = pool.get(SF, ph, n);
+    Field x_lo = pool.get(SF, px, n);
+    Field r = pool.get(SF, ps, n), p = pool.get(SF, ps, n), q = pool.get(SF, ps, n), t = pool.get(SF, ps, n);
     Scalars sc;
     sc.init(lat, n, st);
     CgResult res(n);
-    std::vector<double> rr(n), pp(n), rmax(n), a(n), bb(n), ones(n, 1.0);
-    std::vector<char> done(n, 0);
+    std::vector<double> ones(n, 1.0);
+    FinArgs falpha = sc.f(0, FIN_CG_ALPHA);
+    falpha.a = sigma;
 
-    // r = b - A x_hi in FP64; restart the sloppy recurrence from it
+    // r = b - A x_hi in FP64 accuracy; |r|^2 -> SC_SS; the sloppy copy's |r|^2 -> SC_RR
     auto true_residual = [&]() {
         schur_hisq(lat, op64, sigma, x_hi, q64, t64, nullptr, st);
-        blas_xmy_norm(r_hi, b, q64, sc.part, st);
-        sc.fin(RED_BLOCKS, SC_SS, st);
+        blas_xmy_norm(r_hi, b, q64, sc.part, st, sc.f(SC_SS, FIN_SET));
         blas_copy(r, r_hi, st);
-        blas_copy(p, r, st);
-        sc.pull(st);
-        for (int k = 0; k < n; k++) {
-            double ss = sc.h(k, SC_SS);
-            check_finite(ss, "true residual");
-            rr[k] = pp[k] = ss;
-            rmax[k] = sqrt(ss);
-            if (!done[k] && sqrt(ss) <= tol_abs[k]) {
-                done[k] = 1;
-                res.status[k] = LQ_OK;
-            }
-        }
+        blas_norm2(r, sc.part, st, sc.f(SC_RR, FIN_SET));
     };
     blas_zero(x_lo, st);
     true_residual();
-    auto all_done = [&]() {
-        for (int k = 0; k < n; k++)
-            if (!done[k]) return false;
-        return true;
+    blas_copy(p, r, st);
+    blas_norm2(p, sc.part, st, sc.f(SC_PP, FIN_SET));
+    sc.pull(st);
+    KrylovState ks = krylov_start(sc, res, tol_abs, st);
+    auto iteration = [&](double* dst) {
+        schur_hisq(lat, ops, sigma, p, q, t, sc.part, st, falpha);               // q = A p, alpha
+        blas_cg_xs(x_lo, p, r, q, sc.dev, sc.part, st, sc.f(0, FIN_CG_BETA));   // x, r, |r|^2, beta
+        blas_cg_p_norm(p, r, sc.dev, sc.part, st, sc.f(SC_PP, FIN_SET));         // p = r + beta p, |p|^2
+        if (dst) LQ_CUDA(cudaMemcpyAsync(dst, sc.dev, sizeof(double) * SC_N * n, cudaMemcpyDeviceToHost, st));
     };
-    int it = 0;
-    while (!all_done() && it < maxiter) {
-        int nb = schur_hisq(lat, ops, sigma, p, q, t, sc.part, st);
-        sc.fin(nb, SC_QQ, st);
-        sc.pull(st);
-        for (int k = 0; k < n; k++) {
-            double pap = sigma * pp[k] + sc.h(k, SC_QQ);
-            if (!done[k] && !(pap > 0.0)) fail(LQ_EBREAKDOWN, "CG breakdown: non-positive curvature");
-            a[k] = done[k] ? 0.0 : rr[k] / pap;
-        }
-        blas_axpy_h(x_lo, a.data(), p, st);
-        for (int k = 0; k < n; k++) a[k] = -a[k];
-        blas_axpby_h(r, a.data(), q, ones.data(), sc.part, st);
-        sc.fin(RED_BLOCKS, SC_RRN, st);
-        sc.pull(st);
-        bool update = false;
-        for (int k = 0; k < n; k++) {
-            double rn = sc.h(k, SC_RRN);
-            check_finite(rn, "iterated residual");
-            bb[k] = done[k] ? 0.0 : rn / rr[k];
-            if (!done[k]) {
-                res.iters[k]++;
-                res.applications[k]++;
-                rr[k] = rn;
-                if (sqrt(rn) < delta * rmax[k] || sqrt(rn) <= tol_abs[k]) update = true;
-            }
-        }
-        blas_axpby_h(p, ones.data(), r, bb.data(), sc.part, st);
-        sc.fin(RED_BLOCKS, SC_PP, st);
-        it++;
-        if (it == maxiter) update = true;
-        if (update) {
-            blas_axpy_h(x_hi, ones.data(), x_lo, st);
-            blas_zero(x_lo, st);
-            std::vector<char> was = done;
-            true_residual();
-            for (int k = 0; k < n; k++)
-                if (!was[k]) {
-                    res.updates[k]++;
-                    res.applications[k]++;
-                }
-        } else {
-            sc.pull(st);
-            for (int k = 0; k < n; k++) pp[k] = sc.h(k, SC_PP);
-        }
-    }
+    auto update = [&]() {
+        blas_axpy_h(x_hi, ones.data(), x_lo, st);
+        blas_zero(x_lo, st);
+        true_residual();
+        for (int k = 0; k < n; k++)
+            if (!ks.done[k]) res.applications[k] += 1;
+    };
+    auto after_update = [&](int k) {
+        if (sc.h(k, SC_BREAK) == 0.0) return true;
+        res.status[k] = LQ_EBREAKDOWN;
+        return false;
+    };
+    krylov_loop(lat, sc, res, ks, tol_abs, delta, maxiter, graph_iters, 1, st, iteration, update, after_update);
     return res;
 }
 
@@ -859,7 +764,7 @@ int solve_hisq(Lattice& lat, const lq_op_params& opp, const lq_solve_params& sp,
             }
             // the even part of the full residual is (bhat - A x_e) / m
             for (int k = 0; k < nrhs; k++) tol_abs[k] = 0.5 * sp.tol * bn[k] * m;
-            CgResult cr = cg_hisq(lat, ops, op64, sigma[i], bh, xe, tol_abs, delta, maxiter, st);
+            CgResult cr = cg_hisq(lat, ops, op64, sigma[i], bh, xe, tol_abs, delta, maxiter, sp.graph_iters, st);
             // x_o = (b_o - H_oe x_e) / m
             hisq_dslash(lat, op64, 1, 0, EPI_HOP, 0.0, xe, to, nullptr, nullptr, st);
             blas_copy(xo, to, st);
