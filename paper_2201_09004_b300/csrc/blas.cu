@@ -213,7 +213,7 @@ __global__ void finalize_kernel(const df* part, int nblocks, double* sc, int slo
     df sum(0.f);
     for (int i = threadIdx.x; i < nblocks; i += blockDim.x) sum = sum + pk[i];
     sum = block_sum_df(sum);
-    if (threadIdx.x == 0) fin_apply(sc + (size_t)k * SC_N, df_to_double(sum), slot, op, 0.0);
+    if (threadIdx.x == 0) fin_apply(sc + (size_t)k * SC_N, df_to_double(sum), slot, op);
 }
 
 // ------------------------------------------------------------- BiCGStab

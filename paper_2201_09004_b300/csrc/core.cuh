@@ -116,18 +116,21 @@ __device__ __forceinline__ df block_sum_df(df v) {
 // SC_BREAK is set when a BiCGStab denominator vanishes)
 enum {
     SC_RR = 0, SC_QQ, SC_SS, SC_RRN, SC_ALPHA, SC_BETA, SC_B2, SC_FROZEN, SC_PP,
-    SC_RHO_R, SC_RHO_I, SC_AL_R, SC_AL_I, SC_OM_R, SC_OM_I, SC_BE_R, SC_BE_I, SC_BREAK, SC_N
+    SC_RHO_R, SC_RHO_I, SC_AL_R, SC_AL_I, SC_OM_R, SC_OM_I, SC_BE_R, SC_BE_I, SC_BREAK,
+    SC_SIGMA,  // the rhs's shift sigma of a hermitian operator sigma + K^+ K
+    SC_N
 };
 enum { FIN_SET = 0, FIN_ALPHA = 1, FIN_BETA = 2, FIN_BICG_ALPHA = 3, FIN_BICG_OMEGA = 4, FIN_BICG_BETA = 5,
        FIN_BICG_RHO = 6, FIN_CG_ALPHA = 7, FIN_CG_BETA = 8 };
 
 // apply the scalar step to the total of a reduction (S: the rhs's scalar block).
 // FIN_ALPHA / FIN_BETA: CG on the normal equations; FIN_CG_ALPHA / FIN_CG_BETA:
-// CG on a hermitian operator sigma + K^+ K applied as |K p|^2 (tot) + sigma |p|^2 (SC_PP).
-__device__ __forceinline__ void fin_apply(double* S, double tot, int slot, int op, double a) {
+// CG on a hermitian operator sigma + K^+ K applied as |K p|^2 (tot) + sigma |p|^2
+// (SC_PP), sigma per rhs in SC_SIGMA.
+__device__ __forceinline__ void fin_apply(double* S, double tot, int slot, int op) {
     if (op == FIN_CG_ALPHA) {  // tot = |K p|^2: alpha = rr / (p, A p)
         S[SC_QQ] = tot;
-        const double pap = a * S[SC_PP] + tot;
+        const double pap = S[SC_SIGMA] * S[SC_PP] + tot;
         if (S[SC_FROZEN] != 0.0) {
             S[SC_ALPHA] = 0.0;
         } else if (!(pap > 0.0)) {
@@ -216,7 +219,6 @@ struct FinArgs {
     int slot = 0;
     int op = 0;
     unsigned* count = nullptr;
-    double a = 0.0;  // parameter of the step (the shift sigma of FIN_CG_ALPHA)
 };
 
 // W totals per right-hand side: partial w of rhs k from block b at part[(k * W + w) * nparts + b]
@@ -269,7 +271,7 @@ __device__ __forceinline__ void fin_tail(const df* part, int nparts, int nrhs, c
             sum = sum + df(v.x, v.y);
         }
         sum = block_sum_df(sum);
-        if (threadIdx.x == 0) fin_apply(f.sc + (size_t)k * SC_N, df_to_double(sum), f.slot, f.op, f.a);
+        if (threadIdx.x == 0) fin_apply(f.sc + (size_t)k * SC_N, df_to_double(sum), f.slot, f.op);
     }
     if (threadIdx.x == 0) *f.count = 0u;
 }

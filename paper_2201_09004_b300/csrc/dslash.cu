@@ -198,7 +198,7 @@ static const char* hname(int prec, int epi) {
 }
 
 int hisq_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int epi, double aa, const Field& in,
-                Field& out, const Field* y, df* norm_out, cudaStream_t st, const FinArgs& fin) {
+                Field& out, const Field* y, df* norm_out, cudaStream_t st, const FinArgs& fin, const double* ak) {
     if (in.prec != op.prec || out.prec != op.prec || (y && y->prec != op.prec))
         fail(LQ_EINVAL, "hisq_dslash: field precision does not match the operator");
     if (in.kind != LQ_STAGGERED_FIELD || out.nrhs != in.nrhs) fail(LQ_EINVAL, "hisq_dslash: field shape");
@@ -213,6 +213,7 @@ int hisq_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int epi,
     a.dagger = dagger;
     a.c_naik = op.c_naik;
     a.a = aa;
+    a.ak = ak;
     a.nrhs = in.nrhs;
     a.norm_out = norm_out;
     a.fin = FinArgs();  // the tuner's trial launches never finalise

@@ -24,6 +24,7 @@ struct HisqArgs {
     int dagger;
     double c_naik;
     double a;       // XPAY scale
+    const double* ak = nullptr;  // if non-null: the XPAY scale of rhs k at ak[k * SC_N] (device)
     int nrhs;
     df* norm_out;
     FinArgs fin;  // with norm_out: the last block finalises the sums
@@ -229,7 +230,7 @@ __global__ void __launch_bounds__(256) hisq_dslash_kernel(HisqArgs a) {
             if constexpr (EPI == EPI_XPAY) {
                 T y[6];
                 fload<P, 6, T>(a.y, kb + b, s, y);
-                const T sa = (T)a.a;
+                const T sa = a.ak ? (T)__ldg(a.ak + (size_t)(kb + b) * SC_N) : (T)a.a;
 #pragma unroll
                 for (int k = 0; k < 6; k++) v[k] = sa * y[k] - v[k];
             }

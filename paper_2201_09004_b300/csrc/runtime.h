@@ -226,8 +226,10 @@ struct OpDesc {
 // Returns the number of thread blocks per right-hand side (the partial-sum stride).
 int wilson_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int epi, const Field& in,
                   Field& out, const Field* y, df* norm_out, cudaStream_t st, const FinArgs& fin = FinArgs());
+// ak (device, optional): per-rhs XPAY scale at ak[k * SC_N], replacing a
 int hisq_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int epi, double a, const Field& in,
-                Field& out, const Field* y, df* norm_out, cudaStream_t st, const FinArgs& fin = FinArgs());
+                Field& out, const Field* y, df* norm_out, cudaStream_t st, const FinArgs& fin = FinArgs(),
+                const double* ak = nullptr);
 // site-local out = A_pp^{-1} in (Wilson twisted mass / clover), parity of both fields
 void wilson_ainv_site(Lattice& lat, const OpDesc& op, int parity, int dagger, const Field& in, Field& out,
                       cudaStream_t st);
@@ -271,8 +273,9 @@ void blas_finalize(const df* part, int nblocks, int nrhs, double* sc, int slot, 
 // Schur operators on resident fields (see solver.cu)
 int schur_wilson(Lattice& lat, const OpDesc& op, int dagger, const Field& in, Field& out, Field& tmp, df* part,
                  cudaStream_t st, const FinArgs& fin = FinArgs());
+// sigma_dev (device, optional): per-rhs shift at sigma_dev[k * SC_N], replacing sigma
 int schur_hisq(Lattice& lat, const OpDesc& op, double sigma, const Field& in, Field& out, Field& t, df* part_t,
-               cudaStream_t st, const FinArgs& fin = FinArgs());
+               cudaStream_t st, const FinArgs& fin = FinArgs(), const double* sigma_dev = nullptr);
 // estimated device bytes of a solve's work fields
 size_t solve_workspace_bytes(const Lattice& lat, const lq_op_params& op, const lq_solve_params& sp, int nrhs);
 int solve_wilson(Lattice& lat, const lq_op_params& op, const lq_solve_params& sp, int nrhs, const double* const* b,

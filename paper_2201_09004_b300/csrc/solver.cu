@@ -15,6 +15,7 @@
 // CG (Jegerlehner, the multi-mass algorithm named in Sec. 2.3), and each mass
 // is then refined by the mixed-precision CG.
 #include <math.h>
+#include <string.h>
 
 #include <algorithm>
 #include <vector>
@@ -44,6 +45,7 @@ struct Scalars {
         LQ_CUDA(cudaMemsetAsync(dev, 0, sizeof(double) * SC_N * n, s));
         part = (df*)ws_get(l, sizeof(df) * per * n, false, s);
         host = (double*)ws_get(l, sizeof(double) * SC_N * n, true, s);
+        memset(host, 0, sizeof(double) * SC_N * n);  // a reused buffer holds an earlier solve's scalars
         count = (unsigned*)ws_get(l, 16, false, s);
         LQ_CUDA(cudaMemsetAsync(count, 0, 16, s));
     }
@@ -508,9 +510,9 @@ static OpDesc hisq_desc(const lq_op_params& op, int prec, int recon) {
 // out = sigma in - H_eo H_oe in; t = H_oe in (odd). part_t receives |t|^2 partials,
 // so that (in, out) = sigma |in|^2 + |t|^2 (since -H_eo = H_oe^+).
 int schur_hisq(Lattice& lat, const OpDesc& op, double sigma, const Field& in, Field& out, Field& t, df* part_t,
-               cudaStream_t st, const FinArgs& fin) {
+               cudaStream_t st, const FinArgs& fin, const double* sigma_dev) {
     int nb = hisq_dslash(lat, op, 1, 0, EPI_HOP, 0.0, in, t, nullptr, part_t, st, fin);
-    hisq_dslash(lat, op, 0, 0, EPI_XPAY, sigma, t, out, &in, nullptr, st);
+    hisq_dslash(lat, op, 0, 0, EPI_XPAY, sigma, t, out, &in, nullptr, st, FinArgs(), sigma_dev);
     return nb;
 }
 
@@ -519,9 +521,9 @@ int schur_hisq(Lattice& lat, const OpDesc& op, double sigma, const Field& in, Fi
 // driver: (p, A p) = sigma |p|^2 + |H_oe p|^2 with |H_oe p|^2 finalised in the
 // kernel that forms H_oe p, alpha and beta on the device; a reliable update
 // recomputes r = b - A x_hi in FP64 accuracy and keeps p.
-static CgResult cg_hisq(Lattice& lat, const OpDesc& ops, const OpDesc& op64, double sigma, const Field& b,
-                        Field& x_hi, const std::vector<double>& tol_abs, double delta, int maxiter, int graph_iters,
-                        cudaStream_t st) {
+static CgResult cg_hisq(Lattice& lat, const OpDesc& ops, const OpDesc& op64, const std::vector<double>& sigma,
+                        const Field& b, Field& x_hi, const std::vector<double>& tol_abs, double delta, int maxiter,
+                        int graph_iters, cudaStream_t st) {
     const int n = b.nrhs;
     const int ps = ops.prec, px = ps == LQ_F16 ? LQ_F32 : ps;
     const int SF = LQ_STAGGERED_FIELD;
@@ -532,14 +534,17 @@ static CgResult cg_hisq(Lattice& lat, const OpDesc& ops, const OpDesc& op64, dou
     Field r = pool.get(SF, ps, n), p = pool.get(SF, ps, n), q = pool.get(SF, ps, n), t = pool.get(SF, ps, n);
     Scalars sc;
     sc.init(lat, n, st);
+    // the shift of every right-hand side (one operator sigma_k - H_eo H_oe per rhs)
+    for (int k = 0; k < n; k++) sc.h(k, SC_SIGMA) = sigma[k];
+    LQ_CUDA(cudaMemcpyAsync(sc.dev, sc.host, sizeof(double) * SC_N * n, cudaMemcpyHostToDevice, st));
+    const double* sig = sc.dev + SC_SIGMA;
     CgResult res(n);
     std::vector<double> ones(n, 1.0);
     FinArgs falpha = sc.f(0, FIN_CG_ALPHA);
-    falpha.a = sigma;
 
     // r = b - A x_hi in FP64 accuracy; |r|^2 -> SC_SS; the sloppy copy's |r|^2 -> SC_RR
     auto true_residual = [&]() {
-        schur_hisq(lat, op64, sigma, x_hi, q64, t64, nullptr, st);
+        schur_hisq(lat, op64, 0.0, x_hi, q64, t64, nullptr, st, FinArgs(), sig);
         blas_xmy_norm(r_hi, b, q64, sc.part, st, sc.f(SC_SS, FIN_SET));
         blas_copy(r, r_hi, st);
         blas_norm2(r, sc.part, st, sc.f(SC_RR, FIN_SET));
@@ -551,7 +556,7 @@ static CgResult cg_hisq(Lattice& lat, const OpDesc& ops, const OpDesc& op64, dou
     sc.pull(st);
     KrylovState ks = krylov_start(sc, res, tol_abs, st);
     auto iteration = [&](double* dst) {
-        schur_hisq(lat, ops, sigma, p, q, t, sc.part, st, falpha);               // q = A p, alpha
+        schur_hisq(lat, ops, 0.0, p, q, t, sc.part, st, falpha, sig);           // q = A p, alpha
         blas_cg_xs(x_lo, p, r, q, sc.dev, sc.part, st, sc.f(0, FIN_CG_BETA));   // x, r, |r|^2, beta
         blas_cg_p_norm(p, r, sc.dev, sc.part, st, sc.f(SC_PP, FIN_SET));         // p = r + beta p, |p|^2
         if (dst) LQ_CUDA(cudaMemcpyAsync(dst, sc.dev, sizeof(double) * SC_N * n, cudaMemcpyDeviceToHost, st));
@@ -747,13 +752,18 @@ int solve_hisq(Lattice& lat, const lq_op_params& opp, const lq_solve_params& sp,
         std::vector<double> worst(nrhs, 0.0);
         std::vector<int> status(nrhs, LQ_OK);
         std::vector<double> one(nrhs, 1.0), neg(nrhs, -1.0);
+        // Refinement of every mass by the mixed CG from the multi-shift guess, one
+        // mass at a time: each stops at its own iteration count. (Solving all
+        // masses together as one multi-rhs system with a shift per rhs was measured
+        // slower at 48^3x144: the FP16 HISQ kernel is bound by its per-rhs decode
+        // and arithmetic, not by the shared link loads, and every mass then runs
+        // for the lightest mass's iterations.)
         for (int i = 0; i < ns; i++) {
             const double m = masses[i];
-            // bhat_i = m b_e - c
+            // bhat_i = m b_e - c; initial guess m y_1 - y_2 from the multi-shift stage, or zero
             std::vector<double> am(nrhs, m);
             blas_copy(bh, c, st);
             blas_axpby_h(bh, am.data(), be, neg.data(), nullptr, st);
-            // initial guess: from the multi-shift stage, or zero
             if (ns > 1) {
                 Field y1 = ys[i].sub(0, nrhs), y2 = ys[i].sub(nrhs, nrhs);
                 blas_copy(xe, y2, st);
@@ -764,7 +774,8 @@ int solve_hisq(Lattice& lat, const lq_op_params& opp, const lq_solve_params& sp,
             }
             // the even part of the full residual is (bhat - A x_e) / m
             for (int k = 0; k < nrhs; k++) tol_abs[k] = 0.5 * sp.tol * bn[k] * m;
-            CgResult cr = cg_hisq(lat, ops, op64, sigma[i], bh, xe, tol_abs, delta, maxiter, sp.graph_iters, st);
+            CgResult cr = cg_hisq(lat, ops, op64, std::vector<double>(nrhs, sigma[i]), bh, xe, tol_abs, delta,
+                                  maxiter, sp.graph_iters, st);
             // x_o = (b_o - H_oe x_e) / m
             hisq_dslash(lat, op64, 1, 0, EPI_HOP, 0.0, xe, to, nullptr, nullptr, st);
             blas_copy(xo, to, st);

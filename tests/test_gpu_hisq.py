@@ -103,6 +103,34 @@ def test_hisq_multishift_solve(L, orc, prec):
             assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-10, (k, m)
 
 
+def test_hisq_repeated_solves_reuse_workspace(L, orc):
+    """Consecutive solves on one lattice reuse its work buffers (including the
+    pinned scalar block): single-mass CG with 1 and 4 right-hand sides, graph
+    replay on and off, FP16 and FP32, and a multi-shift solve after them, all
+    meet the oracle's true residual."""
+    dims = (6, 6, 6, 8)
+    lat, V, W = make(L, dims, 49)
+    m = 0.05
+    b = synth.z2_source(dims, 50, ncomp=3).numpy()
+    D = orc.Hisq(dims, V, W, m)
+    op = L.op_params(L.HISQ, m)
+    for prec in (2, 1):
+        for n in (1, 4):
+            for gk in (0, -1):
+                sp = L.solve_params(solver=L.MIXED_CGNR, tol=1e-10, prec_sloppy=prec, graph_iters=gk)
+                xs, info = lat.solve(op, sp, [b] * n)
+                for x, inf in zip(xs, info):
+                    assert inf["status"] == 0, (prec, n, gk)
+                    assert np.linalg.norm(b - D.apply(x)) / np.linalg.norm(b) <= 1e-10
+    masses = [0.01, 0.02, 0.05]
+    sp = L.solve_params(solver=L.MULTISHIFT_CG, tol=1e-10, prec_sloppy=2, masses=masses)
+    xs, info = lat.solve(L.op_params(L.HISQ, masses[0]), sp, [b])
+    assert info[0]["status"] == 0
+    for i, mi in enumerate(masses):
+        Di = orc.Hisq(dims, V, W, mi)
+        assert np.linalg.norm(b - Di.apply(xs[i])) / np.linalg.norm(b) <= 1e-10
+
+
 def test_hisq_full_size_sampled_sites(L, orc):
     """48^3x144 (the HISQ configuration) would need 18 GB of FP64 links on the
     host for the oracle; the kernel is checked at 24^3x48 full size instead on
