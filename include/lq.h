@@ -276,6 +276,43 @@ int64_t lq_launch_count(void);
 int lq_tune_reset(void);
 int lq_tune_force(int code);
 
+/* ----------------------------------------------------------------- overlap */
+
+/* Building blocks of the overlap operator (Sec. 2.3):
+ *   D_ov = (1/rho) (1 + g5 eps(H_w)),  H_w = g5 D_w(-rho),  rho ~ 1.5,
+ * eps the sign function. Fields are full-lattice Wilson spinors in the canonical
+ * layout (host or device per loc); prec is LQ_F64, LQ_F32X2 or LQ_F32. The
+ * lattice needs its thin links; clover and twisted mass are not used. */
+typedef struct {
+    int order;             /* Chebyshev terms used */
+    double max_deviation;  /* max |1 - x P(x^2)| over lambda_min/lambda_max <= x <= 1 */
+} lq_sign_info;
+
+/* out = g5 D_w(-rho) in, with g5 fused into the operator kernel's epilogue. */
+int lq_gamma5_dw_apply(lq_lattice lat, double rho, int prec, int loc, const double* in, double* out,
+                       void* stream);
+
+/* Coefficients of the sign approximation eps(x) ~ x P(x^2) for eps = lambda_min /
+ * lambda_max in (0, 1): P(y) = sum_k c_k T_k((2y - eps^2 - 1)/(1 - eps^2)) (c_0 with
+ * its factor 1/2 applied) interpolates 1/sqrt(y) at the Chebyshev nodes of
+ * [eps^2, 1]; the order is the smallest whose |1 - x P(x^2)| stays <= delta on
+ * [eps, 1] (dense sampling). The paper refines its fit at the error's extrema
+ * instead (a Remez-like exchange); node interpolation is within a small factor of
+ * that minimax error. coeffs (may be NULL) receives *order values, at most
+ * max_order; LQ_EINVAL if more are needed. Host only. */
+int lq_chebyshev_sign(double eps, double delta, int max_order, double* coeffs, int* order, double* max_deviation);
+
+/* out ~ eps(H_w) in on the part of the spectrum with lambda_min <= |lambda| <=
+ * lambda_max: (H_w/lambda_max) P((H_w/lambda_max)^2) in, P from lq_chebyshev_sign,
+ * evaluated by the Clenshaw recurrence (two H_w applications per term). lambda_max
+ * must bound the spectrum (|4 - rho| + 8 always does: eight hops of norm one);
+ * outside [-lambda_max, lambda_max] the polynomial grows without bound. The paper
+ * projects out the lowest modes first (eigenvectors, not built here); the caller
+ * chooses lambda_min below the spectrum it passes. info (may be NULL) gets the
+ * order and the deviation bound. */
+int lq_overlap_sign_apply(lq_lattice lat, double rho, double lambda_min, double lambda_max, double delta, int prec,
+                          int loc, const double* in, double* out, lq_sign_info* info, void* stream);
+
 /* ----------------------------------------------------------------- serving */
 
 /* A request server for continuous batching of solves: requests are queued,

@@ -228,3 +228,93 @@ class Hisq:
                                       ctypes.c_void_p(masses.ctypes.data), _p(b), ptrs, ctypes.c_double(tol),
                                       ctypes.c_int(maxiter), ctypes.byref(it), ctypes.c_void_p(rel.ctypes.data))
         return xs, {"status": st, "iters": it.value, "true_rel_residual": rel.tolist()}
+
+
+# ------------------------------------------------------------------ overlap
+# Building blocks of the overlap operator (Sec. 2.3): H_w = g5 D_w(-rho) and its
+# sign function approximated by eps(x) ~ x P(x^2), x = H_w / lambda_max, with P a
+# Chebyshev polynomial of 1/sqrt(y) on [eps^2, 1] evaluated by the Clenshaw
+# recurrence. Written from the paper's description; the CUDA library computes its
+# own coefficients.
+
+def hermitian_wilson(dims, U, rho, bc_t=-1):
+    """The operator v -> g5 D_w(-rho) v (D_w(-rho) = (4 - rho) - H in this build's sign reading)."""
+    W = Wilson(dims, U, -rho, 0.0, bc_t=bc_t)
+    g5 = np.array([1.0, 1.0, -1.0, -1.0])[:, None]
+
+    def apply(v):
+        return g5 * W.apply(v)
+    return apply
+
+
+def chebyshev_nodes_coeffs(f, a, b, n):
+    """Coefficients c_k (c_0 halved) of the degree n-1 polynomial interpolating f at
+    the n Chebyshev nodes of [a, b], in the basis T_k((2y - a - b)/(b - a))."""
+    j = np.arange(n)
+    theta = np.pi * (j + 0.5) / n
+    y = 0.5 * ((b - a) * np.cos(theta) + a + b)
+    fy = f(y)
+    k = np.arange(n)[:, None]
+    c = 2.0 / n * (np.cos(k * theta[None, :]) @ fy)
+    c[0] *= 0.5
+    return c
+
+
+def clenshaw(c, z, matvec=None):
+    """sum_k c_k T_k(z): z a number or array (matvec None), or, with matvec the map
+    v -> Z v, the vector sum_k c_k T_k(Z) z (z then the vector)."""
+    if matvec is None:
+        b1 = np.zeros_like(np.asarray(z, dtype=float))
+        b2 = np.zeros_like(b1)
+        for ck in c[:0:-1]:
+            b1, b2 = ck + 2.0 * z * b1 - b2, b1
+        return c[0] + z * b1 - b2
+    v = z
+    b1 = np.zeros_like(v)
+    b2 = np.zeros_like(v)
+    for ck in c[:0:-1]:
+        b1, b2 = ck * v + 2.0 * matvec(b1) - b2, b1
+    return c[0] * v + matvec(b1) - b2
+
+
+def sign_deviation(c, eps, npts=3000):
+    """max over x in [eps, 1] of |1 - x P(x^2)|, log-spaced and linear samples."""
+    x = np.concatenate([eps * (1.0 / eps) ** (np.arange(npts + 1) / npts), eps + (1 - eps) * np.arange(npts + 1) / npts])
+    a, b = eps * eps, 1.0
+    z = (2 * x * x - a - b) / (b - a)
+    return float(np.max(np.abs(1.0 - x * clenshaw(c, z))))
+
+
+def chebyshev_sign_coeffs(eps, delta, max_order=65536):
+    """The smallest number of terms (doubling from 8, then bisection) whose sign
+    deviation on [eps, 1] is <= delta; returns (coeffs, deviation)."""
+    a, b = eps * eps, 1.0
+    f = lambda y: 1.0 / np.sqrt(y)
+    hi = 8
+    while True:
+        c = chebyshev_nodes_coeffs(f, a, b, hi)
+        if sign_deviation(c, eps) <= delta:
+            break
+        if hi >= max_order:
+            raise ValueError("more than max_order terms needed")
+        hi = min(2 * hi, max_order)
+    lo = hi // 2
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        if sign_deviation(chebyshev_nodes_coeffs(f, a, b, mid), eps) <= delta:
+            hi = mid
+        else:
+            lo = mid
+    c = chebyshev_nodes_coeffs(f, a, b, hi)
+    return c, sign_deviation(c, eps)
+
+
+def overlap_sign(hw, v, lambda_min, lambda_max, coeffs):
+    """(H/lmax) P((H/lmax)^2) v by Clenshaw, hw the map v -> H_w v."""
+    eps = lambda_min / lambda_max
+    a, b = eps * eps, 1.0
+
+    def Z(w):
+        return (2.0 * hw(hw(w)) / lambda_max ** 2 - (a + b) * w) / (b - a)
+    pv = clenshaw(coeffs, v, matvec=Z)
+    return hw(pv) / lambda_max

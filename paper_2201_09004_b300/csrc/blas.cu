@@ -399,6 +399,27 @@ __global__ void rho_kernel(FieldV r, FieldV r0, df* part, FinArgs fin) {
     partials_w<3>(acc, part, k, fin);
 }
 
+// out = a0 v + a1 t + a2 w - out_old (sub_old) or a0 v + a1 t + a2 w
+template <int P, int NR>
+__global__ void lincomb4_kernel(FieldV out, double a0, FieldV v, double a1, FieldV t, double a2, FieldV w, int sub_old) {
+    typedef typename RealT<P>::T T;
+    const int k = blockIdx.y;
+    const T c0 = (T)a0, c1 = (T)a1, c2 = (T)a2;
+    SITE_LOOP(out.vh) {
+        T vo[NR], vv[NR], vt[NR], vw[NR];
+        fload<P, NR, T>(v, k, s, vv);
+        fload<P, NR, T>(t, k, s, vt);
+        fload<P, NR, T>(w, k, s, vw);
+        if (sub_old) fload<P, NR, T>(out, k, s, vo);
+#pragma unroll
+        for (int q = 0; q < NR; q++) {
+            T r = c0 * vv[q] + c1 * vt[q] + c2 * vw[q];
+            vo[q] = sub_old ? r - vo[q] : r;
+        }
+        fstore<P, NR, T>(out, k, s, vo);
+    }
+}
+
 // ---------------------------------------------------------------- launchers
 static dim3 red_grid(int nrhs) { return dim3(RED_BLOCKS, nrhs); }
 static dim3 upd_grid(int vh, int nrhs) {
@@ -595,6 +616,17 @@ void blas_cg_p_norm(Field& p, const Field& r, const double* sc, df* part, cudaSt
 #define K(NR) cg_p_norm_kernel<P_, NR>
 #define L(P) { constexpr int P_ = P; BY_KIND(p, "blas_cg_p", K, red_grid(p.nrhs), p.view(), r.view(), sc, part, fin); }
     DISPATCH_P(p.prec, L);
+#undef L
+#undef K
+}
+
+void blas_lincomb4(Field& out, double a0, const Field& v, double a1, const Field& t, double a2, const Field& w,
+                   cudaStream_t st, bool sub_old) {
+    if (out.prec != v.prec || out.prec != t.prec || out.prec != w.prec) fail(LQ_EINVAL, "blas_lincomb4: precision mismatch");
+    dim3 g = upd_grid(out.vh, out.nrhs);
+#define K(NR) lincomb4_kernel<P_, NR>
+#define L(P) { constexpr int P_ = P; BY_KIND(out, "blas_lincomb4", K, g, out.view(), a0, v.view(), a1, t.view(), a2, w.view(), (int)sub_old); }
+    DISPATCH_P(out.prec, L);
 #undef L
 #undef K
 }

@@ -446,3 +446,106 @@ extern "C" int lq_schur_field(lq_lattice h, const lq_op_params* op, int dagger, 
     return LQ_OK;
     LQ_CATCH
 }
+
+// ---------------------------------------------------------------- overlap
+static void check_sign_prec(int prec) {
+    if (prec != LQ_F64 && prec != LQ_F32 && prec != LQ_F32X2)
+        fail(LQ_EINVAL, "the overlap building blocks run in LQ_F64, LQ_F32X2 or LQ_F32");
+}
+
+// full-lattice Wilson spinor fields of 2 "rhs" (even sites, odd sites) from / to canonical
+static void import_full(Lattice& L, Field& f, const double* canon, cudaStream_t st) {
+    import_field(L, f, 0, 0, canon, st);
+    import_field(L, f, 1, 1, canon, st);
+}
+static void export_full(Lattice& L, const Field& f, double* canon, cudaStream_t st) {
+    export_field(L, f, 0, 0, canon, st);
+    export_field(L, f, 1, 1, canon, st);
+}
+
+extern "C" int lq_gamma5_dw_apply(lq_lattice h, double rho, int prec, int loc, const double* in, double* out,
+                                  void* stream) {
+    LQ_TRY
+    check_lattice(h);
+    check_sign_prec(prec);
+    if (!in || !out) fail(LQ_EINVAL, "null field");
+    Lattice& L = h->lat;
+    if (!L.canon[LQ_THIN]) fail(LQ_EINVAL, "thin gauge field not loaded");
+    cudaStream_t st = as_stream(stream);
+    const size_t bytes = field_canon_bytes(L, LQ_WILSON_TM);
+    DevBuf bin(loc == LQ_HOST ? bytes : 0, &L, st), bout(loc == LQ_HOST ? bytes : 0, &L, st);
+    const double* din = stage_in(in, bytes, loc, bin, st);
+    double* dout = loc == LQ_HOST ? (double*)bout.p : out;
+    Field fi = ws_field(L, LQ_WILSON_FIELD, prec, 2, st), fo = ws_field(L, LQ_WILSON_FIELD, prec, 2, st);
+    try {
+        import_full(L, fi, din, st);
+        hw_apply_full(L, rho, fi, fo, st);
+        export_full(L, fo, dout, st);
+        if (loc == LQ_HOST) LQ_CUDA(cudaMemcpyAsync(out, dout, bytes, cudaMemcpyDeviceToHost, st));
+        LQ_CUDA(cudaStreamSynchronize(st));
+    } catch (...) {
+        ws_put(L, fi.data, st);
+        ws_put(L, fo.data, st);
+        throw;
+    }
+    ws_put(L, fi.data, st);
+    ws_put(L, fo.data, st);
+    return LQ_OK;
+    LQ_CATCH
+}
+
+extern "C" int lq_chebyshev_sign(double eps, double delta, int max_order, double* coeffs, int* order,
+                                 double* max_deviation) {
+    LQ_TRY
+    if (max_order < 1) fail(LQ_EINVAL, "max_order must be positive");
+    std::vector<double> c;
+    double dev = 0.0;
+    sign_coefficients(eps, delta, max_order, c, dev);
+    if (order) *order = (int)c.size();
+    if (max_deviation) *max_deviation = dev;
+    if (coeffs)
+        for (size_t k = 0; k < c.size(); k++) coeffs[k] = c[k];
+    return LQ_OK;
+    LQ_CATCH
+}
+
+extern "C" int lq_overlap_sign_apply(lq_lattice h, double rho, double lambda_min, double lambda_max, double delta,
+                                     int prec, int loc, const double* in, double* out, lq_sign_info* info,
+                                     void* stream) {
+    LQ_TRY
+    check_lattice(h);
+    check_sign_prec(prec);
+    if (!in || !out) fail(LQ_EINVAL, "null field");
+    if (!(lambda_max > 0.0) || !(lambda_min > 0.0) || !(lambda_min < lambda_max))
+        fail(LQ_EINVAL, "need 0 < lambda_min < lambda_max");
+    Lattice& L = h->lat;
+    if (!L.canon[LQ_THIN]) fail(LQ_EINVAL, "thin gauge field not loaded");
+    std::vector<double> c;
+    double dev = 0.0;
+    sign_coefficients(lambda_min / lambda_max, delta, 1 << 16, c, dev);
+    cudaStream_t st = as_stream(stream);
+    const size_t bytes = field_canon_bytes(L, LQ_WILSON_TM);
+    DevBuf bin(loc == LQ_HOST ? bytes : 0, &L, st), bout(loc == LQ_HOST ? bytes : 0, &L, st);
+    const double* din = stage_in(in, bytes, loc, bin, st);
+    double* dout = loc == LQ_HOST ? (double*)bout.p : out;
+    Field fi = ws_field(L, LQ_WILSON_FIELD, prec, 2, st), fo = ws_field(L, LQ_WILSON_FIELD, prec, 2, st);
+    try {
+        import_full(L, fi, din, st);
+        sign_apply(L, rho, lambda_max, lambda_min / lambda_max, c, fi, fo, st);
+        export_full(L, fo, dout, st);
+        if (loc == LQ_HOST) LQ_CUDA(cudaMemcpyAsync(out, dout, bytes, cudaMemcpyDeviceToHost, st));
+        LQ_CUDA(cudaStreamSynchronize(st));
+    } catch (...) {
+        ws_put(L, fi.data, st);
+        ws_put(L, fo.data, st);
+        throw;
+    }
+    ws_put(L, fi.data, st);
+    ws_put(L, fo.data, st);
+    if (info) {
+        info->order = (int)c.size();
+        info->max_deviation = dev;
+    }
+    return LQ_OK;
+    LQ_CATCH
+}

@@ -92,6 +92,7 @@ int wilson_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int ep
     a.parity = parity;
     a.dagger = dagger;
     a.has_clover = op.action == LQ_WILSON_TM_CLOVER;
+    a.gamma5_out = op.gamma5;
     a.m4 = 4.0 + op.m;
     a.mu = dagger ? -op.mu : op.mu;
     a.nrhs = in.nrhs;

@@ -218,7 +218,8 @@ struct OpDesc {
     int action;
     double m, mu, c_naik;
     int prec;
-    int recon;   // thin (Wilson) / long (HISQ) link compression
+    int recon;       // thin (Wilson) / long (HISQ) link compression
+    int gamma5 = 0;  // Wilson: multiply every result by g5 (the hermitian g5 D_w)
 };
 
 // out = epilogue(D in) for output parity; `y` used by EPI_XPAY (same parity as out).
@@ -261,6 +262,9 @@ void blas_bicg_xr(Field& x, const Field& p, Field& r, const Field& t, const Fiel
                   cudaStream_t st, const FinArgs& fin);
 void blas_bicg_p(Field& p, const Field& r, const Field& v, const double* sc, cudaStream_t st);
 void blas_bicg_rho(const Field& r, const Field& r0, df* part, cudaStream_t st, const FinArgs& fin);
+// out = a0 v + a1 t + a2 w - out (sub_old), or without the last term; per element, all rhs
+void blas_lincomb4(Field& out, double a0, const Field& v, double a1, const Field& t, double a2, const Field& w,
+                   cudaStream_t st, bool sub_old = true);
 // p = r + beta p with partial |p|^2
 void blas_cg_p_norm(Field& p, const Field& r, const double* sc, df* part, cudaStream_t st, const FinArgs& fin);
 // p = r + beta p, beta_k = sc[k*SC_N + SC_BETA]
@@ -276,6 +280,13 @@ int schur_wilson(Lattice& lat, const OpDesc& op, int dagger, const Field& in, Fi
 // sigma_dev (device, optional): per-rhs shift at sigma_dev[k * SC_N], replacing sigma
 int schur_hisq(Lattice& lat, const OpDesc& op, double sigma, const Field& in, Field& out, Field& t, df* part_t,
                cudaStream_t st, const FinArgs& fin = FinArgs(), const double* sigma_dev = nullptr);
+// overlap building blocks (overlap.cu): Chebyshev coefficients of 1/sqrt(y) on
+// [eps^2, 1] meeting the sign deviation delta; g5 D_w(-rho) and eps(g5 D_w(-rho))
+// on full-lattice vectors (fields of 2 rhs: even sites, odd sites)
+void sign_coefficients(double eps, double delta, int max_order, std::vector<double>& c, double& dev);
+void hw_apply_full(Lattice& lat, double rho, const Field& in, Field& out, cudaStream_t st);
+void sign_apply(Lattice& lat, double rho, double lmax, double eps, const std::vector<double>& c, const Field& v,
+                Field& out, cudaStream_t st);
 // estimated device bytes of a solve's work fields
 size_t solve_workspace_bytes(const Lattice& lat, const lq_op_params& op, const lq_solve_params& sp, int nrhs);
 int solve_wilson(Lattice& lat, const lq_op_params& op, const lq_solve_params& sp, int nrhs, const double* const* b,

@@ -30,6 +30,7 @@ struct WilsonArgs {
     int parity;             // output parity
     int dagger;
     int has_clover;
+    int gamma5_out = 0;     // multiply the result by g5 (negate spins 2, 3): the hermitian g5 D_w
     double m4;              // 4 + m
     double mu;              // twisted mass, already negated for the adjoint
     int nrhs;
@@ -728,12 +729,13 @@ __global__ void __launch_bounds__(256, MINB) wilson_dslash_kernel(WilsonArgs a) 
         for (int b = 0; b < NB; b++) {
             if (kb + b >= a.nrhs) break;
             T v[24];
+            const T g5 = a.gamma5_out ? (T)-1 : (T)1;
 #pragma unroll
             for (int sp = 0; sp < 4; sp++)
 #pragma unroll
                 for (int cc = 0; cc < 3; cc++) {
-                    v[(sp * 3 + cc) * 2] = res[b][sp][cc].r;
-                    v[(sp * 3 + cc) * 2 + 1] = res[b][sp][cc].i;
+                    v[(sp * 3 + cc) * 2] = sp < 2 ? res[b][sp][cc].r : g5 * res[b][sp][cc].r;
+                    v[(sp * 3 + cc) * 2 + 1] = sp < 2 ? res[b][sp][cc].i : g5 * res[b][sp][cc].i;
                 }
             if (a.norm_out) {
                 // per-site sum in the kernel's precision, blocks reduce in FP64

@@ -218,10 +218,11 @@ __global__ void __launch_bounds__(256, 2) wilson_dslash_df2_kernel(WilsonArgs a)
 
     float4* out = (float4*)((char*)a.out.data + (size_t)k * a.out.rhs_bytes);
     df nrm(0.f);
+    const bool neg_out = a.gamma5_out && h == 1;  // g5 negates chiral block 1 (spins 2, 3)
     if constexpr (EPI == EPI_HOP) {
 #pragma unroll
         for (int i = 0; i < 6; i++) {
-            if (live) st_cd(out, (size_t)(6 * h + i) * vh + s, w[i]);
+            if (live) st_cd(out, (size_t)(6 * h + i) * vh + s, neg_out ? mk(-w[i].r, -w[i].i) : w[i]);
             nrm = nrm + cnorm2(w[i]);
         }
     } else if constexpr (EPI == EPI_AINV) {
@@ -249,7 +250,7 @@ __global__ void __launch_bounds__(256, 2) wilson_dslash_df2_kernel(WilsonArgs a)
 #pragma unroll
                 for (int j = 0; j < 6; j++) cur[j] = nxt[j];
                 const cd acc = cacc_done(t);
-                if (live) st_cd(out, (size_t)(6 * h + i) * vh + s, acc);
+                if (live) st_cd(out, (size_t)(6 * h + i) * vh + s, neg_out ? mk(-acc.r, -acc.i) : acc);
                 nrm = nrm + cnorm2(acc);
             }
         } else {
@@ -259,7 +260,7 @@ __global__ void __launch_bounds__(256, 2) wilson_dslash_df2_kernel(WilsonArgs a)
 #pragma unroll
             for (int i = 0; i < 6; i++) {
                 const cd o = f * w[i];
-                if (live) st_cd(out, (size_t)(6 * h + i) * vh + s, o);
+                if (live) st_cd(out, (size_t)(6 * h + i) * vh + s, neg_out ? mk(-o.r, -o.i) : o);
                 nrm = nrm + cnorm2(o);
             }
         }
@@ -302,7 +303,7 @@ __global__ void __launch_bounds__(256, 2) wilson_dslash_df2_kernel(WilsonArgs a)
 #pragma unroll
             for (int j = 0; j < 6; j++) cur[j] = nxt[j];
             const cd acc = cacc_done(t);
-            if (live) st_cd(out, (size_t)(6 * h + i) * vh + s, acc);
+            if (live) st_cd(out, (size_t)(6 * h + i) * vh + s, neg_out ? mk(-acc.r, -acc.i) : acc);
             nrm = nrm + cnorm2(acc);
         }
     }

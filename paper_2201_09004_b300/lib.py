@@ -38,7 +38,8 @@ EXPORTS = [
     "lq_last_error", "lq_create_lattice", "lq_destroy_lattice", "lq_lattice_bytes", "lq_lattice_release_workspace", "lq_load_gauge",
     "lq_load_clover", "lq_dslash_apply", "lq_operator_apply", "lq_solve", "lq_field_create",
     "lq_field_destroy", "lq_field_import", "lq_field_export", "lq_dslash_field", "lq_schur_field",
-    "lq_profile_enable", "lq_profile_reset", "lq_profile_query", "lq_launch_count", "lq_tune_reset", "lq_tune_force", "lq_server_create",
+    "lq_profile_enable", "lq_profile_reset", "lq_profile_query", "lq_launch_count", "lq_tune_reset", "lq_tune_force", "lq_gamma5_dw_apply", "lq_chebyshev_sign",
+    "lq_overlap_sign_apply", "lq_server_create",
     "lq_server_destroy", "lq_submit", "lq_poll", "lq_wait", "lq_server_stats", "lq_dslash_apply_noalloc", "lq_request_bytes",
 ]
 
@@ -68,6 +69,10 @@ class SolveInfo(ctypes.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class SignInfo(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int), ("max_deviation", ctypes.c_double)]
 
 
 class Request(ctypes.Structure):
@@ -226,6 +231,26 @@ class Lattice:
                                        ctypes.c_int(prec), ctypes.c_int(loc), p, po, _stream(stream)))
         return out
 
+    def gamma5_dw_apply(self, rho, psi, prec=F64, stream=None):
+        """g5 D_w(-rho) psi on the full lattice (the hermitian Wilson operator of the overlap)."""
+        p, loc, keep = _ptr(psi)
+        out = self._out_like(psi)
+        po, loco, keepo = _ptr(out)
+        _check(lib().lq_gamma5_dw_apply(self.h, ctypes.c_double(rho), ctypes.c_int(prec), ctypes.c_int(loc), p, po,
+                                        _stream(stream)))
+        return out
+
+    def overlap_sign_apply(self, rho, lambda_min, lambda_max, delta, psi, prec=F64, stream=None):
+        """eps(g5 D_w(-rho)) psi by the Chebyshev/Clenshaw approximation; returns (out, info dict)."""
+        p, loc, keep = _ptr(psi)
+        out = self._out_like(psi)
+        po, loco, keepo = _ptr(out)
+        info = SignInfo()
+        _check(lib().lq_overlap_sign_apply(self.h, ctypes.c_double(rho), ctypes.c_double(lambda_min),
+                                           ctypes.c_double(lambda_max), ctypes.c_double(delta), ctypes.c_int(prec),
+                                           ctypes.c_int(loc), p, po, ctypes.byref(info), _stream(stream)))
+        return out, {"order": info.order, "max_deviation": info.max_deviation}
+
     def solve(self, op, params, rhs, stream=None, check=True, out=None):
         """Solves D x = b for every b in rhs (list). Returns (x list, info list).
 
@@ -321,6 +346,18 @@ def profile_query(name=""):
 
 def launch_count():
     return int(lib().lq_launch_count())
+
+
+def chebyshev_sign(eps, delta, max_order=65536):
+    """Coefficients of eps(x) ~ x P(x^2), P = sum_k c_k T_k(z(x^2)) on [eps^2, 1]; returns (coeffs, max_deviation)."""
+    order = ctypes.c_int()
+    dev = ctypes.c_double()
+    _check(lib().lq_chebyshev_sign(ctypes.c_double(eps), ctypes.c_double(delta), ctypes.c_int(max_order), None,
+                                   ctypes.byref(order), ctypes.byref(dev)))
+    buf = (ctypes.c_double * order.value)()
+    _check(lib().lq_chebyshev_sign(ctypes.c_double(eps), ctypes.c_double(delta), ctypes.c_int(order.value), buf,
+                                   ctypes.byref(order), ctypes.byref(dev)))
+    return list(buf), dev.value
 
 
 def tune_reset():

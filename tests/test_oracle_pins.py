@@ -418,3 +418,66 @@ def test_hisq_multishift_equals_independent_solves(orc, hisq_field):
     for m, x in zip(masses, xs):
         xi, ii = orc.Hisq(dims, V, W, m).cgnr(b, tol=1e-12)
         assert rel(x, xi) < 1e-9
+
+
+# ------------------------------------------------------------ overlap pins
+# Sec. 2.3: eps(H_w) ~ x P(x^2) with a Chebyshev polynomial evaluated by Clenshaw.
+
+def test_clenshaw_equals_cosine_series(orc):
+    """The recurrence reproduces sum_k c_k T_k(z) with T_k(z) = cos(k arccos z)."""
+    rng = np.random.default_rng(5)
+    c = rng.normal(size=40)
+    z = np.linspace(-1, 1, 101)
+    direct = sum(c[k] * np.cos(k * np.arccos(z)) for k in range(len(c)))
+    assert np.max(np.abs(orc.clenshaw(c, z) - direct)) < 1e-12
+    # and on vectors through an operator: a diagonal Z gives the same numbers
+    v = rng.normal(size=101)
+    got = orc.clenshaw(c, v, matvec=lambda w: z * w)
+    assert np.max(np.abs(got - direct * v)) < 1e-12
+
+
+def test_chebyshev_sign_interpolates_and_meets_the_bound(orc):
+    """The polynomial equals 1/sqrt(y) at its Chebyshev nodes, and |1 - x P(x^2)|
+    stays below the bound on random points of [eps, 1] not used to choose the order."""
+    eps, delta = 0.05, 1e-5
+    c, dev = orc.chebyshev_sign_coeffs(eps, delta)
+    n = len(c)
+    a, b = eps * eps, 1.0
+    theta = np.pi * (np.arange(n) + 0.5) / n
+    y = 0.5 * ((b - a) * np.cos(theta) + a + b)
+    assert np.max(np.abs(orc.clenshaw(c, np.cos(theta)) - 1 / np.sqrt(y))) < 1e-9
+    x = np.random.default_rng(6).uniform(eps, 1.0, size=20000)
+    z = (2 * x * x - a - b) / (b - a)
+    assert np.max(np.abs(1 - x * orc.clenshaw(c, z))) <= 1.2 * delta
+    assert dev <= delta
+
+
+def _dense(op, shape):
+    n = int(np.prod(shape))
+    cols = []
+    for j in range(n):
+        e = np.zeros(n, dtype=complex)
+        e[j] = 1
+        cols.append(op(e.reshape(shape)).ravel())
+    return np.array(cols).T
+
+
+def test_overlap_sign_against_dense_eigendecomposition_2x4(orc):
+    """On 2^4 (192 x 192): g5 D_w(-rho) is hermitian, and the Chebyshev/Clenshaw sign
+    function applied to a vector equals V sign(L) V^+ v from the exact eigensystem
+    within the deviation bound; applied twice it is the identity."""
+    dims, rho, delta = (2, 2, 2, 2), 1.5, 1e-6
+    U = synth.thin_links(dims, 71, 0.3).numpy()
+    hw = orc.hermitian_wilson(dims, U, rho)
+    shape = (2, 2, 2, 2, 4, 3)
+    H = _dense(hw, shape)
+    assert np.max(np.abs(H - H.conj().T)) < 1e-13
+    lam, V = np.linalg.eigh(H)
+    lmin, lmax = 0.9 * np.min(np.abs(lam)), 1.1 * np.max(np.abs(lam))
+    c, dev = orc.chebyshev_sign_coeffs(lmin / lmax, delta)
+    v = synth.gaussian_field(dims, 72).numpy()
+    exact = (V @ (np.sign(lam) * (V.conj().T @ v.ravel()))).reshape(shape)
+    got = orc.overlap_sign(hw, v, lmin, lmax, c)
+    assert np.linalg.norm(got - exact) <= 2 * delta * np.linalg.norm(v)
+    twice = orc.overlap_sign(hw, got, lmin, lmax, c)
+    assert np.linalg.norm(twice - v) <= 4 * delta * np.linalg.norm(v)
