@@ -617,6 +617,62 @@ def run_hisq_propagator(args):
     print(json.dumps(line), flush=True)
 
 
+def run_overlap(args):
+    """Overlap building blocks on 24^3x64 (the RBC11 shape of the paper's overlap runs):
+    50 applications of the fused g5 D_w(-rho), rho = 1.5, on the full lattice (the
+    paper's Sec. 3 comparison: 0.025 s for 50 D_w with QUDA on one node of 4 V100),
+    and one application of the Chebyshev/Clenshaw sign function eps(g5 D_w(-rho)) on
+    the spectrum interval [0.1, 10.5] to a deviation of 1e-5 (the bound of the
+    paper's Fig. 2), FP64 and double-float."""
+    import torch
+    from paper_2201_09004_b300 import lib, synth
+    torch.cuda.set_device(0)
+    dims, rho = DIMS, 1.5
+    U = synth.thin_links(dims, GAUGE_SEED, device="cuda")
+    lat = lib.Lattice(dims)
+    lat.load_gauge(lib.THIN, U)
+    del U
+    v = synth.gaussian_field(dims, 208, device="cuda")
+    out = {}
+    vh = int(np.prod(dims)) // 2
+    for name, prec in (("f64", lib.F64), ("f32x2", lib.F32X2), ("f32", lib.F32)):
+        lat.gamma5_dw_apply(rho, v, prec=prec)
+        torch.cuda.synchronize()
+        e0, e1 = _events()
+        e0.record()
+        for _ in range(50):
+            lat.gamma5_dw_apply(rho, v, prec=prec)
+        e1.record()
+        torch.cuda.synchronize()
+        s50 = e0.elapsed_time(e1) * 1e-3
+        out["g5dw_50_" + name] = round(s50, 4)
+    # the device-resident kernel time of one full g5 D_w (both parities) inside the sign function
+    lib.profile_reset()
+    lib.profile_enable(True)
+    res = {}
+    for name, prec in (("f64", lib.F64), ("f32x2", lib.F32X2)):
+        e0, e1 = _events()
+        e0.record()
+        _, info = lat.overlap_sign_apply(rho, 0.1, 10.5, 1e-5, v, prec=prec)
+        e1.record()
+        torch.cuda.synchronize()
+        res[name] = {"seconds": round(e0.elapsed_time(e1) * 1e-3, 3), "order": info["order"],
+                     "max_deviation": info["max_deviation"]}
+    lib.profile_enable(False)
+    kern = {}
+    for name in ("wilson_dslash_f64_xpay", "wilson_dslash_f32x2_xpay"):
+        n, t = lib.profile_query(name)
+        if n:
+            kern[name] = {"launches": n, "avg_us": round(t / n * 1e3, 2)}
+    line = {"workload": "overlap", "metric": "g5 D_w(-rho) applications and the Chebyshev sign function, 24^3x64",
+            "config": {"dims": list(dims), "rho": rho, "gauge_seed": GAUGE_SEED, "spectrum": [0.1, 10.5],
+                       "deviation": 1e-5, "note": "seconds of 50 full-lattice applications include the host-array "
+                                                  "copies of lq_gamma5_dw_apply; the kernel times are per parity"},
+            "g5dw_50_applications_s": out, "sign_apply": res, "kernels": kern,
+            "paper_context": "50 D_w on RBC11 24^3x64: 0.025 s (QUDA), 0.088 s (GWU-code), one node of 4 V100"}
+    print(json.dumps(line), flush=True)
+
+
 def run_serving(args):
     """Poisson stream of solve requests (sizes 8^3x16, 16^3x32, 24^3x64, 32^3x64; twisted-mass
     clover with 12 point sources, or HISQ with one Z2 source; masses drawn from [0.005, 0.05];
@@ -787,10 +843,11 @@ def main():
                     help="also time the mixed-precision BiCGStab solve of the same system")
     ap.add_argument("--ref-iters", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="tmc", choices=["tmc", "multirhs", "hisq", "serving", "dslash", "hisq3col"],
+    ap.add_argument("--workload", default="tmc", choices=["tmc", "multirhs", "hisq", "serving", "dslash", "hisq3col", "overlap"],
                     help="tmc: 24^3x64 twisted-mass clover (default, the headline); multirhs: 32^3x96, "
                          "36 right-hand sides; hisq: 48^3x144 multi-shift; serving: Poisson request stream; "
-                         "dslash: the operator kernels alone; hisq3col: HISQ 3-column propagator 24^3x64")
+                         "dslash: the operator kernels alone; hisq3col: HISQ 3-column propagator 24^3x64; "
+                         "overlap: g5 D_w and the sign function")
     ap.add_argument("--requests", type=int, default=100, help="serving: number of requests")
     ap.add_argument("--graph-iters", type=int, default=0,
                     help="CG iterations per CUDA graph (0: library default, -1: no graphs)")
@@ -807,6 +864,8 @@ def main():
         run_dslash(args)
     elif args.workload == "hisq3col":
         run_hisq_propagator(args)
+    elif args.workload == "overlap":
+        run_overlap(args)
     elif args.workload == "serving":
         run_serving(args)
     else:
