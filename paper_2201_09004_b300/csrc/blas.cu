@@ -420,6 +420,40 @@ __global__ void lincomb4_kernel(FieldV out, double a0, FieldV v, double a1, Fiel
     }
 }
 
+// out = g5 in (Wilson fields: negate spins 2 and 3, the reals 12..23)
+template <int P>
+__global__ void gamma5_kernel(FieldV out, FieldV in) {
+    typedef typename RealT<P>::T T;
+    const int k = blockIdx.y;
+    SITE_LOOP(out.vh) {
+        T v[24];
+        fload<P, 24, T>(in, k, s, v);
+#pragma unroll
+        for (int q = 12; q < 24; q++) v[q] = -v[q];
+        fstore<P, 24, T>(out, k, s, v);
+    }
+}
+
+// y += (a_k + i b_k) x per right-hand side k (host scalars)
+template <int P, int NR>
+__global__ void caxpy_h_kernel(FieldV y, FieldV x, HostScalars h) {
+    typedef typename RealT<P>::T T;
+    const int k = blockIdx.y;
+    const cx<T> c = mk((T)h.a[k], (T)h.b[k]);
+    SITE_LOOP(y.vh) {
+        T vy[NR], vx[NR];
+        fload<P, NR, T>(y, k, s, vy);
+        fload<P, NR, T>(x, k, s, vx);
+#pragma unroll
+        for (int j = 0; j < NR / 2; j++) {
+            const cx<T> o = mk(vy[2 * j], vy[2 * j + 1]) + c * mk(vx[2 * j], vx[2 * j + 1]);
+            vy[2 * j] = o.r;
+            vy[2 * j + 1] = o.i;
+        }
+        fstore<P, NR, T>(y, k, s, vy);
+    }
+}
+
 // ---------------------------------------------------------------- launchers
 static dim3 red_grid(int nrhs) { return dim3(RED_BLOCKS, nrhs); }
 static dim3 upd_grid(int vh, int nrhs) {
@@ -627,6 +661,26 @@ void blas_lincomb4(Field& out, double a0, const Field& v, double a1, const Field
 #define K(NR) lincomb4_kernel<P_, NR>
 #define L(P) { constexpr int P_ = P; BY_KIND(out, "blas_lincomb4", K, g, out.view(), a0, v.view(), a1, t.view(), a2, w.view(), (int)sub_old); }
     DISPATCH_P(out.prec, L);
+#undef L
+#undef K
+}
+
+void blas_gamma5(Field& out, const Field& in, cudaStream_t st) {
+    if (out.prec != in.prec || out.kind != LQ_WILSON_FIELD || in.kind != LQ_WILSON_FIELD || out.nrhs != in.nrhs)
+        fail(LQ_EINVAL, "blas_gamma5: Wilson fields of one precision and shape");
+    dim3 g = upd_grid(out.vh, out.nrhs);
+#define L(P) { launch("blas_gamma5", gamma5_kernel<P>, g, dim3(RED_THREADS), st, out.view(), in.view()); }
+    DISPATCH_P(out.prec, L);
+#undef L
+}
+
+void blas_caxpy_h(Field& y, const double* a_re, const double* a_im, const Field& x, cudaStream_t st) {
+    if (y.prec != x.prec || y.nrhs != x.nrhs) fail(LQ_EINVAL, "blas_caxpy_h: field mismatch");
+    HostScalars h = hs(a_re, a_im, y.nrhs);
+    dim3 g = upd_grid(y.vh, y.nrhs);
+#define K(NR) caxpy_h_kernel<P_, NR>
+#define L(P) { constexpr int P_ = P; BY_KIND(y, "blas_caxpy", K, g, y.view(), x.view(), h); }
+    DISPATCH_P(y.prec, L);
 #undef L
 #undef K
 }

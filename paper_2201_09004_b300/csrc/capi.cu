@@ -315,7 +315,7 @@ extern "C" int lq_solve(lq_lattice h, const lq_op_params* op, const lq_solve_par
         st = L.own_stream;
     }
     const size_t bytes = field_canon_bytes(L, op->action);
-    const int nsol = nrhs * ((op->action == LQ_HISQ && sp->solver == LQ_MULTISHIFT_CG) ? std::max(1, sp->nshift) : 1);
+    const int nsol = nrhs * (sp->solver == LQ_MULTISHIFT_CG ? std::max(1, sp->nshift) : 1);
     for (int k = 0; k < nrhs; k++)
         if (!rhs[k]) fail(LQ_EINVAL, "null right-hand side");
     for (int k = 0; k < nsol; k++)
@@ -336,6 +336,7 @@ extern "C" int lq_solve(lq_lattice h, const lq_op_params* op, const lq_solve_par
     }
     int ret;
     if (op->action == LQ_HISQ) ret = solve_hisq(L, *op, *sp, nrhs, db.data(), dx.data(), info, st);
+    else if (sp->solver == LQ_MULTISHIFT_CG) ret = solve_wilson_multishift(L, *op, *sp, nrhs, db.data(), dx.data(), info, st);
     else ret = solve_wilson(L, *op, *sp, nrhs, db.data(), dx.data(), info, st);
     if (loc == LQ_HOST)
         for (int k = 0; k < nsol; k++) LQ_CUDA(cudaMemcpyAsync(x[k], dx[k], bytes, cudaMemcpyDeviceToHost, st));

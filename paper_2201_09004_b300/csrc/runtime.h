@@ -265,6 +265,9 @@ void blas_bicg_rho(const Field& r, const Field& r0, df* part, cudaStream_t st, c
 // out = a0 v + a1 t + a2 w - out (sub_old), or without the last term; per element, all rhs
 void blas_lincomb4(Field& out, double a0, const Field& v, double a1, const Field& t, double a2, const Field& w,
                    cudaStream_t st, bool sub_old = true);
+// out = g5 in (Wilson fields); y += (a_re_k + i a_im_k) x per rhs (host scalars)
+void blas_gamma5(Field& out, const Field& in, cudaStream_t st);
+void blas_caxpy_h(Field& y, const double* a_re, const double* a_im, const Field& x, cudaStream_t st);
 // p = r + beta p with partial |p|^2
 void blas_cg_p_norm(Field& p, const Field& r, const double* sc, df* part, cudaStream_t st, const FinArgs& fin);
 // p = r + beta p, beta_k = sc[k*SC_N + SC_BETA]
@@ -289,8 +292,11 @@ void sign_apply(Lattice& lat, double rho, double lmax, double eps, const std::ve
                 Field& out, cudaStream_t st);
 // estimated device bytes of a solve's work fields
 size_t solve_workspace_bytes(const Lattice& lat, const lq_op_params& op, const lq_solve_params& sp, int nrhs);
+// x0 (optional, device canonical): initial guesses whose even sites start the even-odd CGNR
 int solve_wilson(Lattice& lat, const lq_op_params& op, const lq_solve_params& sp, int nrhs, const double* const* b,
-                 double* const* x, lq_solve_info* info, cudaStream_t st);
+                 double* const* x, lq_solve_info* info, cudaStream_t st, const double* const* x0 = nullptr);
+int solve_wilson_multishift(Lattice& lat, const lq_op_params& op, const lq_solve_params& sp, int nrhs,
+                            const double* const* b, double* const* x, lq_solve_info* info, cudaStream_t st);
 int solve_hisq(Lattice& lat, const lq_op_params& op, const lq_solve_params& sp, int nrhs, const double* const* b,
                double* const* x, lq_solve_info* info, cudaStream_t st);
 

@@ -263,7 +263,7 @@ static KrylovState krylov_start(Scalars& sc, CgResult& res, const std::vector<do
 // p and restarts the norm recurrence from the new r = Mhat^+ s.
 static CgResult cgnr_mixed(Lattice& lat, const OpDesc& ops, const OpDesc& op64, Field& bhat, Field& x_hi,
                            const std::vector<double>& tol_abs, double delta, int maxiter, int graph_iters,
-                           cudaStream_t st) {
+                           cudaStream_t st, bool guess = false) {
     const int n = bhat.nrhs;
     const int ps = ops.prec;
     const int px = ps == LQ_F16 ? LQ_F32 : ps;  // the sloppy solution accumulates in at least FP32
@@ -279,9 +279,14 @@ static CgResult cgnr_mixed(Lattice& lat, const OpDesc& ops, const OpDesc& op64, 
     CgResult res(n);
     std::vector<double> ones(n, 1.0);
 
-    blas_zero(x_hi, st);
-    blas_copy(s_hi, bhat, st);
-    blas_norm2(bhat, sc.part, st, sc.f(SC_SS, FIN_SET));
+    if (guess) {  // x_hi holds the initial guess: s = bhat - Mhat x_hi in FP64 accuracy
+        schur_wilson(lat, op64, 0, x_hi, q64, t64, nullptr, st);
+        blas_xmy_norm(s_hi, bhat, q64, sc.part, st, sc.f(SC_SS, FIN_SET));
+    } else {
+        blas_zero(x_hi, st);
+        blas_copy(s_hi, bhat, st);
+        blas_norm2(bhat, sc.part, st, sc.f(SC_SS, FIN_SET));
+    }
     blas_copy(s_lo, s_hi, st);
     blas_zero(x_lo, st);
     schur_wilson(lat, ops, 1, s_lo, r, t, sc.part, st, sc.f(SC_RR, FIN_SET));
@@ -385,7 +390,7 @@ static CgResult bicgstab_mixed(Lattice& lat, const OpDesc& ops, const OpDesc& op
 }
 
 int solve_wilson(Lattice& lat, const lq_op_params& opp, const lq_solve_params& sp, int nrhs, const double* const* b,
-                 double* const* x, lq_solve_info* info, cudaStream_t st) {
+                 double* const* x, lq_solve_info* info, cudaStream_t st, const double* const* x0) {
     if (opp.action == LQ_WILSON_TM_CLOVER && !lat.has_clover) fail(LQ_EINVAL, "clover action without clover term");
     if (!lat.canon[LQ_THIN]) fail(LQ_EINVAL, "thin gauge field not loaded");
     if (nrhs < 1 || nrhs > 64) fail(LQ_EINVAL, "nrhs must be in [1, 64]");
@@ -446,9 +451,12 @@ int solve_wilson(Lattice& lat, const lq_op_params& opp, const lq_solve_params& s
         blas_copy(bhat, be, st);
         blas_axpy_h(bhat, ones.data(), te, st);
 
+        if (x0)
+            for (int k = 0; k < nrhs; k++) import_field(lat, xe, k, 0, x0[k], st);
         CgResult cr = sp.solver == LQ_BICGSTAB
                           ? bicgstab_mixed(lat, ops, op64, bhat, xe, tol_abs, delta, maxiter, sp.graph_iters, st)
-                          : cgnr_mixed(lat, ops, op64, bhat, xe, tol_abs, delta, maxiter, sp.graph_iters, st);
+                          : cgnr_mixed(lat, ops, op64, bhat, xe, tol_abs, delta, maxiter, sp.graph_iters, st,
+                                       x0 != nullptr);
 
         // x_o = A_oo^{-1} (b_o + H_oe x_e)
         wilson_dslash(lat, op64, 1, 0, EPI_HOP, xe, to, nullptr, nullptr, st);
@@ -491,6 +499,218 @@ int solve_wilson(Lattice& lat, const lq_op_params& opp, const lq_solve_params& s
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (ret != LQ_OK) set_last_error("solve: not every right-hand side reached the tolerance");
+    return ret;
+}
+
+// Twisted-mass multi-mass solve (no clover). M(mu) = M0 + i mu g5 and M0^+ = g5 M0 g5
+// make the cross terms of the normal operator cancel: M(mu)^+ M(mu) = A + mu^2 with
+// A = M0^+ M0. So
+//   x(mu_i) = (A + mu_i^2)^{-1} M(mu_i)^+ b = y1_i - i mu_i y2_i,
+//   y1_i = (A + mu_i^2)^{-1} M0^+ b,   y2_i = (A + mu_i^2)^{-1} g5 b,
+// two right-hand sides per source for one multi-shift CG (the multi-mass solver of
+// Sec. 2.3) on the full lattice: the even-odd Schur complement is not a shift in mu.
+// The multi-shift stage runs in the sloppy precision; each x(mu_i) then starts the
+// mixed-precision even-odd CGNR of its own system, which brings it to the tolerance.
+int solve_wilson_multishift(Lattice& lat, const lq_op_params& opp, const lq_solve_params& sp, int nrhs,
+                            const double* const* b, double* const* x, lq_solve_info* info, cudaStream_t st) {
+    if (opp.action != LQ_WILSON_TM) fail(LQ_EINVAL, "Wilson multi-shift: twisted mass without clover only");
+    if (!lat.canon[LQ_THIN]) fail(LQ_EINVAL, "thin gauge field not loaded");
+    if (nrhs < 1 || nrhs > 16) fail(LQ_EINVAL, "nrhs must be in [1, 16] for the Wilson multi-shift solve");
+    const int ns = sp.nshift;
+    if (ns < 1 || ns > 16 || !sp.masses) fail(LQ_EINVAL, "multi-shift solve needs 1..16 twisted masses");
+    std::vector<double> mus(sp.masses, sp.masses + ns);
+    for (int i = 0; i < ns; i++) {
+        if (!std::isfinite(mus[i]) || mus[i] < 0.0) fail(LQ_EINVAL, "twisted masses must be finite and >= 0");
+        if (i > 0 && mus[i] <= mus[i - 1]) fail(LQ_EINVAL, "twisted masses must be ascending");
+    }
+    const int ps = sp.prec_sloppy;
+    if (ps < LQ_F64 || ps > LQ_F16) fail(LQ_EINVAL, "prec_sloppy");
+    if (!(sp.tol > 0)) fail(LQ_EINVAL, "tol must be positive");
+    const int maxiter = sp.maxiter > 0 ? sp.maxiter : 100000;
+    lq_op_params op0 = opp;
+    op0.mu = 0.0;
+    const OpDesc d = wilson_desc(op0, ps, sp.recon_sloppy == 12 ? 12 : 18);
+    const int WF = LQ_WILSON_FIELD, nsys = 2 * nrhs, nf = 2 * nsys;
+    std::vector<double> sigma(ns);
+    for (int i = 0; i < ns; i++) sigma[i] = mus[i] * mus[i];
+
+    int ms_iters = 0;
+    {
+        Pool pool(lat, st);
+        // full-lattice vectors: rhs h * nsys + j is half h (0 even, 1 odd sites) of system j;
+        // systems j < nrhs are M0^+ b_j, systems nrhs + j are g5 b_j
+        Field B = pool.get(WF, ps, 2 * nrhs);
+        for (int k = 0; k < nrhs; k++) {
+            import_field(lat, B, k, 0, b[k], st);
+            import_field(lat, B, nrhs + k, 1, b[k], st);
+        }
+        Field R = pool.get(WF, ps, nf), Q = pool.get(WF, ps, nf), T = pool.get(WF, ps, nf);
+        for (int h = 0; h < 2; h++) {
+            Field bo = B.sub((1 - h) * nrhs, nrhs), bh = B.sub(h * nrhs, nrhs), rh = R.sub(h * nsys, nrhs);
+            wilson_dslash(lat, d, h, 1, EPI_XPAY, bo, rh, &bh, nullptr, st);  // (M0^+ b)_h
+            Field g = R.sub(h * nsys + nrhs, nrhs);
+            blas_gamma5(g, bh, st);
+        }
+        // x <- M0 in (dag 0) or M0^+ in (dag 1) on all systems
+        auto m0 = [&](int dag, const Field& in, Field& out) {
+            for (int h = 0; h < 2; h++) {
+                const Field same = in.sub(h * nsys, nsys), other = in.sub((1 - h) * nsys, nsys);
+                Field o = out.sub(h * nsys, nsys);
+                wilson_dslash(lat, d, h, dag, EPI_XPAY, other, o, &same, nullptr, st);
+            }
+        };
+        std::vector<Field> Y, P;
+        for (int i = 0; i < ns; i++) {
+            Y.push_back(pool.get(WF, ps, nf));
+            P.push_back(pool.get(WF, ps, nf));
+            blas_zero(Y[i], st);
+            blas_copy(P[i], R, st);
+        }
+        Scalars sc;
+        sc.init(lat, nf, st);
+        // per-system norm: the halves' partials, added on the host
+        auto norms = [&](int slot, std::vector<double>& out) {
+            sc.pull(st);
+            out.resize(nsys);
+            for (int j = 0; j < nsys; j++) out[j] = sc.h(j, slot) + sc.h(nsys + j, slot);
+        };
+        auto per_rhs = [&](const std::vector<double>& v) {  // system values repeated for both halves
+            std::vector<double> o(nf);
+            for (int j = 0; j < nsys; j++) o[j] = o[nsys + j] = v[j];
+            return o;
+        };
+        blas_norm2(R, sc.part, st, sc.f(SC_RR, FIN_SET));
+        std::vector<double> rr, pp, b2;
+        norms(SC_RR, rr);
+        pp = rr;
+        b2 = rr;
+        const double tol_ms = ps == LQ_F64 ? 0.1 * sp.tol : (ps == LQ_F32 ? 1e-6 : 1e-3);
+        std::vector<double> alpha(nsys), beta(nsys), alpha_prev(nsys, 1.0), beta_prev(nsys, 0.0);
+        std::vector<std::vector<double>> zeta(ns, std::vector<double>(nsys, 1.0)), zeta_prev = zeta, zn = zeta;
+        std::vector<std::vector<char>> active(ns, std::vector<char>(nsys, 1));
+        for (int j = 0; j < nsys; j++) {
+            check_finite(b2[j], "source");
+            if (b2[j] == 0.0)
+                for (int i = 0; i < ns; i++) active[i][j] = 0;
+        }
+        auto any_active = [&]() {
+            for (int i = 0; i < ns; i++)
+                for (int j = 0; j < nsys; j++)
+                    if (active[i][j]) return true;
+            return false;
+        };
+        std::vector<double> tt, rrn, ppn, ones(nf, 1.0);
+        while (any_active() && ms_iters < maxiter) {
+            m0(0, P[0], T);
+            blas_norm2(T, sc.part, st, sc.f(SC_QQ, FIN_SET));
+            m0(1, T, Q);
+            norms(SC_QQ, tt);
+            for (int j = 0; j < nsys; j++) {
+                const double pap = sigma[0] * pp[j] + tt[j];
+                alpha[j] = (pap > 0.0 && b2[j] > 0.0) ? rr[j] / pap : 0.0;
+                for (int i = 1; i < ns; i++) {
+                    const double dd = sigma[i] - sigma[0];
+                    const double den = alpha[j] * beta_prev[j] * (zeta_prev[i][j] - zeta[i][j]) +
+                                       zeta_prev[i][j] * alpha_prev[j] * (1.0 + dd * alpha[j]);
+                    zn[i][j] = den != 0.0 ? zeta[i][j] * zeta_prev[i][j] * alpha_prev[j] / den : 0.0;
+                }
+            }
+            // Q = (A + sigma_0) P_0
+            blas_axpy_h(Q, per_rhs(std::vector<double>(nsys, sigma[0])).data(), P[0], st);
+            for (int i = 0; i < ns; i++) {
+                std::vector<double> ai(nsys);
+                for (int j = 0; j < nsys; j++)
+                    ai[j] = !active[i][j] ? 0.0 : (i == 0 ? alpha[j] : alpha[j] * zn[i][j] / zeta[i][j]);
+                blas_axpy_h(Y[i], per_rhs(ai).data(), P[i], st);
+            }
+            std::vector<double> na(nsys);
+            for (int j = 0; j < nsys; j++) na[j] = -alpha[j];
+            blas_axpby_h(R, per_rhs(na).data(), Q, ones.data(), sc.part, st);
+            sc.fin(RED_BLOCKS, SC_RRN, st);
+            norms(SC_RRN, rrn);
+            for (int j = 0; j < nsys; j++) {
+                check_finite(rrn[j], "multi-shift residual");
+                beta[j] = rr[j] > 0.0 ? rrn[j] / rr[j] : 0.0;
+                rr[j] = rrn[j];
+            }
+            blas_axpby_h(P[0], ones.data(), R, per_rhs(beta).data(), sc.part, st);
+            sc.fin(RED_BLOCKS, SC_PP, st);
+            for (int i = 1; i < ns; i++) {
+                std::vector<double> zz(nsys), bz(nsys);
+                for (int j = 0; j < nsys; j++) {
+                    const double zr = zeta[i][j] != 0.0 ? zn[i][j] / zeta[i][j] : 0.0;
+                    zz[j] = active[i][j] ? zn[i][j] : 0.0;
+                    bz[j] = active[i][j] ? beta[j] * zr * zr : 1.0;
+                }
+                blas_axpby_h(P[i], per_rhs(zz).data(), R, per_rhs(bz).data(), nullptr, st);
+            }
+            for (int j = 0; j < nsys; j++) {
+                for (int i = 1; i < ns; i++) {
+                    zeta_prev[i][j] = zeta[i][j];
+                    zeta[i][j] = zn[i][j];
+                }
+                alpha_prev[j] = alpha[j];
+                beta_prev[j] = beta[j];
+                for (int i = 0; i < ns; i++) {
+                    const double z = i == 0 ? 1.0 : fabs(zeta[i][j]);
+                    if (active[i][j] && z * sqrt(rr[j]) <= tol_ms * sqrt(b2[j])) active[i][j] = 0;
+                }
+            }
+            norms(SC_PP, ppn);
+            pp = ppn;
+            ms_iters++;
+        }
+        // x(mu_i) = y1_i - i mu_i y2_i, written to the caller's arrays as the refinement's guesses
+        Field X = pool.get(WF, ps, 2 * nrhs);
+        for (int i = 0; i < ns; i++) {
+            std::vector<double> re(nrhs, 0.0), im(nrhs, -mus[i]);
+            for (int h = 0; h < 2; h++) {
+                Field xh = X.sub(h * nrhs, nrhs);
+                blas_copy(xh, Y[i].sub(h * nsys, nrhs), st);
+                blas_caxpy_h(xh, re.data(), im.data(), Y[i].sub(h * nsys + nrhs, nrhs), st);
+            }
+            for (int k = 0; k < nrhs; k++) {
+                export_field(lat, X, k, 0, x[k * ns + i], st);
+                export_field(lat, X, nrhs + k, 1, x[k * ns + i], st);
+            }
+        }
+        LQ_CUDA(cudaStreamSynchronize(st));
+    }
+
+    // refinement of every twisted mass by the mixed-precision even-odd CGNR from its guess
+    int ret = LQ_OK;
+    std::vector<lq_solve_info> acc(nrhs);
+    for (int k = 0; k < nrhs; k++) {
+        acc[k] = lq_solve_info{LQ_OK, ms_iters, 0, 2 * ms_iters, 0.0, 0.0};
+    }
+    for (int i = 0; i < ns; i++) {
+        lq_op_params opi = opp;
+        opi.mu = mus[i];
+        lq_solve_params spi = sp;
+        spi.solver = ps == LQ_F64 ? LQ_CGNR : LQ_MIXED_CGNR;
+        spi.nshift = 0;
+        spi.masses = nullptr;
+        std::vector<double*> xi(nrhs);
+        std::vector<const double*> x0(nrhs);
+        for (int k = 0; k < nrhs; k++) {
+            xi[k] = x[k * ns + i];
+            x0[k] = x[k * ns + i];
+        }
+        std::vector<lq_solve_info> inf(nrhs);
+        int r = solve_wilson(lat, opi, spi, nrhs, b, xi.data(), inf.data(), st, x0.data());
+        if (r != LQ_OK && ret == LQ_OK) ret = r;
+        for (int k = 0; k < nrhs; k++) {
+            acc[k].iters += inf[k].iters;
+            acc[k].reliable_updates += inf[k].reliable_updates;
+            acc[k].operator_applications += inf[k].operator_applications;
+            acc[k].true_rel_residual = std::max(acc[k].true_rel_residual, inf[k].true_rel_residual);
+            acc[k].seconds += inf[k].seconds;
+            if (inf[k].status != LQ_OK && acc[k].status == LQ_OK) acc[k].status = inf[k].status;
+        }
+    }
+    if (info)
+        for (int k = 0; k < nrhs; k++) info[k] = acc[k];
     if (ret != LQ_OK) set_last_error("solve: not every right-hand side reached the tolerance");
     return ret;
 }

@@ -228,6 +228,40 @@ def test_bicgstab_clover_multi_rhs_equals_cgnr(L, orc, prec):
         assert rel_err(x, y) < 1e-8
 
 
+@pytest.mark.parametrize("prec", [1, 2])
+def test_twisted_multishift_solve(L, orc, prec):
+    """Several twisted masses at once (no clover): one multi-shift CG on
+    M0^+ M0 + mu^2 for the two sources M0^+ b and g5 b, then each mass refined by
+    the mixed CGNR from that guess; every solution meets the oracle's true
+    residual for its own mu and equals the single-mass solve."""
+    dims = (4, 4, 4, 8)
+    lat, U = make(L, dims, 109)
+    m, mus = 0.1, [0.01, 0.03, 0.1]
+    bs = [synth.z2_source(dims, 209).numpy(), synth.point_source(dims, (1, 2, 3, 4), 0, 2).numpy()]
+    op = L.op_params(L.WILSON_TM, m, mus[0])
+    sp = L.solve_params(solver=L.MULTISHIFT_CG, tol=1e-10, prec_sloppy=prec, masses=mus)
+    xs, info = lat.solve(op, sp, bs)
+    assert len(xs) == len(bs) * len(mus)
+    for k, b in enumerate(bs):
+        assert info[k]["status"] == 0
+        for i, mu in enumerate(mus):
+            x = xs[k * len(mus) + i]
+            assert true_residual(orc, dims, U, None, m, mu, b, x) <= 1e-10, (k, mu)
+            x1, _ = lat.solve(L.op_params(L.WILSON_TM, m, mu),
+                              L.solve_params(solver=L.MIXED_CGNR, tol=1e-10, prec_sloppy=prec), [b])
+            assert rel_err(x, x1[0]) < 1e-8
+
+
+def test_twisted_multishift_rejects_clover(L):
+    dims = (4, 4, 4, 4)
+    lat, U = make(L, dims, 110, c_sw=1.0)
+    op = L.op_params(L.WILSON_TM_CLOVER, 0.1, 0.01, c_sw=1.0)
+    b = synth.z2_source(dims, 210).numpy()
+    with pytest.raises(L.LqError) as e:
+        lat.solve(op, L.solve_params(solver=L.MULTISHIFT_CG, masses=[0.01, 0.02]), [b])
+    assert e.value.code == L.LQ_EINVAL
+
+
 def test_workspace_kept_between_solves(L, orc):
     """The work buffers a solve takes stay with the lattice: a second solve
     allocates nothing more and returns bit-identical solutions (the reductions
