@@ -617,6 +617,53 @@ def run_hisq_propagator(args):
     print(json.dumps(line), flush=True)
 
 
+def run_twisted_multimass(args):
+    """Twisted mass without clover on 24^3x64 (m = 0.05), one Z2 source and the three
+    twisted masses of the multi-right-hand-side workload, mu in {0.004, 0.008, 0.016}:
+    one multi-shift solve (full-lattice multi-shift CG on M0^+ M0 + mu^2, then a mixed
+    CGNR refinement per mass) against three separate mixed CGNR solves."""
+    import torch
+    from paper_2201_09004_b300 import lib, synth
+    torch.cuda.set_device(0)
+    dims, m, mus = DIMS, MASS, [0.004, 0.008, 0.016]
+    U = synth.thin_links(dims, GAUGE_SEED, device="cuda")
+    lat = lib.Lattice(dims)
+    lat.load_gauge(lib.THIN, U)
+    del U
+    b = synth.z2_source(dims, SOURCE_SEED, device="cuda")
+    xs = [torch.empty_like(b) for _ in mus]
+    op = lib.op_params(lib.WILSON_TM, m, mus[0])
+    spm = lib.solve_params(solver=lib.MULTISHIFT_CG, tol=TOL, prec_sloppy=args.prec, recon_sloppy=lib.R12,
+                           masses=mus)
+    lat.solve(op, spm, [b], out=xs)
+    torch.cuda.synchronize()
+    e0, e1 = _events()
+    e0.record()
+    _, info = lat.solve(op, spm, [b], out=xs)
+    e1.record()
+    torch.cuda.synchronize()
+    t_ms = e0.elapsed_time(e1) * 1e-3
+    sps = lib.solve_params(solver=lib.MIXED_CGNR, tol=TOL, prec_sloppy=args.prec, recon_sloppy=lib.R12)
+    e0, e1 = _events()
+    e0.record()
+    iters = []
+    for i, mu in enumerate(mus):
+        _, inf = lat.solve(lib.op_params(lib.WILSON_TM, m, mu), sps, [b], out=xs[i:i + 1])
+        iters.append(inf[0]["iters"])
+    e1.record()
+    torch.cuda.synchronize()
+    t_sep = e0.elapsed_time(e1) * 1e-3
+    line = {"workload": "twisted_multimass", "metric": "time to solution of three twisted masses at true residual 1e-10",
+            "value": round(t_ms, 3), "unit": "s", "higher_is_better": False,
+            "config": {"dims": list(dims), "m": m, "mus": mus, "sloppy_precision": args.prec, "gauge_seed": GAUGE_SEED,
+                       "source_seed": SOURCE_SEED},
+            "iters": info[0]["iters"], "true_rel_residual_max": info[0]["true_rel_residual"],
+            "status": info[0]["status"],
+            "separate_mixed_cgnr": {"seconds": round(t_sep, 3), "iters": iters},
+            "speedup_vs_separate": round(t_sep / t_ms, 2)}
+    print(json.dumps(line), flush=True)
+
+
 def run_overlap(args):
     """Overlap building blocks on 24^3x64 (the RBC11 shape of the paper's overlap runs):
     50 applications of the fused g5 D_w(-rho), rho = 1.5, on the full lattice (the
@@ -843,11 +890,11 @@ def main():
                     help="also time the mixed-precision BiCGStab solve of the same system")
     ap.add_argument("--ref-iters", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="tmc", choices=["tmc", "multirhs", "hisq", "serving", "dslash", "hisq3col", "overlap"],
+    ap.add_argument("--workload", default="tmc", choices=["tmc", "multirhs", "hisq", "serving", "dslash", "hisq3col", "overlap", "tmms"],
                     help="tmc: 24^3x64 twisted-mass clover (default, the headline); multirhs: 32^3x96, "
                          "36 right-hand sides; hisq: 48^3x144 multi-shift; serving: Poisson request stream; "
                          "dslash: the operator kernels alone; hisq3col: HISQ 3-column propagator 24^3x64; "
-                         "overlap: g5 D_w and the sign function")
+                         "overlap: g5 D_w and the sign function; tmms: twisted multi-mass solve")
     ap.add_argument("--requests", type=int, default=100, help="serving: number of requests")
     ap.add_argument("--graph-iters", type=int, default=0,
                     help="CG iterations per CUDA graph (0: library default, -1: no graphs)")
@@ -866,6 +913,8 @@ def main():
         run_hisq_propagator(args)
     elif args.workload == "overlap":
         run_overlap(args)
+    elif args.workload == "tmms":
+        run_twisted_multimass(args)
     elif args.workload == "serving":
         run_serving(args)
     else:
