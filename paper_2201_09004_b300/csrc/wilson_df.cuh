@@ -134,9 +134,10 @@ __global__ void __launch_bounds__(256, 2) wilson_dslash_df2_kernel(WilsonArgs a)
             cp_async_commit();
             return bs;
         };
-        cd up[3], lo2[3], lo3[3];  // upper spin h, lower spins 2 and 3
+        // upper spin h, lower spins 2 and 3: lazily normalised sums over the eight hops
+        cacc upa[3], l2a[3], l3a[3];
 #pragma unroll
-        for (int q = 0; q < 3; q++) up[q] = lo2[q] = lo3[q] = mk(df(0.f), df(0.f));
+        for (int q = 0; q < 3; q++) upa[q] = l2a[q] = l3a[q] = cacc_zero();
         float bs_next = issue(0, 0);
 #pragma unroll 1
         for (int hop = 0; hop < 8; hop++) {
@@ -169,11 +170,13 @@ __global__ void __launch_bounds__(256, 2) wilson_dslash_df2_kernel(WilsonArgs a)
             for (int q = 0; q < 3; q++) {
                 const float4 va = sl[(9 + h * 3 + q) * spb];
                 const float4 vp = sl[(9 + pb * 3 + q) * spb];
-                const cd pa = mk(df(va.x, va.y), df(va.z, va.w));
-                const cd pp = mk(df(vp.x, vp.y), df(vp.z, vp.w));
-                hv[q] = pa + cunit(pp, cn != neg_sp, ci);
+                // the sum stays unnormalised (exact high part, rounding in the low part)
+                cacc t = cacc_zero();
+                cacc_add(t, mk(df(va.x, va.y), df(va.z, va.w)));
+                cacc_add(t, cunit(mk(df(vp.x, vp.y), df(vp.z, vp.w)), cn != neg_sp, ci));
+                hv[q] = mk(df(t.r.hi, t.r.lo), df(t.i.hi, t.i.lo));
             }
-            cd r[3];
+            cd r[3];  // U hv or U^+ hv, unnormalised
 #pragma unroll
             for (int i = 0; i < 3; i++) {
                 cacc t = cacc_zero();
@@ -182,7 +185,7 @@ __global__ void __launch_bounds__(256, 2) wilson_dslash_df2_kernel(WilsonArgs a)
                     if (fwd) cacc_mac(t, U[i][j], hv[j]);
                     else cacc_cjmac(t, U[j][i], hv[j]);
                 }
-                r[i] = cacc_done(t);
+                r[i] = mk(df(t.r.hi, t.r.lo), df(t.i.hi, t.i.lo));
             }
             // rebuild: upper spin h gets r; lower spin (3 if to3 else 2) gets +-r or +-i r
             const bool flip = bs < 0.f;  // time boundary
@@ -192,11 +195,18 @@ __global__ void __launch_bounds__(256, 2) wilson_dslash_df2_kernel(WilsonArgs a)
 #pragma unroll
             for (int q = 0; q < 3; q++) {
                 const cd rq = flip ? mk(-r[q].r, -r[q].i) : r[q];
-                up[q] = up[q] + rq;
+                cacc_add(upa[q], rq);
                 const cd e = cunit(rq, en != neg_sp, ei);
-                if (to3) lo3[q] = lo3[q] + e;
-                else lo2[q] = lo2[q] + e;
+                if (to3) cacc_add(l3a[q], e);
+                else cacc_add(l2a[q], e);
             }
+        }
+        cd up[3], lo2[3], lo3[3];
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            up[q] = cacc_done(upa[q]);
+            lo2[q] = cacc_done(l2a[q]);
+            lo3[q] = cacc_done(l3a[q]);
         }
         if constexpr (EPI == EPI_XPAY) {
             const float4* yb = (const float4*)((const char*)a.y.data + (size_t)k * a.y.rhs_bytes);
