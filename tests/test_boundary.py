@@ -48,3 +48,24 @@ def test_invalid_lattice_is_rejected_without_gpu():
     assert code == lib.LQ_EINVAL
     with pytest.raises(lib.LqError):
         lib.Lattice((2, 2, 2, 3))
+
+
+def test_null_handles_and_bad_arguments_are_rejected_without_gpu():
+    """Every entry point that takes a lattice checks it (and its arguments) before
+    touching the GPU: a null handle or a bad enum is LQ_EINVAL with a message."""
+    ensure_library()
+    from paper_2201_09004_b300 import lib
+    L = lib.lib()
+    buf = (ctypes.c_double * 8)()
+    info = lib.SignInfo()
+    assert L.lq_gamma5_dw_apply(None, ctypes.c_double(1.5), 0, 0, buf, buf, None) == lib.LQ_EINVAL
+    assert L.lq_overlap_sign_apply(None, ctypes.c_double(1.5), ctypes.c_double(0.1), ctypes.c_double(8.0),
+                                   ctypes.c_double(1e-5), 0, 0, buf, buf, ctypes.byref(info), None) == lib.LQ_EINVAL
+    assert b"lattice" in L.lq_last_error()
+    op = lib.op_params(lib.WILSON_TM, 0.1, 0.05)
+    sp = lib.solve_params(solver=lib.BICGSTAB)
+    ptrs = (ctypes.POINTER(ctypes.c_double) * 1)()
+    assert L.lq_solve(None, ctypes.byref(op), ctypes.byref(sp), 1, ptrs, ptrs, 0, None, None) == lib.LQ_EINVAL
+    assert L.lq_tune_force(-1) == lib.LQ_EINVAL
+    assert L.lq_tune_force(0) == lib.LQ_OK
+    assert L.lq_lattice_release_workspace(None, None) == lib.LQ_EINVAL
