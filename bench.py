@@ -56,7 +56,7 @@ FLOPS_PER_SITE = {"hop": 1320, "ainv": 1320 + 2 * 6 * 6 * 8, "xpay": 1320 + 2 * 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of the
 # benchmark configuration (profiles/wilson_dslash_f16_ainv_24x24x24x64.md); set back to
 # None whenever the kernel changes after the capture.
-NCU_TRAFFIC = {"wilson_dslash_f16_ainv": 254_870_000}
+NCU_TRAFFIC = {"wilson_dslash_f16_ainv": 255_050_000}
 
 REASONS = {
     0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap", 0x8: "hw_slowdown",
@@ -769,22 +769,32 @@ def run_serving(args):
     def serve(reqs, arrivals, fp64, slots):
         srv = lib.Server(200 << 30, slots)
         t_start = time.perf_counter()
+        outstanding, done = [], {}
+
+        def collect(timeout_ms):
+            # finished solutions are fetched (and dropped) as soon as they are ready, so the
+            # server's host copies of large multi-RHS results never pile up
+            for t in list(outstanding):
+                if not srv.wait(t, timeout_ms):
+                    continue
+                _, info, times, code = srv.poll(t)
+                done[t] = (times["finished"] - times["submitted"], code)
+                outstanding.remove(t)
+
         tickets = []
         for (si, g, kind, mass), ta in zip(reqs, arrivals):
             while time.perf_counter() - t_start < ta:
+                collect(0)
                 time.sleep(0.0005)
             op, sp = params(kind, mass, fp64)
-            tickets.append(srv.submit(lats[(si, g)], op, sp, srcs[(si, kind)]))
-        lat_s, statuses = [], []
-        for t in tickets:
-            srv.wait(t, 3600 * 1000)
-            res = srv.poll(t)
-            _, info, times, code = res
-            lat_s.append(times["finished"] - times["submitted"])
-            statuses.append(code)
+            t = srv.submit(lats[(si, g)], op, sp, srcs[(si, kind)])
+            tickets.append(t)
+            outstanding.append(t)
+        while outstanding:
+            collect(3600 * 1000)
         wall = time.perf_counter() - t_start
         srv.close()
-        return np.array(lat_s), wall, statuses
+        return (np.array([done[t][0] for t in tickets]), wall, [done[t][1] for t in tickets])
 
     # warm-up (tuning, clover inverses) on one request of every (size, kind)
     warm = [(si, 0, k, 0.02) for si in range(len(sizes)) for k in ("tmc", "hisq")]
