@@ -42,21 +42,31 @@ WORKLOAD = "wilson_tm_clover_24x24x24x64_eo_mixed_cg"
 
 # Algorithmic bytes per output site of the hopping kernels (compulsory traffic, one pass):
 #   spinor in (neighbours counted once) + 8 links + epilogue operands + spinor out.
-#   FP16 spinor = 24 x 2 B + 4 B norm = 52 B; FP16 R12 link = 24 B; FP32 spinor 96 B, R12 link 48 B.
-#   AINV epilogue reads A^{-1} (144 reals + norm); XPAY reads the clover (72 reals + norm) and y.
-BYTES_PER_SITE = {
-    "wilson_dslash_f16_ainv": 52 + 8 * 24 + (144 * 2 + 4) + 52,
-    "wilson_dslash_f16_xpay": 52 + 8 * 24 + (72 * 2 + 4) + 52 + 52,
-    "wilson_dslash_f32_ainv": 96 + 8 * 48 + 144 * 4 + 96,
-    "wilson_dslash_f32_xpay": 96 + 8 * 48 + 72 * 4 + 96 + 96,
-    "wilson_dslash_f64_ainv": 192 + 8 * 144 + 144 * 8 + 192,
-    "wilson_dslash_f64_xpay": 192 + 8 * 144 + 72 * 8 + 192 + 192,
-}
+#   FP16 spinor = 24 x 2 B + 4 B norm = 52 B; FP32 spinor 96 B; FP64 192 B. A link is
+#   `recon` reals (18 / 12 / 8) of 2 / 4 B; the FP64 kernels always read R18 (144 B).
+#   AINV epilogue reads A^{-1} (144 reals + FP16 norm); XPAY reads the clover (72 reals
+#   + FP16 norm) and y.
+KERNELS = ["wilson_dslash_f16_ainv", "wilson_dslash_f16_xpay", "wilson_dslash_f32_ainv", "wilson_dslash_f32_xpay",
+           "wilson_dslash_f64_ainv", "wilson_dslash_f64_xpay"]
+_SPINOR = {"f16": 52, "f32": 96, "f64": 192}
+_REAL = {"f16": 2, "f32": 4, "f64": 8}
+
+
+def bytes_per_site(name, recon=12):
+    prec, epi = name.split("_")[2:4]
+    sp, rb = _SPINOR[prec], _REAL[prec]
+    link = rb * (18 if prec == "f64" else recon)
+    norm = 4 if prec == "f16" else 0
+    if epi == "ainv":
+        return sp + 8 * link + 144 * rb + norm + sp
+    return sp + 8 * link + 72 * rb + norm + sp + sp
+
+
 FLOPS_PER_SITE = {"hop": 1320, "ainv": 1320 + 2 * 6 * 6 * 8, "xpay": 1320 + 2 * 36 * 8 + 48}
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of the
 # benchmark configuration (profiles/wilson_dslash_f16_ainv_24x24x24x64.md); set back to
 # None whenever the kernel changes after the capture.
-NCU_TRAFFIC = {"wilson_dslash_f16_ainv": 255_050_000}
+NCU_TRAFFIC = {("wilson_dslash_f16_ainv", 12): 255_050_000}
 
 REASONS = {
     0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap", 0x8: "hw_slowdown",
@@ -161,7 +171,7 @@ def gpu_arm(args):
     dev = f"cuda:{local}"
     lat, b = setup_gpu(dev)
     op = lib.op_params(lib.WILSON_TM_CLOVER, MASS, MU, c_sw=C_SW)
-    sp = lib.solve_params(solver=lib.MIXED_CGNR, tol=TOL, delta=0.1, prec_sloppy=args.prec, recon_sloppy=lib.R12,
+    sp = lib.solve_params(solver=lib.MIXED_CGNR, tol=TOL, delta=0.1, prec_sloppy=args.prec, recon_sloppy=args.recon,
                           graph_iters=args.graph_iters)
     stream = torch.cuda.current_stream()
     x = torch.empty_like(b)
@@ -213,7 +223,7 @@ def gpu_arm(args):
 
     # dominant kernel and its roofline, from the events recorded in the timed region
     kernels = {}
-    for name in BYTES_PER_SITE:
+    for name in KERNELS:
         n, tot = lib.profile_query(name)
         if n:
             kernels[name] = (n, tot)
@@ -222,7 +232,7 @@ def gpu_arm(args):
     n, tot = kernels[dom]
     vh = int(np.prod(DIMS)) // 2
     avg_s = tot / n * 1e-3
-    byts = BYTES_PER_SITE[dom] * vh
+    byts = bytes_per_site(dom, args.recon) * vh
     peak, peak_kind = measured_peaks()
     achieved = byts / avg_s / 1e9
     epi = dom.rsplit("_", 1)[1]
@@ -230,11 +240,11 @@ def gpu_arm(args):
                 "frac": round(achieved / peak, 4), "peak_source": peak_kind, "frac_of_nominal_8tbs": round(achieved / 8000.0, 4),
                 "algorithmic_bytes_per_launch": byts, "avg_launch_us": round(avg_s * 1e6, 2),
                 "gflops": round(FLOPS_PER_SITE[epi] * vh / avg_s / 1e9, 1),
-                "share_of_kernel_time": round(tot / all_t, 4), "traffic": NCU_TRAFFIC.get(dom),
+                "share_of_kernel_time": round(tot / all_t, 4), "traffic": NCU_TRAFFIC.get((dom, args.recon)),
                 "pass": "second timed pass of the same steps with per-launch CUDA events",
                 "profiled_ms_per_step": round(profiled_ms, 3)}
     per_kernel = {k: {"launches": v[0], "ms": round(v[1], 3),
-                      "gbs": round(BYTES_PER_SITE[k] * vh / (v[1] / v[0] * 1e-3) / 1e9, 1)} for k, v in kernels.items()}
+                      "gbs": round(bytes_per_site(k, args.recon) * vh / (v[1] / v[0] * 1e-3) / 1e9, 1)} for k, v in kernels.items()}
     # device time per solve of every kernel family in the timed region
     breakdown = {}
     for name in ["wilson_dslash_f16", "wilson_dslash_f32x2", "wilson_dslash_f32_", "wilson_ainv_site", "blas_cg_xs",
@@ -267,7 +277,7 @@ def gpu_arm(args):
     bicg = None
     if args.bicgstab_steps > 0:
         spb = lib.solve_params(solver=lib.BICGSTAB, tol=TOL, delta=0.1, prec_sloppy=args.prec,
-                               recon_sloppy=lib.R12, graph_iters=args.graph_iters)
+                               recon_sloppy=args.recon, graph_iters=args.graph_iters)
         lat.solve(op, spb, [b], stream=stream, out=[x])  # tunes the BiCGStab kernels
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -305,7 +315,7 @@ def gpu_arm(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "dims": list(DIMS), "action": "wilson twisted-mass clover",
                        "c_sw": C_SW, "m": MASS, "mu": MU, "gauge_seed": GAUGE_SEED, "source_seed": SOURCE_SEED,
-                       "tol": TOL, "sloppy_precision": args.prec, "recon": 12, "delta": 0.1,
+                       "tol": TOL, "sloppy_precision": args.prec, "recon": args.recon, "delta": 0.1,
                        "graph_iters": args.graph_iters,
                        "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (clover inverse, clover and links ~0.3 GB per step)"},
@@ -362,7 +372,7 @@ def run_multirhs(args):
     site = synth.seeded_site(dims, 303)
     srcs = [synth.point_source(dims, site, sp, c, device="cuda") for sp in range(4) for c in range(3)]
     xs = [torch.empty_like(srcs[0]) for _ in srcs]
-    sp = lib.solve_params(solver=lib.MIXED_CGNR, tol=TOL, prec_sloppy=args.prec, recon_sloppy=lib.R12)
+    sp = lib.solve_params(solver=lib.MIXED_CGNR, tol=TOL, prec_sloppy=args.prec, recon_sloppy=args.recon)
     ops = [lib.op_params(lib.WILSON_TM_CLOVER, m, mu, c_sw=csw) for mu in mus]
     for op in ops:  # warm-up: clover inverses per mass, tuning of the NB = 4 kernels
         lat.solve(op, sp, srcs[:4], out=xs[:4])
@@ -387,7 +397,7 @@ def run_multirhs(args):
            "wilson_dslash_f16_xpay": n * 52 + 8 * 24 + (72 * 2 + 4) + n * 52 + n * 52}
     kern = _kernel_table(list(bps) + ["wilson_dslash_f32x2_ainv", "wilson_dslash_f32x2_xpay"], vh, bps)
     # the same 36 right-hand sides with mixed-precision BiCGStab on the Schur operator
-    spb = lib.solve_params(solver=lib.BICGSTAB, tol=TOL, prec_sloppy=args.prec, recon_sloppy=lib.R12)
+    spb = lib.solve_params(solver=lib.BICGSTAB, tol=TOL, prec_sloppy=args.prec, recon_sloppy=args.recon)
     lat.solve(ops[0], spb, srcs[:4], out=xs[:4])
     torch.cuda.synchronize()
     e0, e1 = _events()
@@ -409,7 +419,7 @@ def run_multirhs(args):
     line = {"workload": "multirhs", "metric": "time to solution of 36 right-hand sides at true residual 1e-10",
             "value": round(tts, 3), "unit": "s", "higher_is_better": False,
             "config": {"dims": list(dims), "c_sw": csw, "m": m, "mus": mus, "nrhs": 36, "site": list(site),
-                       "sloppy_precision": args.prec, "rhs_per_call": 12},
+                       "sloppy_precision": args.prec, "recon": args.recon, "rhs_per_call": 12},
             "iters_max": max(i["iters"] for i in infos),
             "true_rel_residual_max": max(i["true_rel_residual"] for i in infos),
             "all_converged": all(i["status"] == 0 for i in infos),
@@ -426,8 +436,9 @@ def run_multirhs(args):
 
 def run_dslash(args):
     """The operator kernels alone on resident fields (24^3x64, one output parity per
-    launch): FP16 / FP32 R12 hopping term, the FP16 A^-1 D and A y - D kernels of the
-    Schur operator, and the HISQ FP16 hopping term on the same volume. L2 is flushed
+    launch): FP16 / FP32 hopping term, the FP16 A^-1 D and A y - D kernels of the
+    Schur operator, and the HISQ FP16 hopping term on the same volume, each with R12
+    and with R8 links (thin Wilson / long HISQ links). L2 is flushed
     (a 256 MB write) before every timed launch; each launch is timed alone with CUDA
     events on its stream. Reports algorithmic GB/s against the measured copy peak
     and the nominal 8 TB/s."""
@@ -468,15 +479,18 @@ def run_dslash(args):
         return float(np.median(ts))
 
     out = {}
-    opw = lib.op_params(lib.WILSON_TM_CLOVER, MASS, MU, c_sw=C_SW)
-    oph = lib.op_params(lib.HISQ, 0.01)
     psi = synth.gaussian_field(dims, 206, device="cuda")
     chi = synth.gaussian_field(dims, 207, ncomp=3, device="cuda")
-    cases = [("wilson_hop_f16_r12", lib.F16, 52 + 8 * 24 + 52, "hop"),
-             ("wilson_hop_f32_r12", lib.F32, 96 + 8 * 48 + 96, "hop"),
-             ("wilson_schur_f16_r12 (A^-1 D + A y - D)", lib.F16, (52 + 8 * 24 + 292 + 52) + (52 + 8 * 24 + 148 + 52 + 52), "schur"),
-             ("hisq_hop_f16", lib.F16, 16 + 8 * 36 + 8 * 24 + 16, "hisq")]
-    for name, prec, bps, kind in cases:
+    cases = []
+    for r in (12, 8):
+        cases += [(f"wilson_hop_f16_r{r}", lib.F16, 52 + 8 * 2 * r + 52, "hop", r),
+                  (f"wilson_hop_f32_r{r}", lib.F32, 96 + 8 * 4 * r + 96, "hop", r),
+                  (f"wilson_schur_f16_r{r} (A^-1 D + A y - D)", lib.F16,
+                   (52 + 8 * 2 * r + 292 + 52) + (52 + 8 * 2 * r + 148 + 52 + 52), "schur", r),
+                  (f"hisq_hop_f16_long_r{r}", lib.F16, 16 + 8 * 36 + 8 * 2 * r + 16, "hisq", r)]
+    for name, prec, bps, kind, r in cases:
+        opw = lib.op_params(lib.WILSON_TM_CLOVER, MASS, MU, c_sw=C_SW, recon=r)
+        oph = lib.op_params(lib.HISQ, 0.01, recon=r)
         if kind == "hisq":
             fi = lib.Field(lat, lib.STAGGERED_FIELD, prec)
             fo = lib.Field(lat, lib.STAGGERED_FIELD, prec)
@@ -525,18 +539,18 @@ def run_hisq(args):
     gen_s = time.perf_counter() - t0
     xs = [torch.empty_like(b) for _ in masses]
     op = lib.op_params(lib.HISQ, masses[0])
-    sp = lib.solve_params(solver=lib.MULTISHIFT_CG, tol=TOL, prec_sloppy=args.prec, recon_sloppy=lib.R12,
+    sp = lib.solve_params(solver=lib.MULTISHIFT_CG, tol=TOL, prec_sloppy=args.prec, recon_sloppy=args.recon,
                           masses=masses)
     # warm-up on a lattice of the same volume is the solve itself; tune with a short solve
     lat.solve(op, lib.solve_params(solver=lib.MULTISHIFT_CG, tol=1e-3, prec_sloppy=args.prec,
-                                   recon_sloppy=lib.R12, masses=masses), [b], out=xs, check=False)
+                                   recon_sloppy=args.recon, masses=masses), [b], out=xs, check=False)
     torch.cuda.synchronize()
     # the multi-shift stage alone (its sloppy tolerance is ~1e-3 in FP16, so a 1e-3 solve
     # adds almost no refinement): the time split between the stages of the full solve
     e0, e1 = _events()
     e0.record()
     _, info_ms = lat.solve(op, lib.solve_params(solver=lib.MULTISHIFT_CG, tol=1e-3, prec_sloppy=args.prec,
-                                                recon_sloppy=lib.R12, masses=masses), [b], out=xs, check=False)
+                                                recon_sloppy=args.recon, masses=masses), [b], out=xs, check=False)
     e1.record()
     torch.cuda.synchronize()
     ms_stage = {"seconds": round(e0.elapsed_time(e1) * 1e-3, 3), "iters": info_ms[0]["iters"]}
@@ -556,7 +570,8 @@ def run_hisq(args):
     kern = _kernel_table(list(bps) + ["hisq_dslash_f32x2_hop", "hisq_dslash_f32x2_xpay"], vh, bps)
     line = {"workload": "hisq", "metric": "time to solution, multi-shift over 4 masses at true residual 1e-10",
             "value": round(tts, 3), "unit": "s", "higher_is_better": False,
-            "config": {"dims": list(dims), "masses": masses, "c_naik": -1.0 / 24.0, "sloppy_precision": args.prec},
+            "config": {"dims": list(dims), "masses": masses, "c_naik": -1.0 / 24.0, "sloppy_precision": args.prec,
+                       "recon_long": args.recon},
             "iters": info[0]["iters"], "reliable_updates": info[0]["reliable_updates"],
             "true_rel_residual_max_over_shifts": info[0]["true_rel_residual"], "status": info[0]["status"],
             "setup_seconds": round(gen_s, 1), "multishift_stage_to_1e-3": ms_stage, "kernels": kern}
@@ -584,7 +599,7 @@ def run_hisq_propagator(args):
     srcs = [synth.point_source(dims, site, None, c, device="cuda") for c in range(3)]
     xs = [torch.empty_like(srcs[0]) for _ in srcs]
     op = lib.op_params(lib.HISQ, m)
-    sp = lib.solve_params(solver=lib.MIXED_CGNR, tol=TOL, prec_sloppy=args.prec, recon_sloppy=lib.R12)
+    sp = lib.solve_params(solver=lib.MIXED_CGNR, tol=TOL, prec_sloppy=args.prec, recon_sloppy=args.recon)
     lat.solve(op, sp, srcs, out=xs)  # tunes
     torch.cuda.synchronize()
     e0, e1 = _events()
@@ -608,7 +623,7 @@ def run_hisq_propagator(args):
     line = {"workload": "hisq_propagator", "metric": "time to solution of a HISQ 3-column propagator at true residual 1e-10",
             "value": round(tts, 3), "unit": "s", "higher_is_better": False,
             "config": {"dims": list(dims), "m": m, "c_naik": -1.0 / 24.0, "site": list(site), "nrhs": 3,
-                       "sloppy_precision": args.prec, "fat_seed": 104, "long_seed": 105},
+                       "sloppy_precision": args.prec, "recon_long": args.recon, "fat_seed": 104, "long_seed": 105},
             "iters_max": max(i["iters"] for i in info), "true_rel_residual_max": max(i["true_rel_residual"] for i in info),
             "all_converged": all(i["status"] == 0 for i in info),
             "fp64_one_at_a_time": {"seconds": round(t64, 3), "iters_max": max(i["iters"] for i in i64)},
@@ -633,7 +648,7 @@ def run_twisted_multimass(args):
     b = synth.z2_source(dims, SOURCE_SEED, device="cuda")
     xs = [torch.empty_like(b) for _ in mus]
     op = lib.op_params(lib.WILSON_TM, m, mus[0])
-    spm = lib.solve_params(solver=lib.MULTISHIFT_CG, tol=TOL, prec_sloppy=args.prec, recon_sloppy=lib.R12,
+    spm = lib.solve_params(solver=lib.MULTISHIFT_CG, tol=TOL, prec_sloppy=args.prec, recon_sloppy=args.recon,
                            masses=mus)
     lat.solve(op, spm, [b], out=xs)
     torch.cuda.synchronize()
@@ -643,7 +658,7 @@ def run_twisted_multimass(args):
     e1.record()
     torch.cuda.synchronize()
     t_ms = e0.elapsed_time(e1) * 1e-3
-    sps = lib.solve_params(solver=lib.MIXED_CGNR, tol=TOL, prec_sloppy=args.prec, recon_sloppy=lib.R12)
+    sps = lib.solve_params(solver=lib.MIXED_CGNR, tol=TOL, prec_sloppy=args.prec, recon_sloppy=args.recon)
     e0, e1 = _events()
     e0.record()
     iters = []
@@ -655,8 +670,8 @@ def run_twisted_multimass(args):
     t_sep = e0.elapsed_time(e1) * 1e-3
     line = {"workload": "twisted_multimass", "metric": "time to solution of three twisted masses at true residual 1e-10",
             "value": round(t_ms, 3), "unit": "s", "higher_is_better": False,
-            "config": {"dims": list(dims), "m": m, "mus": mus, "sloppy_precision": args.prec, "gauge_seed": GAUGE_SEED,
-                       "source_seed": SOURCE_SEED},
+            "config": {"dims": list(dims), "m": m, "mus": mus, "sloppy_precision": args.prec, "recon": args.recon,
+                       "gauge_seed": GAUGE_SEED, "source_seed": SOURCE_SEED},
             "iters": info[0]["iters"], "true_rel_residual_max": info[0]["true_rel_residual"],
             "status": info[0]["status"],
             "separate_mixed_cgnr": {"seconds": round(t_sep, 3), "iters": iters},
@@ -763,7 +778,7 @@ def run_serving(args):
         if fp64:
             sp = lib.solve_params(solver=lib.CGNR, tol=TOL, prec_sloppy=lib.F64)
         else:
-            sp = lib.solve_params(solver=lib.MIXED_CGNR, tol=TOL, prec_sloppy=lib.F16, recon_sloppy=lib.R12)
+            sp = lib.solve_params(solver=lib.MIXED_CGNR, tol=TOL, prec_sloppy=lib.F16, recon_sloppy=args.recon)
         return op, sp
 
     def serve(reqs, arrivals, fp64, slots):
@@ -894,6 +909,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--prec", type=int, default=2, help="sloppy precision: 1 = FP32, 2 = FP16 storage")
+    ap.add_argument("--recon", type=int, default=12, choices=[8, 12, 18],
+                    help="link compression of the sloppy operator (thin / long links)")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--cpu-iters", type=int, default=8)
     ap.add_argument("--bicgstab-steps", type=int, default=3,

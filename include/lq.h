@@ -80,7 +80,12 @@ typedef enum {
  * bytes and computed on the FP32 pipes; the mixed-precision solvers use it for
  * their FP64-accuracy steps because B300's FP64 rate is 1/64 of its FP32 rate. */
 typedef enum { LQ_F64 = 0, LQ_F32 = 1, LQ_F16 = 2, LQ_F32X2 = 3 } lq_prec;
-typedef enum { LQ_R18 = 18, LQ_R12 = 12 } lq_recon;            /* link compression (R12: two rows of SU(3)) */
+/* Link compression, for SU(3) links (thin Wilson links, HISQ long links; fat links
+ * are always R18). R12: rows 0 and 1, row 2 = conj(row0 x row1). R8: u01, u02, u10
+ * and the phases of u00 and u20; the rest follows from unitarity and det = 1
+ * (LQ_F32 / LQ_F16 only; undefined where |u00| = 1, e.g. a unit gauge field, which
+ * the packing step rejects with LQ_EINVAL). */
+typedef enum { LQ_R18 = 18, LQ_R12 = 12, LQ_R8 = 8 } lq_recon;
 typedef enum { LQ_THIN = 0, LQ_FAT = 1, LQ_LONG = 2 } lq_gauge_kind;
 typedef enum { LQ_HOST = 0, LQ_DEVICE = 1 } lq_loc;
 typedef enum { LQ_WILSON_TM = 0, LQ_WILSON_TM_CLOVER = 1, LQ_HISQ = 2 } lq_action;
@@ -100,6 +105,9 @@ typedef struct {
     double mu;
     double c_sw;
     double c_naik;
+    int recon;       /* lq_recon of the thin / long links in lq_dslash_apply, lq_dslash_apply_noalloc
+                        and lq_operator_apply at LQ_F32 / LQ_F16 (0 = LQ_R12; LQ_F64 and LQ_F32X2
+                        always use LQ_R18). The solvers take recon_sloppy instead. */
 } lq_op_params;
 
 /* Solver parameters.
@@ -126,7 +134,7 @@ typedef struct {
     double delta;     /* reliable-update threshold (0.1) */
     int maxiter;
     int prec_sloppy;  /* lq_prec */
-    int recon_sloppy; /* lq_recon for thin/long links in the sloppy operator */
+    int recon_sloppy; /* lq_recon for thin/long links in the sloppy operator (0 = LQ_R18) */
     int nshift;
     const double* masses;
     int graph_iters;  /* Krylov iterations captured per CUDA graph and replayed with one

@@ -66,6 +66,8 @@ static void check_lattice(lq_lattice lat) {
 static void check_op(const lq_op_params* op) {
     if (!op) fail(LQ_EINVAL, "null operator parameters");
     if (op->action < LQ_WILSON_TM || op->action > LQ_HISQ) fail(LQ_EINVAL, "unknown action");
+    if (op->recon != 0 && op->recon != 8 && op->recon != 12 && op->recon != 18)
+        fail(LQ_EINVAL, "recon must be 0, 8, 12 or 18");
 }
 
 static void check_prec(int prec) {
@@ -195,7 +197,7 @@ static OpDesc make_desc(const lq_op_params* op, int prec) {
     d.mu = op->action == LQ_HISQ ? 0.0 : op->mu;
     d.c_naik = op->c_naik;
     d.prec = prec;
-    d.recon = (prec == LQ_F64 || prec == LQ_F32X2) ? 18 : 12;
+    d.recon = (prec == LQ_F64 || prec == LQ_F32X2) ? 18 : (op->recon == 0 ? 12 : op->recon);
     return d;
 }
 

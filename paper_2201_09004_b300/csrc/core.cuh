@@ -571,12 +571,64 @@ __device__ __forceinline__ void fstore(const FieldV& f, int k, int s, const T* v
 // --------------------------------------------------------------- links
 // Links of parity p and direction mu: block (p*4 + mu) of NC chunks x vh.
 // R = 18: all nine entries. R = 12: rows 0 and 1; row 2 = conj(row0 x row1),
-// exact for SU(3). Boundary signs are never stored in links.
+// exact for SU(3). R = 8: u01, u02, u10 and the phases arg(u00)/pi and
+// arg(u20)/pi (the phases stored times the field's scale, so that the FP16
+// codec treats all eight reals alike); the rest follows from SU(3), see
+// su3_recon8. Boundary signs are never stored in links.
 struct GaugeV {
     const void* data;
     int vh;
     float scale;  // FP16 fixed-point scale (max |entry| of the field); 1 otherwise
 };
+
+__device__ __forceinline__ void sincospi_t(float x, float* s, float* c) { sincospif(x, s, c); }
+__device__ __forceinline__ void sincospi_t(double x, double* s, double* c) { sincospi(x, s, c); }
+
+// SU(3) from eight reals. Row 0 and column 0 have unit norm, which gives
+// |u00|^2 = 1 - |u01|^2 - |u02|^2 =: 1 - N and |u20|^2 = N - |u10|^2; with the
+// stored phases that fixes row 0 and column 0. For a unitary matrix of
+// determinant 1 every entry equals the complex conjugate of its cofactor, so
+//   u10 w1 - u20 v1 = conj(u02),   u20 v2 - u10 w2 = conj(u01)
+// (rows v = row 1, w = row 2), and column 0 is orthogonal to columns 1 and 2:
+//   conj(u10) v1 + conj(u20) w1 = -conj(u00) u01,
+//   conj(u10) v2 + conj(u20) w2 = -conj(u00) u02.
+// Each pair is a 2x2 linear system of determinant -+(|u10|^2 + |u20|^2) = -+N,
+// solved by Cramer's rule below. N = 0 (|u00| = 1) is singular: the packing
+// step refuses such fields. FAST (FP16 links, whose entries carry 2^-15
+// absolute error anyway) takes the hardware approximations of sin, cos,
+// 1/sqrt and 1/x (absolute errors near 1e-6 and below) instead of the
+// correctly rounded library functions.
+template <typename T, bool FAST = false>
+__device__ __forceinline__ void su3_recon8(const T v[8], cx<T> U[3][3]) {
+    const cx<T> u1 = mk(v[0], v[1]), u2 = mk(v[2], v[3]), v0 = mk(v[4], v[5]);
+    const T n = v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + v[3] * v[3];
+    const T q0 = fmax((T)1 - n, (T)0);
+    const T q2 = fmax(n - v[4] * v[4] - v[5] * v[5], (T)0);
+    T a0, a2, s0, c0, s2, c2, inv;
+    if constexpr (FAST && std::is_same<T, float>::value) {
+        a0 = q0 > 0.f ? q0 * rsqrtf(q0) : 0.f;
+        a2 = q2 > 0.f ? q2 * rsqrtf(q2) : 0.f;
+        const float pi = 3.14159265358979f;
+        __sincosf(pi * v[6], &s0, &c0);
+        __sincosf(pi * v[7], &s2, &c2);
+        inv = __fdividef(1.f, n);
+    } else {
+        a0 = sqrt(q0);
+        a2 = sqrt(q2);
+        sincospi_t(v[6], &s0, &c0);
+        sincospi_t(v[7], &s2, &c2);
+        inv = (T)1 / n;
+    }
+    const cx<T> u0 = mk(a0 * c0, a0 * s0), w0 = mk(a2 * c2, a2 * s2);
+    const cx<T> p1 = cj(u0) * u1, p2 = cj(u0) * u2;
+    U[0][0] = u0; U[0][1] = u1; U[0][2] = u2;
+    U[1][0] = v0;
+    U[2][0] = w0;
+    U[1][1] = -inv * (cj(u2 * w0) + p1 * v0);
+    U[2][1] = inv * (cj(u2 * v0) - p1 * w0);
+    U[1][2] = inv * (cj(u1 * w0) - p2 * v0);
+    U[2][2] = -inv * (p2 * w0 + cj(u1 * v0));
+}
 
 template <int P, int R, typename T>
 __device__ __forceinline__ void load_link(const GaugeV& g, int p, int mu, int s, cx<T> U[3][3]) {
@@ -584,19 +636,77 @@ __device__ __forceinline__ void load_link(const GaugeV& g, int p, int mu, int s,
     const char* base = (const char*)g.data + (size_t)(p * 4 + mu) * Lay::NC * g.vh * sizeof(typename Lay::C);
     T v[R];
     load_reals<P, R, T>(base, g.vh, s, g.scale, v);
-#pragma unroll
-    for (int a = 0; a < 2; a++)
-#pragma unroll
-        for (int b = 0; b < 3; b++) U[a][b] = mk(v[(a * 3 + b) * 2], v[(a * 3 + b) * 2 + 1]);
-    if constexpr (R == 18) {
-#pragma unroll
-        for (int b = 0; b < 3; b++) U[2][b] = mk(v[(6 + b) * 2], v[(6 + b) * 2 + 1]);
+    if constexpr (R == 8) {
+        const T is = (T)1 / (T)g.scale;
+        v[6] *= is;
+        v[7] *= is;
+        su3_recon8<T, P == P16>(v, U);
+        return;
     } else {
-        // row2 = conj(row0 x row1)
-        U[2][0] = cj(U[0][1] * U[1][2] - U[0][2] * U[1][1]);
-        U[2][1] = cj(U[0][2] * U[1][0] - U[0][0] * U[1][2]);
-        U[2][2] = cj(U[0][0] * U[1][1] - U[0][1] * U[1][0]);
+#pragma unroll
+        for (int a = 0; a < 2; a++)
+#pragma unroll
+            for (int b = 0; b < 3; b++) U[a][b] = mk(v[(a * 3 + b) * 2], v[(a * 3 + b) * 2 + 1]);
+        if constexpr (R == 18) {
+#pragma unroll
+            for (int b = 0; b < 3; b++) U[2][b] = mk(v[(6 + b) * 2], v[(6 + b) * 2 + 1]);
+        } else {
+            // row2 = conj(row0 x row1)
+            U[2][0] = cj(U[0][1] * U[1][2] - U[0][2] * U[1][1]);
+            U[2][1] = cj(U[0][2] * U[1][0] - U[0][0] * U[1][2]);
+            U[2][2] = cj(U[0][0] * U[1][1] - U[0][1] * U[1][0]);
+        }
     }
+}
+
+// A link from its raw chunks (software-pipelined hops). FP32: U is the link.
+// FP16 with R = 18 / 12: U holds the link divided by scale/32767 (integer codes;
+// R12's third row is rescaled once here), and the caller folds scale/32767 into
+// its per-hop factor. FP16 with R = 8: U is the link (the reconstruction needs
+// true values), so the caller folds in nothing.
+template <int P, int R, typename T>
+__device__ __forceinline__ void decode_link(const typename Layout<P, R>::C* u, float scale, cx<T> U[3][3]) {
+    typedef Layout<P, R> LU;
+    T lv[R];
+#pragma unroll
+    for (int k = 0; k < LU::NC; k++) {
+        if constexpr (P == P16) unpack_codes16<R, T>(u[k], lv + k * LU::RPC);
+        else unpack_chunk<P, R, T>(u[k], 1.f, lv + k * LU::RPC);
+    }
+    if constexpr (R == 8) {
+        // FP16: entries are codes * scale/32767 and the phases codes/32767; FP32: scale = 1
+        const T fe = P == P16 ? (T)(scale * (1.f / 32767.f)) : (T)1;
+        const T fp = P == P16 ? (T)(1.f / 32767.f) : (T)1;
+#pragma unroll
+        for (int k = 0; k < 6; k++) lv[k] *= fe;
+        lv[6] *= fp;
+        lv[7] *= fp;
+        su3_recon8<T, P == P16>(lv, U);
+    } else {
+#pragma unroll
+        for (int r = 0; r < 2; r++)
+#pragma unroll
+            for (int q = 0; q < 3; q++) U[r][q] = mk(lv[(r * 3 + q) * 2], lv[(r * 3 + q) * 2 + 1]);
+        if constexpr (R == 18) {
+#pragma unroll
+            for (int q = 0; q < 3; q++) U[2][q] = mk(lv[(6 + q) * 2], lv[(6 + q) * 2 + 1]);
+        } else {
+            U[2][0] = cj(U[0][1] * U[1][2] - U[0][2] * U[1][1]);
+            U[2][1] = cj(U[0][2] * U[1][0] - U[0][0] * U[1][2]);
+            U[2][2] = cj(U[0][0] * U[1][1] - U[0][1] * U[1][0]);
+            if constexpr (P == P16) {  // conj(row0 x row1) of codes carries the scale twice
+                const T fu = (T)(scale * (1.f / 32767.f));
+#pragma unroll
+                for (int q = 0; q < 3; q++) U[2][q] = fu * U[2][q];
+            }
+        }
+    }
+}
+
+// the factor that decode_link leaves to its caller
+template <int P, int R>
+__device__ __forceinline__ float link_factor(float scale) {
+    return (P == P16 && R != 8) ? scale * (1.f / 32767.f) : 1.f;
 }
 
 // out = U v, out = U^+ v

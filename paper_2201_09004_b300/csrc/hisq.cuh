@@ -121,36 +121,15 @@ template <int J, int P, int R, typename T>
 __device__ __forceinline__ void stag_apply(const GaugeV& G, const StagRaw<P, R>& r, T coef, cx<T> acc[3]) {
     constexpr bool FWD = (J & 1) == 0;
     typedef Layout<P, 6> LS;
-    typedef Layout<P, R> LU;
-    T v[6], lv[R];
+    T v[6];
 #pragma unroll
     for (int k = 0; k < LS::NC; k++) {
         if constexpr (P == P16) unpack_codes16<6, T>(r.sp[k], v + k * LS::RPC);
         else unpack_chunk<P, 6, T>(r.sp[k], 1.f, v + k * LS::RPC);
     }
-#pragma unroll
-    for (int k = 0; k < LU::NC; k++) {
-        if constexpr (P == P16) unpack_codes16<R, T>(r.u[k], lv + k * LU::RPC);
-        else unpack_chunk<P, R, T>(r.u[k], 1.f, lv + k * LU::RPC);
-    }
-    const float fu = G.scale * (1.f / 32767.f);
     cx<T> U[3][3];
-#pragma unroll
-    for (int i = 0; i < 2; i++)
-#pragma unroll
-        for (int q = 0; q < 3; q++) U[i][q] = mk(lv[(i * 3 + q) * 2], lv[(i * 3 + q) * 2 + 1]);
-    if constexpr (R == 18) {
-#pragma unroll
-        for (int q = 0; q < 3; q++) U[2][q] = mk(lv[(6 + q) * 2], lv[(6 + q) * 2 + 1]);
-    } else {
-        U[2][0] = cj(U[0][1] * U[1][2] - U[0][2] * U[1][1]);
-        U[2][1] = cj(U[0][2] * U[1][0] - U[0][0] * U[1][2]);
-        U[2][2] = cj(U[0][0] * U[1][1] - U[0][1] * U[1][0]);
-        if constexpr (P == P16) {  // conj(row0 x row1) of codes carries the scale twice
-#pragma unroll
-            for (int q = 0; q < 3; q++) U[2][q] = (T)fu * U[2][q];
-        }
-    }
+    decode_link<P, R, T>(r.u, G.scale, U);
+    const float fu = link_factor<P, R>(G.scale);
     const cx<T> ps[3] = {mk(v[0], v[1]), mk(v[2], v[3]), mk(v[4], v[5])};
     cx<T> o[3];
     if constexpr (FWD) su3_mv(U, ps, o);

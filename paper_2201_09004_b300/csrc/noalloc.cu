@@ -145,6 +145,8 @@ extern "C" int lq_dslash_apply_noalloc(lq_lattice h, const lq_op_params* op, int
         if (!h || !op || !in || !out) fail(LQ_EINVAL, "null argument");
         if (op->action < LQ_WILSON_TM || op->action > LQ_HISQ) fail(LQ_EINVAL, "unknown action");
         if (prec < LQ_F64 || prec > LQ_F16) fail(LQ_EINVAL, "unknown precision");
+        if (op->recon != 0 && op->recon != 8 && op->recon != 12 && op->recon != 18)
+            fail(LQ_EINVAL, "recon must be 0, 8, 12 or 18");
         if (parity != 0 && parity != 1) fail(LQ_EINVAL, "parity must be 0 or 1");
         Lattice& lat = h->lat;
         const bool hisq = op->action == LQ_HISQ;
@@ -154,7 +156,7 @@ extern "C" int lq_dslash_apply_noalloc(lq_lattice h, const lq_op_params* op, int
             fail(LQ_EINVAL, "lattice too large for lq_dslash_apply_noalloc: needs " + std::to_string(2 * per) +
                                 " bytes of scratch, the maximum is " + std::to_string(kNoallocScratchBytes) +
                                 " (use lq_dslash_apply)");
-        const int recon = prec == LQ_F64 ? 18 : 12;
+        const int recon = (prec == LQ_F64 || prec == LQ_F32X2) ? 18 : (op->recon == 0 ? 12 : op->recon);
         GaugeV g1{}, g2{};
         bool ok = hisq ? (packed_links(lat, LQ_FAT, prec, 18, &g1) && packed_links(lat, LQ_LONG, prec, recon, &g2))
                        : packed_links(lat, LQ_THIN, prec, recon, &g1);
@@ -175,15 +177,18 @@ extern "C" int lq_dslash_apply_noalloc(lq_lattice h, const lq_op_params* op, int
         fi.norm = prec == LQ_F16 ? (float*)(base + fi.rhs_bytes) : nullptr;
         fo.norm = prec == LQ_F16 ? (float*)(base + per + fo.rhs_bytes) : nullptr;
         cudaStream_t st = (cudaStream_t)stream;
-        if (hisq) {
-            if (prec == LQ_F64) run_noalloc<P64, 6, 18>(lat, true, g1, g2, parity, dagger, op->c_naik, in, out, fi, fo, st);
-            else if (prec == LQ_F32) run_noalloc<P32, 6, 12>(lat, true, g1, g2, parity, dagger, op->c_naik, in, out, fi, fo, st);
-            else run_noalloc<P16, 6, 12>(lat, true, g1, g2, parity, dagger, op->c_naik, in, out, fi, fo, st);
-        } else {
-            if (prec == LQ_F64) run_noalloc<P64, 24, 18>(lat, false, g1, g2, parity, dagger, 0.0, in, out, fi, fo, st);
-            else if (prec == LQ_F32) run_noalloc<P32, 24, 12>(lat, false, g1, g2, parity, dagger, 0.0, in, out, fi, fo, st);
-            else run_noalloc<P16, 24, 12>(lat, false, g1, g2, parity, dagger, 0.0, in, out, fi, fo, st);
-        }
+        const double cn = hisq ? op->c_naik : 0.0;
+#define LQ_NOALLOC(P, R)                                                                              \
+    (hisq ? run_noalloc<P, 6, R>(lat, true, g1, g2, parity, dagger, cn, in, out, fi, fo, st)          \
+          : run_noalloc<P, 24, R>(lat, false, g1, g2, parity, dagger, cn, in, out, fi, fo, st))
+        if (prec == LQ_F64) LQ_NOALLOC(P64, 18);
+        else if (prec == LQ_F32 && recon == 8) LQ_NOALLOC(P32, 8);
+        else if (prec == LQ_F32 && recon == 18) LQ_NOALLOC(P32, 18);
+        else if (prec == LQ_F32) LQ_NOALLOC(P32, 12);
+        else if (recon == 8) LQ_NOALLOC(P16, 8);
+        else if (recon == 18) LQ_NOALLOC(P16, 18);
+        else LQ_NOALLOC(P16, 12);
+#undef LQ_NOALLOC
         LQ_CUDA(cudaStreamSynchronize(st));
         return LQ_OK;
     } catch (const Error& e) {

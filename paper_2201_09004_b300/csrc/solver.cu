@@ -103,6 +103,13 @@ struct CgResult {
     explicit CgResult(int n) : iters(n, 0), updates(n, 0), applications(n, 0), status(n, LQ_ENOTCONV) {}
 };
 
+// link compression of the sloppy operator: 8, 12, or 18 (also for 0)
+static int sloppy_recon(const lq_solve_params& sp) {
+    if (sp.recon_sloppy == 8 || sp.recon_sloppy == 12) return sp.recon_sloppy;
+    if (sp.recon_sloppy == 0 || sp.recon_sloppy == 18) return 18;
+    fail(LQ_EINVAL, "recon_sloppy must be 8, 12 or 18");
+}
+
 // =================================================================== Wilson
 static OpDesc wilson_desc(const lq_op_params& op, int prec, int recon) {
     OpDesc d;
@@ -399,7 +406,7 @@ int solve_wilson(Lattice& lat, const lq_op_params& opp, const lq_solve_params& s
     if (sp.solver != LQ_CGNR && sp.solver != LQ_MIXED_CGNR && sp.solver != LQ_BICGSTAB)
         fail(LQ_EINVAL, "solver kind for a Wilson action");
     if (!(sp.tol > 0)) fail(LQ_EINVAL, "tol must be positive");
-    const int recon = sp.recon_sloppy == 12 ? 12 : 18;
+    const int recon = sloppy_recon(sp);
     // the FP64-accuracy steps: native FP64 for the plain FP64 solver, double-float
     // (FP32 pipes) when the iterations run in FP32 / FP16
     const int ph = ps == LQ_F64 ? LQ_F64 : LQ_F32X2;
@@ -530,7 +537,7 @@ int solve_wilson_multishift(Lattice& lat, const lq_op_params& opp, const lq_solv
     const int maxiter = sp.maxiter > 0 ? sp.maxiter : 100000;
     lq_op_params op0 = opp;
     op0.mu = 0.0;
-    const OpDesc d = wilson_desc(op0, ps, sp.recon_sloppy == 12 ? 12 : 18);
+    const OpDesc d = wilson_desc(op0, ps, sloppy_recon(sp));
     const int WF = LQ_WILSON_FIELD, nsys = 2 * nrhs, nf = 2 * nsys;
     std::vector<double> sigma(ns);
     for (int i = 0; i < ns; i++) sigma[i] = mus[i] * mus[i];
@@ -902,7 +909,7 @@ int solve_hisq(Lattice& lat, const lq_op_params& opp, const lq_solve_params& sp,
     int ps = sp.prec_sloppy;
     if (ps < LQ_F64 || ps > LQ_F16) fail(LQ_EINVAL, "prec_sloppy");
     if (!(sp.tol > 0)) fail(LQ_EINVAL, "tol must be positive");
-    const int recon = sp.recon_sloppy == 12 ? 12 : 18;
+    const int recon = sloppy_recon(sp);
     const int ph = ps == LQ_F64 ? LQ_F64 : LQ_F32X2;
     const OpDesc op64 = hisq_desc(opp, ph, 18);
     const OpDesc ops = hisq_desc(opp, ps, recon);

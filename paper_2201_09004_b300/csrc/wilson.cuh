@@ -446,7 +446,6 @@ __device__ __forceinline__ void process_hop(const WilsonArgs& a, const HopRaw<P,
     constexpr int MU = H >> 1;
     constexpr bool FWD = (H & 1) == 0;
     typedef Layout<P, 24> LS;
-    typedef Layout<P, R> LU;
     // FP16: spinor and link stay in integer codes (value / scale); the two scales
     // and the boundary sign multiply the 12 reals of the rotated half spinor once
     T v[24];
@@ -455,30 +454,9 @@ __device__ __forceinline__ void process_hop(const WilsonArgs& a, const HopRaw<P,
         if constexpr (P == P16) unpack_codes16<24, T>(h.sp[k], v + k * LS::RPC);
         else unpack_chunk<P, 24, T>(h.sp[k], 1.f, v + k * LS::RPC);
     }
-    T lv[R];
-    const float fu = a.U.scale * (1.f / 32767.f);
-#pragma unroll
-    for (int k = 0; k < LU::NC; k++) {
-        if constexpr (P == P16) unpack_codes16<R, T>(h.u[k], lv + k * LU::RPC);
-        else unpack_chunk<P, R, T>(h.u[k], 1.f, lv + k * LU::RPC);
-    }
     cx<T> U[3][3];
-#pragma unroll
-    for (int r = 0; r < 2; r++)
-#pragma unroll
-        for (int q = 0; q < 3; q++) U[r][q] = mk(lv[(r * 3 + q) * 2], lv[(r * 3 + q) * 2 + 1]);
-    if constexpr (R == 18) {
-#pragma unroll
-        for (int q = 0; q < 3; q++) U[2][q] = mk(lv[(6 + q) * 2], lv[(6 + q) * 2 + 1]);
-    } else {
-        U[2][0] = cj(U[0][1] * U[1][2] - U[0][2] * U[1][1]);
-        U[2][1] = cj(U[0][2] * U[1][0] - U[0][0] * U[1][2]);
-        U[2][2] = cj(U[0][0] * U[1][1] - U[0][1] * U[1][0]);
-        if constexpr (P == P16) {  // conj(row0 x row1) of codes carries the scale twice
-#pragma unroll
-            for (int q = 0; q < 3; q++) U[2][q] = (T)fu * U[2][q];
-        }
-    }
+    decode_link<P, R, T>(h.u, a.U.scale, U);
+    const float fu = link_factor<P, R>(a.U.scale);
     cx<T> ps[4][3], h0[3], h1[3], r0[3], r1[3];
     to_spinor(v, ps);
     const T sp = FWD ? sf : -sf;  // projector (1 + sp g_mu)
