@@ -89,13 +89,17 @@ typedef enum { LQ_R18 = 18, LQ_R12 = 12, LQ_R8 = 8 } lq_recon;
 typedef enum { LQ_THIN = 0, LQ_FAT = 1, LQ_LONG = 2 } lq_gauge_kind;
 typedef enum { LQ_HOST = 0, LQ_DEVICE = 1 } lq_loc;
 typedef enum { LQ_WILSON_TM = 0, LQ_WILSON_TM_CLOVER = 1, LQ_HISQ = 2 } lq_action;
+/* The paper's complex mass m_cri + omega (Sec. 2.1 Eq. 1) read as the twisted mass
+ * i mu g5 (default), or literally as the scalar i mu. */
+typedef enum { LQ_TWIST_GAMMA5 = 0, LQ_TWIST_SCALAR = 1 } lq_twist;
 typedef enum { LQ_CGNR = 0, LQ_MIXED_CGNR = 1, LQ_MULTISHIFT_CG = 2, LQ_BICGSTAB = 3 } lq_solver;
 typedef enum { LQ_OP_FULL = 0, LQ_OP_SCHUR = 1 } lq_op_form;
 typedef enum { LQ_WILSON_FIELD = 0, LQ_STAGGERED_FIELD = 1 } lq_field_kind;
 typedef enum { LQ_EVEN = 0, LQ_ODD = 1 } lq_parity;
 
 /* Operator parameters. For Wilson actions m and mu are the real and twisted
- * mass (M = (4+m) + i mu g5 + C - H); c_sw is used only for
+ * mass (M = (4+m) + i mu g5 + C - H, or M = (4+m) + i mu + C - H with
+ * twist_mode = LQ_TWIST_SCALAR); c_sw is used only for
  * LQ_WILSON_TM_CLOVER and must match the c_sw of lq_load_clover. For LQ_HISQ,
  * m is the staggered mass and c_naik the coefficient of the three-hop term
  * (tree level: -1/24). */
@@ -108,6 +112,7 @@ typedef struct {
     int recon;       /* lq_recon of the thin / long links in lq_dslash_apply, lq_dslash_apply_noalloc
                         and lq_operator_apply at LQ_F32 / LQ_F16 (0 = LQ_R12; LQ_F64 and LQ_F32X2
                         always use LQ_R18). The solvers take recon_sloppy instead. */
+    int twist_mode;  /* lq_twist (Wilson actions); the Wilson multi-shift solve needs LQ_TWIST_GAMMA5 */
 } lq_op_params;
 
 /* Solver parameters.

@@ -68,6 +68,7 @@ static void check_op(const lq_op_params* op) {
     if (op->action < LQ_WILSON_TM || op->action > LQ_HISQ) fail(LQ_EINVAL, "unknown action");
     if (op->recon != 0 && op->recon != 8 && op->recon != 12 && op->recon != 18)
         fail(LQ_EINVAL, "recon must be 0, 8, 12 or 18");
+    if (op->twist_mode != LQ_TWIST_GAMMA5 && op->twist_mode != LQ_TWIST_SCALAR) fail(LQ_EINVAL, "unknown twist_mode");
 }
 
 static void check_prec(int prec) {
@@ -198,6 +199,7 @@ static OpDesc make_desc(const lq_op_params* op, int prec) {
     d.c_naik = op->c_naik;
     d.prec = prec;
     d.recon = (prec == LQ_F64 || prec == LQ_F32X2) ? 18 : (op->recon == 0 ? 12 : op->recon);
+    d.twist = op->twist_mode;
     return d;
 }
 

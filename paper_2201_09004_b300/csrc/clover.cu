@@ -10,7 +10,8 @@
 // Packed per block: 6 real diagonal entries, then the 15 upper off-diagonal
 // entries (row-major, i<j) as complex numbers: 36 reals, 72 per site.
 // A = (4+m) + C + i mu g5 is, per block b with g5 = chi_b = +1/-1,
-// A_b = (4+m) + C_b + i chi_b mu; its inverse is stored as 36 complex numbers
+// A_b = (4+m) + C_b + i mu_b with mu_b = chi_b mu (mu_b = mu for the scalar
+// twist (4+m) + i mu + C); its inverse is stored as 36 complex numbers
 // (row-major) per block, 144 reals per site, and computed by Gauss-Jordan
 // elimination with partial pivoting in FP64.
 #include <string.h>
@@ -233,7 +234,7 @@ __global__ void clover_pack_kernel(const double* canon, Geo g, void* out) {
 }
 
 // A^{-1} per site from packed C (FP64), Gauss-Jordan with partial pivoting
-__global__ void ainv_kernel(const void* cl, Geo g, double m4, double mu, void* out) {
+__global__ void ainv_kernel(const void* cl, Geo g, double m4, double mu0, double mu1, void* out) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const int p = blockIdx.y;
     if (s >= g.vh) return;
@@ -241,13 +242,13 @@ __global__ void ainv_kernel(const void* cl, Geo g, double m4, double mu, void* o
     load_reals<P64, 72, double>((const char*)cl + (size_t)p * 36 * g.vh * sizeof(double2), g.vh, s, 1.f, v);
     double o[144];
     for (int b = 0; b < 2; b++) {
-        const double chi = b == 0 ? 1.0 : -1.0;
+        const double mub = b == 0 ? mu0 : mu1;
         zd A[6][12];
         const double* w = v + 36 * b;
         for (int i = 0; i < 6; i++)
             for (int j = 0; j < 12; j++) A[i][j] = mk(0.0, 0.0);
         for (int i = 0; i < 6; i++) {
-            A[i][i] = mk(w[i] + m4, chi * mu);
+            A[i][i] = mk(w[i] + m4, mub);
             A[i][6 + i] = mk(1.0, 0.0);
         }
         int q = 0;
@@ -357,11 +358,11 @@ void load_clover_canonical(Lattice& lat, const double* canon_dev, cudaStream_t s
 }
 
 // builds A^{-1} in precision prec only (through a temporary FP64 copy)
-void build_ainv(Lattice& lat, double m, double mu, int prec, Lattice::Ainv& out, cudaStream_t st) {
+void build_ainv(Lattice& lat, double m, double mu0, double mu1, int prec, Lattice::Ainv& out, cudaStream_t st) {
     void* d64 = dev_alloc(&lat, rec_bytes(LQ_F64, 144, lat.vh));
     dim3 grid((lat.vh + 63) / 64, 2);
-    launch("clover_inverse", ainv_kernel, grid, dim3(64), st, (const void*)lat.clovC[LQ_F64], lat.geo, 4.0 + m, mu,
-           d64);
+    launch("clover_inverse", ainv_kernel, grid, dim3(64), st, (const void*)lat.clovC[LQ_F64], lat.geo, 4.0 + m, mu0,
+           mu1, d64);
     if (prec == LQ_F64) {
         out.data[LQ_F64] = d64;
         return;
@@ -389,7 +390,7 @@ static void free_ainv_entry(Lattice& lat, Lattice::Ainv& a) {
 }
 
 // drop least-recently-used unpinned entries beyond the cache size, never `keep` (lat.mu held)
-static void trim_ainv(Lattice& lat, const std::pair<double, double>* keep) {
+static void trim_ainv(Lattice& lat, const std::tuple<double, double, double>* keep) {
     while (lat.ainv.size() > kAinvCache) {
         auto victim = lat.ainv.end();
         for (auto it = lat.ainv.begin(); it != lat.ainv.end(); ++it)
@@ -402,9 +403,9 @@ static void trim_ainv(Lattice& lat, const std::pair<double, double>* keep) {
     }
 }
 
-void pin_ainv(Lattice& lat, double m, double mu, bool pin) {
+void pin_ainv(Lattice& lat, double m, double mu0, double mu1, bool pin) {
     std::lock_guard<std::mutex> lk(lat.mu);
-    auto& e = lat.ainv[std::make_pair(m, mu)];
+    auto& e = lat.ainv[std::make_tuple(m, mu0, mu1)];
     e.last_use = ++lat.ainv_clock;
     e.pins += pin ? 1 : -1;
     if (!pin) trim_ainv(lat, nullptr);
@@ -417,15 +418,16 @@ const void* clover_block(Lattice& lat, int prec, int parity, const float** norm)
     return (const char*)lat.clovC[prec] + per * parity;
 }
 
-const void* ainv_block(Lattice& lat, double m, double mu, int prec, int parity, const float** norm, cudaStream_t st) {
+const void* ainv_block(Lattice& lat, double m, double mu0, double mu1, int prec, int parity, const float** norm,
+                       cudaStream_t st) {
     std::lock_guard<std::mutex> lk(lat.mu);
     if (!lat.has_clover) fail(LQ_EINVAL, "clover term not loaded");
-    const auto key = std::make_pair(m, mu);
+    const auto key = std::make_tuple(m, mu0, mu1);
     auto& e = lat.ainv[key];
     e.last_use = ++lat.ainv_clock;
     if (!e.data[prec]) {
         if (stream_capturing(st)) fail(LQ_EINVAL, "clover inverse for a new (m, mu) requested during capture");
-        build_ainv(lat, m, mu, prec, e, st);
+        build_ainv(lat, m, mu0, mu1, prec, e, st);
     }
     const void* ptr = (const char*)e.data[prec] + rec_bytes(prec, 144, lat.vh) / 2 * parity;
     *norm = prec == LQ_F16 ? e.norm + (size_t)parity * lat.vh : nullptr;

@@ -33,6 +33,7 @@ int wilson_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int ep
     a.gamma5_out = op.gamma5;
     a.m4 = 4.0 + op.m;
     a.mu = dagger ? -op.mu : op.mu;
+    a.mu1 = dagger ? -mu_block1(op) : mu_block1(op);
     a.nrhs = in.nrhs;
     a.norm_out = norm_out;
     a.fin = FinArgs();  // the tuner's trial launches never finalise
@@ -40,7 +41,7 @@ int wilson_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int ep
     a.clov_norm = nullptr;
     if (a.has_clover) {
         if (epi == EPI_XPAY) a.clov = clover_block(lat, op.prec, parity, &a.clov_norm);
-        else if (epi == EPI_AINV) a.clov = ainv_block(lat, op.m, op.mu, op.prec, parity, &a.clov_norm, st);
+        else if (epi == EPI_AINV) a.clov = ainv_block(lat, op.m, op.mu, mu_block1(op), op.prec, parity, &a.clov_norm, st);
     }
     const int nb = (op.prec == LQ_F32 || op.prec == LQ_F16) ? pick_rg(a.nrhs) : 1;
     const char* name = wname(op.prec, epi);
@@ -91,11 +92,12 @@ void wilson_ainv_site(Lattice& lat, const OpDesc& op, int parity, int dagger, co
     a.has_clover = op.action == LQ_WILSON_TM_CLOVER;
     a.m4 = 4.0 + op.m;
     a.mu = dagger ? -op.mu : op.mu;
+    a.mu1 = dagger ? -mu_block1(op) : mu_block1(op);
     a.nrhs = in.nrhs;
     a.norm_out = nullptr;
     a.clov = nullptr;
     a.clov_norm = nullptr;
-    if (a.has_clover) a.clov = ainv_block(lat, op.m, op.mu, in.prec, parity, &a.clov_norm, st);
+    if (a.has_clover) a.clov = ainv_block(lat, op.m, op.mu, mu_block1(op), in.prec, parity, &a.clov_norm, st);
     dim3 grid((lat.vh + 127) / 128, in.nrhs);
     if (in.prec == LQ_F64) launch("wilson_ainv_site", wilson_ainv_site_kernel<P64>, grid, dim3(128), st, a);
     else if (in.prec == LQ_F32X2)

@@ -126,6 +126,7 @@ void run_noalloc(Lattice& lat, bool hisq, const GaugeV& g1, const GaugeV& g2, in
         a.has_clover = 0;
         a.m4 = 4.0;
         a.mu = 0.0;
+        a.mu1 = 0.0;
         a.nrhs = 1;
         a.norm_out = nullptr;
         launch("wilson_dslash_noalloc", wilson_dslash_kernel<P, R, EPI_HOP, 1>, grid, dim3(block), st, a);

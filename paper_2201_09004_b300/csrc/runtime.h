@@ -159,7 +159,7 @@ struct Lattice {
         int pins = 0;           // solves currently using this entry
         uint64_t last_use = 0;  // for least-recently-used eviction
     };
-    std::map<std::pair<double, double>, Ainv> ainv;  // (m, mu) -> A^{-1}, at most kAinvCache unpinned
+    std::map<std::tuple<double, double, double>, Ainv> ainv;  // (m, mu0, mu1) -> A^{-1}, at most kAinvCache unpinned
     uint64_t ainv_clock = 0;
     // Work buffers of the solvers (device fields, pinned host scalars), kept
     // between solves so that a solve allocates nothing once the lattice is warm.
@@ -183,10 +183,12 @@ struct Lattice {
 GaugeV gauge_view(Lattice& lat, int kind, int prec, int recon);
 // pointer to parity block of the clover (C, 72 reals) / inverse (144 reals)
 const void* clover_block(Lattice& lat, int prec, int parity, const float** norm);
-const void* ainv_block(Lattice& lat, double m, double mu, int prec, int parity, const float** norm, cudaStream_t st);
+// mu0 / mu1: the twisted mass on chiral block 0 (spins 0, 1) / 1 (spins 2, 3)
+const void* ainv_block(Lattice& lat, double m, double mu0, double mu1, int prec, int parity, const float** norm,
+                       cudaStream_t st);
 void free_clover(Lattice& lat);
 // keep the clover inverse of (m, mu) resident while a solve runs
-void pin_ainv(Lattice& lat, double m, double mu, bool pin);
+void pin_ainv(Lattice& lat, double m, double mu0, double mu1, bool pin);
 enum { kAinvCache = 8 };
 
 void* dev_alloc(Lattice* lat, size_t bytes);
@@ -211,7 +213,7 @@ void gauge_maxabs(const double* canon, int V, float* out, cudaStream_t st);
 // ------------------------------------------------------------------ clover
 void build_clover(Lattice& lat, double c_sw, cudaStream_t st);
 void load_clover_canonical(Lattice& lat, const double* canon_dev, cudaStream_t st);
-void build_ainv(Lattice& lat, double m, double mu, int prec, Lattice::Ainv& out, cudaStream_t st);
+void build_ainv(Lattice& lat, double m, double mu0, double mu1, int prec, Lattice::Ainv& out, cudaStream_t st);
 
 // ------------------------------------------------------------------ dslash
 struct OpDesc {
@@ -220,7 +222,11 @@ struct OpDesc {
     int prec;
     int recon;       // thin (Wilson) / long (HISQ) link compression
     int gamma5 = 0;  // Wilson: multiply every result by g5 (the hermitian g5 D_w)
+    int twist = LQ_TWIST_GAMMA5;  // Wilson: i mu g5 or the scalar i mu
 };
+
+// twisted mass on chiral block 1 (spins 2, 3): -mu for i mu g5, +mu for the scalar twist
+inline double mu_block1(const OpDesc& d) { return d.twist == LQ_TWIST_SCALAR ? d.mu : -d.mu; }
 
 // out = epilogue(D in) for output parity; `y` used by EPI_XPAY (same parity as out).
 // norm_out: optional per-block partials of |out|^2 (nrhs * blocks).

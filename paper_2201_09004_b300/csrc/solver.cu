@@ -119,6 +119,7 @@ static OpDesc wilson_desc(const lq_op_params& op, int prec, int recon) {
     d.c_naik = op.c_naik;
     d.prec = prec;
     d.recon = prec == LQ_F64 ? 18 : recon;
+    d.twist = op.twist_mode;
     return d;
 }
 
@@ -418,10 +419,12 @@ int solve_wilson(Lattice& lat, const lq_op_params& opp, const lq_solve_params& s
 
     // the clover inverse of this (m, mu) stays resident for the whole solve
     struct Pin {
-        Lattice& l; double m, mu; bool on;
-        Pin(Lattice& l_, double m_, double mu_, bool on_) : l(l_), m(m_), mu(mu_), on(on_) { if (on) pin_ainv(l, m, mu, true); }
-        ~Pin() { if (on) pin_ainv(l, m, mu, false); }
-    } pin(lat, opp.m, opp.mu, opp.action == LQ_WILSON_TM_CLOVER);
+        Lattice& l; double m, mu0, mu1; bool on;
+        Pin(Lattice& l_, double m_, double mu0_, double mu1_, bool on_) : l(l_), m(m_), mu0(mu0_), mu1(mu1_), on(on_) {
+            if (on) pin_ainv(l, m, mu0, mu1, true);
+        }
+        ~Pin() { if (on) pin_ainv(l, m, mu0, mu1, false); }
+    } pin(lat, opp.m, ops.mu, mu_block1(ops), opp.action == LQ_WILSON_TM_CLOVER);
     cudaEvent_t e0, e1;
     LQ_CUDA(cudaEventCreate(&e0));
     LQ_CUDA(cudaEventCreate(&e1));
@@ -522,6 +525,8 @@ int solve_wilson(Lattice& lat, const lq_op_params& opp, const lq_solve_params& s
 int solve_wilson_multishift(Lattice& lat, const lq_op_params& opp, const lq_solve_params& sp, int nrhs,
                             const double* const* b, double* const* x, lq_solve_info* info, cudaStream_t st) {
     if (opp.action != LQ_WILSON_TM) fail(LQ_EINVAL, "Wilson multi-shift: twisted mass without clover only");
+    if (opp.twist_mode != LQ_TWIST_GAMMA5)
+        fail(LQ_EINVAL, "Wilson multi-shift: M^+ M = M0^+ M0 + mu^2 holds for the i mu g5 twist only");
     if (!lat.canon[LQ_THIN]) fail(LQ_EINVAL, "thin gauge field not loaded");
     if (nrhs < 1 || nrhs > 16) fail(LQ_EINVAL, "nrhs must be in [1, 16] for the Wilson multi-shift solve");
     const int ns = sp.nshift;

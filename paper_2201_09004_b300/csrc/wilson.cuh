@@ -8,8 +8,9 @@
 // expanded back, so a hop costs 2 SU(3) mat-vecs instead of 4. The link of a
 // direction is loaded once and used for all NB right-hand sides.
 //
-// Epilogues (A = (4+m) + i mu g5 + C is site-local; mu's sign is flipped by
-// the host for the adjoint, and C is hermitian):
+// Epilogues (A = (4+m) + i mu g5 + C is site-local, or (4+m) + i mu + C with the
+// scalar twist: the twisted mass is mu on chiral block 0 and mu1 = -mu or +mu on
+// block 1; both signs are flipped by the host for the adjoint, and C is hermitian):
 //   EPI_HOP   out = D psi
 //   EPI_AINV  out = A^{-1} D psi     (A^{-1} stored per site, or analytic without clover)
 //   EPI_XPAY  out = A y - D psi      (y: same-parity input; gives M = A - H and the
@@ -32,7 +33,8 @@ struct WilsonArgs {
     int has_clover;
     int gamma5_out = 0;     // multiply the result by g5 (negate spins 2, 3): the hermitian g5 D_w
     double m4;              // 4 + m
-    double mu;              // twisted mass, already negated for the adjoint
+    double mu;              // twisted mass on chiral block 0 (spins 0, 1), already negated for the adjoint
+    double mu1;             // the same on block 1 (spins 2, 3): -mu (i mu g5) or mu (scalar twist)
     int nrhs;
     df* norm_out;       // if non-null: per-block partial sums of |out|^2, per rhs
     FinArgs fin;        // with norm_out: the last block finalises the sums
@@ -652,15 +654,15 @@ __global__ void __launch_bounds__(256, MINB) wilson_dslash_kernel(WilsonArgs a) 
                 else
                     ainv_apply<P, NB, T>(a, s, acc, res);
             } else {
-                // A^{-1} = ((4+m) - i mu g5) / ((4+m)^2 + mu^2)
-                const T m4 = (T)a.m4, mu = (T)a.mu;
+                // A^{-1} = ((4+m) - i mu_b) / ((4+m)^2 + mu^2) on chiral block b
+                const T m4 = (T)a.m4, mu = (T)a.mu, mu1 = (T)a.mu1;
                 const T inv = (T)1 / (m4 * m4 + mu * mu);
 #pragma unroll
                 for (int b = 0; b < NB; b++)
 #pragma unroll
                     for (int sp = 0; sp < 4; sp++) {
-                        const T chi = sp < 2 ? (T)1 : (T)-1;
-                        const cx<T> f = mk(m4 * inv, -chi * mu * inv);
+                        const T mub = sp < 2 ? mu : mu1;
+                        const cx<T> f = mk(m4 * inv, -mub * inv);
 #pragma unroll
                         for (int cc = 0; cc < 3; cc++) res[b][sp][cc] = f * acc[b][sp][cc];
                     }
@@ -684,13 +686,12 @@ __global__ void __launch_bounds__(256, MINB) wilson_dslash_kernel(WilsonArgs a) 
                 }
                 to_spinor(v, yv[b]);
             }
-            const T m4 = (T)a.m4, mu = (T)a.mu;
+            const T m4 = (T)a.m4, mu = (T)a.mu, mu1 = (T)a.mu1;
 #pragma unroll
             for (int b = 0; b < NB; b++)
 #pragma unroll
                 for (int sp = 0; sp < 4; sp++) {
-                    const T chi = sp < 2 ? (T)1 : (T)-1;
-                    const cx<T> f = mk(m4, chi * mu);
+                    const cx<T> f = mk(m4, sp < 2 ? mu : mu1);
 #pragma unroll
                     for (int cc = 0; cc < 3; cc++) res[b][sp][cc] = f * yv[b][sp][cc] - acc[b][sp][cc];
                 }
@@ -750,12 +751,11 @@ __global__ void __launch_bounds__(256) wilson_ainv_site_kernel(WilsonArgs a) {
         if constexpr (P == PDF) ainv_apply_rows<P, T>(a, s, w[0], res[0]);
         else ainv_apply<P, 1, T>(a, s, w, res);
     } else {
-        const T m4 = (T)a.m4, mu = (T)a.mu;
+        const T m4 = (T)a.m4, mu = (T)a.mu, mu1 = (T)a.mu1;
         const T inv = (T)1 / (m4 * m4 + mu * mu);
 #pragma unroll
         for (int sp = 0; sp < 4; sp++) {
-            const T chi = sp < 2 ? (T)1 : (T)-1;
-            const cx<T> f = mk(m4 * inv, -chi * mu * inv);
+            const cx<T> f = mk(m4 * inv, -(sp < 2 ? mu : mu1) * inv);
 #pragma unroll
             for (int cc = 0; cc < 3; cc++) res[0][sp][cc] = f * w[0][sp][cc];
         }

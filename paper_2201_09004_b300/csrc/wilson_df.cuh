@@ -264,9 +264,9 @@ __global__ void __launch_bounds__(256, 2) wilson_dslash_df2_kernel(WilsonArgs a)
                 nrm = nrm + cnorm2(acc);
             }
         } else {
-            // A^{-1} = ((4+m) - i chi mu) / ((4+m)^2 + mu^2), chi = +1 on block 0, -1 on block 1
+            // A^{-1} = ((4+m) - i mu_h) / ((4+m)^2 + mu^2) on chiral block h (mu_0 = mu, mu_1 = mu1)
             const double inv = 1.0 / (a.m4 * a.m4 + a.mu * a.mu);
-            const cd f = mk(df(a.m4 * inv), df((h ? 1.0 : -1.0) * a.mu * inv));
+            const cd f = mk(df(a.m4 * inv), df(-(h ? a.mu1 : a.mu) * inv));
 #pragma unroll
             for (int i = 0; i < 6; i++) {
                 const cd o = f * w[i];
@@ -274,8 +274,8 @@ __global__ void __launch_bounds__(256, 2) wilson_dslash_df2_kernel(WilsonArgs a)
                 nrm = nrm + cnorm2(o);
             }
         }
-    } else {  // EPI_XPAY: out = ((4+m) + i chi mu + C) y - w on block h
-        const cd f = mk(df(a.m4), df((h ? -1.0 : 1.0) * a.mu));
+    } else {  // EPI_XPAY: out = ((4+m) + i mu_h + C) y - w on block h
+        const cd f = mk(df(a.m4), df(h ? a.mu1 : a.mu));
         // C block h: 6 real diagonal entries (3 chunks) then the 15 upper entries
         // (row-major, i < j); chunk (i, j) of row i is the diagonal pair for j == i.
         // The chunks of row i+1 are in flight while row i is computed.

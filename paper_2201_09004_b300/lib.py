@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(_HERE, "liblq.so")
 LQ_OK, LQ_EINVAL, LQ_ENOMEM, LQ_ENOTCONV, LQ_EBREAKDOWN, LQ_ENAN, LQ_EAGAIN, LQ_ETIMEOUT, LQ_ECUDA, LQ_EBUSY = range(10)
 F64, F32, F16, F32X2 = 0, 1, 2, 3
 R18, R12, R8 = 18, 12, 8
+TWIST_GAMMA5, TWIST_SCALAR = 0, 1
 THIN, FAT, LONG = 0, 1, 2
 HOST, DEVICE = 0, 1
 WILSON_TM, WILSON_TM_CLOVER, HISQ = 0, 1, 2
@@ -52,7 +53,8 @@ class LqError(RuntimeError):
 
 class OpParams(ctypes.Structure):
     _fields_ = [("action", ctypes.c_int), ("m", ctypes.c_double), ("mu", ctypes.c_double),
-                ("c_sw", ctypes.c_double), ("c_naik", ctypes.c_double), ("recon", ctypes.c_int)]
+                ("c_sw", ctypes.c_double), ("c_naik", ctypes.c_double), ("recon", ctypes.c_int),
+                ("twist_mode", ctypes.c_int)]
 
 
 class SolveParams(ctypes.Structure):
@@ -133,9 +135,10 @@ def _stream(stream):
     return ctypes.c_void_p(int(stream))
 
 
-def op_params(action, m, mu=0.0, c_sw=0.0, c_naik=-1.0 / 24.0, recon=0):
-    """recon: link compression of the operator-apply calls at F32 / F16 (0 = R12)."""
-    return OpParams(int(action), float(m), float(mu), float(c_sw), float(c_naik), int(recon))
+def op_params(action, m, mu=0.0, c_sw=0.0, c_naik=-1.0 / 24.0, recon=0, twist_mode=0):
+    """recon: link compression of the operator-apply calls at F32 / F16 (0 = R12).
+    twist_mode: TWIST_GAMMA5 (i mu g5) or TWIST_SCALAR (i mu)."""
+    return OpParams(int(action), float(m), float(mu), float(c_sw), float(c_naik), int(recon), int(twist_mode))
 
 
 def solve_params(solver=MIXED_CGNR, tol=1e-10, delta=0.1, maxiter=100000, prec_sloppy=F32, recon_sloppy=R12,

@@ -69,3 +69,28 @@ def test_null_handles_and_bad_arguments_are_rejected_without_gpu():
     assert L.lq_tune_force(-1) == lib.LQ_EINVAL
     assert L.lq_tune_force(0) == lib.LQ_OK
     assert L.lq_lattice_release_workspace(None, None) == lib.LQ_EINVAL
+
+
+def test_ctypes_structures_match_the_header_layout(tmp_path):
+    """Every struct the binding marshals has the header's size and field offsets
+    (a C program compiled against include/lq.h prints them)."""
+    import subprocess
+    from paper_2201_09004_b300 import lib
+    structs = {"lq_op_params": lib.OpParams, "lq_solve_params": lib.SolveParams, "lq_solve_info": lib.SolveInfo,
+               "lq_sign_info": lib.SignInfo, "lq_request": lib.Request, "lq_request_times": lib.RequestTimes}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "lq.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l}
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
