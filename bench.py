@@ -293,6 +293,26 @@ def gpu_arm(args):
                 "reliable_updates": ib[0]["reliable_updates"], "operator_applications": ib[0]["operator_applications"],
                 "true_rel_residual": ib[0]["true_rel_residual"], "speedup_over_mixed_cgnr": round(1.0 / (sb * value / world), 2)}
 
+    # mixed-precision restarted GCR directly on the Schur operator (same system and tolerance)
+    gcr = None
+    if args.gcr_steps > 0:
+        spg = lib.solve_params(solver=lib.GCR, tol=TOL, delta=0.1, prec_sloppy=args.prec, recon_sloppy=args.recon,
+                               restart=args.gcr_restart)
+        lat.solve(op, spg, [b], stream=stream, out=[x])
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ig = None
+        for _ in range(args.gcr_steps):
+            _, ig = lat.solve(op, spg, [b], stream=stream, out=[x])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sg = e0.elapsed_time(e1) * 1e-3 / args.gcr_steps
+        gcr = {"solves_per_s": round(1.0 / sg, 3), "iters": ig[0]["iters"], "restart": args.gcr_restart or 12,
+               "defect_corrections": ig[0]["reliable_updates"], "operator_applications": ig[0]["operator_applications"],
+               "true_rel_residual": ig[0]["true_rel_residual"], "speedup_over_mixed_cgnr": round(1.0 / (sg * value / world), 2)}
+
     # end to end through the C ABI with pinned host buffers
     bh = b.cpu().pin_memory()
     xh = torch.empty_like(bh).pin_memory()
@@ -324,7 +344,7 @@ def gpu_arm(args):
             "latency_ms": {"p50": round(float(np.percentile(lat_ms, 50)), 3),
                            "p99": round(float(np.percentile(lat_ms, 99)), 3)},
             "roofline": roofline, "kernels": per_kernel, "time_breakdown": breakdown, "fp64": fp64,
-            "bicgstab": bicg, "e2e": e2e,
+            "bicgstab": bicg, "gcr": gcr, "e2e": e2e,
             "gpu_launches": int(launches), "clocks": clocks,
         }
         if not args.no_cpu_baseline:
@@ -735,6 +755,60 @@ def run_overlap(args):
     print(json.dumps(line), flush=True)
 
 
+def run_eigen(args):
+    """Low modes of H_w = g5 D_w(-rho) on 24^3x64 (the RBC11 shape of the paper's
+    overlap eigensolver runs, Sec. 2.3), rho = 1.5: the Chebyshev-filtered
+    thick-restart Arnoldi eigensolver to |H_w z - lambda z| <= tol, then the sign
+    function on one vector with those modes deflated against the same function
+    without deflation (lambda_min below the lowest mode), both in double-float."""
+    import torch
+    from paper_2201_09004_b300 import lib, synth
+    torch.cuda.set_device(0)
+    dims, rho, lmax = DIMS, 1.5, 10.5
+    U = synth.thin_links(dims, GAUGE_SEED, device="cuda")
+    lat = lib.Lattice(dims)
+    lat.load_gauge(lib.THIN, U)
+    del U
+    v = synth.gaussian_field(dims, 209, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ev, Z, info = lat.hw_eigensolve(rho, args.nev, args.lambda_cut, lmax, tol=args.eig_tol, nkv=args.nkv,
+                                    degree=args.degree, max_restarts=args.max_restarts, like=v, check=False)
+    torch.cuda.synchronize()
+    t_eig = time.perf_counter() - t0
+    lmin_defl = float(np.max(np.abs(ev)))
+    lmin_plain = 0.95 * float(np.min(np.abs(ev)))
+    e0, e1 = _events()
+    e0.record()
+    sd, infod = lat.overlap_sign_apply_deflated(rho, lmin_defl, lmax, 1e-8, ev, Z, v)
+    e1.record()
+    torch.cuda.synchronize()
+    t_defl = e0.elapsed_time(e1) * 1e-3
+    e0, e1 = _events()
+    e0.record()
+    sp, infop = lat.overlap_sign_apply(rho, lmin_plain, lmax, 1e-8, v, prec=lib.F32X2)
+    e1.record()
+    torch.cuda.synchronize()
+    t_plain = e0.elapsed_time(e1) * 1e-3
+    diff = float(torch.linalg.vector_norm(sd - sp) / torch.linalg.vector_norm(sp))
+    line = {"workload": "eigen",
+            "metric": "time to the nev lowest eigenpairs of g5 D_w(-rho), and the deflated sign function",
+            "value": round(info["seconds"], 3), "unit": "s", "higher_is_better": False,
+            "config": {"dims": list(dims), "rho": rho, "nev": args.nev, "nkv": args.nkv, "degree": args.degree,
+                       "lambda_cut": args.lambda_cut, "lambda_max": lmax, "tol": args.eig_tol,
+                       "gauge_seed": GAUGE_SEED, "precision": "double-float"},
+            "eigensolver": {"converged": info["converged"], "restarts": info["restarts"],
+                            "hw_applications": info["operator_applications"], "max_residual": info["max_residual"],
+                            "wall_s": round(t_eig, 3), "abs_lambda_range": [float(np.min(np.abs(ev))), lmin_defl],
+                            "evals": [round(float(x), 10) for x in ev]},
+            "sign_function": {"deflated": {"seconds": round(t_defl, 3), "order": infod["order"],
+                                           "lambda_min": lmin_defl},
+                              "plain": {"seconds": round(t_plain, 3), "order": infop["order"],
+                                        "lambda_min": lmin_plain},
+                              "relative_difference": diff, "deviation_bound": 1e-8}}
+    print(json.dumps(line), flush=True)
+
+
 def run_serving(args):
     """Poisson stream of solve requests (sizes 8^3x16, 16^3x32, 24^3x64, 32^3x64; twisted-mass
     clover with 12 point sources, or HISQ with one Z2 source; masses drawn from [0.005, 0.05];
@@ -811,10 +885,32 @@ def run_serving(args):
         srv.close()
         return (np.array([done[t][0] for t in tickets]), wall, [done[t][1] for t in tickets])
 
+    def serve_fifo(reqs, arrivals):
+        """The FP64 comparator: one request at a time in arrival order. Request i is
+        submitted once it has arrived and request i-1 has finished (the queue waits
+        on the client, so it holds no copies of sources in the server); its latency
+        is that wait plus the server's submit-to-finish time."""
+        srv = lib.Server(200 << 30, 1)
+        t_start = time.perf_counter()
+        lat_s, statuses = [], []
+        for (si, g, kind, mass), ta in zip(reqs, arrivals):
+            while time.perf_counter() - t_start < ta:
+                time.sleep(0.0005)
+            op, sp = params(kind, mass, True)
+            queued = time.perf_counter() - t_start - ta
+            t = srv.submit(lats[(si, g)], op, sp, srcs[(si, kind)])
+            srv.wait(t, 3600 * 1000)
+            _, info, times, code = srv.poll(t)
+            lat_s.append(queued + times["finished"] - times["submitted"])
+            statuses.append(code)
+        wall = time.perf_counter() - t_start
+        srv.close()
+        return np.array(lat_s), wall, statuses
+
     # warm-up (tuning, clover inverses) on one request of every (size, kind)
     warm = [(si, 0, k, 0.02) for si in range(len(sizes)) for k in ("tmc", "hisq")]
     serve(warm, [0.0] * len(warm), False, 1)
-    serve(warm[:2], [0.0] * 2, True, 1)
+    serve_fifo(warm[:2], [0.0] * 2)
     # capacity of the mixed server: back-to-back service of a calibration batch
     calib = make_requests(16)
     _, wall_c, _ = serve(calib, [0.0] * len(calib), False, 4)
@@ -824,7 +920,7 @@ def run_serving(args):
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))
     arrivals -= arrivals[0]
     lat_mixed, wall_mixed, st_mixed = serve(reqs, arrivals, False, 4)
-    lat_fifo, wall_fifo, st_fifo = serve(reqs, arrivals, True, 1)
+    lat_fifo, wall_fifo, st_fifo = serve_fifo(reqs, arrivals)
     ms = lambda a, q: round(float(np.percentile(a, q)) * 1e3, 1)
     line = {"workload": "serving", "metric": "p50/p99 request latency and solves/s on a Poisson trace",
             "requests": len(reqs), "rate_per_s": round(rate, 3), "capacity_calibration_per_s": round(capacity, 3),
@@ -915,9 +1011,18 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=8)
     ap.add_argument("--bicgstab-steps", type=int, default=3,
                     help="also time the mixed-precision BiCGStab solve of the same system")
+    ap.add_argument("--gcr-steps", type=int, default=3,
+                    help="also time the mixed-precision restarted GCR solve of the same system")
+    ap.add_argument("--gcr-restart", type=int, default=0, help="GCR directions before a restart (0 = 12)")
     ap.add_argument("--ref-iters", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="tmc", choices=["tmc", "multirhs", "hisq", "serving", "dslash", "hisq3col", "overlap", "tmms"],
+    ap.add_argument("--nev", type=int, default=2, help="eigen: low modes wanted")
+    ap.add_argument("--nkv", type=int, default=24, help="eigen: Krylov basis size")
+    ap.add_argument("--degree", type=int, default=64, help="eigen: Chebyshev filter degree")
+    ap.add_argument("--lambda-cut", type=float, default=0.53, help="eigen: filter edge")
+    ap.add_argument("--eig-tol", type=float, default=1e-8, help="eigen: residual bound")
+    ap.add_argument("--max-restarts", type=int, default=30, help="eigen: restart limit")
+    ap.add_argument("--workload", default="tmc", choices=["tmc", "multirhs", "hisq", "serving", "dslash", "hisq3col", "overlap", "tmms", "eigen"],
                     help="tmc: 24^3x64 twisted-mass clover (default, the headline); multirhs: 32^3x96, "
                          "36 right-hand sides; hisq: 48^3x144 multi-shift; serving: Poisson request stream; "
                          "dslash: the operator kernels alone; hisq3col: HISQ 3-column propagator 24^3x64; "
@@ -944,6 +1049,8 @@ def main():
         run_twisted_multimass(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif args.workload == "eigen":
+        run_eigen(args)
     else:
         gpu_arm(args)
 

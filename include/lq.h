@@ -92,7 +92,7 @@ typedef enum { LQ_WILSON_TM = 0, LQ_WILSON_TM_CLOVER = 1, LQ_HISQ = 2 } lq_actio
 /* The paper's complex mass m_cri + omega (Sec. 2.1 Eq. 1) read as the twisted mass
  * i mu g5 (default), or literally as the scalar i mu. */
 typedef enum { LQ_TWIST_GAMMA5 = 0, LQ_TWIST_SCALAR = 1 } lq_twist;
-typedef enum { LQ_CGNR = 0, LQ_MIXED_CGNR = 1, LQ_MULTISHIFT_CG = 2, LQ_BICGSTAB = 3 } lq_solver;
+typedef enum { LQ_CGNR = 0, LQ_MIXED_CGNR = 1, LQ_MULTISHIFT_CG = 2, LQ_BICGSTAB = 3, LQ_GCR = 4 } lq_solver;
 typedef enum { LQ_OP_FULL = 0, LQ_OP_SCHUR = 1 } lq_op_form;
 typedef enum { LQ_WILSON_FIELD = 0, LQ_STAGGERED_FIELD = 1 } lq_field_kind;
 typedef enum { LQ_EVEN = 0, LQ_ODD = 1 } lq_parity;
@@ -128,6 +128,14 @@ typedef struct {
  *                     FP64 reliable updates as LQ_MIXED_CGNR (delta; none for
  *                     prec_sloppy = LQ_F64). A vanishing BiCGStab denominator ends
  *                     that right-hand side with LQ_EBREAKDOWN.
+ *   LQ_GCR:           Wilson actions; restarted GCR (generalised conjugate
+ *                     residual: each new direction is the current residual, its
+ *                     image under the operator made orthogonal to the earlier
+ *                     ones) directly on the even-odd Schur operator, in
+ *                     prec_sloppy, keeping `restart` directions (0 = 12, at most
+ *                     16); at every restart, and whenever the residual fell below
+ *                     delta times its value at the last restart, the solution is
+ *                     accumulated and the residual recomputed in FP64 accuracy.
  *   LQ_MULTISHIFT_CG: HISQ only; one Krylov space for all nshift masses
  *                     masses[0..nshift-1] (ascending) in prec_sloppy, then each
  *                     mass refined by the mixed-precision CG; x gets nrhs*nshift
@@ -144,6 +152,7 @@ typedef struct {
     const double* masses;
     int graph_iters;  /* Krylov iterations captured per CUDA graph and replayed with one
                          launch: 0 = the library's choice (1), < 0 = no graphs */
+    int restart;      /* LQ_GCR: directions kept before a restart (0 = 12, at most 16) */
 } lq_solve_params;
 
 typedef struct {
@@ -320,11 +329,50 @@ int lq_chebyshev_sign(double eps, double delta, int max_order, double* coeffs, i
  * evaluated by the Clenshaw recurrence (two H_w applications per term). lambda_max
  * must bound the spectrum (|4 - rho| + 8 always does: eight hops of norm one);
  * outside [-lambda_max, lambda_max] the polynomial grows without bound. The paper
- * projects out the lowest modes first (eigenvectors, not built here); the caller
- * chooses lambda_min below the spectrum it passes. info (may be NULL) gets the
- * order and the deviation bound. */
+ * projects out the lowest modes first (lq_overlap_sign_apply_deflated); here the
+ * caller chooses lambda_min below the spectrum it passes. info (may be NULL) gets
+ * the order and the deviation bound. */
 int lq_overlap_sign_apply(lq_lattice lat, double rho, double lambda_min, double lambda_max, double delta, int prec,
                           int loc, const double* in, double* out, lq_sign_info* info, void* stream);
+
+/* Low modes of H_w (Sec. 2.3, the eigensolver of the overlap operator): the nev
+ * eigenpairs with the smallest |lambda|. A Chebyshev polynomial T_d of
+ * w(H_w^2) = (2 H_w^2 - a - b)/(b - a), [a, b] = [lambda_cut^2, lambda_max^2], keeps
+ * the eigenvectors and makes the modes below lambda_cut the largest eigenvalues;
+ * a thick-restart Arnoldi iteration (full re-orthogonalisation) finds them, and a
+ * Rayleigh-Ritz step with H_w itself gives the eigenvalues (with their sign) and
+ * checks |H_w z - lambda z| <= tol. Arithmetic in double-float (FP64 accuracy). */
+typedef struct {
+    int nev;            /* eigenpairs wanted, 1..48 */
+    int nkv;            /* Krylov basis size, nev + 2 .. 64 (0 = min(2 nev + 8, 64)) */
+    int degree;         /* degree of the Chebyshev filter, rounded up to even (0 = 24) */
+    double lambda_cut;  /* filter edge: above the nev-th |lambda|, below lambda_max */
+    double lambda_max;  /* bound on |H_w| (|4 - rho| + 8 always is one) */
+    double tol;         /* absolute residual bound on |H_w z - lambda z| (|z| = 1) */
+    int max_restarts;   /* 0 = 100 */
+} lq_eig_params;
+
+typedef struct {
+    int converged;               /* 1 if every residual met tol */
+    int restarts;
+    int operator_applications;   /* H_w applications */
+    double max_residual;
+    double seconds;
+} lq_eig_info;
+
+/* evals (host, nev) in ascending |lambda|; evecs (may be NULL): nev canonical FP64
+ * full-lattice Wilson spinors (host or device per loc), unit norm, each fixed up to
+ * a phase. LQ_ENOTCONV if max_restarts passed first (the best pairs are returned). */
+int lq_hw_eigensolve(lq_lattice lat, double rho, const lq_eig_params* p, int loc, double* evals, double* const* evecs,
+                     lq_eig_info* info, void* stream);
+
+/* lq_overlap_sign_apply deflated by nev eigenpairs of H_w (evals and unit evecs as
+ * lq_hw_eigensolve returns them, in the canonical layout per loc): their part of
+ * in gets its exact sign, the polynomial acts on the rest, so lambda_min only has
+ * to lie below the remaining spectrum. Computed in double-float. */
+int lq_overlap_sign_apply_deflated(lq_lattice lat, double rho, double lambda_min, double lambda_max, double delta,
+                                   int nev, const double* evals, const double* const* evecs, int loc,
+                                   const double* in, double* out, lq_sign_info* info, void* stream);
 
 /* ----------------------------------------------------------------- serving */
 

@@ -318,3 +318,36 @@ def overlap_sign(hw, v, lambda_min, lambda_max, coeffs):
         return (2.0 * hw(hw(w)) / lambda_max ** 2 - (a + b) * w) / (b - a)
     pv = clenshaw(coeffs, v, matvec=Z)
     return hw(pv) / lambda_max
+
+
+def hermitian_wilson_dense(dims, U, rho, bc_t=-1):
+    """The matrix of v -> g5 D_w(-rho) v in the canonical ordering (site-major,
+    spin, colour), built column by column from unit vectors (small lattices)."""
+    hw = hermitian_wilson(dims, U, rho, bc_t)
+    lx, ly, lz, lt = dims
+    n = lx * ly * lz * lt * 12
+    H = np.empty((n, n), dtype=np.complex128)
+    e = np.zeros(n, dtype=np.complex128)
+    for j in range(n):
+        e[j] = 1.0
+        H[:, j] = hw(e.reshape(lt, lz, ly, lx, 4, 3)).ravel()
+        e[j] = 0.0
+    return H
+
+
+def hw_low_modes(dims, U, rho, nev, bc_t=-1):
+    """The nev eigenpairs of g5 D_w(-rho) with the smallest |lambda| (the target of
+    the eigensolver of Sec. 2.3), by a dense hermitian eigendecomposition: (evals
+    in ascending |lambda|, evecs as canonical spinors, the whole spectrum ascending)."""
+    H = hermitian_wilson_dense(dims, U, rho, bc_t)
+    w, Z = np.linalg.eigh(H)
+    idx = np.argsort(np.abs(w), kind="stable")[:nev]
+    lx, ly, lz, lt = dims
+    return w[idx], [Z[:, i].reshape(lt, lz, ly, lx, 4, 3) for i in idx], w
+
+
+def sign_exact(dims, U, rho, v, bc_t=-1):
+    """eps(H_w) v from the dense eigendecomposition: Z sign(Lambda) Z^+ v."""
+    H = hermitian_wilson_dense(dims, U, rho, bc_t)
+    w, Z = np.linalg.eigh(H)
+    return (Z @ (np.sign(w) * (Z.conj().T @ v.ravel()))).reshape(v.shape)

@@ -454,6 +454,110 @@ __global__ void caxpy_h_kernel(FieldV y, FieldV x, HostScalars h) {
     }
 }
 
+// ------------------------------------------------------- GCR and Gram-Schmidt
+// partial (re, im) of <v_i, w> = sum conj(v_i) w for i = blockIdx.z; the fields v_i
+// are listed in device memory; part[((k * nv + i) * 2 + c) * gridDim.x + block]
+template <int P, int NR>
+__global__ void cdot_multi_kernel(const FieldV* vs, FieldV w, df* part) {
+    typedef typename RealT<P>::T T;
+    const int k = blockIdx.y, i = blockIdx.z;
+    const FieldV a = vs[i];
+    df acc[2] = {df(0.f), df(0.f)};
+    SITE_LOOP(w.vh) {
+        T va[NR], vw[NR];
+        fload<P, NR, T>(a, k, s, va);
+        fload<P, NR, T>(w, k, s, vw);
+        T re = (T)0, im = (T)0;
+#pragma unroll
+        for (int j = 0; j < NR / 2; j++) {
+            re = fma(va[2 * j], vw[2 * j], re);
+            re = fma(va[2 * j + 1], vw[2 * j + 1], re);
+            im = fma(va[2 * j], vw[2 * j + 1], im);
+            im = fma(-va[2 * j + 1], vw[2 * j], im);
+        }
+        acc[0] = acc[0] + df_of(re);
+        acc[1] = acc[1] + df_of(im);
+    }
+#pragma unroll
+    for (int c = 0; c < 2; c++) {
+        const df r = block_sum_df(acc[c]);
+        if (threadIdx.x == 0) part[((size_t)(k * gridDim.z + i) * 2 + c) * gridDim.x + blockIdx.x] = r;
+    }
+}
+
+// q_j -= sum_{i<j} c_i q_i and p_j -= sum_{i<j} c_i p_i (ps may be null: q only),
+// c_i = coef[(k * cstride + i) * 2 + {0, 1}]
+template <int P, int NR>
+__global__ void gcr_orth_kernel(const FieldV* qs, const FieldV* ps, int j, const double* coef, int cstride) {
+    typedef typename RealT<P>::T T;
+    const int k = blockIdx.y;
+    const FieldV qj = qs[j];
+    const FieldV pj = ps ? ps[j] : qj;
+    SITE_LOOP(qj.vh) {
+        T vq[NR], vp[NR];
+        fload<P, NR, T>(qj, k, s, vq);
+        if (ps) fload<P, NR, T>(pj, k, s, vp);
+        for (int i = 0; i < j; i++) {
+            const double* ci = coef + ((size_t)k * cstride + i) * 2;
+            const cx<T> c = mk((T)__ldg(ci), (T)__ldg(ci + 1));
+            T a[NR];
+            fload<P, NR, T>(qs[i], k, s, a);
+#pragma unroll
+            for (int q = 0; q < NR / 2; q++) {
+                const cx<T> o = ld_c(vq, q) - c * ld_c(a, q);
+                vq[2 * q] = o.r;
+                vq[2 * q + 1] = o.i;
+            }
+            if (!ps) continue;
+            fload<P, NR, T>(ps[i], k, s, a);
+#pragma unroll
+            for (int q = 0; q < NR / 2; q++) {
+                const cx<T> o = ld_c(vp, q) - c * ld_c(a, q);
+                vp[2 * q] = o.r;
+                vp[2 * q + 1] = o.i;
+            }
+        }
+        fstore<P, NR, T>(qj, k, s, vq);
+        if (ps) fstore<P, NR, T>(pj, k, s, vp);
+    }
+}
+
+// x += a p, r -= a q, partial |r|^2 (part[k * gridDim.x + block]); a = alpha[2k] + i alpha[2k+1]
+template <int PX, int P, int NR>
+__global__ void gcr_xr_kernel(FieldV x, FieldV p, FieldV r, FieldV q, const double* alpha, df* part) {
+    typedef typename RealT<P>::T T;
+    typedef typename MathT<PX, P>::T TX;
+    const int k = blockIdx.y;
+    const cx<TX> ax = mk((TX)__ldg(alpha + 2 * k), (TX)__ldg(alpha + 2 * k + 1));
+    const cx<T> a = mk((T)__ldg(alpha + 2 * k), (T)__ldg(alpha + 2 * k + 1));
+    df acc(0.f);
+    SITE_LOOP(x.vh) {
+        T vp[NR], vr[NR], vq[NR];
+        TX vx[NR];
+        fload<P, NR, T>(p, k, s, vp);
+        fload<P, NR, T>(r, k, s, vr);
+        fload<P, NR, T>(q, k, s, vq);
+        fload<PX, NR, TX>(x, k, s, vx);
+        T rr = (T)0;
+#pragma unroll
+        for (int j = 0; j < NR / 2; j++) {
+            const cx<TX> ox = mk(vx[2 * j], vx[2 * j + 1]) + ax * mk((TX)vp[2 * j], (TX)vp[2 * j + 1]);
+            vx[2 * j] = ox.r;
+            vx[2 * j + 1] = ox.i;
+            const cx<T> orr = ld_c(vr, j) - a * ld_c(vq, j);
+            vr[2 * j] = orr.r;
+            vr[2 * j + 1] = orr.i;
+            rr = fma(orr.r, orr.r, rr);
+            rr = fma(orr.i, orr.i, rr);
+        }
+        fstore<PX, NR, TX>(x, k, s, vx);
+        fstore<P, NR, T>(r, k, s, vr);
+        acc = acc + df_of(rr);
+    }
+    const df t = block_sum_df(acc);
+    if (threadIdx.x == 0) part[(size_t)k * gridDim.x + blockIdx.x] = t;
+}
+
 // ---------------------------------------------------------------- launchers
 static dim3 red_grid(int nrhs) { return dim3(RED_BLOCKS, nrhs); }
 static dim3 upd_grid(int vh, int nrhs) {
@@ -697,6 +801,44 @@ void blas_cg_p(Field& p, const Field& r, const double* sc, cudaStream_t st) {
 
 void blas_finalize(const df* part, int nblocks, int nrhs, double* sc, int slot, int op, cudaStream_t st) {
     launch("blas_finalize", finalize_kernel, dim3(nrhs), dim3(256), st, part, nblocks, sc, slot, op);
+}
+
+void blas_cdot_multi(const FieldV* vs_dev, int nv, const Field& w, df* part, cudaStream_t st) {
+    dim3 g(RED_BLOCKS, w.nrhs, nv);
+#define K(NR) cdot_multi_kernel<P_, NR>
+#define L(P) { constexpr int P_ = P; BY_KIND(w, "blas_multi_dots", K, g, vs_dev, w.view(), part); }
+    DISPATCH_P(w.prec, L);
+#undef L
+#undef K
+}
+
+void blas_gcr_orth(const FieldV* qs_dev, const FieldV* ps_dev, int j, const double* coef_dev, int cstride,
+                   const Field& like, cudaStream_t st) {
+    dim3 g = upd_grid(like.vh, like.nrhs);
+#define K(NR) gcr_orth_kernel<P_, NR>
+#define L(P) { constexpr int P_ = P; BY_KIND(like, "blas_orth", K, g, qs_dev, ps_dev, j, coef_dev, cstride); }
+    DISPATCH_P(like.prec, L);
+#undef L
+#undef K
+}
+
+template <int PX>
+static void gcr_xr_from(Field& x, const Field& p, Field& r, const Field& q, const double* alpha, df* part,
+                        cudaStream_t st) {
+#define K(NR) gcr_xr_kernel<PX, P_, NR>
+#define L(P) { constexpr int P_ = P; BY_KIND(x, "blas_gcr_xr", K, red_grid(x.nrhs), x.view(), p.view(), r.view(), q.view(), alpha, part); }
+    DISPATCH_P(p.prec, L);
+#undef L
+#undef K
+}
+
+void blas_gcr_xr(Field& x, const Field& p, Field& r, const Field& q, const double* alpha_dev, df* part,
+                 cudaStream_t st) {
+    if (p.prec != r.prec || p.prec != q.prec) fail(LQ_EINVAL, "blas_gcr_xr: precision mismatch");
+    if (x.prec == LQ_F64) gcr_xr_from<P64>(x, p, r, q, alpha_dev, part, st);
+    else if (x.prec == LQ_F32) gcr_xr_from<P32>(x, p, r, q, alpha_dev, part, st);
+    else if (x.prec == LQ_F16) gcr_xr_from<P16>(x, p, r, q, alpha_dev, part, st);
+    else gcr_xr_from<PDF>(x, p, r, q, alpha_dev, part, st);
 }
 
 }  // namespace lq

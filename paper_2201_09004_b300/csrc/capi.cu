@@ -554,3 +554,111 @@ extern "C" int lq_overlap_sign_apply(lq_lattice h, double rho, double lambda_min
     return LQ_OK;
     LQ_CATCH
 }
+
+extern "C" int lq_hw_eigensolve(lq_lattice h, double rho, const lq_eig_params* p, int loc, double* evals,
+                                double* const* evecs, lq_eig_info* info, void* stream) {
+    LQ_TRY
+    check_lattice(h);
+    if (!p || !evals) fail(LQ_EINVAL, "null argument");
+    if (loc != LQ_HOST && loc != LQ_DEVICE) fail(LQ_EINVAL, "loc must be LQ_HOST or LQ_DEVICE");
+    Lattice& L = h->lat;
+    if (!L.canon[LQ_THIN]) fail(LQ_EINVAL, "thin gauge field not loaded");
+    cudaStream_t st = as_stream(stream);
+    cudaEvent_t e0, e1;
+    LQ_CUDA(cudaEventCreate(&e0));
+    LQ_CUDA(cudaEventCreate(&e1));
+    LQ_CUDA(cudaEventRecord(e0, st));
+    std::vector<double> ev;
+    std::vector<Field> vecs;
+    lq_eig_info inf{};
+    try {
+        hw_eigensolve(L, rho, *p, ev, vecs, inf, st);
+        LQ_CUDA(cudaEventRecord(e1, st));
+        if (evecs) {
+            const size_t bytes = field_canon_bytes(L, LQ_WILSON_TM);
+            DevBuf bout(loc == LQ_HOST ? bytes : 0, &L, st);
+            for (int i = 0; i < p->nev; i++) {
+                if (!evecs[i]) continue;
+                double* dout = loc == LQ_HOST ? (double*)bout.p : evecs[i];
+                export_full(L, vecs[i], dout, st);
+                if (loc == LQ_HOST) LQ_CUDA(cudaMemcpyAsync(evecs[i], dout, bytes, cudaMemcpyDeviceToHost, st));
+                LQ_CUDA(cudaStreamSynchronize(st));
+            }
+        }
+        LQ_CUDA(cudaStreamSynchronize(st));
+    } catch (...) {
+        for (auto& f : vecs) ws_put(L, f.data, st);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        throw;
+    }
+    for (auto& f : vecs) ws_put(L, f.data, st);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    inf.seconds = ms * 1e-3;
+    for (int i = 0; i < p->nev; i++) evals[i] = ev[i];
+    if (info) *info = inf;
+    if (!inf.converged) {
+        set_last_error("lq_hw_eigensolve: max_restarts reached before every residual met tol");
+        return LQ_ENOTCONV;
+    }
+    return LQ_OK;
+    LQ_CATCH
+}
+
+extern "C" int lq_overlap_sign_apply_deflated(lq_lattice h, double rho, double lambda_min, double lambda_max,
+                                              double delta, int nev, const double* evals,
+                                              const double* const* evecs, int loc, const double* in, double* out,
+                                              lq_sign_info* info, void* stream) {
+    LQ_TRY
+    check_lattice(h);
+    if (!in || !out) fail(LQ_EINVAL, "null field");
+    if (nev < 0 || nev > 64 || (nev > 0 && (!evals || !evecs))) fail(LQ_EINVAL, "need nev in [0, 64] eigenpairs");
+    if (loc != LQ_HOST && loc != LQ_DEVICE) fail(LQ_EINVAL, "loc must be LQ_HOST or LQ_DEVICE");
+    if (!(lambda_max > 0.0) || !(lambda_min > 0.0) || !(lambda_min < lambda_max))
+        fail(LQ_EINVAL, "need 0 < lambda_min < lambda_max");
+    Lattice& L = h->lat;
+    if (!L.canon[LQ_THIN]) fail(LQ_EINVAL, "thin gauge field not loaded");
+    for (int i = 0; i < nev; i++)
+        if (!evecs[i]) fail(LQ_EINVAL, "null eigenvector");
+    std::vector<double> c;
+    double dev = 0.0;
+    sign_coefficients(lambda_min / lambda_max, delta, 1 << 16, c, dev);
+    cudaStream_t st = as_stream(stream);
+    const size_t bytes = field_canon_bytes(L, LQ_WILSON_TM);
+    DevBuf bin(loc == LQ_HOST ? bytes : 0, &L, st), bout(loc == LQ_HOST ? bytes : 0, &L, st);
+    std::vector<Field> held;
+    try {
+        std::vector<Field> vecs;
+        std::vector<double> ev(evals, evals + nev);
+        for (int i = 0; i < nev; i++) {
+            Field f = ws_field(L, LQ_WILSON_FIELD, LQ_F32X2, 2, st);
+            held.push_back(f);
+            import_full(L, f, stage_in(evecs[i], bytes, loc, bin, st), st);
+            vecs.push_back(f);
+        }
+        Field fi = ws_field(L, LQ_WILSON_FIELD, LQ_F32X2, 2, st);
+        held.push_back(fi);
+        Field fo = ws_field(L, LQ_WILSON_FIELD, LQ_F32X2, 2, st);
+        held.push_back(fo);
+        import_full(L, fi, stage_in(in, bytes, loc, bin, st), st);
+        sign_apply_deflated(L, rho, lambda_max, lambda_min / lambda_max, c, ev, vecs, fi, fo, st);
+        double* dout = loc == LQ_HOST ? (double*)bout.p : out;
+        export_full(L, fo, dout, st);
+        if (loc == LQ_HOST) LQ_CUDA(cudaMemcpyAsync(out, dout, bytes, cudaMemcpyDeviceToHost, st));
+        LQ_CUDA(cudaStreamSynchronize(st));
+    } catch (...) {
+        for (auto& f : held) ws_put(L, f.data, st);
+        throw;
+    }
+    for (auto& f : held) ws_put(L, f.data, st);
+    if (info) {
+        info->order = (int)c.size();
+        info->max_deviation = dev;
+    }
+    return LQ_OK;
+    LQ_CATCH
+}
+

@@ -245,6 +245,7 @@ void wilson_ainv_site(Lattice& lat, const OpDesc& op, int parity, int dagger, co
 // All BLAS kernels work on whole fields of one parity, per right-hand side.
 // Reductions write per-block partials to `part`, then finalize into dev scalars.
 enum { RED_BLOCKS = 148 * 4, RED_THREADS = 256 };
+enum { GCR_MAX = 16, GCR_DEFAULT = 12 };  // directions kept by the GCR solver before a restart
 void blas_norm2(const Field& x, df* part, cudaStream_t st, const FinArgs& fin = FinArgs());          // part[k*RED_BLOCKS + b]
 void blas_copy(Field& dst, const Field& src, cudaStream_t st);           // with precision conversion
 void blas_zero(Field& x, cudaStream_t st);
@@ -279,6 +280,16 @@ void blas_cg_p_norm(Field& p, const Field& r, const double* sc, df* part, cudaSt
 // p = r + beta p, beta_k = sc[k*SC_N + SC_BETA]
 void blas_cg_p(Field& p, const Field& r, const double* sc, cudaStream_t st);
 
+// GCR and Gram-Schmidt steps. Partials of <v_i, w> (i < nv, fields listed in device
+// memory) at part[((k * nv + i) * 2 + re/im) * RED_BLOCKS + block]; q_j -= sum_{i<j} c_i q_i
+// and p_j -= sum_{i<j} c_i p_i (ps_dev null: q only) with c_i = coef[(k * cstride + i) * 2 +
+// re/im] (device); x += a_k p, r -= a_k q with partial |r|^2 at part[k * RED_BLOCKS + block]
+void blas_cdot_multi(const FieldV* vs_dev, int nv, const Field& w, df* part, cudaStream_t st);
+void blas_gcr_orth(const FieldV* qs_dev, const FieldV* ps_dev, int j, const double* coef_dev, int cstride,
+                   const Field& like, cudaStream_t st);
+void blas_gcr_xr(Field& x, const Field& p, Field& r, const Field& q, const double* alpha_dev, df* part,
+                 cudaStream_t st);
+
 // sum part[k*nblocks ...] (compensated, fixed order) into sc[k*SC_N + slot], or apply `op`
 void blas_finalize(const df* part, int nblocks, int nrhs, double* sc, int slot, int op, cudaStream_t st);
 
@@ -296,6 +307,14 @@ void sign_coefficients(double eps, double delta, int max_order, std::vector<doub
 void hw_apply_full(Lattice& lat, double rho, const Field& in, Field& out, cudaStream_t st);
 void sign_apply(Lattice& lat, double rho, double lmax, double eps, const std::vector<double>& c, const Field& v,
                 Field& out, cudaStream_t st);
+// low modes of H_w (eigen.cu): nev eigenvalues (ascending |lambda|) and double-float
+// full-lattice eigenvectors in fields from the workspace cache (the caller returns them)
+void hw_eigensolve(Lattice& lat, double rho, const lq_eig_params& p, std::vector<double>& evals,
+                   std::vector<Field>& evecs, lq_eig_info& info, cudaStream_t st);
+// eps(H_w) v with the eigenvectors projected out of the polynomial's argument (double-float fields)
+void sign_apply_deflated(Lattice& lat, double rho, double lmax, double eps, const std::vector<double>& c,
+                         const std::vector<double>& evals, const std::vector<Field>& evecs, const Field& v, Field& out,
+                         cudaStream_t st);
 // estimated device bytes of a solve's work fields
 size_t solve_workspace_bytes(const Lattice& lat, const lq_op_params& op, const lq_solve_params& sp, int nrhs);
 // x0 (optional, device canonical): initial guesses whose even sites start the even-odd CGNR

@@ -11,6 +11,7 @@
 #include <chrono>
 #include <condition_variable>
 #include <deque>
+#include <new>
 #include <set>
 #include <thread>
 #include <unordered_map>
@@ -26,8 +27,10 @@ struct Request {
     uint64_t ticket;
     lq_request req;
     std::vector<double> masses;
-    std::vector<std::vector<double>> rhs;  // nrhs canonical host arrays
-    std::vector<std::vector<double>> x;    // solutions
+    std::vector<std::vector<double>> rhs;  // nrhs canonical host arrays, dropped once solved
+    std::vector<std::vector<double>> x;    // solutions, allocated when the request is admitted
+    int nsol = 0;
+    size_t n = 0;                          // reals per canonical field
     std::vector<lq_solve_info> info;
     size_t reserve = 0;
     double t_submit = 0, t_admit = 0, t_finish = 0;
@@ -74,7 +77,8 @@ size_t solve_workspace_bytes(const Lattice& lat, const lq_op_params& op, const l
     size_t canon = (size_t)lat.V * (hisq ? 6 : 24) * sizeof(double) * (size_t)(nrhs + nrhs * ns);
     size_t b;
     if (!hisq) {
-        b = 7 * f64 + 3 * f64 + fx + (sp.solver == LQ_BICGSTAB ? 6 : 5) * fs;
+        const int kg = sp.restart > 0 ? sp.restart : GCR_DEFAULT;
+        b = 7 * f64 + 3 * f64 + fx + (sp.solver == LQ_BICGSTAB ? 6 : sp.solver == LQ_GCR ? 2 + 2 * kg : 5) * fs;
     } else {
         b = 8 * f64 + 3 * f64 + fx + 4 * fs;
         if (ns > 1) b += (size_t)(3 + 2 * ns) * field_bytes(kind, ps, 2 * nrhs, lat.vh);
@@ -118,9 +122,17 @@ void lq_server_s::worker() {
             }
             if (!r) break;
         }
-        int status;
-        {
-            const int nsol = (int)r->x.size();
+        int status = LQ_OK;
+        // host memory of a request: its sources while queued, the solutions from
+        // admission until polled
+        try {
+            r->x.assign(r->nsol, std::vector<double>(r->n));
+        } catch (const std::bad_alloc&) {
+            std::vector<std::vector<double>>().swap(r->x);
+            status = LQ_ENOMEM;
+        }
+        if (status == LQ_OK) {
+            const int nsol = r->nsol;
             std::vector<const double*> b(r->rhs.size());
             std::vector<double*> x(nsol);
             for (size_t k = 0; k < b.size(); k++) b[k] = r->rhs[k].data();
@@ -132,6 +144,7 @@ void lq_server_s::worker() {
             // the admission ledger counts a request's work buffers only while it runs
             ws_release(r->req.lat->lat);
         }
+        std::vector<std::vector<double>>().swap(r->rhs);
         {
             std::lock_guard<std::mutex> lk(mu);
             r->status = status;
@@ -214,8 +227,8 @@ extern "C" int lq_submit(lq_server s, const lq_request* req, const double* const
         }
         r->rhs.emplace_back(rhs[k], rhs[k] + n);
     }
-    const int nsol = req->nrhs * (ms ? req->solve.nshift : 1);
-    r->x.assign(nsol, std::vector<double>(n, 0.0));
+    r->nsol = req->nrhs * (ms ? req->solve.nshift : 1);
+    r->n = n;
     r->info.assign(req->nrhs, lq_solve_info{});
     r->reserve = solve_workspace_bytes(L, req->op, req->solve, req->nrhs);
     {

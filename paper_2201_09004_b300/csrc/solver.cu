@@ -397,6 +397,176 @@ static CgResult bicgstab_mixed(Lattice& lat, const OpDesc& ops, const OpDesc& op
     return res;
 }
 
+// Restarted GCR (generalised conjugate residual) directly on Mhat for all
+// right-hand sides of bhat, in the sloppy precision, inside a defect correction
+// in FP64 accuracy. Step j takes the current residual as the new direction p_j,
+// forms q_j = Mhat p_j, makes q_j orthogonal to the earlier q_i by classical
+// Gram-Schmidt (the same combination applied to p_j keeps q_j = Mhat p_j), and
+// moves x along p_j and r along q_j by alpha = <q_j, r>/|q_j|^2, which makes |r|
+// minimal over the kept directions. After kmax directions, or once |r| is below
+// delta times its value at the restart (or below the target), x_lo is folded into
+// x_hi, r = bhat - Mhat x_hi is recomputed in FP64 accuracy and the directions are
+// dropped. The scalars of every step are summed on the host from per-block
+// double-float partials (fixed order).
+static CgResult gcr_mixed(Lattice& lat, const OpDesc& ops, const OpDesc& op64, Field& bhat, Field& x_hi,
+                          const std::vector<double>& tol_abs, double delta, int maxiter, int kmax, cudaStream_t st) {
+    const int n = bhat.nrhs;
+    const int ps = ops.prec;
+    const int px = ps == LQ_F16 ? LQ_F32 : ps;
+    const int WF = LQ_WILSON_FIELD;
+    const int RB = RED_BLOCKS;
+    Pool pool(lat, st);
+    const int ph = op64.prec;
+    Field r_hi = pool.get(WF, ph, n), q64 = pool.get(WF, ph, n), t64 = pool.get(WF, ph, n);
+    Field x_lo = pool.get(WF, px, n);
+    Field r = pool.get(WF, ps, n), tmp = pool.get(WF, ps, n);
+    std::vector<Field> P, Q;
+    for (int i = 0; i < kmax; i++) {
+        P.push_back(pool.get(WF, ps, n));
+        Q.push_back(pool.get(WF, ps, n));
+    }
+    // device lists of field views: q_0..q_{kmax-1}, p_0..p_{kmax-1}, and (q_j, r) per j
+    std::vector<FieldV> lists;
+    for (int i = 0; i < kmax; i++) lists.push_back(Q[i].view());
+    for (int i = 0; i < kmax; i++) lists.push_back(P[i].view());
+    for (int i = 0; i < kmax; i++) {
+        lists.push_back(Q[i].view());
+        lists.push_back(r.view());
+    }
+    const size_t part_n = (size_t)n * std::max(kmax, 2) * 2 * RB;
+    struct Buffers {
+        Lattice& l; cudaStream_t s; std::vector<void*> ptrs;
+        void* get(size_t bytes, bool pinned) {
+            ptrs.push_back(ws_get(l, bytes, pinned, s));
+            return ptrs.back();
+        }
+        ~Buffers() { for (void* p : ptrs) ws_put(l, p, s); }
+    } buf{lat, st, {}};
+    FieldV* lists_dev = (FieldV*)buf.get(sizeof(FieldV) * lists.size(), false);
+    df* part = (df*)buf.get(sizeof(df) * part_n, false);
+    df* hpart = (df*)buf.get(sizeof(df) * part_n, true);
+    double* coef_dev = (double*)buf.get(sizeof(double) * 2 * n * kmax, false);
+    double* alpha_dev = (double*)buf.get(sizeof(double) * 2 * n, false);
+    std::vector<double> coef_h((size_t)2 * n * kmax), alpha_h((size_t)2 * n);
+    // pageable sources: each copy is staged before the call returns
+    LQ_CUDA(cudaMemcpyAsync(lists_dev, lists.data(), sizeof(FieldV) * lists.size(), cudaMemcpyHostToDevice, st));
+    const FieldV* qlist = lists_dev;
+    const FieldV* plist = lists_dev + kmax;
+    auto pull = [&](size_t count) {
+        LQ_CUDA(cudaMemcpyAsync(hpart, part, sizeof(df) * count, cudaMemcpyDeviceToHost, st));
+        LQ_CUDA(cudaStreamSynchronize(st));
+    };
+    auto total = [&](size_t row) {  // sum of the RB partials of one row, fixed order
+        double s = 0.0;
+        for (int b = 0; b < RB; b++) s += (double)hpart[row * RB + b].hi + (double)hpart[row * RB + b].lo;
+        return s;
+    };
+
+    CgResult res(n);
+    std::vector<char> done(n, 0);
+    std::vector<double> rref(n), nq((size_t)n * kmax, 0.0);
+    std::vector<double> ones(n, 1.0);
+    std::vector<int> stuck(n, 0);
+    blas_zero(x_hi, st);
+    blas_zero(x_lo, st);
+    blas_copy(r_hi, bhat, st);
+    blas_norm2(r_hi, part, st);
+    blas_copy(r, r_hi, st);
+    pull((size_t)n * RB);
+    for (int k = 0; k < n; k++) {
+        rref[k] = sqrt(total(k));
+        check_finite(rref[k], "source");
+        if (rref[k] <= tol_abs[k]) {
+            done[k] = 1;
+            res.status[k] = LQ_OK;
+        }
+    }
+    auto all_done = [&]() {
+        for (int k = 0; k < n; k++)
+            if (!done[k]) return false;
+        return true;
+    };
+    int it = 0;
+    while (!all_done() && it < maxiter) {
+        std::vector<char> broke(n, 0);
+        for (int j = 0;; j++) {
+            blas_copy(P[j], r, st);
+            schur_wilson(lat, ops, 0, P[j], Q[j], tmp, nullptr, st);
+            if (j > 0) {  // c_i = <q_i, q_j> / |q_i|^2, then q_j -= sum c_i q_i (and p_j alike)
+                blas_cdot_multi(qlist, j, Q[j], part, st);
+                pull((size_t)n * j * 2 * RB);
+                for (int k = 0; k < n; k++)
+                    for (int i = 0; i < j; i++) {
+                        const size_t row = ((size_t)k * j + i) * 2;
+                        const double d = nq[(size_t)k * kmax + i];
+                        const bool use = !done[k] && d > 0.0;
+                        coef_h[((size_t)k * kmax + i) * 2] = use ? total(row) / d : 0.0;
+                        coef_h[((size_t)k * kmax + i) * 2 + 1] = use ? total(row + 1) / d : 0.0;
+                    }
+                LQ_CUDA(cudaMemcpyAsync(coef_dev, coef_h.data(), sizeof(double) * coef_h.size(), cudaMemcpyHostToDevice,
+                                        st));
+                blas_gcr_orth(qlist, plist, j, coef_dev, kmax, Q[j], st);
+            }
+            // |q_j|^2 and <r, q_j>: alpha = <q_j, r> / |q_j|^2 = conj(<r, q_j>) / |q_j|^2
+            blas_cdot_multi(lists_dev + 2 * kmax + 2 * j, 2, Q[j], part, st);
+            pull((size_t)n * 4 * RB);
+            bool restart = false;
+            for (int k = 0; k < n; k++) {
+                const double qq = total((size_t)k * 4), rq_re = total((size_t)k * 4 + 2),
+                             rq_im = total((size_t)k * 4 + 3);
+                nq[(size_t)k * kmax + j] = qq;
+                const bool ok = !done[k] && qq > 0.0 && std::isfinite(qq);
+                if (!done[k] && !ok) {
+                    check_finite(qq, "GCR direction");
+                    broke[k] = 1;
+                    restart = true;
+                }
+                alpha_h[2 * k] = ok ? rq_re / qq : 0.0;
+                alpha_h[2 * k + 1] = ok ? -rq_im / qq : 0.0;
+            }
+            LQ_CUDA(cudaMemcpyAsync(alpha_dev, alpha_h.data(), sizeof(double) * alpha_h.size(), cudaMemcpyHostToDevice,
+                                    st));
+            blas_gcr_xr(x_lo, P[j], r, Q[j], alpha_dev, part, st);
+            pull((size_t)n * RB);
+            it++;
+            for (int k = 0; k < n; k++) {
+                if (done[k]) continue;
+                res.iters[k]++;
+                res.applications[k]++;
+                const double rn = sqrt(total(k));
+                check_finite(rn, "iterated residual");
+                if (rn <= tol_abs[k] || rn < delta * rref[k]) restart = true;
+            }
+            if (restart || j + 1 == kmax || it >= maxiter) break;
+        }
+        // defect correction: x_hi += x_lo, r = bhat - Mhat x_hi in FP64 accuracy
+        blas_axpy_h(x_hi, ones.data(), x_lo, st);
+        blas_zero(x_lo, st);
+        schur_wilson(lat, op64, 0, x_hi, q64, t64, nullptr, st);
+        blas_xmy_norm(r_hi, bhat, q64, part, st);
+        blas_copy(r, r_hi, st);
+        pull((size_t)n * RB);
+        for (int k = 0; k < n; k++) {
+            if (done[k]) continue;
+            res.updates[k]++;
+            res.applications[k]++;
+            const double rn = sqrt(total(k));
+            check_finite(rn, "true residual");
+            // a breakdown that recurs with no progress ends this right-hand side
+            stuck[k] = (broke[k] && !(rn < 0.999 * rref[k])) ? stuck[k] + 1 : 0;
+            rref[k] = rn;
+            if (rn <= tol_abs[k]) {
+                done[k] = 1;
+                res.status[k] = LQ_OK;
+            } else if (stuck[k] > 4) {
+                done[k] = 1;
+                res.status[k] = LQ_EBREAKDOWN;
+            }
+        }
+    }
+    return res;
+}
+
 int solve_wilson(Lattice& lat, const lq_op_params& opp, const lq_solve_params& sp, int nrhs, const double* const* b,
                  double* const* x, lq_solve_info* info, cudaStream_t st, const double* const* x0) {
     if (opp.action == LQ_WILSON_TM_CLOVER && !lat.has_clover) fail(LQ_EINVAL, "clover action without clover term");
@@ -404,8 +574,9 @@ int solve_wilson(Lattice& lat, const lq_op_params& opp, const lq_solve_params& s
     if (nrhs < 1 || nrhs > 64) fail(LQ_EINVAL, "nrhs must be in [1, 64]");
     int ps = sp.prec_sloppy;
     if (ps < LQ_F64 || ps > LQ_F16) fail(LQ_EINVAL, "prec_sloppy");
-    if (sp.solver != LQ_CGNR && sp.solver != LQ_MIXED_CGNR && sp.solver != LQ_BICGSTAB)
+    if (sp.solver != LQ_CGNR && sp.solver != LQ_MIXED_CGNR && sp.solver != LQ_BICGSTAB && sp.solver != LQ_GCR)
         fail(LQ_EINVAL, "solver kind for a Wilson action");
+    if (sp.restart < 0 || sp.restart > GCR_MAX) fail(LQ_EINVAL, "restart must be in [0, 16]");
     if (!(sp.tol > 0)) fail(LQ_EINVAL, "tol must be positive");
     const int recon = sloppy_recon(sp);
     // the FP64-accuracy steps: native FP64 for the plain FP64 solver, double-float
@@ -465,6 +636,9 @@ int solve_wilson(Lattice& lat, const lq_op_params& opp, const lq_solve_params& s
             for (int k = 0; k < nrhs; k++) import_field(lat, xe, k, 0, x0[k], st);
         CgResult cr = sp.solver == LQ_BICGSTAB
                           ? bicgstab_mixed(lat, ops, op64, bhat, xe, tol_abs, delta, maxiter, sp.graph_iters, st)
+                      : sp.solver == LQ_GCR
+                          ? gcr_mixed(lat, ops, op64, bhat, xe, tol_abs, delta, maxiter,
+                                      sp.restart > 0 ? sp.restart : GCR_DEFAULT, st)
                           : cgnr_mixed(lat, ops, op64, bhat, xe, tol_abs, delta, maxiter, sp.graph_iters, st,
                                        x0 != nullptr);
 
@@ -911,6 +1085,8 @@ int solve_hisq(Lattice& lat, const lq_op_params& opp, const lq_solve_params& sp,
                double* const* x, lq_solve_info* info, cudaStream_t st) {
     if (!lat.canon[LQ_FAT] || !lat.canon[LQ_LONG]) fail(LQ_EINVAL, "HISQ needs fat and long links loaded");
     if (nrhs < 1 || nrhs > 32) fail(LQ_EINVAL, "nrhs must be in [1, 32] for HISQ");
+    if (sp.solver == LQ_BICGSTAB || sp.solver == LQ_GCR)
+        fail(LQ_EINVAL, "BiCGStab and GCR are for Wilson actions (the HISQ Schur operator is hermitian positive)");
     int ps = sp.prec_sloppy;
     if (ps < LQ_F64 || ps > LQ_F16) fail(LQ_EINVAL, "prec_sloppy");
     if (!(sp.tol > 0)) fail(LQ_EINVAL, "tol must be positive");

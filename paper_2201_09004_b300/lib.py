@@ -27,7 +27,7 @@ TWIST_GAMMA5, TWIST_SCALAR = 0, 1
 THIN, FAT, LONG = 0, 1, 2
 HOST, DEVICE = 0, 1
 WILSON_TM, WILSON_TM_CLOVER, HISQ = 0, 1, 2
-CGNR, MIXED_CGNR, MULTISHIFT_CG, BICGSTAB = 0, 1, 2, 3
+CGNR, MIXED_CGNR, MULTISHIFT_CG, BICGSTAB, GCR = 0, 1, 2, 3, 4
 OP_FULL, OP_SCHUR = 0, 1
 WILSON_FIELD, STAGGERED_FIELD = 0, 1
 
@@ -40,7 +40,7 @@ EXPORTS = [
     "lq_load_clover", "lq_dslash_apply", "lq_operator_apply", "lq_solve", "lq_field_create",
     "lq_field_destroy", "lq_field_import", "lq_field_export", "lq_dslash_field", "lq_schur_field",
     "lq_profile_enable", "lq_profile_reset", "lq_profile_query", "lq_launch_count", "lq_tune_reset", "lq_tune_force", "lq_gamma5_dw_apply", "lq_chebyshev_sign",
-    "lq_overlap_sign_apply", "lq_server_create",
+    "lq_overlap_sign_apply", "lq_hw_eigensolve", "lq_overlap_sign_apply_deflated", "lq_server_create",
     "lq_server_destroy", "lq_submit", "lq_poll", "lq_wait", "lq_server_stats", "lq_dslash_apply_noalloc", "lq_request_bytes",
 ]
 
@@ -61,7 +61,7 @@ class SolveParams(ctypes.Structure):
     _fields_ = [("solver", ctypes.c_int), ("tol", ctypes.c_double), ("delta", ctypes.c_double),
                 ("maxiter", ctypes.c_int), ("prec_sloppy", ctypes.c_int), ("recon_sloppy", ctypes.c_int),
                 ("nshift", ctypes.c_int), ("masses", ctypes.POINTER(ctypes.c_double)),
-                ("graph_iters", ctypes.c_int)]
+                ("graph_iters", ctypes.c_int), ("restart", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -75,6 +75,20 @@ class SolveInfo(ctypes.Structure):
 
 class SignInfo(ctypes.Structure):
     _fields_ = [("order", ctypes.c_int), ("max_deviation", ctypes.c_double)]
+
+
+class EigParams(ctypes.Structure):
+    _fields_ = [("nev", ctypes.c_int), ("nkv", ctypes.c_int), ("degree", ctypes.c_int),
+                ("lambda_cut", ctypes.c_double), ("lambda_max", ctypes.c_double), ("tol", ctypes.c_double),
+                ("max_restarts", ctypes.c_int)]
+
+
+class EigInfo(ctypes.Structure):
+    _fields_ = [("converged", ctypes.c_int), ("restarts", ctypes.c_int), ("operator_applications", ctypes.c_int),
+                ("max_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class Request(ctypes.Structure):
@@ -142,9 +156,9 @@ def op_params(action, m, mu=0.0, c_sw=0.0, c_naik=-1.0 / 24.0, recon=0, twist_mo
 
 
 def solve_params(solver=MIXED_CGNR, tol=1e-10, delta=0.1, maxiter=100000, prec_sloppy=F32, recon_sloppy=R12,
-                 masses=None, graph_iters=0):
+                 masses=None, graph_iters=0, restart=0):
     sp = SolveParams(int(solver), float(tol), float(delta), int(maxiter), int(prec_sloppy), int(recon_sloppy), 0, None,
-                     int(graph_iters))
+                     int(graph_iters), int(restart))
     if masses is not None:
         arr = (ctypes.c_double * len(masses))(*[float(m) for m in masses])
         sp.nshift = len(masses)
@@ -253,6 +267,47 @@ class Lattice:
         _check(lib().lq_overlap_sign_apply(self.h, ctypes.c_double(rho), ctypes.c_double(lambda_min),
                                            ctypes.c_double(lambda_max), ctypes.c_double(delta), ctypes.c_int(prec),
                                            ctypes.c_int(loc), p, po, ctypes.byref(info), _stream(stream)))
+        return out, {"order": info.order, "max_deviation": info.max_deviation}
+
+    def hw_eigensolve(self, rho, nev, lambda_cut, lambda_max, tol=1e-9, nkv=0, degree=0, max_restarts=0,
+                      like=None, stream=None, check=True):
+        """The nev lowest-|lambda| eigenpairs of g5 D_w(-rho); returns (evals, evecs list, info dict).
+        Eigenvectors are host arrays, or device tensors if `like` is one."""
+        p = EigParams(int(nev), int(nkv), int(degree), float(lambda_cut), float(lambda_max), float(tol),
+                      int(max_restarts))
+        shape = self.dims[::-1] + (4, 3)
+        if like is not None and _is_torch(like) and like.is_cuda:
+            import torch
+            vecs = [torch.empty(shape, dtype=torch.complex128, device=like.device) for _ in range(max(nev, 1))]
+        else:
+            vecs = [np.empty(shape, dtype=np.complex128) for _ in range(max(nev, 1))]
+        ptrs = [_ptr(v) for v in vecs]
+        loc = ptrs[0][1]
+        arr = (ctypes.c_void_p * len(vecs))(*[q[0].value for q in ptrs])
+        evals = (ctypes.c_double * max(nev, 1))()
+        info = EigInfo()
+        code = lib().lq_hw_eigensolve(self.h, ctypes.c_double(rho), ctypes.byref(p), ctypes.c_int(loc), evals, arr,
+                                      ctypes.byref(info), _stream(stream))
+        if check or code not in (LQ_OK, LQ_ENOTCONV):
+            _check(code)
+        return np.array(evals[:nev]), vecs[:nev], info.as_dict()
+
+    def overlap_sign_apply_deflated(self, rho, lambda_min, lambda_max, delta, evals, evecs, psi, stream=None):
+        """eps(g5 D_w(-rho)) psi with the given eigenpairs deflated; returns (out, info dict)."""
+        p, loc, keep = _ptr(psi)
+        out = self._out_like(psi)
+        po, loco, keepo = _ptr(out)
+        nev = len(evecs)
+        vp = [_ptr(v) for v in evecs]
+        if any(q[1] != loc for q in vp):
+            raise ValueError("eigenvectors and the field must live on the same side (host or device)")
+        arr = (ctypes.c_void_p * max(nev, 1))(*[q[0].value for q in vp])
+        ev = (ctypes.c_double * max(nev, 1))(*[float(x) for x in evals])
+        info = SignInfo()
+        _check(lib().lq_overlap_sign_apply_deflated(self.h, ctypes.c_double(rho), ctypes.c_double(lambda_min),
+                                                    ctypes.c_double(lambda_max), ctypes.c_double(delta),
+                                                    ctypes.c_int(nev), ev, arr, ctypes.c_int(loc), p, po,
+                                                    ctypes.byref(info), _stream(stream)))
         return out, {"order": info.order, "max_deviation": info.max_deviation}
 
     def solve(self, op, params, rhs, stream=None, check=True, out=None):
