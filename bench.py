@@ -66,7 +66,7 @@ FLOPS_PER_SITE = {"hop": 1320, "ainv": 1320 + 2 * 6 * 6 * 8, "xpay": 1320 + 2 * 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of the
 # benchmark configuration (profiles/wilson_dslash_f16_ainv_24x24x24x64.md); set back to
 # None whenever the kernel changes after the capture.
-NCU_TRAFFIC = {("wilson_dslash_f16_ainv", 12): 255_050_000}
+NCU_TRAFFIC = {("wilson_dslash_f16_ainv", 12): 254_847_232}
 
 REASONS = {
     0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap", 0x8: "hw_slowdown",
@@ -778,34 +778,43 @@ def run_eigen(args):
     t_eig = time.perf_counter() - t0
     lmin_defl = float(np.max(np.abs(ev)))
     lmin_plain = 0.95 * float(np.min(np.abs(ev)))
+    eig = {"converged": info["converged"], "restarts": info["restarts"],
+           "hw_applications": info["operator_applications"], "max_residual": info["max_residual"],
+           "wall_s": round(t_eig, 3), "abs_lambda_range": [float(np.min(np.abs(ev))), lmin_defl],
+           "evals": [round(float(x), 10) for x in ev]}
+    config = {"dims": list(dims), "rho": rho, "nev": args.nev, "nkv": args.nkv, "degree": args.degree,
+              "lambda_cut": args.lambda_cut, "lambda_max": lmax, "tol": args.eig_tol,
+              "gauge_seed": GAUGE_SEED, "precision": "double-float"}
+    metric = "time to the nev lowest eigenpairs of g5 D_w(-rho), and the deflated sign function"
+    if not info["converged"]:  # the deflated sign function needs converged eigenpairs
+        print(json.dumps({"workload": "eigen", "metric": metric, "value": round(info["seconds"], 3), "unit": "s",
+                          "higher_is_better": False, "config": config, "eigensolver": eig}), flush=True)
+        return
     e0, e1 = _events()
     e0.record()
     sd, infod = lat.overlap_sign_apply_deflated(rho, lmin_defl, lmax, 1e-8, ev, Z, v)
     e1.record()
     torch.cuda.synchronize()
     t_defl = e0.elapsed_time(e1) * 1e-3
-    e0, e1 = _events()
-    e0.record()
-    sp, infop = lat.overlap_sign_apply(rho, lmin_plain, lmax, 1e-8, v, prec=lib.F32X2)
-    e1.record()
-    torch.cuda.synchronize()
-    t_plain = e0.elapsed_time(e1) * 1e-3
-    diff = float(torch.linalg.vector_norm(sd - sp) / torch.linalg.vector_norm(sp))
-    line = {"workload": "eigen",
-            "metric": "time to the nev lowest eigenpairs of g5 D_w(-rho), and the deflated sign function",
+    # the same function without deflation must cover the lowest mode; a mode near zero
+    # can make that polynomial longer than the library allows (65536 terms)
+    try:
+        e0, e1 = _events()
+        e0.record()
+        sp, infop = lat.overlap_sign_apply(rho, lmin_plain, lmax, 1e-8, v, prec=lib.F32X2)
+        e1.record()
+        torch.cuda.synchronize()
+        plain = {"seconds": round(e0.elapsed_time(e1) * 1e-3, 3), "order": infop["order"], "lambda_min": lmin_plain}
+        diff = float(torch.linalg.vector_norm(sd - sp) / torch.linalg.vector_norm(sp))
+    except lib.LqError as e:
+        plain = {"lambda_min": lmin_plain, "error": str(e)}
+        diff = None
+    line = {"workload": "eigen", "metric": metric,
             "value": round(info["seconds"], 3), "unit": "s", "higher_is_better": False,
-            "config": {"dims": list(dims), "rho": rho, "nev": args.nev, "nkv": args.nkv, "degree": args.degree,
-                       "lambda_cut": args.lambda_cut, "lambda_max": lmax, "tol": args.eig_tol,
-                       "gauge_seed": GAUGE_SEED, "precision": "double-float"},
-            "eigensolver": {"converged": info["converged"], "restarts": info["restarts"],
-                            "hw_applications": info["operator_applications"], "max_residual": info["max_residual"],
-                            "wall_s": round(t_eig, 3), "abs_lambda_range": [float(np.min(np.abs(ev))), lmin_defl],
-                            "evals": [round(float(x), 10) for x in ev]},
+            "config": config, "eigensolver": eig,
             "sign_function": {"deflated": {"seconds": round(t_defl, 3), "order": infod["order"],
                                            "lambda_min": lmin_defl},
-                              "plain": {"seconds": round(t_plain, 3), "order": infop["order"],
-                                        "lambda_min": lmin_plain},
-                              "relative_difference": diff, "deviation_bound": 1e-8}}
+                              "plain": plain, "relative_difference": diff, "deviation_bound": 1e-8}}
     print(json.dumps(line), flush=True)
 
 
@@ -1018,8 +1027,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nev", type=int, default=2, help="eigen: low modes wanted")
     ap.add_argument("--nkv", type=int, default=24, help="eigen: Krylov basis size")
-    ap.add_argument("--degree", type=int, default=64, help="eigen: Chebyshev filter degree")
-    ap.add_argument("--lambda-cut", type=float, default=0.53, help="eigen: filter edge")
+    ap.add_argument("--degree", type=int, default=96, help="eigen: Chebyshev filter degree")
+    ap.add_argument("--lambda-cut", type=float, default=0.525, help="eigen: filter edge")
     ap.add_argument("--eig-tol", type=float, default=1e-8, help="eigen: residual bound")
     ap.add_argument("--max-restarts", type=int, default=30, help="eigen: restart limit")
     ap.add_argument("--workload", default="tmc", choices=["tmc", "multirhs", "hisq", "serving", "dslash", "hisq3col", "overlap", "tmms", "eigen"],
