@@ -69,6 +69,12 @@ def test_null_handles_and_bad_arguments_are_rejected_without_gpu():
     assert L.lq_tune_force(-1) == lib.LQ_EINVAL
     assert L.lq_tune_force(0) == lib.LQ_OK
     assert L.lq_lattice_release_workspace(None, None) == lib.LQ_EINVAL
+    ep = lib.EigParams(4, 0, 0, 1.0, 10.5, 1e-8, 0)
+    evals = (ctypes.c_double * 4)()
+    assert L.lq_hw_eigensolve(None, ctypes.c_double(1.5), ctypes.byref(ep), 0, evals, None, None, None) == lib.LQ_EINVAL
+    assert L.lq_overlap_sign_apply_deflated(None, ctypes.c_double(1.5), ctypes.c_double(0.5), ctypes.c_double(10.5),
+                                            ctypes.c_double(1e-8), 0, None, None, 0, buf, buf, None,
+                                            None) == lib.LQ_EINVAL
 
 
 def test_ctypes_structures_match_the_header_layout(tmp_path):
@@ -77,7 +83,8 @@ def test_ctypes_structures_match_the_header_layout(tmp_path):
     import subprocess
     from paper_2201_09004_b300 import lib
     structs = {"lq_op_params": lib.OpParams, "lq_solve_params": lib.SolveParams, "lq_solve_info": lib.SolveInfo,
-               "lq_sign_info": lib.SignInfo, "lq_request": lib.Request, "lq_request_times": lib.RequestTimes}
+               "lq_sign_info": lib.SignInfo, "lq_request": lib.Request, "lq_request_times": lib.RequestTimes,
+               "lq_eig_params": lib.EigParams, "lq_eig_info": lib.EigInfo}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "lq.h"', "int main(void) {"]
     for cname, py in structs.items():
         lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
