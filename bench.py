@@ -348,7 +348,7 @@ def gpu_arm(args):
             "gpu_launches": int(launches), "clocks": clocks,
         }
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(args.cpu_iters)
+            line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
@@ -968,44 +968,77 @@ def oracle_setup():
     return _ORACLE["W"], _ORACLE["b"]
 
 
-def cpu_baseline(niter):
-    """The oracle's FP64 CGNR on the full lattice: niter iterations timed, scaled by
-    the oracle's own iteration count for a complete solve."""
+def oracle_seconds_per_iteration(threads, n1, n2):
+    """Seconds per FP64 CGNR iteration of the oracle on the full 24^3x64 system with
+    `threads` OpenMP threads, taken differentially: runs of n1 and n2 iterations are
+    timed and (t2 - t1) / (n2 - n1) is returned, so the setup that every run repeats
+    (allocation, the first M^+ b, the final residual) cancels."""
+    import oracle
     W, b = oracle_setup()
-    t0 = time.perf_counter()
-    W.cgnr_fixed(b, niter)
-    s = time.perf_counter() - t0
+    oracle.set_threads(threads)
+    ts = []
+    for n in (n1, n2):
+        t0 = time.perf_counter()
+        W.cgnr_fixed(b, n)
+        ts.append(time.perf_counter() - t0)
+    return (ts[1] - ts[0]) / (n2 - n1), sum(ts)
+
+
+# iterations of the two timed runs per core count: about 10-20 s of host time in all
+ORACLE_SAMPLE = {1: (1, 2), "all": (2, 6)}
+
+
+def cpu_baseline_runs(n1_all=None, n2_all=None):
+    """The oracle timed on 1 core and on all host cores, each as solves/s scaled by
+    the oracle's own iteration count for a complete solve."""
     full = oracle_iterations()
-    per_solve = s / niter * full
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count()))
-    return {"value": round(1.0 / per_solve, 6), "unit": "solves/s", "cores": cores, "kind": "oracle",
-            "sample": f"{niter} FP64 CGNR iterations of the oracle on the full 24^3x64 lattice ({s:.1f} s), "
-                      f"scaled to its {full} iterations per solve"}
+    out = []
+    for cores in (1, os.cpu_count() or 1):
+        n1, n2 = ORACLE_SAMPLE[1] if cores == 1 else (n1_all or ORACLE_SAMPLE["all"][0], n2_all or ORACLE_SAMPLE["all"][1])
+        per_it, spent = oracle_seconds_per_iteration(cores, n1, n2)
+        out.append({"value": round(1.0 / (per_it * full), 6), "unit": "solves/s", "cores": cores, "kind": "oracle",
+                    "seconds_per_iteration": round(per_it, 4),
+                    "sample": f"FP64 CGNR of the oracle on the full 24^3x64 lattice: runs of {n1} and {n2} iterations "
+                              f"({spent:.1f} s), per iteration (t{n2} - t{n1}) / {n2 - n1}, scaled to its {full} "
+                              f"iterations per solve"})
+    return out
+
+
+def cpu_baseline():
+    """cpu_baseline of the bench line: the all-core number, with the 1-core one beside it."""
+    one, allc = cpu_baseline_runs()
+    line = dict(allc)
+    line["one_core"] = one
+    return line
 
 
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    W, b = oracle_setup()
+    import oracle
+    oracle_setup()
     full = oracle_iterations()
-    for _ in range(args.warmup):
-        W.cgnr_fixed(b, 1)
+    cores = os.cpu_count() or 1
+    oracle_seconds_per_iteration(cores, 1, 2)  # warm-up (page-in, thread pool)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        W.cgnr_fixed(b, args.ref_iters)
+    per_it = []
+    for _ in range(max(args.steps, 1)):
+        pi, _ = oracle_seconds_per_iteration(cores, 1, 1 + args.ref_iters)
+        per_it.append(pi)
     s = time.perf_counter() - t0
-    per_solve = s / (args.steps * args.ref_iters) * full
+    per_solve = float(np.median(per_it)) * full
     value = 1.0 / per_solve
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count()))
-    sample = (f"each step: {args.ref_iters} FP64 CGNR iterations of the oracle on the full 24^3x64 lattice, "
-              f"scaled to its {full} iterations per solve")
+    one = cpu_baseline_runs()[0]
+    sample = (f"each step: FP64 CGNR runs of 1 and {1 + args.ref_iters} iterations of the oracle on the full "
+              f"24^3x64 lattice on {cores} cores, per iteration the difference, median over steps, scaled to its "
+              f"{full} iterations per solve")
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "solves/s", "n_gpus": 0,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(s / args.steps * 1e3, 1),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(s / max(args.steps, 1) * 1e3, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "dims": list(DIMS), "c_sw": C_SW, "m": MASS, "mu": MU},
             "cpu_baseline": {"value": round(value, 6), "unit": "solves/s", "cores": cores, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "one_core": one},
             "e2e": {"value": round(value, 6), "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -1020,7 +1053,6 @@ def main():
     ap.add_argument("--recon", type=int, default=12, choices=[8, 12, 18],
                     help="link compression of the sloppy operator (thin / long links)")
     ap.add_argument("--fp64-steps", type=int, default=2)
-    ap.add_argument("--cpu-iters", type=int, default=8)
     ap.add_argument("--bicgstab-steps", type=int, default=3,
                     help="also time the mixed-precision BiCGStab solve of the same system")
     ap.add_argument("--gcr-steps", type=int, default=3,

@@ -167,40 +167,53 @@ typedef struct {
 /* ------------------------------------------------------------------ errors */
 
 /* Message of the last failure on the calling thread ("" if none). The pointer
- * stays valid until the next failing call on the same thread. */
+ * stays valid until the next failing call on the same thread.
+ * Paper: no counterpart (error reporting of this library). */
 const char* lq_last_error(void);
 
 /* --------------------------------------------------------------- lattices */
 
 /* Creates a lattice of extents dims[4] = {Lx, Ly, Lz, Lt} (each even, >= 2) with
  * time boundary sign t_boundary (+1 periodic, -1 antiperiodic), on the current
- * CUDA device. *out receives the handle. LQ_EINVAL for odd or too small extents. */
+ * CUDA device. *out receives the handle. LQ_EINVAL for odd or too small extents.
+ * Paper: Sec. 2.1-2.2 (the four-dimensional lattice on which the operators of
+ * Eq. 2-4 act, with the site and parity conventions stated above) and Table 1
+ * (the ensembles' volumes L^3 x T, whose shapes the synthetic fields take). */
 int lq_create_lattice(const int dims[4], int t_boundary, lq_lattice* out);
 
-/* Frees every device buffer of the lattice. Accepts NULL. */
+/* Frees every device buffer of the lattice. Accepts NULL.
+ * Paper: no counterpart (resource management of this library). */
 int lq_destroy_lattice(lq_lattice lat);
 
 /* Device bytes the lattice currently holds (links, clover, caches, and the
- * solver work buffers it keeps between solves). */
+ * solver work buffers it keeps between solves).
+ * Paper: no counterpart (memory accounting of this library). */
 int lq_lattice_bytes(lq_lattice lat, size_t* bytes);
 
 /* Frees the solver work buffers the lattice keeps between solves (device
  * fields, staging buffers, pinned host scalars) that no running solve uses.
  * *freed (may be NULL) receives the device bytes released. A later solve
  * allocates them again. Not part of the paper's method: a memory-management
- * call of this library. */
+ * call of this library.
+ * Paper: no counterpart. */
 int lq_lattice_release_workspace(lq_lattice lat, size_t* freed);
 
 /* Loads links in the canonical gauge layout (host or device, FP64). kind
  * selects the thin links of the Wilson actions, or the fat / long links of
  * HISQ (Sec. 2.2). The library packs them into its even-odd layout in every
- * precision it needs; the caller may free its buffer after the call. */
+ * precision it needs; the caller may free its buffer after the call.
+ * Paper: Sec. 2.1 Eq. 2 (the links U_mu of the Wilson hopping term) and Sec. 2.2
+ * Eq. 4 with the HISQ action's fat one-hop and long three-hop links. */
 int lq_load_gauge(lq_lattice lat, int kind, int loc, const double* links);
 
 /* Clover term of Sec. 2.1 Eq. 3. clover == NULL builds it on the device from
  * the thin links already loaded, with coefficient c_sw; otherwise clover is a
  * canonical 12x12-per-site array (host or device) that must be hermitian and
- * commute with g5 (its two 6x6 chiral blocks are used). */
+ * commute with g5 (its two 6x6 chiral blocks are used).
+ * Paper: Sec. 2.1 Eq. 3 (the clover term), and Sec. 2.1's remark that the
+ * twisted-mass clover inverse has a complex diagonal, so the whole clover term
+ * and its inverse are computed on the GPU itself (built here on the device,
+ * the inverse per (m, mu) on first use). */
 int lq_load_clover(lq_lattice lat, int loc, const double* clover, double c_sw);
 
 /* ----------------------------------------------------- operator application */
@@ -210,7 +223,11 @@ int lq_load_clover(lq_lattice lat, int loc, const double* clover, double c_sw);
  * is the staggered H of Eq. 4. in/out are canonical spinors (colour vectors for
  * HISQ) in FP64, at loc; the operator runs in precision prec (inputs are
  * rounded to it). stream is a cudaStream_t or NULL for the default stream;
- * the call returns after the result is in out. */
+ * the call returns after the result is in out.
+ * Paper: Sec. 2.1 Eq. 2 (the Wilson hopping term: the sum over mu and the
+ * projectors (1 +- g_mu)) and Sec. 2.2 Eq. 4 (the staggered hopping term with
+ * the phases of the spin diagonalisation); the hopping kernel is the "dslash
+ * kernel" on which Sec. 2.3 builds the overlap operator. */
 int lq_dslash_apply(lq_lattice lat, const lq_op_params* op, int parity, int dagger, int prec, int loc,
                     const double* in, double* out, void* stream);
 
@@ -230,7 +247,7 @@ int lq_dslash_apply(lq_lattice lat, const lq_op_params* op, int parity, int dagg
  *     so make it before any stream capture;
  *   - all calls share the scratch array: calls that can overlap on the GPU
  *     (other streams or threads) race, so the caller must order them.
- * Returns after the result is in out. */
+ * The call synchronises `stream` and returns after the result is in out. */
 int lq_dslash_apply_noalloc(lq_lattice lat, const lq_op_params* op, int parity, int dagger, int prec,
                             const double* in, double* out, void* stream);
 
@@ -238,7 +255,11 @@ int lq_dslash_apply_noalloc(lq_lattice lat, const lq_op_params* op, int parity, 
  * HISQ) on the full lattice. form = LQ_OP_SCHUR: the even-odd Schur operator
  * on even sites, Mhat = A_ee - H_eo A_oo^{-1} H_oe for Wilson (A = 4+m+i mu g5+C)
  * and m^2 - H_eo H_oe for HISQ; only the even sites of in are read and only
- * the even sites of out are written (odd sites of out are set to 0). */
+ * the even sites of out are written (odd sites of out are set to 0).
+ * Paper: Sec. 2.1 Eq. 1-3 (D_w(m_cri + omega) with the clover term, in the
+ * twisted reading of omega) and Sec. 2.2 Eq. 4 (D = m + H); the even-odd Schur
+ * form is the preconditioning of the GPU inverters whose timings Tables 2-3
+ * report. */
 int lq_operator_apply(lq_lattice lat, const lq_op_params* op, int form, int dagger, int prec, int loc,
                       const double* in, double* out, void* stream);
 
@@ -249,7 +270,15 @@ int lq_operator_apply(lq_lattice lat, const lq_op_params* op, int form, int dagg
  * FP64 arrays at loc (x must hold nrhs*nshift arrays for multi-shift). info
  * (may be NULL) receives one entry per right-hand side. Right-hand sides are
  * solved together with the multi-right-hand-side operator.
- * Returns LQ_OK if every system reached tol, LQ_ENOTCONV if any did not. */
+ * Returns LQ_OK if every system reached tol, LQ_ENOTCONV if any did not.
+ * Paper: the inverters whose propagator timings Tables 2-3 report.
+ *   LQ_CGNR, LQ_MIXED_CGNR: the QUDA CG the paper calls (Sec. 2.2, Table 3's
+ *     GPU CG), in mixed precision with reliable updates after the
+ *     mixed-precision solvers of Clark et al. cited in Sec. 1;
+ *   LQ_BICGSTAB: Table 2's CPU solver (BiCGStab, Sec. 2.1);
+ *   LQ_GCR: Table 2's GPU solver (GCR, Sec. 2.1);
+ *   LQ_MULTISHIFT_CG: the multi-mass algorithm (Jegerlehner) of Sec. 2.3,
+ *     here for HISQ's several masses and, without clover, twisted masses. */
 int lq_solve(lq_lattice lat, const lq_op_params* op, const lq_solve_params* params, int nrhs,
              const double* const* rhs, double* const* x, int loc, lq_solve_info* info, void* stream);
 
@@ -257,21 +286,29 @@ int lq_solve(lq_lattice lat, const lq_op_params* op, const lq_solve_params* para
 
 /* A spinor or colour field resident on the device in the library's internal
  * even-odd layout and precision, for callers that keep data on the GPU across
- * calls (and for timing the kernels alone): nrhs fields of one parity. */
+ * calls (and for timing the kernels alone): nrhs fields of one parity.
+ * Paper: no counterpart (residency of the spinor fields on the GPU between
+ * calls, the data movement that the GPU inverters of Sec. 1 avoid). */
 int lq_field_create(lq_lattice lat, int kind, int prec, int nrhs, lq_field* out);
+/* Paper: no counterpart. */
 int lq_field_destroy(lq_field f);
 /* copy canonical FP64 data (host or device; only sites of `parity` are read)
  * into right-hand side k of the field, and back (sites of the other parity in
- * `canonical` are left untouched) */
+ * `canonical` are left untouched)
+ * Paper: no counterpart (layout conversion of this library). */
 int lq_field_import(lq_field f, int k, int parity, int loc, const double* canonical, void* stream);
+/* Paper: no counterpart (layout conversion of this library). */
 int lq_field_export(lq_field f, int k, int parity, int loc, double* canonical, void* stream);
 
 /* out = H_{parity, 1-parity} in on resident fields, all right-hand sides of the
- * field at once (multi-right-hand-side kernel). Asynchronous on stream. */
+ * field at once (multi-right-hand-side kernel). Asynchronous on stream.
+ * Paper: Sec. 2.1 Eq. 2 / Sec. 2.2 Eq. 4 (hopping term), applied to the columns
+ * of a propagator together (Table 2's 12-column, Table 3's 3-column ones). */
 int lq_dslash_field(lq_lattice lat, const lq_op_params* op, int parity, int dagger, lq_field in,
                     lq_field out, void* stream);
 /* out = Mhat in (Schur operator, even parity) on resident fields; tmp is a
- * scratch field of the same shape used for the odd sites. Asynchronous on stream. */
+ * scratch field of the same shape used for the odd sites. Asynchronous on stream.
+ * Paper: Sec. 2.1 Eq. 1-3 in even-odd form, as in lq_operator_apply. */
 int lq_schur_field(lq_lattice lat, const lq_op_params* op, int dagger, lq_field in, lq_field out,
                    lq_field tmp, void* stream);
 
@@ -281,10 +318,14 @@ int lq_schur_field(lq_lattice lat, const lq_op_params* op, int dagger, lq_field 
  * events on its own stream; lq_profile_query returns, for kernels whose name
  * contains `name`, the number of launches and their summed device time since
  * the last reset (this synchronises the recorded events). */
+/* Paper: no counterpart (instrumentation of this library). */
 int lq_profile_enable(int on);
+/* Paper: no counterpart. */
 int lq_profile_reset(void);
+/* Paper: no counterpart. */
 int lq_profile_query(const char* name, int64_t* launches, double* total_ms);
-/* number of kernel launches the library issued since the last reset */
+/* number of kernel launches the library issued since the last reset
+ * Paper: no counterpart. */
 int64_t lq_launch_count(void);
 
 /* Autotuner controls (the tuner times each candidate launch configuration of a
@@ -294,8 +335,12 @@ int64_t lq_launch_count(void);
  * size; 1000 + block size for the FP32/FP16 Wilson kernel built with its
  * registers capped at 85 per thread; 2000 + block size for its single-RHS build
  * with two hops of gathers in flight); 0 lifts the restriction. For tests and diagnostics;
- * not part of the paper's method. */
+ * not part of the paper's method.
+ * Paper: Sec. 2.3's remark on the speed of the Wilson kernel, credited to
+ * QUDA's auto-tuning (the tuner itself); the controls have no counterpart. */
 int lq_tune_reset(void);
+/* Paper: Sec. 2.3 (QUDA's auto-tuning), as lq_tune_reset; the restriction itself
+ * has no counterpart. */
 int lq_tune_force(int code);
 
 /* ----------------------------------------------------------------- overlap */
@@ -310,7 +355,9 @@ typedef struct {
     double max_deviation;  /* max |1 - x P(x^2)| over lambda_min/lambda_max <= x <= 1 */
 } lq_sign_info;
 
-/* out = g5 D_w(-rho) in, with g5 fused into the operator kernel's epilogue. */
+/* out = g5 D_w(-rho) in, with g5 fused into the operator kernel's epilogue.
+ * Paper: Sec. 2.3 (the kernel that combines g5 and D_w to save bandwidth, and the
+ * 50 D_w applications timed there). */
 int lq_gamma5_dw_apply(lq_lattice lat, double rho, int prec, int loc, const double* in, double* out,
                        void* stream);
 
@@ -321,7 +368,9 @@ int lq_gamma5_dw_apply(lq_lattice lat, double rho, int prec, int loc, const doub
  * [eps, 1] (dense sampling). The paper refines its fit at the error's extrema
  * instead (a Remez-like exchange); node interpolation is within a small factor of
  * that minimax error. coeffs (may be NULL) receives *order values, at most
- * max_order; LQ_EINVAL if more are needed. Host only. */
+ * max_order; LQ_EINVAL if more are needed. Host only.
+ * Paper: Sec. 2.3 (the Chebyshev approximation of the sign function and its
+ * error, Fig. 2). */
 int lq_chebyshev_sign(double eps, double delta, int max_order, double* coeffs, int* order, double* max_deviation);
 
 /* out ~ eps(H_w) in on the part of the spectrum with lambda_min <= |lambda| <=
@@ -331,7 +380,8 @@ int lq_chebyshev_sign(double eps, double delta, int max_order, double* coeffs, i
  * outside [-lambda_max, lambda_max] the polynomial grows without bound. The paper
  * projects out the lowest modes first (lq_overlap_sign_apply_deflated); here the
  * caller chooses lambda_min below the spectrum it passes. info (may be NULL) gets
- * the order and the deviation bound. */
+ * the order and the deviation bound.
+ * Paper: Sec. 2.3 (eps(H_w) by the Chebyshev polynomial in the overlap operator). */
 int lq_overlap_sign_apply(lq_lattice lat, double rho, double lambda_min, double lambda_max, double delta, int prec,
                           int loc, const double* in, double* out, lq_sign_info* info, void* stream);
 
@@ -363,13 +413,17 @@ typedef struct {
 /* evals (host, nev) in ascending |lambda|; evecs (may be NULL): nev canonical FP64
  * full-lattice Wilson spinors (host or device per loc), unit norm, each fixed up to
  * a phase. LQ_ENOTCONV if max_restarts passed first (the best pairs are returned). */
+/* Paper: Sec. 2.3 and Table 4 (low eigenvectors of g5 D_w by a Chebyshev-accelerated
+ * restarted Arnoldi method). */
 int lq_hw_eigensolve(lq_lattice lat, double rho, const lq_eig_params* p, int loc, double* evals, double* const* evecs,
                      lq_eig_info* info, void* stream);
 
 /* lq_overlap_sign_apply deflated by nev eigenpairs of H_w (evals and unit evecs as
  * lq_hw_eigensolve returns them, in the canonical layout per loc): their part of
  * in gets its exact sign, the polynomial acts on the rest, so lambda_min only has
- * to lie below the remaining spectrum. Computed in double-float. */
+ * to lie below the remaining spectrum. Computed in double-float.
+ * Paper: Sec. 2.3 (the low modes projected out before the polynomial; the
+ * deflation used for the overlap propagators). */
 int lq_overlap_sign_apply_deflated(lq_lattice lat, double rho, double lambda_min, double lambda_max, double delta,
                                    int nev, const double* evals, const double* const* evecs, int loc,
                                    const double* in, double* out, lq_sign_info* info, void* stream);
@@ -396,22 +450,32 @@ typedef struct {
     double finished;
 } lq_request_times;
 
+/* Paper: Sec. 1 and Sec. 3 (one interface through which an application calls
+ * the GPU inverters of several actions, here for a stream of propagator
+ * requests); the serving loop itself (admission by memory, continuous batching)
+ * is this library's addition and has no counterpart in the paper. */
 int lq_server_create(size_t hbm_budget_bytes, int max_slots, lq_server* out);
-/* stops the workers after the admitted requests finish; queued ones are dropped */
+/* stops the workers after the admitted requests finish; queued ones are dropped
+ * Paper: no counterpart. */
 int lq_server_destroy(lq_server s);
 /* rhs: nrhs canonical FP64 host arrays, copied before the call returns.
- * LQ_ENOMEM if the request alone can never fit in the budget. */
+ * LQ_ENOMEM if the request alone can never fit in the budget.
+ * Paper: Sec. 1 and Sec. 3 (the inverter call of the uniform interface, queued). */
 int lq_submit(lq_server s, const lq_request* req, const double* const* rhs, uint64_t* ticket);
 /* LQ_EAGAIN until done; then copies nrhs*max(1,nshift) solutions into x (host
  * arrays), per-rhs info and the timestamps (either may be NULL), forgets the
- * ticket and returns the solve's status */
+ * ticket and returns the solve's status
+ * Paper: Sec. 1 and Sec. 3 (the result of that inverter call). */
 int lq_poll(lq_server s, uint64_t ticket, double* const* x, lq_solve_info* info, lq_request_times* times);
-/* blocks up to timeout_ms for the ticket to finish; LQ_ETIMEOUT otherwise */
+/* blocks up to timeout_ms for the ticket to finish; LQ_ETIMEOUT otherwise
+ * Paper: no counterpart. */
 int lq_wait(lq_server s, uint64_t ticket, int timeout_ms);
 /* device bytes the server reserves for this request while it runs (its solver
- * work fields and staging, not counting the resident lattice) */
+ * work fields and staging, not counting the resident lattice)
+ * Paper: no counterpart. */
 int lq_request_bytes(const lq_request* req, size_t* bytes);
-/* requests queued, running, and device bytes currently reserved by running requests */
+/* requests queued, running, and device bytes currently reserved by running requests
+ * Paper: no counterpart. */
 int lq_server_stats(lq_server s, int* queued, int* running, size_t* reserved_bytes);
 
 #ifdef __cplusplus

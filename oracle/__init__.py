@@ -20,14 +20,39 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
-_LIB = os.path.join(_HERE, "liboracle.so")
+
+
+def _host_tag() -> str:
+    """A tag of this host's CPU (model and instruction-set flags): the library is
+    built with -march=native, so a copy built on another machine is not reused."""
+    import hashlib
+    import platform
+    text = platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith(("model name", "flags")):
+                    text += line
+                    if line.startswith("flags"):
+                        break
+    except OSError:
+        pass
+    return hashlib.sha1(text.encode()).hexdigest()[:10]
+
+
+_LIB = os.path.join(_HERE, f"liboracle_{_host_tag()}.so")
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c (gcc, -O2, OpenMP, no fast-math) into liboracle.so."""
+    """Compile oracle.c (gcc -O3 -march=native, OpenMP; ISO C11, so no floating-point
+    contraction, and no fast-math: every operation rounds as written) into a library
+    named for this host's CPU."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", _LIB, _SRC, "-lm"]
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O3", "-march=native", "-std=c11", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+               "-o", tmp, _SRC, "-lm"]
         subprocess.check_call(cmd)
+        os.replace(tmp, _LIB)
     return _LIB
 
 
@@ -52,7 +77,17 @@ def lib():
         _lib = ctypes.CDLL(build())
         _lib.or_plaquette.restype = ctypes.c_double
         _lib.or_wilson_cgnr_fixed.restype = ctypes.c_double
+        _lib.or_get_threads.restype = ctypes.c_int
     return _lib
+
+
+def set_threads(n: int) -> None:
+    """Number of OpenMP threads the oracle's site loops use from now on."""
+    lib().or_set_threads(ctypes.c_int(int(n)))
+
+
+def get_threads() -> int:
+    return int(lib().or_get_threads())
 
 
 def _c(a: np.ndarray) -> np.ndarray:

@@ -49,6 +49,7 @@
  */
 #include <complex.h>
 #include <math.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -655,6 +656,10 @@ int or_wilson_bicgstab(const or_wilson* p, const double* b, double* x, double to
     int64_t n = (int64_t)p->L[0] * p->L[1] * p->L[2] * p->L[3] * 12;
     return bicgstab(wilson_op, p, n, (const cplx*)b, (cplx*)x, tol, maxiter, iters, relres);
 }
+
+/* Threads of the OpenMP loops over sites (timing on a stated number of cores). */
+void or_set_threads(int n) { omp_set_num_threads(n > 0 ? n : 1); }
+int or_get_threads(void) { return omp_get_max_threads(); }
 
 /* A fixed number of CGNR iterations (for timing a bounded sample). */
 double or_wilson_cgnr_fixed(const or_wilson* p, const double* b, double* x, int niter) {

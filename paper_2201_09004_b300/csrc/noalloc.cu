@@ -52,36 +52,6 @@ void* scratch_address() {
     return g_scratch_ptr[dev];
 }
 
-__device__ __forceinline__ int lex_site(const Geo& g, const int c[4]) {
-    return c[0] + g.L[0] * (c[1] + g.L[1] * (c[2] + g.L[2] * c[3]));
-}
-
-template <int P, int NR>
-__global__ void noalloc_import_kernel(const double* canon, Geo g, int parity, FieldV f) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= g.vh) return;
-    int c[4];
-    cb_coords(g, s, parity, c);
-    const double* src = canon + (size_t)lex_site(g, c) * NR;
-    double v[NR];
-#pragma unroll
-    for (int k = 0; k < NR; k++) v[k] = src[k];
-    fstore<P, NR, double>(f, 0, s, v);
-}
-
-template <int P, int NR>
-__global__ void noalloc_export_kernel(double* canon, Geo g, int parity, FieldV f) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= g.vh) return;
-    int c[4];
-    cb_coords(g, s, parity, c);
-    double* dst = canon + (size_t)lex_site(g, c) * NR;
-    double v[NR];
-    fload<P, NR, double>(f, 0, s, v);
-#pragma unroll
-    for (int k = 0; k < NR; k++) dst[k] = v[k];
-}
-
 // packed links of a kind already resident in the lattice, or nothing
 bool packed_links(Lattice& lat, int kind, int prec, int recon, GaugeV* out) {
     std::lock_guard<std::mutex> lk(lat.mu);
@@ -93,10 +63,10 @@ bool packed_links(Lattice& lat, int kind, int prec, int recon, GaugeV* out) {
 
 template <int P, int NR, int R>
 void run_noalloc(Lattice& lat, bool hisq, const GaugeV& g1, const GaugeV& g2, int parity, int dagger, double c_naik,
-                 const double* in, double* out, const Field& fi, const Field& fo, cudaStream_t st) {
+                 const double* in, double* out, Field& fi, const Field& fo, cudaStream_t st) {
     const int block = 128;
     dim3 grid((lat.vh + block - 1) / block);
-    launch("noalloc_import", noalloc_import_kernel<P, NR>, grid, dim3(block), st, in, lat.geo, 1 - parity, fi.view());
+    import_field(lat, fi, 0, 1 - parity, in, st);
     if (hisq) {
         HisqArgs a;
         a.g = lat.geo;
@@ -132,7 +102,7 @@ void run_noalloc(Lattice& lat, bool hisq, const GaugeV& g1, const GaugeV& g2, in
         launch("wilson_dslash_noalloc", wilson_dslash_kernel<P, R, EPI_HOP, 1>, grid, dim3(block), st, a);
     }
     LQ_CUDA(cudaMemsetAsync(out, 0, (size_t)lat.V * NR * sizeof(double), st));
-    launch("noalloc_export", noalloc_export_kernel<P, NR>, grid, dim3(block), st, out, lat.geo, parity, fo.view());
+    export_field(lat, fo, 0, parity, out, st);
 }
 
 }  // namespace

@@ -232,11 +232,22 @@ class Lattice:
         return out
 
     def dslash_apply_noalloc(self, op, parity, psi, out, dagger=False, prec=F64, stream=None):
-        """lq_dslash_apply_noalloc: device tensors in/out, no device allocation in the library."""
+        """lq_dslash_apply_noalloc: device tensors in/out, no device allocation in the library.
+        The library writes V * ncomp complex128 entries into out, so both tensors are
+        checked for that size, dtype and device before the call."""
+        import torch
+        if not (_is_torch(psi) and psi.is_cuda and _is_torch(out) and out.is_cuda):
+            raise ValueError("lq_dslash_apply_noalloc takes device tensors")
+        ncomp = 3 if op.action == HISQ else 12
+        for name, t in (("psi", psi), ("out", out)):
+            if t.dtype != torch.complex128:
+                raise ValueError(f"{name} must be complex128, got {t.dtype}")
+            if t.numel() != self.volume * ncomp:
+                raise ValueError(f"{name} must hold {self.volume * ncomp} entries for this lattice, got {t.numel()}")
+        if psi.device != out.device:
+            raise ValueError("psi and out must be on the same device")
         p, loc, keep = _ptr(psi)
         po, loco, keepo = _ptr(out)
-        if loc != DEVICE or loco != DEVICE:
-            raise ValueError("lq_dslash_apply_noalloc takes device arrays")
         _check(lib().lq_dslash_apply_noalloc(self.h, ctypes.byref(op), ctypes.c_int(parity), ctypes.c_int(int(dagger)),
                                              ctypes.c_int(prec), p, po, _stream(stream)))
         return out

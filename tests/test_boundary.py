@@ -25,6 +25,32 @@ def test_header_declares_the_boundary():
         assert required in names
 
 
+def declaration_comments():
+    """Each declared entry point with the comment text that precedes its declaration
+    (back to the previous declaration, or to a blank line above its comment)."""
+    src = open(os.path.join(ROOT, "include", "lq.h")).read()
+    # the same text with every ';' inside a comment blanked, so that only code ends a declaration
+    code = re.sub(r"/\*.*?\*/", lambda c: c.group(0).replace(";", " "), src, flags=re.S)
+    out = {}
+    for m in re.finditer(r"^(?:int|int64_t|const char\*)\s+(lq_[a-z_0-9]+)\s*\(", src, flags=re.M):
+        before = src[: m.start()]
+        end = code[: m.start()].rfind(";")
+        chunk = before[end + 1:]
+        out[m.group(1)] = " ".join(re.findall(r"/\*(.*?)\*/", chunk, flags=re.S))
+    return out
+
+
+def test_every_entry_point_names_its_passage():
+    """Every exported call's comment says which passage of the paper defines what it
+    computes (a section, equation or table), or that the paper has no counterpart."""
+    comments = declaration_comments()
+    assert sorted(comments) == header_functions()
+    for name, text in comments.items():
+        cited = re.search(r"Paper:.*?(Sec\. \d|Eq\. \d|Table \d)", text, flags=re.S)
+        none = "no counterpart" in text
+        assert cited or none, name
+
+
 def test_library_exports_every_declared_symbol():
     ensure_library()
     from paper_2201_09004_b300 import lib

@@ -1,0 +1,189 @@
+"""Parity with the FP64 oracle at the benchmark's own sizes.
+
+The benchmark's numbers rest on these: the Wilson twisted-mass clover system on
+24^3x64 with the benchmark's seeds (Sec. 2.1 Eq. 2-3, the MILC12/RBC11 shape of
+Table 1), solved by the mixed-precision CG exactly as the benchmark launches it
+and checked by the oracle's own FP64 residual on the whole lattice; the clover
+Schur and full operators on sampled sites of that lattice; one call with the 12
+spin-colour point sources of a propagator (Table 2's 12-column propagators) on
+the fused multi-right-hand-side path; and the HISQ multi-shift solve down to the
+lightest mass of the HISQ configuration (Sec. 2.2, Table 3).
+
+Where the whole-lattice oracle operator would be repeated too often, the oracle's
+site-list forms (pinned on the CPU to equal the whole-lattice ones) compute the
+sampled outputs one by one.
+"""
+import numpy as np
+import pytest
+
+from helpers import TOL, ensure_library, rel_err
+from paper_2201_09004_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+DIMS = (24, 24, 24, 64)
+C_SW, MASS, MU = 1.05, 0.05, 0.01
+GAUGE_SEED, SOURCE_SEED = 102, 202
+
+
+@pytest.fixture(scope="module")
+def L():
+    ensure_library()
+    from paper_2201_09004_b300 import lib
+    return lib
+
+
+@pytest.fixture(scope="module")
+def headline(L, orc):
+    """The benchmark system: device lattice and the oracle operator on the host."""
+    U = synth.thin_links(DIMS, GAUGE_SEED, device="cuda")
+    b = synth.z2_source(DIMS, SOURCE_SEED, device="cuda")
+    lat = L.Lattice(DIMS, -1)
+    lat.load_gauge(L.THIN, U)
+    lat.load_clover(C_SW)
+    Uh = U.cpu().numpy()
+    del U
+    W = orc.Wilson(DIMS, Uh, MASS, MU, clover=orc.clover(DIMS, Uh, C_SW))
+    yield lat, W, b
+    lat.close()
+
+
+def lex_coords(dims, i):
+    lx, ly, lz, _ = dims
+    return i % lx, (i // lx) % ly, (i // (lx * ly)) % lz, i // (lx * ly * lz)
+
+
+def neighbours(dims, sites):
+    """The 8 nearest neighbours (lexicographic index) of every site."""
+    lx, ly, lz, lt = dims
+    x, y, z, t = lex_coords(dims, sites)
+    out = []
+    for c, L_, step in ((x, lx, 1), (y, ly, lx), (z, lz, lx * ly), (t, lt, lx * ly * lz)):
+        for d in (1, -1):
+            out.append(sites + ((c + d) % L_ - c) * step)
+    return np.unique(np.concatenate(out))
+
+
+def sample_sites(dims, parity, n, seed):
+    V = int(np.prod(dims))
+    cand = np.random.default_rng(seed).integers(0, V, size=4 * n)
+    x, y, z, t = lex_coords(dims, cand)
+    return np.unique(cand[(x + y + z + t) % 2 == parity])[:n]
+
+
+def site_matrix(W, dims, sites, dagger):
+    """A(x) (or A(x)^+) of M = A - H at the given sites of one parity, 12x12 each:
+    M applied to a unit vector placed on all of these sites, read at the same
+    sites, where the hopping term contributes nothing (it links opposite parities)."""
+    V = int(np.prod(dims))
+    A = np.empty((len(sites), 12, 12), dtype=complex)
+    e = np.zeros((V, 12), dtype=complex)
+    for j in range(12):
+        e[:] = 0
+        e[sites, j] = 1
+        A[:, :, j] = W.apply_sites(e.reshape(W.shape()), sites, dagger=dagger).reshape(-1, 12)
+    return A
+
+
+def schur_at_sites(W, dims, v, sites, dagger):
+    """(Mhat v)(s) for even sites s, Mhat = A_ee - H_eo A_oo^{-1} H_oe (the adjoint for
+    dagger): M applied to [v_e ; A_oo^{-1} H_oe v_e], which is needed only on the odd
+    neighbours of the sampled sites."""
+    V = int(np.prod(dims))
+    x, y, z, t = lex_coords(dims, np.arange(V))
+    even = ((x + y + z + t) % 2 == 0)
+    ve = np.where(even[:, None], v.reshape(V, 12), 0)
+    nb = neighbours(dims, sites)
+    h = W.hop_sites(ve.reshape(W.shape()), nb, dagger=dagger).reshape(-1, 12)
+    z_o = np.linalg.solve(site_matrix(W, dims, nb, dagger), h[..., None])[..., 0]
+    full = ve.copy()
+    full[nb] = z_o
+    return W.apply_sites(full.reshape(W.shape()), sites, dagger=dagger).reshape(-1, 12)
+
+
+def test_headline_solve_true_residual_by_the_oracle(L, headline):
+    """The benchmark's solve (mixed CGNR, FP16 storage, R12 links, delta 0.1, graphs
+    on) from the benchmark's source: the oracle's FP64 residual |b - M x| / |b| on the
+    whole lattice is at most 1e-10 and agrees with the library's own report to 1 %."""
+    lat, W, b = headline
+    op = L.op_params(L.WILSON_TM_CLOVER, MASS, MU, c_sw=C_SW)
+    sp = L.solve_params(solver=L.MIXED_CGNR, tol=1e-10, delta=0.1, prec_sloppy=L.F16, recon_sloppy=12)
+    xs, info = lat.solve(op, sp, [b])
+    assert info[0]["status"] == 0
+    bh = b.cpu().numpy()
+    r = bh - W.apply(xs[0].cpu().numpy())
+    res = float(np.linalg.norm(r) / np.linalg.norm(bh))
+    assert res <= 1e-10, res
+    assert abs(res / info[0]["true_rel_residual"] - 1) < 0.01, (res, info[0]["true_rel_residual"])
+
+
+@pytest.mark.parametrize("prec", [1, 2, 3])
+def test_full_size_schur_and_full_operator_with_clover(L, headline, prec):
+    """Clover-built Schur operator (both the operator and its adjoint) and the full
+    clover twisted-mass operator on 24^3x64, at 2000 sampled output sites each,
+    in FP32, FP16 storage and double-float."""
+    lat, W, _ = headline
+    op = L.op_params(L.WILSON_TM_CLOVER, MASS, MU, c_sw=C_SW)
+    v = synth.gaussian_field(DIMS, 209, device="cuda")
+    vh = v.cpu().numpy()
+    V = int(np.prod(DIMS))
+    sites = sample_sites(DIMS, 0, 2000, 71)
+    for dagger in (False, True):
+        got = lat.operator_apply(op, v, form=L.OP_SCHUR, dagger=dagger, prec=prec).cpu().numpy().reshape(V, 12)
+        ref = schur_at_sites(W, DIMS, vh, sites, dagger)
+        assert rel_err(got[sites], ref) < 10 * TOL[prec], (prec, dagger)
+    both = np.concatenate([sample_sites(DIMS, 0, 1000, 72), sample_sites(DIMS, 1, 1000, 73)])
+    for dagger in (False, True):
+        got = lat.operator_apply(op, v, form=L.OP_FULL, dagger=dagger, prec=prec).cpu().numpy().reshape(V, 12)
+        ref = W.apply_sites(vh, both, dagger=dagger).reshape(-1, 12)
+        assert rel_err(got[both], ref) < TOL[prec], (prec, dagger)
+
+
+@pytest.mark.parametrize("solver", ["MIXED_CGNR", "BICGSTAB"])
+def test_twelve_point_sources_in_one_call(L, orc, solver):
+    """The 12 spin-colour point sources of a propagator in one solve call (three
+    groups of four right-hand sides on the fused multi-RHS kernels, the path of the
+    multi-RHS and serving workloads), clover twisted mass on 16^3x32; every column's
+    true residual recomputed by the oracle is at most 1e-10."""
+    dims = (16, 16, 16, 32)
+    csw, m, mu = 1.04, 0.04, 0.008
+    U = synth.thin_links(dims, 103)
+    lat = L.Lattice(dims, -1)
+    lat.load_gauge(L.THIN, U.cuda())
+    lat.load_clover(csw)
+    site = synth.seeded_site(dims, 303)
+    srcs = [synth.point_source(dims, site, s, c, device="cuda") for s in range(4) for c in range(3)]
+    op = L.op_params(L.WILSON_TM_CLOVER, m, mu, c_sw=csw)
+    sp = L.solve_params(solver=getattr(L, solver), tol=1e-10, prec_sloppy=L.F16, recon_sloppy=12)
+    xs, info = lat.solve(op, sp, srcs)
+    Uh = U.numpy()
+    W = orc.Wilson(dims, Uh, m, mu, clover=orc.clover(dims, Uh, csw))
+    for k, (b, x) in enumerate(zip(srcs, xs)):
+        assert info[k]["status"] == 0, k
+        bh = b.cpu().numpy()
+        res = np.linalg.norm(bh - W.apply(x.cpu().numpy())) / np.linalg.norm(bh)
+        assert res <= 1e-10, (k, res)
+    lat.close()
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_hisq_multishift_down_to_the_lightest_mass(L, orc, prec):
+    """Multi-shift CG over the HISQ configuration's masses {0.002, 0.01, 0.02, 0.05}
+    on 8^3x16, every mass's true residual recomputed by the oracle."""
+    dims = (8, 8, 8, 16)
+    V = synth.fat_links(dims, 104)
+    Wl = synth.long_links(dims, 105)
+    lat = L.Lattice(dims, -1)
+    lat.load_gauge(L.FAT, V.cuda())
+    lat.load_gauge(L.LONG, Wl.cuda())
+    masses = [0.002, 0.01, 0.02, 0.05]
+    b = synth.z2_source(dims, 204, ncomp=3)
+    sp = L.solve_params(solver=L.MULTISHIFT_CG, tol=1e-10, prec_sloppy=prec, masses=masses)
+    xs, info = lat.solve(L.op_params(L.HISQ, masses[0]), sp, [b.cuda()])
+    assert info[0]["status"] == 0
+    bh = b.numpy()
+    for i, m in enumerate(masses):
+        D = orc.Hisq(dims, V.numpy(), Wl.numpy(), m)
+        res = np.linalg.norm(bh - D.apply(xs[i].cpu().numpy())) / np.linalg.norm(bh)
+        assert res <= 1e-10, (m, res)
+    lat.close()

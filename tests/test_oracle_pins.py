@@ -481,3 +481,27 @@ def test_overlap_sign_against_dense_eigendecomposition_2x4(orc):
     assert np.linalg.norm(got - exact) <= 2 * delta * np.linalg.norm(v)
     twice = orc.overlap_sign(hw, got, lmin, lmax, c)
     assert np.linalg.norm(twice - v) <= 4 * delta * np.linalg.norm(v)
+
+
+@pytest.mark.parametrize("dagger", [False, True])
+def test_site_sampled_operators_equal_full_lattice_ones(orc, rough_field, hisq_field, dagger):
+    """The site-list forms of the oracle (used by the full-size GPU tests, where
+    the whole-lattice operator is too slow to repeat) give exactly the values of
+    the whole-lattice operator at the same sites, in any site order, for the
+    Wilson hopping term, the clover twisted-mass operator and the HISQ hop."""
+    dims, U = rough_field
+    C = orc.clover(dims, U, 1.05)
+    psi = synth.gaussian_field(dims, 61).numpy()
+    V = int(np.prod(dims))
+    sites = np.random.default_rng(62).permutation(V)[: V // 3]
+    W = orc.Wilson(dims, U, 0.05, 0.1, clover=C)
+    assert np.array_equal(W.hop_sites(psi, sites, dagger=dagger),
+                          W.hop(psi, dagger=dagger).reshape(V, 4, 3)[sites])
+    assert np.array_equal(W.apply_sites(psi, sites, dagger=dagger),
+                          W.apply(psi, dagger=dagger).reshape(V, 4, 3)[sites])
+    hdims, Vf, Wl = hisq_field
+    H = orc.Hisq(hdims, Vf, Wl, 0.0)
+    chi = synth.gaussian_field(hdims, 63, ncomp=3).numpy()
+    hv = int(np.prod(hdims))
+    hsites = np.random.default_rng(64).permutation(hv)[: hv // 3]
+    assert np.array_equal(H.hop_sites(chi, hsites, dagger=dagger), H.hop(chi, dagger=dagger).reshape(hv, 3)[hsites])
