@@ -63,10 +63,33 @@ def bytes_per_site(name, recon=12):
 
 
 FLOPS_PER_SITE = {"hop": 1320, "ainv": 1320 + 2 * 6 * 6 * 8, "xpay": 1320 + 2 * 36 * 8 + 48}
-# dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of the
-# benchmark configuration (profiles/wilson_dslash_f16_ainv_24x24x24x64.md); set back to
-# None whenever the kernel changes after the capture.
-NCU_TRAFFIC = {("wilson_dslash_f16_ainv", 12): 254_847_232}
+
+# The sources of the FP16 Wilson kernels: an ncu traffic figure is used only while their
+# hash is the one the capture was taken with.
+KERNEL_SOURCES = ["core.cuh", "wilson.cuh", "wilson_x2.cuh", "dslash.cu", "dslash_launch.cuh"]
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha1()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2201_09004_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def ncu_traffic(kernel):
+    """dram__bytes_read.sum + dram__bytes_write.sum per launch of `kernel` from a committed
+    ncu summary (a line 'traffic: <kernel> <source hash> <bytes>' in profiles/*.md) taken
+    with the current kernel sources; None if there is none."""
+    import glob
+    want = kernel_source_hash()
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        for line in open(path):
+            parts = line.strip().strip("`").split()
+            if len(parts) == 4 and parts[0] == "traffic:" and parts[1] == kernel and parts[2] == want:
+                return int(parts[3])
+    return None
 
 REASONS = {
     0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap", 0x8: "hw_slowdown",
@@ -240,7 +263,8 @@ def gpu_arm(args):
                 "frac": round(achieved / peak, 4), "peak_source": peak_kind, "frac_of_nominal_8tbs": round(achieved / 8000.0, 4),
                 "algorithmic_bytes_per_launch": byts, "avg_launch_us": round(avg_s * 1e6, 2),
                 "gflops": round(FLOPS_PER_SITE[epi] * vh / avg_s / 1e9, 1),
-                "share_of_kernel_time": round(tot / all_t, 4), "traffic": NCU_TRAFFIC.get((dom, args.recon)),
+                "share_of_kernel_time": round(tot / all_t, 4),
+                "traffic": ncu_traffic(dom) if args.recon == 12 else None, "kernel_source_hash": kernel_source_hash(),
                 "pass": "second timed pass of the same steps with per-launch CUDA events",
                 "profiled_ms_per_step": round(profiled_ms, 3)}
     per_kernel = {k: {"launches": v[0], "ms": round(v[1], 3),
@@ -313,6 +337,33 @@ def gpu_arm(args):
                "defect_corrections": ig[0]["reliable_updates"], "operator_applications": ig[0]["operator_applications"],
                "true_rel_residual": ig[0]["true_rel_residual"], "speedup_over_mixed_cgnr": round(1.0 / (sg * value / world), 2)}
 
+    # the same solve with its inner CG iterations in one persistent cooperative kernel
+    # (k iterations per launch), against CUDA-graph replay of 1 and 4 iterations per graph
+    persistent = None
+    if args.persistent_steps > 0:
+        def rate(spx, steps):
+            lat.solve(op, spx, [b], stream=stream, out=[x])
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            inf = None
+            for _ in range(steps):
+                _, inf = lat.solve(op, spx, [b], stream=stream, out=[x])
+            e1.record(stream)
+            torch.cuda.synchronize()
+            sec = e0.elapsed_time(e1) * 1e-3 / steps
+            return {"solves_per_s": round(1.0 / sec, 3), "iters": inf[0]["iters"],
+                    "reliable_updates": inf[0]["reliable_updates"], "true_rel_residual": inf[0]["true_rel_residual"]}
+        persistent = {}
+        for k in (1, 4):
+            persistent[f"persistent_{k}_iters_per_launch"] = rate(
+                lib.solve_params(solver=lib.MIXED_CGNR, tol=TOL, delta=0.1, prec_sloppy=args.prec,
+                                 recon_sloppy=args.recon, persistent=k), args.persistent_steps)
+            persistent[f"graph_{k}_iters_per_graph"] = rate(
+                lib.solve_params(solver=lib.MIXED_CGNR, tol=TOL, delta=0.1, prec_sloppy=args.prec,
+                                 recon_sloppy=args.recon, graph_iters=k), args.persistent_steps)
+
     # end to end through the C ABI with pinned host buffers
     bh = b.cpu().pin_memory()
     xh = torch.empty_like(bh).pin_memory()
@@ -344,11 +395,19 @@ def gpu_arm(args):
             "latency_ms": {"p50": round(float(np.percentile(lat_ms, 50)), 3),
                            "p99": round(float(np.percentile(lat_ms, 99)), 3)},
             "roofline": roofline, "kernels": per_kernel, "time_breakdown": breakdown, "fp64": fp64,
-            "bicgstab": bicg, "gcr": gcr, "e2e": e2e,
+            "bicgstab": bicg, "gcr": gcr, "persistent": persistent, "e2e": e2e,
             "gpu_launches": int(launches), "clocks": clocks,
         }
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
+        # the other single-GPU configurations, measured in the same run: 36 right-hand
+        # sides at 32^3x96 (multi-RHS kernels, mixed CGNR) and the 48^3x144 HISQ multi-shift
+        if args.with_configs and world == 1:
+            lat.close()
+            del b, x
+            torch.cuda.empty_cache()
+            line["multirhs_32x32x32x96"] = run_multirhs(args)
+            line["hisq_48x48x48x144"] = run_hisq(args)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
@@ -392,6 +451,7 @@ def run_multirhs(args):
     site = synth.seeded_site(dims, 303)
     srcs = [synth.point_source(dims, site, sp, c, device="cuda") for sp in range(4) for c in range(3)]
     xs = [torch.empty_like(srcs[0]) for _ in srcs]
+    tp0 = time.perf_counter()
     sp = lib.solve_params(solver=lib.MIXED_CGNR, tol=TOL, prec_sloppy=args.prec, recon_sloppy=args.recon)
     ops = [lib.op_params(lib.WILSON_TM_CLOVER, m, mu, c_sw=csw) for mu in mus]
     for op in ops:  # warm-up: clover inverses per mass, tuning of the NB = 4 kernels
@@ -410,12 +470,49 @@ def run_multirhs(args):
     lib.profile_enable(False)
     tts = e0.elapsed_time(e1) * 1e-3
     vh = int(np.prod(dims)) // 2
-    # algorithmic bytes per site of one launch over the 12 right-hand sides of a call:
-    # links and the clover (inverse) block once, spinors per right-hand side
+    # algorithmic bytes per site of one launch over the 12 right-hand sides of a call: the
+    # spinors per right-hand side, the links and the clover (inverse) record once per group
+    # of 4 right-hand sides (the threads of one site; the 3 groups meet them in L2 at best)
     n = len(srcs)
-    bps = {"wilson_dslash_f16_ainv": n * 52 + 8 * 24 + (144 * 2 + 4) + n * 52,
-           "wilson_dslash_f16_xpay": n * 52 + 8 * 24 + (72 * 2 + 4) + n * 52 + n * 52}
+    groups = (n + 3) // 4
+    bps = {"wilson_dslash_f16_ainv": n * 52 + groups * (8 * 24 + (144 * 2 + 4)) + n * 52,
+           "wilson_dslash_f16_xpay": n * 52 + groups * (8 * 24 + (72 * 2 + 4)) + n * 52 + n * 52}
     kern = _kernel_table(list(bps) + ["wilson_dslash_f32x2_ainv", "wilson_dslash_f32x2_xpay"], vh, bps)
+    for k in ("wilson_dslash_f16_ainv", "wilson_dslash_f16_xpay"):
+        if k in kern:
+            kern[k]["gbs_per_rhs"] = round(kern[k]["gbs"] / n, 1)
+    # the batching gain alone: the same mixed-precision solver one right-hand side per call
+    single = []
+    for op in ops:
+        lat.solve(op, sp, [srcs[0]], out=[xs[0]])  # tunes the single-RHS kernels of this mass
+        torch.cuda.synchronize()
+        e0, e1 = _events()
+        e0.record()
+        for j in range(2):
+            _, inf = lat.solve(op, sp, [srcs[4 * j + 1]], out=[xs[0]])
+        e1.record()
+        torch.cuda.synchronize()
+        single.append(e0.elapsed_time(e1) * 1e-3 / 2)
+    t_single36 = 12 * sum(single)
+    # device time per right-hand side of each kernel family, batched (12 per call) and single
+    families = ["wilson_dslash_f16", "wilson_dslash_f32x2", "blas_cg_xs", "blas_cg_p", "blas_finalize", "blas_",
+                "import_field", "export_field", "wilson_ainv_site"]
+    per_rhs = {"batched_12": {}, "single": {}}
+    for f in families:
+        n_, t_ = lib.profile_query(f)
+        if n_:
+            per_rhs["batched_12"][f] = round(t_ / 36, 3)
+    lib.profile_reset()
+    lib.profile_enable(True)
+    _, inf1 = lat.solve(ops[1], sp, [srcs[2]], out=[xs[0]])
+    torch.cuda.synchronize()
+    lib.profile_enable(False)
+    for f in families:
+        n_, t_ = lib.profile_query(f)
+        if n_:
+            per_rhs["single"][f] = round(t_, 3)
+    per_rhs["note"] = "ms of device time per right-hand side (profiled; 'blas_' is every BLAS kernel)"
+    per_rhs["single_iters"] = inf1[0]["iters"]
     # the same 36 right-hand sides with mixed-precision BiCGStab on the Schur operator
     spb = lib.solve_params(solver=lib.BICGSTAB, tol=TOL, prec_sloppy=args.prec, recon_sloppy=args.recon)
     lat.solve(ops[0], spb, srcs[:4], out=xs[:4])
@@ -446,11 +543,58 @@ def run_multirhs(args):
             "fp64_single_rhs": {"seconds_per_solve": round(t64, 3), "iters": i64[0]["iters"],
                                 "seconds_for_36_extrapolated": round(36 * t64, 3)},
             "speedup_vs_fp64_single_rhs": round(36 * t64 / tts, 2),
+            "mixed_single_rhs": {"seconds_per_solve_per_mass": [round(t, 4) for t in single],
+                                 "seconds_for_36_extrapolated": round(t_single36, 3),
+                                 "sample": "2 point sources per mass, one per call, times 12"},
+            "batching_gain_vs_mixed_single_rhs": round(t_single36 / tts, 2),
+            "device_ms_per_rhs": per_rhs,
+            "wall_seconds_incl_setup": round(time.perf_counter() - tp0, 1),
             "bicgstab": {"seconds": round(tts_b, 3), "iters_max": max(i["iters"] for i in binfos),
                          "true_rel_residual_max": max(i["true_rel_residual"] for i in binfos),
                          "all_converged": all(i["status"] == 0 for i in binfos),
                          "speedup_vs_fp64_single_rhs": round(36 * t64 / tts_b, 2)},
             "kernels": kern}
+    lat.close()
+    torch.cuda.empty_cache()
+    return line
+
+
+def run_delta(args):
+    """The reliable-update threshold delta against the sloppy precision on the headline
+    system (24^3x64 twisted-mass clover, mixed CGNR to 1e-10): iterations, reliable
+    updates, time to solution and the device time of the double-float operator, per
+    (delta, precision) pair."""
+    import torch
+    from paper_2201_09004_b300 import lib
+    torch.cuda.set_device(0)
+    lat, b = setup_gpu("cuda")
+    op = lib.op_params(lib.WILSON_TM_CLOVER, MASS, MU, c_sw=C_SW)
+    x = torch.empty_like(b)
+    rows = []
+    for prec in (lib.F16, lib.F32):
+        for delta in (0.1, 0.05, 0.02, 0.01):
+            sp = lib.solve_params(solver=lib.MIXED_CGNR, tol=TOL, delta=delta, prec_sloppy=prec, recon_sloppy=12)
+            lat.solve(op, sp, [b], out=[x])
+            torch.cuda.synchronize()
+            lib.profile_reset()
+            lib.profile_enable(True)
+            e0, e1 = _events()
+            e0.record()
+            reps = 3
+            for _ in range(reps):
+                _, inf = lat.solve(op, sp, [b], out=[x])
+            e1.record()
+            torch.cuda.synchronize()
+            lib.profile_enable(False)
+            n_df, t_df = lib.profile_query("wilson_dslash_f32x2")
+            rows.append({"sloppy": {lib.F16: "f16", lib.F32: "f32"}[prec], "delta": delta,
+                         "iters": inf[0]["iters"], "reliable_updates": inf[0]["reliable_updates"],
+                         "ms_per_solve": round(e0.elapsed_time(e1) / reps, 2),
+                         "double_float_operator_ms_per_solve": round(t_df / reps, 2),
+                         "true_rel_residual": inf[0]["true_rel_residual"]})
+    line = {"workload": "delta", "metric": "mixed CGNR against the reliable-update threshold and sloppy precision",
+            "config": {"dims": list(DIMS), "tol": TOL, "note": "timed with per-launch events (profiling on)"},
+            "rows": rows}
     print(json.dumps(line), flush=True)
 
 
@@ -595,7 +739,10 @@ def run_hisq(args):
             "iters": info[0]["iters"], "reliable_updates": info[0]["reliable_updates"],
             "true_rel_residual_max_over_shifts": info[0]["true_rel_residual"], "status": info[0]["status"],
             "setup_seconds": round(gen_s, 1), "multishift_stage_to_1e-3": ms_stage, "kernels": kern}
-    print(json.dumps(line), flush=True)
+    lat.close()
+    del b, xs
+    torch.cuda.empty_cache()
+    return line
 
 
 def run_hisq_propagator(args):
@@ -923,6 +1070,12 @@ def run_serving(args):
     warm = [(si, 0, k, 0.02) for si in range(len(sizes)) for k in ("tmc", "hisq")]
     serve(warm, [0.0] * len(warm), False, 1)
     serve_fifo(warm[:2], [0.0] * 2)
+    ms = lambda a, q: round(float(np.percentile(a, q)) * 1e3, 1)
+
+    def summary(lat_s, wall, st, n):
+        return {"p50_ms": ms(lat_s, 50), "p99_ms": ms(lat_s, 99), "solves_per_s": round(n / wall, 3),
+                "all_ok": all(c == 0 for c in st)}
+
     # capacity of the mixed server: back-to-back service of a calibration batch
     calib = make_requests(16)
     _, wall_c, _ = serve(calib, [0.0] * len(calib), False, 4)
@@ -932,18 +1085,30 @@ def run_serving(args):
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))
     arrivals -= arrivals[0]
     lat_mixed, wall_mixed, st_mixed = serve(reqs, arrivals, False, 4)
-    lat_fifo, wall_fifo, st_fifo = serve_fifo(reqs, arrivals)
-    ms = lambda a, q: round(float(np.percentile(a, q)) * 1e3, 1)
     line = {"workload": "serving", "metric": "p50/p99 request latency and solves/s on a Poisson trace",
             "requests": len(reqs), "rate_per_s": round(rate, 3), "capacity_calibration_per_s": round(capacity, 3),
-            "mixed_continuous_batching": {"p50_ms": ms(lat_mixed, 50), "p99_ms": ms(lat_mixed, 99),
-                                          "solves_per_s": round(len(reqs) / wall_mixed, 3),
-                                          "all_ok": all(c == 0 for c in st_mixed), "slots": 4},
-            "fifo_fp64_one_at_a_time": {"p50_ms": ms(lat_fifo, 50), "p99_ms": ms(lat_fifo, 99),
-                                        "solves_per_s": round(len(reqs) / wall_fifo, 3),
-                                        "all_ok": all(c == 0 for c in st_fifo)},
+            "mixed_continuous_batching": dict(summary(lat_mixed, wall_mixed, st_mixed, len(reqs)), slots=4),
             "config": {"sizes": [list(d) for d in sizes], "actions": ["wilson_tm_clover 12 rhs", "hisq 1 rhs"],
                        "mass_range": [0.005, 0.05], "gauge_seeds_per_size": 2, "tol": TOL, "trace_seed": 505}}
+    # both servers on one trace at a rate the FIFO FP64 server sustains (0.8 x its own
+    # measured capacity), so that its latencies measure solves rather than an ever-growing queue
+    if args.fifo_requests > 0:
+        calib_f = make_requests(6)
+        t0 = time.perf_counter()
+        serve_fifo(calib_f, [0.0] * len(calib_f))
+        cap_f = len(calib_f) / (time.perf_counter() - t0)
+        rate_f = 0.8 * cap_f
+        reqs_f = make_requests(args.fifo_requests)
+        arr_f = np.cumsum(rng.exponential(1.0 / rate_f, size=len(reqs_f)))
+        arr_f -= arr_f[0]
+        lm, wm, sm = serve(reqs_f, arr_f, False, 4)
+        lf, wf, sf = serve_fifo(reqs_f, arr_f)
+        line["at_fifo_sustainable_rate"] = {
+            "requests": len(reqs_f), "rate_per_s": round(rate_f, 4), "fifo_capacity_calibration_per_s": round(cap_f, 4),
+            "mixed_continuous_batching": summary(lm, wm, sm, len(reqs_f)),
+            "fifo_fp64_one_at_a_time": summary(lf, wf, sf, len(reqs_f)),
+            "p50_ratio_fifo_over_mixed": round(float(np.percentile(lf, 50) / np.percentile(lm, 50)), 2),
+            "p99_ratio_fifo_over_mixed": round(float(np.percentile(lf, 99) / np.percentile(lm, 99)), 2)}
     print(json.dumps(line), flush=True)
 
 
@@ -1058,6 +1223,10 @@ def main():
     ap.add_argument("--gcr-steps", type=int, default=3,
                     help="also time the mixed-precision restarted GCR solve of the same system")
     ap.add_argument("--gcr-restart", type=int, default=0, help="GCR directions before a restart (0 = 12)")
+    ap.add_argument("--with-configs", type=int, default=1,
+                    help="1: also run the 36-RHS 32^3x96 and the 48^3x144 HISQ workloads into the line")
+    ap.add_argument("--persistent-steps", type=int, default=3,
+                    help="also time the solve with the persistent CG kernel and with 1 / 4 iterations per graph")
     ap.add_argument("--ref-iters", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--eig-dims", type=int, nargs=4, default=[8, 8, 8, 16], help="eigen: lattice extents x y z t")
@@ -1067,12 +1236,14 @@ def main():
     ap.add_argument("--lambda-cut", type=float, default=0.6, help="eigen: filter edge")
     ap.add_argument("--eig-tol", type=float, default=1e-8, help="eigen: residual bound")
     ap.add_argument("--max-restarts", type=int, default=30, help="eigen: restart limit")
-    ap.add_argument("--workload", default="tmc", choices=["tmc", "multirhs", "hisq", "serving", "dslash", "hisq3col", "overlap", "tmms", "eigen"],
+    ap.add_argument("--workload", default="tmc", choices=["tmc", "multirhs", "hisq", "serving", "dslash", "hisq3col", "overlap", "tmms", "eigen", "delta"],
                     help="tmc: 24^3x64 twisted-mass clover (default, the headline); multirhs: 32^3x96, "
                          "36 right-hand sides; hisq: 48^3x144 multi-shift; serving: Poisson request stream; "
                          "dslash: the operator kernels alone; hisq3col: HISQ 3-column propagator 24^3x64; "
                          "overlap: g5 D_w and the sign function; tmms: twisted multi-mass solve")
-    ap.add_argument("--requests", type=int, default=100, help="serving: number of requests")
+    ap.add_argument("--requests", type=int, default=400, help="serving: number of requests")
+    ap.add_argument("--fifo-requests", type=int, default=40,
+                    help="serving: requests of the trace at the FIFO FP64 server's sustainable rate (0: skip)")
     ap.add_argument("--graph-iters", type=int, default=0,
                     help="CG iterations per CUDA graph (0: library default, -1: no graphs)")
     args = ap.parse_args()
@@ -1081,9 +1252,9 @@ def main():
     if args.impl == "reference":
         reference_arm(args)
     elif args.workload == "multirhs":
-        run_multirhs(args)
+        print(json.dumps(run_multirhs(args)), flush=True)
     elif args.workload == "hisq":
-        run_hisq(args)
+        print(json.dumps(run_hisq(args)), flush=True)
     elif args.workload == "dslash":
         run_dslash(args)
     elif args.workload == "hisq3col":
@@ -1096,6 +1267,8 @@ def main():
         run_serving(args)
     elif args.workload == "eigen":
         run_eigen(args)
+    elif args.workload == "delta":
+        run_delta(args)
     else:
         gpu_arm(args)
 

@@ -153,6 +153,11 @@ typedef struct {
     int graph_iters;  /* Krylov iterations captured per CUDA graph and replayed with one
                          launch: 0 = the library's choice (1), < 0 = no graphs */
     int restart;      /* LQ_GCR: directions kept before a restart (0 = 12, at most 16) */
+    int persistent;   /* LQ_MIXED_CGNR, Wilson clover, prec_sloppy LQ_F16, recon_sloppy LQ_R12, one
+                         right-hand side: > 0 runs that many CG iterations per launch of one persistent
+                         cooperative kernel (grid-wide barriers between the operator, vector and
+                         reduction phases) instead of separate kernels and graphs; 0 = off. Other
+                         configurations ignore it. */
 } lq_solve_params;
 
 typedef struct {
@@ -343,6 +348,15 @@ int lq_tune_reset(void);
  * has no counterpart. */
 int lq_tune_force(int code);
 
+/* Test of the bounded grid-wide barrier that the persistent CG kernel uses: one
+ * cooperative launch of `blocks` blocks (<= 64) meets `rounds` times at a barrier
+ * that waits for `expect` blocks (blocks <= expect <= 64). With expect == blocks
+ * every barrier completes (LQ_OK, *failed = 0); with expect > blocks the first wait
+ * runs out after about half a second, the kernel returns and the call gives
+ * LQ_ETIMEOUT with *failed = 1. No GPU state is left behind either way.
+ * Paper: no counterpart (a diagnostic of this library). */
+int lq_barrier_selftest(int blocks, int expect, int rounds, int* failed);
+
 /* ----------------------------------------------------------------- overlap */
 
 /* Building blocks of the overlap operator (Sec. 2.3):
@@ -432,7 +446,10 @@ int lq_overlap_sign_apply_deflated(lq_lattice lat, double rho, double lambda_min
 
 /* A request server for continuous batching of solves: requests are queued,
  * admitted while their estimated device memory fits in hbm_budget_bytes (next
- * to the lattices they use), at most max_slots at once; each admitted request
+ * to the lattices they use), at most max_slots at once. Admission takes the
+ * first queued request, in arrival order, that fits: one that does not fit yet
+ * is overtaken by later ones that do, at most 2 * max_slots times, after which
+ * nothing behind it is admitted before it (no starvation). Each admitted request
  * runs on its own worker thread and CUDA stream, so solves that arrive while
  * others are on the GPU start as soon as a slot and memory free up and then
  * overlap with them on the device. Lattices (gauge and clover fields) are

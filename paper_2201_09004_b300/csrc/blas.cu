@@ -211,7 +211,17 @@ __global__ void finalize_kernel(const df* part, int nblocks, double* sc, int slo
     const int k = blockIdx.x;
     const df* pk = part + (size_t)k * nblocks;
     df sum(0.f);
-    for (int i = threadIdx.x; i < nblocks; i += blockDim.x) sum = sum + pk[i];
+    // sixteen partials in flight per thread, added in the order of one at a time
+    const int B = blockDim.x;
+    for (int i0 = threadIdx.x; i0 < nblocks; i0 += 16 * B) {
+        float2 v[16];
+#pragma unroll
+        for (int j = 0; j < 16; j++)
+            v[j] = i0 + j * B < nblocks ? __ldcg((const float2*)(pk + i0 + j * B)) : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < 16; j++)
+            if (i0 + j * B < nblocks) sum = sum + df(v[j].x, v[j].y);
+    }
     sum = block_sum_df(sum);
     if (threadIdx.x == 0) fin_apply(sc + (size_t)k * SC_N, df_to_double(sum), slot, op);
 }

@@ -99,6 +99,15 @@ extern "C" int lq_create_lattice(const int dims[4], int t_boundary, lq_lattice* 
     L.geo.lxh = dims[0] / 2;
     L.geo.vh = L.vh;
     L.geo.bc_t = t_boundary;
+    {
+        const int ds[3] = {dims[0] / 2, dims[1], dims[2]};
+        L.geo.fast = 1;
+        for (int k = 0; k < 3; k++) {
+            const unsigned long long d = (unsigned long long)ds[k];
+            L.geo.fdiv[k] = d == 1 ? 0u : (unsigned)(((1ull << 32) + d - 1) / d);
+            if ((unsigned long long)L.vh * d >= (1ull << 32)) L.geo.fast = 0;
+        }
+    }
     cudaGetDevice(&L.device);
     *out = h;
     return LQ_OK;

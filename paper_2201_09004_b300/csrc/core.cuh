@@ -118,6 +118,7 @@ enum {
     SC_RR = 0, SC_QQ, SC_SS, SC_RRN, SC_ALPHA, SC_BETA, SC_B2, SC_FROZEN, SC_PP,
     SC_RHO_R, SC_RHO_I, SC_AL_R, SC_AL_I, SC_OM_R, SC_OM_I, SC_BE_R, SC_BE_I, SC_BREAK,
     SC_SIGMA,  // the rhs's shift sigma of a hermitian operator sigma + K^+ K
+    SC_ITERS,  // iterations done by the persistent CG kernel (running total)
     SC_N
 };
 enum { FIN_SET = 0, FIN_ALPHA = 1, FIN_BETA = 2, FIN_BICG_ALPHA = 3, FIN_BICG_OMEGA = 4, FIN_BICG_BETA = 5,
@@ -240,7 +241,16 @@ __device__ __forceinline__ void fin_tail_w(const df* part, int nparts, int nrhs,
         for (int w = 0; w < W; w++) {
             const df* pk = part + (size_t)(k * W + w) * nparts;
             df sum(0.f);
-            for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+            const int B = blockDim.x;
+            int i = threadIdx.x;
+            for (; i + 7 * B < nparts; i += 8 * B) {  // eight in flight, same order of additions
+                float2 v[8];
+#pragma unroll
+                for (int j = 0; j < 8; j++) v[j] = __ldcg((const float2*)(pk + i + j * B));
+#pragma unroll
+                for (int j = 0; j < 8; j++) sum = sum + df(v[j].x, v[j].y);
+            }
+            for (; i < nparts; i += B) {
                 const float2 v = __ldcg((const float2*)(pk + i));
                 sum = sum + df(v.x, v.y);
             }
@@ -266,9 +276,17 @@ __device__ __forceinline__ void fin_tail(const df* part, int nparts, int nrhs, c
     for (int k = 0; k < nrhs; k++) {
         const df* pk = part + (size_t)k * nparts;
         df sum(0.f);
-        for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
-            const float2 v = __ldcg((const float2*)(pk + i));
-            sum = sum + df(v.x, v.y);
+        // sixteen partials in flight per thread (missing ones read as zero, which adds
+        // nothing), added in the same order as one at a time
+        const int B = blockDim.x;
+        for (int i0 = threadIdx.x; i0 < nparts; i0 += 16 * B) {
+            float2 v[16];
+#pragma unroll
+            for (int j = 0; j < 16; j++)
+                v[j] = i0 + j * B < nparts ? __ldcg((const float2*)(pk + i0 + j * B)) : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int j = 0; j < 16; j++)
+                if (i0 + j * B < nparts) sum = sum + df(v[j].x, v[j].y);
         }
         sum = block_sum_df(sum);
         if (threadIdx.x == 0) fin_apply(f.sc + (size_t)k * SC_N, df_to_double(sum), f.slot, f.op);
@@ -323,6 +341,10 @@ struct Geo {
     int lxh;      // Lx / 2
     int vh;       // V / 2 (sites per parity)
     int bc_t;     // time boundary sign, +1 or -1
+    // multiply-high divisors by lxh, L[1], L[2]: n / d = umulhi(n, ceil(2^32 / d)),
+    // exact while n d < 2^32 (0 stands for d = 1); fast = 0 where that fails
+    unsigned fdiv[3];
+    int fast;
 };
 
 __device__ __forceinline__ void cb_coords(const Geo& g, int cb, int p, int c[4]) {

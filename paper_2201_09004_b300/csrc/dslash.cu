@@ -4,8 +4,58 @@
 #include <string>
 
 #include "dslash_launch.cuh"
+#include "wilson_x2.cuh"
 
 namespace lq {
+
+// FP16 / R12 single-right-hand-side kernels on packed FP32 pairs (wilson_x2.cuh).
+// Tuning codes (variant * 1000 + block size):
+//   3: registers for 4 resident blocks of 128 threads (128 per thread), two hops in flight;
+//   4: 6 blocks (85 registers), two hops in flight;
+//   5: 5 blocks (102 registers), one hop in flight;  6: 6 blocks, one hop in flight;
+//   7: blocks of 256 threads, 2 resident (128 registers), two hops in flight (half the
+//      blocks, and so half the partial sums of a fused reduction).
+enum { kX2 = 3000, kX2c = 4000, kX2d = 5000, kX2e = 6000, kX2w = 7000 };
+
+template <int EPI, bool DAG, int MINB, int DEPTH, int BT = 128>
+static void wl_x2(const char* name, const WilsonArgs& a, int block, cudaStream_t st) {
+    dim3 grid((a.g.vh + block - 1) / block);
+    launch_smem(name, wilson_f16x2_kernel<EPI, DAG, MINB, DEPTH, BT>, grid, dim3(block), x2_smem_bytes<EPI>(block),
+                st, a);
+}
+
+// several right-hand sides, RG = 4 threads per site (variants 3 and 5 of the single-RHS codes)
+template <int EPI, bool DAG, int MINB, int DEPTH>
+static void wl_x2m(const char* name, const WilsonArgs& a, int block, cudaStream_t st) {
+    constexpr int RG = 4;
+    const int ngroups = (a.nrhs + RG - 1) / RG;
+    dim3 grid(site_blocks(a.g.vh, block, RG) * ngroups);
+    launch_smem(name, wilson_f16x2_mrhs_kernel<EPI, DAG, MINB, DEPTH, RG>, grid, dim3(block),
+                x2_smem_bytes<EPI>(block, RG), st, a);
+}
+
+template <int EPI, bool DAG>
+static void wl_x2_var(const char* name, const WilsonArgs& a, int cfg, cudaStream_t st) {
+    if (a.nrhs > 1) {
+        if (cfg / 1000 == 5) wl_x2m<EPI, DAG, 5, 1>(name, a, cfg % 1000, st);
+        else wl_x2m<EPI, DAG, 4, 2>(name, a, cfg % 1000, st);
+        return;
+    }
+    const int block = cfg % 1000;
+    switch (cfg / 1000) {
+        case 4: wl_x2<EPI, DAG, 6, 2>(name, a, block, st); break;
+        case 5: wl_x2<EPI, DAG, 5, 1>(name, a, block, st); break;
+        case 6: wl_x2<EPI, DAG, 6, 1>(name, a, block, st); break;
+        case 7: wl_x2<EPI, DAG, 2, 2, 256>(name, a, block, st); break;
+        default: wl_x2<EPI, DAG, 4, 2>(name, a, block, st); break;
+    }
+}
+
+template <int EPI>
+static void wl_x2_cfg(const char* name, const WilsonArgs& a, int cfg, cudaStream_t st) {
+    if (a.dagger) wl_x2_var<EPI, true>(name, a, cfg, st);
+    else wl_x2_var<EPI, false>(name, a, cfg, st);
+}
 
 static const char* wname(int prec, int epi) {
     static const char* n[4][3] = {
@@ -16,8 +66,8 @@ static const char* wname(int prec, int epi) {
     return n[prec][epi];
 }
 
-int wilson_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int epi, const Field& in, Field& out,
-                  const Field* y, df* norm_out, cudaStream_t st, const FinArgs& fin) {
+WilsonArgs wilson_args(Lattice& lat, const OpDesc& op, int parity, int dagger, int epi, const Field& in, Field& out,
+                       const Field* y, cudaStream_t st) {
     if (in.prec != op.prec || out.prec != op.prec || (y && y->prec != op.prec))
         fail(LQ_EINVAL, "wilson_dslash: field precision does not match the operator");
     if (in.kind != LQ_WILSON_FIELD || out.nrhs != in.nrhs) fail(LQ_EINVAL, "wilson_dslash: field shape");
@@ -34,19 +84,38 @@ int wilson_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int ep
     a.m4 = 4.0 + op.m;
     a.mu = dagger ? -op.mu : op.mu;
     a.mu1 = dagger ? -mu_block1(op) : mu_block1(op);
+    a.m4f = (float)a.m4;
+    a.muf = (float)a.mu;
+    a.mu1f = (float)a.mu1;
     a.nrhs = in.nrhs;
-    a.norm_out = norm_out;
-    a.fin = FinArgs();  // the tuner's trial launches never finalise
+    a.norm_out = nullptr;
+    a.fin = FinArgs();
     a.clov = nullptr;
     a.clov_norm = nullptr;
     if (a.has_clover) {
         if (epi == EPI_XPAY) a.clov = clover_block(lat, op.prec, parity, &a.clov_norm);
         else if (epi == EPI_AINV) a.clov = ainv_block(lat, op.m, op.mu, mu_block1(op), op.prec, parity, &a.clov_norm, st);
     }
+    return a;
+}
+
+int wilson_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int epi, const Field& in, Field& out,
+                  const Field* y, df* norm_out, cudaStream_t st, const FinArgs& fin) {
+    WilsonArgs a = wilson_args(lat, op, parity, dagger, epi, in, out, y, st);
+    a.norm_out = norm_out;
+    a.fin = FinArgs();  // the tuner's trial launches never finalise
     const int nb = (op.prec == LQ_F32 || op.prec == LQ_F16) ? pick_rg(a.nrhs) : 1;
     const char* name = wname(op.prec, epi);
+    // the packed-pair FP16 kernels: R12 links, one right-hand side, the clover epilogues
+    // (or none), no g5 on the output, and lattices whose site index fits the fast division
+    const bool x2 = op.prec == LQ_F16 && op.recon == 12 && (a.nrhs == 1 || nb == 4) && !a.gamma5_out &&
+                    lat.geo.fast && (epi == EPI_HOP || a.has_clover);
     auto run = [&](int block) {  // block: a tuning code (see wl_nb)
-        if (op.prec == LQ_F64) {
+        if (x2 && block >= kX2) {
+            if (epi == EPI_HOP) wl_x2_cfg<EPI_HOP>(name, a, block, st);
+            else if (epi == EPI_AINV) wl_x2_cfg<EPI_AINV>(name, a, block, st);
+            else wl_x2_cfg<EPI_XPAY>(name, a, block, st);
+        } else if (op.prec == LQ_F64) {
             if (op.recon == 18) wl_epi<P64, 18>(name, a, epi, nb, block, st);
             else wl_epi<P64, 12>(name, a, epi, nb, block, st);
         } else if (op.prec == LQ_F32X2) {
@@ -71,6 +140,14 @@ int wilson_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int ep
         for (int b : {64, 128, 256}) cand.push_back(kCapped + b);
     if ((op.prec == LQ_F32 || op.prec == LQ_F16) && nb == 1)
         for (int b : {64, 128}) cand.push_back(kDeep + b);
+    if (x2 && a.nrhs == 1) {
+        for (int v : {kX2, kX2c, kX2d, kX2e})
+            for (int b : {64, 128}) cand.push_back(v + b);
+        cand.push_back(kX2w + 256);
+    }
+    if (x2 && a.nrhs > 1)
+        for (int v : {kX2, kX2d})
+            for (int b : {64, 128}) cand.push_back(v + b);
     int cfg = tuned_block(key, st, run, cand);
     a.fin = norm_out ? fin : FinArgs();
     run(cfg);

@@ -248,14 +248,19 @@ int tuned_block(const std::string& key, cudaStream_t st, const std::function<voi
             } catch (const Error&) {
                 continue;
             }
-            LQ_CUDA(cudaEventRecord(a, st));
-            for (int r = 0; r < 3; r++) run(bs);
-            LQ_CUDA(cudaEventRecord(b, st));
-            LQ_CUDA(cudaEventSynchronize(b));
-            float ms = 0.f;
-            LQ_CUDA(cudaEventElapsedTime(&ms, a, b));
+            // three separately timed launches; the median is the candidate's time
+            float t3[3];
+            for (int r = 0; r < 3; r++) {
+                LQ_CUDA(cudaEventRecord(a, st));
+                run(bs);
+                LQ_CUDA(cudaEventRecord(b, st));
+                LQ_CUDA(cudaEventSynchronize(b));
+                LQ_CUDA(cudaEventElapsedTime(&t3[r], a, b));
+            }
+            std::sort(t3, t3 + 3);
+            const float ms = t3[1];
             static const bool log = getenv("LQ_TUNE_LOG") != nullptr;  // diagnostics: every candidate's time
-            if (log) fprintf(stderr, "lq tune %s candidate %d: %.2f us\n", key.c_str(), bs, ms * 1e3f / 3.f);
+            if (log) fprintf(stderr, "lq tune %s candidate %d: %.2f us\n", key.c_str(), bs, ms * 1e3f);
             if (ms < best_ms) {
                 best_ms = ms;
                 best = bs;

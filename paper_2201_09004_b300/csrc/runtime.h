@@ -237,6 +237,19 @@ int wilson_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int ep
 int hisq_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int epi, double a, const Field& in,
                 Field& out, const Field* y, df* norm_out, cudaStream_t st, const FinArgs& fin = FinArgs(),
                 const double* ak = nullptr);
+// the arguments of a Wilson operator launch (links, fields, clover or A^{-1} block)
+struct WilsonArgs;
+WilsonArgs wilson_args(Lattice& lat, const OpDesc& op, int parity, int dagger, int epi, const Field& in, Field& out,
+                       const Field* y, cudaStream_t st);
+// the inner iterations of the mixed CGNR in one persistent cooperative kernel (persistent.cu):
+// FP16 sloppy operator with R12 links and clover, one right-hand side
+bool persistent_cg_supported(const Lattice& lat, const OpDesc& op, int nrhs);
+int persistent_cg_blocks(const Lattice& lat);
+// up to iters CG iterations on x (FP32), p, s, q, r (FP16, even), t (FP16, odd), stopping
+// after the one whose |s|^2 falls below stop2; sc: the scalar block (SC_ITERS counts the
+// iterations done); part: 2 * persistent_cg_blocks() partials; bar: 2 zeroed counters
+void persistent_cg_run(Lattice& lat, const OpDesc& op, Field& x, Field& p, Field& s, Field& q, Field& r, Field& t,
+                       double* sc, df* part, unsigned* bar, int iters, double stop2, cudaStream_t st);
 // site-local out = A_pp^{-1} in (Wilson twisted mass / clover), parity of both fields
 void wilson_ainv_site(Lattice& lat, const OpDesc& op, int parity, int dagger, const Field& in, Field& out,
                       cudaStream_t st);

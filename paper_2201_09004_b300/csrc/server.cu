@@ -1,11 +1,15 @@
 // server.cu -- request server for propagator solves with continuous batching.
 //
-// Requests wait in a FIFO queue. A request is admitted when a worker slot is
-// free and its estimated device workspace, added to what the running requests
-// have reserved, fits in the HBM budget (the resident lattices are counted
-// once, when first used). Each worker owns a CUDA stream, so an admitted
-// request starts while earlier ones are still on the GPU and their kernels
-// overlap. A request that cannot fit even alone is rejected at submission.
+// Requests wait in a queue in arrival order. When a worker slot is free, the
+// first queued request whose estimated device workspace, added to what the
+// running requests have reserved, fits in the HBM budget is admitted (the
+// resident lattices are counted once, when first used); a request that does not
+// fit yet is overtaken by later ones that do, but at most max_bypass() times,
+// after which nothing behind it is admitted until it is (so a large request is
+// not starved by a stream of small ones). Each worker owns a CUDA stream, so an
+// admitted request starts while earlier ones are still on the GPU and their
+// kernels overlap. A request that cannot fit even alone is rejected at
+// submission.
 #include <string.h>
 
 #include <chrono>
@@ -36,6 +40,7 @@ struct Request {
     double t_submit = 0, t_admit = 0, t_finish = 0;
     int status = LQ_EAGAIN;
     bool done = false;
+    int bypassed = 0;                      // times a later request was admitted first
 };
 
 }  // namespace
@@ -57,6 +62,8 @@ struct lq_server_s {
     std::chrono::steady_clock::time_point t0;
     std::vector<std::thread> workers;
 
+    // how often a queued request may be overtaken before it blocks the queue
+    int max_bypass() const { return 2 * max_slots; }
     double now() const {
         return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
@@ -101,22 +108,31 @@ void lq_server_s::worker() {
             std::unique_lock<std::mutex> lk(mu);
             for (;;) {
                 if (stop) break;
-                if (!queue.empty()) {
-                    Request* head = queue.front();
-                    Lattice* L = &head->req.lat->lat;
-                    size_t extra = seen_lattices.count(L) ? 0 : L->bytes;
-                    if (reserved + lattice_bytes + extra + head->reserve <= budget || running == 0) {
-                        queue.pop_front();
-                        if (extra) {
-                            seen_lattices.insert(L);
-                            lattice_bytes += extra;
-                        }
-                        reserved += head->reserve;
-                        running++;
-                        head->t_admit = now();
-                        r = head;
+                // the first request in arrival order that fits; one that has been
+                // overtaken max_bypass() times holds back everything behind it
+                auto pick = queue.end();
+                size_t extra = 0;
+                for (auto it = queue.begin(); it != queue.end(); ++it) {
+                    Lattice* L = &(*it)->req.lat->lat;
+                    extra = seen_lattices.count(L) ? 0 : L->bytes;
+                    if (reserved + lattice_bytes + extra + (*it)->reserve <= budget || running == 0) {
+                        pick = it;
                         break;
                     }
+                    if ((*it)->bypassed >= max_bypass()) break;
+                }
+                if (pick != queue.end()) {
+                    for (auto it = queue.begin(); it != pick; ++it) (*it)->bypassed++;
+                    r = *pick;
+                    queue.erase(pick);
+                    if (extra) {
+                        seen_lattices.insert(&r->req.lat->lat);
+                        lattice_bytes += extra;
+                    }
+                    reserved += r->reserve;
+                    running++;
+                    r->t_admit = now();
+                    break;
                 }
                 cv_work.wait(lk);
             }

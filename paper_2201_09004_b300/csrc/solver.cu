@@ -151,7 +151,7 @@ struct KrylovState {
 template <class Iter, class Update, class After>
 static void krylov_loop(Lattice& lat, Scalars& sc, CgResult& res, KrylovState& ks, const std::vector<double>& tol_abs,
                         double delta, int maxiter, int graph_iters, int apps_per_iter, cudaStream_t st,
-                        Iter iteration, Update update, After after_update) {
+                        Iter iteration, Update update, After after_update, int per_call = 1) {
     const int n = sc.nrhs;
     auto all_done = [&]() {
         for (int k = 0; k < n; k++)
@@ -177,7 +177,7 @@ static void krylov_loop(Lattice& lat, Scalars& sc, CgResult& res, KrylovState& k
     int it = 0, launch_no = 0, pending = -1;  // launch whose scalars are in flight
     while (!all_done() && it < maxiter) {
         const int gi = launch_no & 1;
-        int steps = 1;
+        int steps = per_call;  // iterations one call of iteration() runs (a persistent kernel: several)
         if (use_graphs && it > 0 && it + gk <= maxiter) {
             Graph& g = graphs[gi];
             if (!g.exec) {
@@ -219,6 +219,8 @@ static void krylov_loop(Lattice& lat, Scalars& sc, CgResult& res, KrylovState& k
             const double* hs = slot(prev);
             for (int k = 0; k < n; k++) {
                 if (ks.done[k]) continue;
+                if (hs[(size_t)k * SC_N + SC_BREAK] >= 2.0)
+                    fail(LQ_ECUDA, "a grid barrier of the persistent CG kernel timed out");
                 if (hs[(size_t)k * SC_N + SC_BREAK] != 0.0) upd = true;
                 double ss = sqrt(hs[(size_t)k * SC_N + SC_SS]);
                 check_finite(ss, "iterated residual");
@@ -271,7 +273,7 @@ static KrylovState krylov_start(Scalars& sc, CgResult& res, const std::vector<do
 // p and restarts the norm recurrence from the new r = Mhat^+ s.
 static CgResult cgnr_mixed(Lattice& lat, const OpDesc& ops, const OpDesc& op64, Field& bhat, Field& x_hi,
                            const std::vector<double>& tol_abs, double delta, int maxiter, int graph_iters,
-                           cudaStream_t st, bool guess = false) {
+                           cudaStream_t st, bool guess = false, int persistent = 0) {
     const int n = bhat.nrhs;
     const int ps = ops.prec;
     const int px = ps == LQ_F16 ? LQ_F32 : ps;  // the sloppy solution accumulates in at least FP32
@@ -295,17 +297,48 @@ static CgResult cgnr_mixed(Lattice& lat, const OpDesc& ops, const OpDesc& op64, 
         blas_copy(s_hi, bhat, st);
         blas_norm2(bhat, sc.part, st, sc.f(SC_SS, FIN_SET));
     }
+    // partial sums of |q|^2 and |r|^2 that the CG vector kernels finalise themselves
+    const size_t nper = std::max<size_t>((size_t)(lat.vh + 7) / 8, (size_t)3 * RED_BLOCKS) * n;
+    df* part_q = (df*)ws_get(lat, sizeof(df) * nper, false, st);
+    df* part_r = (df*)ws_get(lat, sizeof(df) * nper, false, st);
+    struct PartCleanup {
+        Lattice& l; void* a; void* b; cudaStream_t s;
+        ~PartCleanup() { ws_put(l, a, s); ws_put(l, b, s); }
+    } part_cleanup{lat, part_q, part_r, st};
     blas_copy(s_lo, s_hi, st);
     blas_zero(x_lo, st);
-    schur_wilson(lat, ops, 1, s_lo, r, t, sc.part, st, sc.f(SC_RR, FIN_SET));
+    int nr = schur_wilson(lat, ops, 1, s_lo, r, t, part_r, st, sc.f(SC_RR, FIN_SET));
     blas_copy(p, r, st);
     sc.pull(st);
     KrylovState ks = krylov_start(sc, res, tol_abs, st);
+    // persistent: that many iterations per launch of one cooperative kernel (persistent.cu)
+    const bool pers = persistent > 0 && persistent_cg_supported(lat, ops, n);
+    unsigned* bar = nullptr;
+    df* ppart = nullptr;
+    if (pers) {
+        bar = (unsigned*)ws_get(lat, 16, false, st);
+        LQ_CUDA(cudaMemsetAsync(bar, 0, 16, st));
+        ppart = (df*)ws_get(lat, sizeof(df) * 2 * persistent_cg_blocks(lat), false, st);
+    }
+    struct PersistCleanup {
+        Lattice& l; void* a; void* b; cudaStream_t s;
+        ~PersistCleanup() { if (a) ws_put(l, a, s); if (b) ws_put(l, b, s); }
+    } pcleanup{lat, bar, ppart, st};
     auto iteration = [&](double* dst) {
-        schur_wilson(lat, ops, 0, p, q, t, sc.part, st, sc.f(0, FIN_ALPHA));
-        blas_cg_xs(x_lo, p, s_lo, q, sc.dev, sc.part, st, sc.f(SC_SS, FIN_SET));
-        schur_wilson(lat, ops, 1, s_lo, r, t, sc.part, st, sc.f(0, FIN_BETA));
-        blas_cg_p(p, r, sc.dev, st);
+        if (pers) {
+            const double th = std::max(delta * ks.rmax[0], tol_abs[0]);
+            persistent_cg_run(lat, ops, x_lo, p, s_lo, q, r, t, sc.dev, ppart, bar, persistent, th * th, st);
+        } else {
+            // the reductions of the two operator applications are finalised by one small
+            // kernel each (a finalising last block would make every block of the operator
+            // wait for a memory fence and an atomic at its end)
+            const int nq = schur_wilson(lat, ops, 0, p, q, t, part_q, st);
+            blas_finalize(part_q, nq, n, sc.dev, 0, FIN_ALPHA, st);
+            blas_cg_xs(x_lo, p, s_lo, q, sc.dev, sc.part, st, sc.f(SC_SS, FIN_SET));
+            nr = schur_wilson(lat, ops, 1, s_lo, r, t, part_r, st);
+            blas_finalize(part_r, nr, n, sc.dev, 0, FIN_BETA, st);
+            blas_cg_p(p, r, sc.dev, st);
+        }
         if (dst) LQ_CUDA(cudaMemcpyAsync(dst, sc.dev, sizeof(double) * SC_N * n, cudaMemcpyDeviceToHost, st));
     };
     auto update = [&]() {
@@ -314,12 +347,17 @@ static CgResult cgnr_mixed(Lattice& lat, const OpDesc& ops, const OpDesc& op64, 
         schur_wilson(lat, op64, 0, x_hi, q64, t64, nullptr, st);
         blas_xmy_norm(s_hi, bhat, q64, sc.part, st, sc.f(SC_SS, FIN_SET));
         blas_copy(s_lo, s_hi, st);
-        schur_wilson(lat, ops, 1, s_lo, r, t, sc.part, st, sc.f(SC_RR, FIN_SET));
+        nr = schur_wilson(lat, ops, 1, s_lo, r, t, part_r, st, sc.f(SC_RR, FIN_SET));
         for (int k = 0; k < n; k++)
             if (!ks.done[k]) res.applications[k] += 2;
     };
-    krylov_loop(lat, sc, res, ks, tol_abs, delta, maxiter, graph_iters, 2, st, iteration, update,
-                [](int) { return true; });
+    krylov_loop(lat, sc, res, ks, tol_abs, delta, maxiter, pers ? -1 : graph_iters, 2, st, iteration, update,
+                [](int) { return true; }, pers ? persistent : 1);
+    if (pers) {  // the loop counted whole launches; the kernel counted the iterations it did
+        sc.pull(st);
+        res.iters[0] = (int)sc.h(0, SC_ITERS);
+        res.applications[0] = 2 * res.iters[0] + 2 * res.updates[0];
+    }
     return res;
 }
 
@@ -640,7 +678,7 @@ int solve_wilson(Lattice& lat, const lq_op_params& opp, const lq_solve_params& s
                           ? gcr_mixed(lat, ops, op64, bhat, xe, tol_abs, delta, maxiter,
                                       sp.restart > 0 ? sp.restart : GCR_DEFAULT, st)
                           : cgnr_mixed(lat, ops, op64, bhat, xe, tol_abs, delta, maxiter, sp.graph_iters, st,
-                                       x0 != nullptr);
+                                       x0 != nullptr, sp.solver == LQ_MIXED_CGNR ? sp.persistent : 0);
 
         // x_o = A_oo^{-1} (b_o + H_oe x_e)
         wilson_dslash(lat, op64, 1, 0, EPI_HOP, xe, to, nullptr, nullptr, st);

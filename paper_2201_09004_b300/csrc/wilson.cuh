@@ -38,6 +38,7 @@ struct WilsonArgs {
     int nrhs;
     df* norm_out;       // if non-null: per-block partial sums of |out|^2, per rhs
     FinArgs fin;        // with norm_out: the last block finalises the sums
+    float m4f, muf, mu1f;  // m4, mu, mu1 rounded to FP32 once on the host (FP32 kernels)
 };
 
 // spin projection h = top two spins of (1 + s g_mu) psi, for psi as cx[4][3]

@@ -42,6 +42,7 @@ EXPORTS = [
     "lq_profile_enable", "lq_profile_reset", "lq_profile_query", "lq_launch_count", "lq_tune_reset", "lq_tune_force", "lq_gamma5_dw_apply", "lq_chebyshev_sign",
     "lq_overlap_sign_apply", "lq_hw_eigensolve", "lq_overlap_sign_apply_deflated", "lq_server_create",
     "lq_server_destroy", "lq_submit", "lq_poll", "lq_wait", "lq_server_stats", "lq_dslash_apply_noalloc", "lq_request_bytes",
+    "lq_barrier_selftest",
 ]
 
 
@@ -61,7 +62,7 @@ class SolveParams(ctypes.Structure):
     _fields_ = [("solver", ctypes.c_int), ("tol", ctypes.c_double), ("delta", ctypes.c_double),
                 ("maxiter", ctypes.c_int), ("prec_sloppy", ctypes.c_int), ("recon_sloppy", ctypes.c_int),
                 ("nshift", ctypes.c_int), ("masses", ctypes.POINTER(ctypes.c_double)),
-                ("graph_iters", ctypes.c_int), ("restart", ctypes.c_int)]
+                ("graph_iters", ctypes.c_int), ("restart", ctypes.c_int), ("persistent", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -156,9 +157,9 @@ def op_params(action, m, mu=0.0, c_sw=0.0, c_naik=-1.0 / 24.0, recon=0, twist_mo
 
 
 def solve_params(solver=MIXED_CGNR, tol=1e-10, delta=0.1, maxiter=100000, prec_sloppy=F32, recon_sloppy=R12,
-                 masses=None, graph_iters=0, restart=0):
+                 masses=None, graph_iters=0, restart=0, persistent=0):
     sp = SolveParams(int(solver), float(tol), float(delta), int(maxiter), int(prec_sloppy), int(recon_sloppy), 0, None,
-                     int(graph_iters), int(restart))
+                     int(graph_iters), int(restart), int(persistent))
     if masses is not None:
         arr = (ctypes.c_double * len(masses))(*[float(m) for m in masses])
         sp.nshift = len(masses)
@@ -428,6 +429,14 @@ def chebyshev_sign(eps, delta, max_order=65536):
     _check(lib().lq_chebyshev_sign(ctypes.c_double(eps), ctypes.c_double(delta), ctypes.c_int(order.value), buf,
                                    ctypes.byref(order), ctypes.byref(dev)))
     return list(buf), dev.value
+
+
+def barrier_selftest(blocks, expect, rounds=1):
+    """lq_barrier_selftest: (status code, failed flag) of the bounded grid-barrier test."""
+    failed = ctypes.c_int(-1)
+    code = lib().lq_barrier_selftest(ctypes.c_int(blocks), ctypes.c_int(expect), ctypes.c_int(rounds),
+                                     ctypes.byref(failed))
+    return code, failed.value
 
 
 def tune_reset():

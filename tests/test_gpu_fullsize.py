@@ -101,13 +101,16 @@ def schur_at_sites(W, dims, v, sites, dagger):
     return W.apply_sites(full.reshape(W.shape()), sites, dagger=dagger).reshape(-1, 12)
 
 
-def test_headline_solve_true_residual_by_the_oracle(L, headline):
+@pytest.mark.parametrize("persistent", [0, 4])
+def test_headline_solve_true_residual_by_the_oracle(L, headline, persistent):
     """The benchmark's solve (mixed CGNR, FP16 storage, R12 links, delta 0.1, graphs
-    on) from the benchmark's source: the oracle's FP64 residual |b - M x| / |b| on the
-    whole lattice is at most 1e-10 and agrees with the library's own report to 1 %."""
+    on; and with its inner iterations in the persistent kernel) from the benchmark's
+    source: the oracle's FP64 residual |b - M x| / |b| on the whole lattice is at most
+    1e-10 and agrees with the library's own report to 1 %."""
     lat, W, b = headline
     op = L.op_params(L.WILSON_TM_CLOVER, MASS, MU, c_sw=C_SW)
-    sp = L.solve_params(solver=L.MIXED_CGNR, tol=1e-10, delta=0.1, prec_sloppy=L.F16, recon_sloppy=12)
+    sp = L.solve_params(solver=L.MIXED_CGNR, tol=1e-10, delta=0.1, prec_sloppy=L.F16, recon_sloppy=12,
+                        persistent=persistent)
     xs, info = lat.solve(op, sp, [b])
     assert info[0]["status"] == 0
     bh = b.cpu().numpy()

@@ -121,3 +121,46 @@ def test_poll_unknown_ticket_and_timeout(L, world):
     with pytest.raises(L.LqError):
         srv.poll(12345)
     srv.close()
+
+
+def test_small_request_overtakes_a_blocked_large_one(L):
+    """A request that cannot fit next to the running one does not hold back a later,
+    smaller request that does fit: the small one is admitted first, the large one
+    once the running request has finished; every result converges."""
+    big_dims, small_dims = (16, 16, 16, 32), (4, 4, 4, 8)
+    big = L.Lattice(big_dims)
+    big.load_gauge(L.THIN, synth.thin_links(big_dims, 911).cuda())
+    big.load_clover(1.05)
+    small = L.Lattice(small_dims)
+    small.load_gauge(L.THIN, synth.thin_links(small_dims, 912).cuda())
+    small.load_clover(1.05)
+    op = L.op_params(L.WILSON_TM_CLOVER, 0.05, 0.02, c_sw=1.05)
+    slow = L.solve_params(solver=L.CGNR, tol=1e-10, prec_sloppy=L.F64)   # keeps the first request running
+    fast = L.solve_params(solver=L.MIXED_CGNR, tol=1e-10, prec_sloppy=L.F16)
+    site = synth.seeded_site(big_dims, 913)
+    big_rhs = [synth.point_source(big_dims, site, s, c).numpy() for s in range(4) for c in range(3)]
+    small_rhs = [synth.z2_source(small_dims, 914).numpy()]
+    # warm caches (clover inverses, tuned kernels) so the lattices' resident bytes are final
+    for lat, sp, rhs in ((big, slow, big_rhs[:1]), (big, fast, big_rhs[:1]), (small, fast, small_rhs)):
+        lat.solve(op, sp, rhs)
+        lat.release_workspace()
+    probe = L.Server(1 << 40, 1)
+    r_big = probe.request_bytes(big, op, slow, len(big_rhs))
+    r_small = probe.request_bytes(small, op, fast, 1)
+    probe.close()
+    assert r_small < 0.25 * r_big
+    budget = big.device_bytes() + small.device_bytes() + r_big + r_small + r_big // 2
+    srv = L.Server(budget, 2)
+    t_run = srv.submit(big, op, slow, big_rhs)
+    t_large = srv.submit(big, op, slow, big_rhs)   # cannot fit while t_run runs
+    t_small = srv.submit(small, op, fast, small_rhs)
+    times = {}
+    for name, t in (("run", t_run), ("large", t_large), ("small", t_small)):
+        assert srv.wait(t, 600000)
+        _, info, tm, code = srv.poll(t)
+        assert code == 0, name
+        times[name] = tm
+    srv.close()
+    assert times["small"]["admitted"] < times["large"]["admitted"]
+    assert times["small"]["finished"] < times["run"]["finished"]
+    assert times["large"]["admitted"] >= times["run"]["finished"] - 1e-3

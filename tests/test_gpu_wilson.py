@@ -123,8 +123,14 @@ def test_schur_operator(L, orc, prec):
         assert rel_err(got, ref) < 10 * TOL[prec], (prec, dagger)
 
 
-@pytest.mark.parametrize("prec", [1, 2])
-@pytest.mark.parametrize("code", [64, 128, 256, 1064, 1128, 1256, 2064, 2128])
+# tuning codes: block size; 1000 + block: registers capped at 85; 2000 + block: two hops
+# in flight; 3000 - 6000 + block: the FP16 packed-pair kernels (128 / 85 registers with
+# two hops in flight, 102 / 85 registers with one)
+CODES = [(p, c) for p in (1, 2) for c in (64, 128, 256, 1064, 1128, 1256, 2064, 2128)] + \
+        [(2, c) for c in (3064, 3128, 4064, 4128, 5064, 5128, 6064, 6128, 7256)]
+
+
+@pytest.mark.parametrize("prec,code", CODES)
 def test_each_tuning_candidate(L, orc, prec, code):
     """Every launch configuration the autotuner may pick (block sizes; the
     register-capped build; two hops of gathers in flight) gives the oracle's hopping term and Schur operator,
@@ -148,6 +154,36 @@ def test_each_tuning_candidate(L, orc, prec, code):
             ref = schur_reference(orc, dims, U, C, 0.05, 0.1, v, dagger=dagger)
             got = lat.operator_apply(op, v, form=L.OP_SCHUR, dagger=dagger, prec=prec)
             assert rel_err(got, ref) < 10 * TOL[prec], (code, prec, dagger)
+    finally:
+        L.tune_force(0)
+        L.tune_reset()
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 8), (6, 4, 4, 6), (2, 2, 2, 2), (2, 4, 6, 8), (8, 2, 4, 4)])
+@pytest.mark.parametrize("code", [3128, 4064, 5128, 6064, 7256])
+def test_packed_pair_kernels_on_every_geometry(L, orc, dims, code):
+    """The FP16 packed-pair kernels (their own neighbour indexing) on extents of 2,
+    ragged blocks and unequal extents: hopping term per parity and adjoint, and the
+    clover Schur operator, against the oracle."""
+    lat, U = make(L, dims, 35, c_sw=1.05)
+    C = orc.clover(dims, U, 1.05)
+    op = L.op_params(L.WILSON_TM_CLOVER, 0.05, 0.1, c_sw=1.05)
+    v = synth.gaussian_field(dims, 36).numpy()
+    mask = parity_mask(dims)
+    W = orc.Wilson(dims, U, 0.0, 0.0)
+    try:
+        L.tune_reset()
+        L.tune_force(code)
+        for dagger in (False, True):
+            ref = W.hop(v, dagger=dagger)
+            for p in (0, 1):
+                src = np.where((mask == 1 - p)[..., None, None], v, 0)
+                got = lat.dslash_apply(op, p, src, dagger=dagger, prec=2)
+                assert np.all(got[mask != p] == 0)
+                assert rel_err(got[mask == p], ref[mask == p]) < TOL[2], (dims, code, dagger, p)
+            ref = schur_reference(orc, dims, U, C, 0.05, 0.1, v, dagger=dagger)
+            got = lat.operator_apply(op, v, form=L.OP_SCHUR, dagger=dagger, prec=2)
+            assert rel_err(got, ref) < 10 * TOL[2], (dims, code, dagger)
     finally:
         L.tune_force(0)
         L.tune_reset()
@@ -409,3 +445,76 @@ def test_multi_rhs_operator_equals_single(L, prec, nrhs):
             one = lat.operator_apply(op, p, form=L.OP_SCHUR, dagger=dagger, prec=prec).cpu().numpy()
             mask = parity_mask(dims) == 0
             assert rel_err(got[mask], one[mask]) < TOL[prec], (prec, nrhs, k, dagger)
+
+
+@pytest.mark.parametrize("per_launch", [1, 4, 16])
+def test_persistent_cg_solve(L, orc, per_launch):
+    """The mixed CGNR with its inner iterations in one persistent cooperative kernel
+    (grid-wide barriers between the operator, vector and reduction phases): FP16
+    sloppy operator with clover, on a lattice with a ragged last block; the oracle's
+    true residual meets 1e-10 and the solution agrees with the per-kernel path."""
+    dims = (6, 4, 4, 10)
+    lat, U = make(L, dims, 37, c_sw=1.05)
+    C = orc.clover(dims, U, 1.05)
+    op = L.op_params(L.WILSON_TM_CLOVER, 0.05, 0.02, c_sw=1.05)
+    b = synth.z2_source(dims, 38).numpy()
+    base = L.solve_params(solver=L.MIXED_CGNR, tol=1e-10, prec_sloppy=L.F16)
+    pers = L.solve_params(solver=L.MIXED_CGNR, tol=1e-10, prec_sloppy=L.F16, persistent=per_launch)
+    (x0,), (i0,) = lat.solve(op, base, [b])
+    (x1,), (i1,) = lat.solve(op, pers, [b])
+    assert i1["status"] == 0
+    assert true_residual(orc, dims, U, C, 0.05, 0.02, b, x1) <= 1e-10
+    assert rel_err(x1, x0) < 1e-8
+    assert i1["iters"] >= i0["iters"] - 2
+
+
+def test_bounded_grid_barrier_reports_a_wait_that_runs_out(L):
+    """The barrier of the persistent kernel: complete when every block arrives, and
+    a status (not a hang) when one never does."""
+    code, failed = L.barrier_selftest(4, 4, rounds=50)
+    assert code == 0 and failed == 0
+    code, failed = L.barrier_selftest(2, 3, rounds=1)
+    assert code == L.LQ_ETIMEOUT and failed == 1
+    code, failed = L.barrier_selftest(4, 4, rounds=3)  # the GPU is usable afterwards
+    assert code == 0 and failed == 0
+
+
+@pytest.mark.parametrize("nrhs", [4, 5, 12])
+@pytest.mark.parametrize("code", [3064, 3128, 5064, 5128])
+def test_packed_pair_multi_rhs_kernels(L, orc, nrhs, code):
+    """The FP16 packed-pair kernels with four threads per site (one right-hand side
+    each, shared links and clover records; a ragged last group for 5 right-hand
+    sides): hopping term and clover Schur operator of every right-hand side against
+    the oracle, on a lattice with a ragged last block."""
+    import torch
+    dims = (6, 4, 4, 6)
+    lat, U = make(L, dims, 39, c_sw=1.05)
+    C = orc.clover(dims, U, 1.05)
+    op = L.op_params(L.WILSON_TM_CLOVER, 0.05, 0.1, c_sw=1.05)
+    mask = parity_mask(dims)
+    W = orc.Wilson(dims, U, 0.0, 0.0)
+    vs = [synth.gaussian_field(dims, 400 + k).numpy() for k in range(nrhs)]
+    try:
+        L.tune_reset()
+        L.tune_force(code)
+        for dagger in (False, True):
+            fi = L.Field(lat, L.WILSON_FIELD, 2, nrhs)
+            fo = L.Field(lat, L.WILSON_FIELD, 2, nrhs)
+            ft = L.Field(lat, L.WILSON_FIELD, 2, nrhs)
+            for k, v in enumerate(vs):
+                fi.load(k, 1, torch.from_numpy(v).cuda())
+            L.dslash_field(lat, op, 0, fi, fo, dagger=dagger)
+            for k, v in enumerate(vs):
+                got = fo.store(k, 0, torch.zeros(v.shape, dtype=torch.complex128, device="cuda")).cpu().numpy()
+                ref = W.hop(np.where((mask == 1)[..., None, None], v, 0), dagger=dagger)
+                assert rel_err(got[mask == 0], ref[mask == 0]) < TOL[2], (code, nrhs, k, dagger)
+            for k, v in enumerate(vs):
+                fi.load(k, 0, torch.from_numpy(v).cuda())
+            L.schur_field(lat, op, fi, fo, ft, dagger=dagger)
+            for k, v in enumerate(vs):
+                got = fo.store(k, 0, torch.zeros(v.shape, dtype=torch.complex128, device="cuda")).cpu().numpy()
+                ref = schur_reference(orc, dims, U, C, 0.05, 0.1, v, dagger=dagger)
+                assert rel_err(got[mask == 0], ref[mask == 0]) < 10 * TOL[2], (code, nrhs, k, dagger)
+    finally:
+        L.tune_force(0)
+        L.tune_reset()
