@@ -378,7 +378,9 @@ __device__ __forceinline__ int cb_hop(const Geo& g, const int c[4], int mu, int 
 // ----------------------------------------------------------------- storage
 template <int P, int NR> struct Chunk;
 template <int NR> struct Chunk<P64, NR> { typedef double2 C; enum { RPC = 2 }; };
-template <int NR> struct Chunk<PDF, NR> { typedef float4 C; enum { RPC = 2 }; };  // (hi, lo) x 2
+// double-float: two reals v0, v1 as (v0.hi, v1.hi, v0.lo, v1.lo), so that for a complex
+// number the high parts (re, im) and the low parts are aligned register pairs
+template <int NR> struct Chunk<PDF, NR> { typedef float4 C; enum { RPC = 2 }; };
 template <int NR> struct Chunk<P32, NR> {
     typedef typename std::conditional<NR % 4 == 0, float4, float2>::type C;
     enum { RPC = (NR % 4 == 0) ? 4 : 2 };
@@ -417,8 +419,8 @@ __device__ __forceinline__ void unpack_chunk(const typename Layout<P, NR>::C& c,
     if constexpr (P == P64) {
         v[0] = (T)c.x; v[1] = (T)c.y;
     } else if constexpr (P == PDF) {
-        v[0] = from_df<T>(df(c.x, c.y));
-        v[1] = from_df<T>(df(c.z, c.w));
+        v[0] = from_df<T>(df(c.x, c.z));
+        v[1] = from_df<T>(df(c.y, c.w));
     } else if constexpr (P == P32) {
         if constexpr (Lay::RPC == 4) {
             v[0] = (T)c.x; v[1] = (T)c.y; v[2] = (T)c.z; v[3] = (T)c.w;
@@ -556,7 +558,7 @@ __device__ __forceinline__ void store_reals(void* base, int stride, int s, float
                 c.x = (double)v[2 * k]; c.y = (double)v[2 * k + 1];
             } else if constexpr (P == PDF) {
                 const df a0 = to_df(v[2 * k]), a1 = to_df(v[2 * k + 1]);
-                c.x = a0.hi; c.y = a0.lo; c.z = a1.hi; c.w = a1.lo;
+                c.x = a0.hi; c.y = a1.hi; c.z = a0.lo; c.w = a1.lo;
             } else if constexpr (Lay::RPC == 4) {
                 c.x = (float)v[4 * k]; c.y = (float)v[4 * k + 1]; c.z = (float)v[4 * k + 2]; c.w = (float)v[4 * k + 3];
             } else {

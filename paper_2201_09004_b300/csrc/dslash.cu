@@ -138,6 +138,8 @@ int wilson_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int ep
     std::vector<int> cand = {64, 128, 256};
     if ((op.prec == LQ_F32 || op.prec == LQ_F16) && nb != 2)
         for (int b : {64, 128, 256}) cand.push_back(kCapped + b);
+    if (op.prec == LQ_F32X2 && epi != EPI_HOP)  // the double-float epilogue without row prefetch
+        for (int b : {64, 128, 256}) cand.push_back(1000 + b);
     if ((op.prec == LQ_F32 || op.prec == LQ_F16) && nb == 1)
         for (int b : {64, 128}) cand.push_back(kDeep + b);
     if (x2 && a.nrhs == 1) {

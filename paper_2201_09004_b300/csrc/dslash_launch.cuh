@@ -63,9 +63,15 @@ static void wl_epi(const char* name, WilsonArgs a, int epi, int nb, int block, c
 
 // double-float: two threads per site, one right-hand side per grid row
 template <int EPI, bool SITE>
-static void wl_df(const char* name, WilsonArgs a, int block, cudaStream_t st) {
+static void wl_df(const char* name, WilsonArgs a, int cfg, cudaStream_t st) {
+    const int block = cfg % 1000;
     dim3 grid(site_blocks(a.g.vh, block, 2), a.nrhs);
-    launch_smem(name, wilson_dslash_df2_kernel<EPI, SITE>, grid, dim3(block), SITE ? 0 : df2_smem_bytes(block), st, a);
+    // cfg / 1000 == 1: the epilogue without row prefetch (fewer registers)
+    if (cfg / 1000 == 1)
+        launch_smem(name, wilson_dslash_df2_kernel<EPI, SITE, false>, grid, dim3(block), SITE ? 0 : df2_smem_bytes(block),
+                    st, a);
+    else
+        launch_smem(name, wilson_dslash_df2_kernel<EPI, SITE>, grid, dim3(block), SITE ? 0 : df2_smem_bytes(block), st, a);
 }
 
 // HISQ

@@ -14,7 +14,9 @@
 // partial sums with two-lane shuffles so that thread h holds chiral block h
 // (spins 2h and 2h+1), and applies the site-local epilogue to that 6-vector:
 // block h of A^{-1}, or A y - D psi with block h of the clover term. Each
-// output row is written as soon as it is formed.
+// output row is written as soon as it is formed. The real and imaginary parts of
+// every complex double-float value are register pairs, and each operation on them
+// is one packed FP32 instruction for both.
 #pragma once
 #include "wilson.cuh"
 
@@ -22,78 +24,104 @@ namespace lq {
 
 typedef cx<df> cd;
 
-__device__ __forceinline__ cd ld_cd(const float4* base, size_t idx) {
+// A complex double-float number as two register pairs: h = (re.hi, im.hi), l = (re.lo,
+// im.lo), the layout of a double-float chunk (see core.cuh). The arithmetic below runs
+// on both lanes at once with the packed FP32 instructions of B300 (one instruction for
+// two operations); a - b is fma(b, -1, a), exact in its product and rounded once.
+struct cdp {
+    float2 h, l;
+};
+__device__ __forceinline__ float2 p2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, p2(-1.f, -1.f), a); }
+__device__ __forceinline__ cdp ld_cdp(const float4* base, size_t idx) {
     const float4 c = __ldg(base + idx);
-    return mk(df(c.x, c.y), df(c.z, c.w));
+    return cdp{p2(c.x, c.y), p2(c.z, c.w)};
 }
-__device__ __forceinline__ void st_cd(float4* base, size_t idx, cd v) {
-    base[idx] = make_float4(v.r.hi, v.r.lo, v.i.hi, v.i.lo);
+__device__ __forceinline__ cdp cdp_of(float4 c) { return cdp{p2(c.x, c.y), p2(c.z, c.w)}; }
+__device__ __forceinline__ void st_cdp(float4* base, size_t idx, cdp v) {
+    base[idx] = make_float4(v.h.x, v.h.y, v.l.x, v.l.y);
+}
+__device__ __forceinline__ cdp cdp_neg(cdp v) {
+    return cdp{__fmul2_rn(v.h, p2(-1.f, -1.f)), __fmul2_rn(v.l, p2(-1.f, -1.f))};
+}
+// v * (+-1 or +-i)
+__device__ __forceinline__ cdp cdp_unit(cdp v, bool neg, bool isi) {
+    const float2 sg = isi ? p2(neg ? 1.f : -1.f, neg ? -1.f : 1.f) : p2(neg ? -1.f : 1.f, neg ? -1.f : 1.f);
+    const float2 h = isi ? p2(v.h.y, v.h.x) : v.h;  // i (a + ib) = -b + ia
+    const float2 l = isi ? p2(v.l.y, v.l.x) : v.l;
+    return cdp{__fmul2_rn(h, sg), __fmul2_rn(l, sg)};
 }
 // value of the other thread of the pair (lanes 2g, 2g+1)
-__device__ __forceinline__ cd pair_swap(cd v) {
-    cd o;
-    o.r.hi = __shfl_xor_sync(0xffffffffu, v.r.hi, 1);
-    o.r.lo = __shfl_xor_sync(0xffffffffu, v.r.lo, 1);
-    o.i.hi = __shfl_xor_sync(0xffffffffu, v.i.hi, 1);
-    o.i.lo = __shfl_xor_sync(0xffffffffu, v.i.lo, 1);
+__device__ __forceinline__ cdp pair_swap(cdp v) {
+    cdp o;
+    o.h.x = __shfl_xor_sync(0xffffffffu, v.h.x, 1);
+    o.h.y = __shfl_xor_sync(0xffffffffu, v.h.y, 1);
+    o.l.x = __shfl_xor_sync(0xffffffffu, v.l.x, 1);
+    o.l.y = __shfl_xor_sync(0xffffffffu, v.l.y, 1);
     return o;
 }
-__device__ __forceinline__ df cnorm2(cd v) { return v.r * v.r + v.i * v.i; }
 
-// Dot-product accumulator: the running sum keeps its high part exact with a
-// two-sum per term and collects every rounding and product error in a plain
-// FP32 low part, normalised once at the end (12 FP32 instructions per real
-// multiply-add instead of 17 for a normalised double-float multiply and add).
-struct dfacc {
-    float hi, lo;
+// Lazily normalised sum of both lanes: the high pair is kept exact by a two-sum per
+// term, every rounding and product error goes to the plain low pair, normalised once
+// at the end (per real multiply-add 6 packed instructions instead of 12 scalar ones).
+struct caccp {
+    float2 h, l;
 };
-__device__ __forceinline__ void acc_prod(dfacc& a, df x, df y) {  // a += x y
-    const float p = __fmul_rn(x.hi, y.hi);
-    float e = __fmaf_rn(x.hi, y.hi, -p);
-    e = __fmaf_rn(x.hi, y.lo, e);
-    e = __fmaf_rn(x.lo, y.hi, e);
-    const float s = __fadd_rn(a.hi, p);
-    const float bb = __fsub_rn(s, a.hi);
-    const float t = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-    a.hi = s;
-    a.lo = __fadd_rn(a.lo, __fadd_rn(t, e));
+__device__ __forceinline__ caccp caccp_zero() { return caccp{p2(0.f, 0.f), p2(0.f, 0.f)}; }
+// a += x (both lanes)
+__device__ __forceinline__ void accp_add(caccp& a, float2 xh, float2 xl) {
+    const float2 s = __fadd2_rn(a.h, xh);
+    const float2 bb = sub2(s, a.h);
+    const float2 t = __fadd2_rn(sub2(a.h, sub2(s, bb)), sub2(xh, bb));
+    a.h = s;
+    a.l = __fadd2_rn(a.l, __fadd2_rn(t, xl));
 }
-__device__ __forceinline__ void acc_add(dfacc& a, df x) {  // a += x
-    const float s = __fadd_rn(a.hi, x.hi);
-    const float bb = __fsub_rn(s, a.hi);
-    const float t = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(x.hi, bb));
-    a.hi = s;
-    a.lo = __fadd_rn(a.lo, __fadd_rn(t, x.lo));
+// a += x y (both lanes)
+__device__ __forceinline__ void accp_prod(caccp& a, float2 xh, float2 xl, float2 yh, float2 yl) {
+    const float2 p = __fmul2_rn(xh, yh);
+    float2 e = __ffma2_rn(xh, yh, __fmul2_rn(p, p2(-1.f, -1.f)));
+    e = __ffma2_rn(xh, yl, e);
+    e = __ffma2_rn(xl, yh, e);
+    accp_add(a, p, e);
 }
-__device__ __forceinline__ df acc_done(dfacc a) { return df_fast_two_sum(a.hi, a.lo); }
-
-struct cacc {
-    dfacc r, i;
-};
-__device__ __forceinline__ cacc cacc_zero() { return cacc{{0.f, 0.f}, {0.f, 0.f}}; }
-__device__ __forceinline__ void cacc_mac(cacc& a, cd x, cd y) {  // a += x y
-    acc_prod(a.r, x.r, y.r);
-    acc_prod(a.r, -x.i, y.i);
-    acc_prod(a.i, x.r, y.i);
-    acc_prod(a.i, x.i, y.r);
+__device__ __forceinline__ void caccp_add(caccp& a, cdp x) { accp_add(a, x.h, x.l); }
+// a += x y (complex): (re, im) += (x.re, x.re) (y.re, y.im) + (-x.im, x.im) (y.im, y.re)
+__device__ __forceinline__ void caccp_mac(caccp& a, cdp x, cdp y) {
+    accp_prod(a, p2(x.h.x, x.h.x), p2(x.l.x, x.l.x), y.h, y.l);
+    accp_prod(a, p2(-x.h.y, x.h.y), p2(-x.l.y, x.l.y), p2(y.h.y, y.h.x), p2(y.l.y, y.l.x));
 }
-__device__ __forceinline__ void cacc_cjmac(cacc& a, cd x, cd y) {  // a += conj(x) y
-    acc_prod(a.r, x.r, y.r);
-    acc_prod(a.r, x.i, y.i);
-    acc_prod(a.i, x.r, y.i);
-    acc_prod(a.i, -x.i, y.r);
+// a += conj(x) y: (re, im) += (x.re, x.re) (y.re, y.im) + (x.im, -x.im) (y.im, y.re)
+__device__ __forceinline__ void caccp_cjmac(caccp& a, cdp x, cdp y) {
+    accp_prod(a, p2(x.h.x, x.h.x), p2(x.l.x, x.l.x), y.h, y.l);
+    accp_prod(a, p2(x.h.y, -x.h.y), p2(x.l.y, -x.l.y), p2(y.h.y, y.h.x), p2(y.l.y, y.l.x));
 }
-__device__ __forceinline__ void cacc_add(cacc& a, cd x) {
-    acc_add(a.r, x.r);
-    acc_add(a.i, x.i);
+// the unnormalised sum as a value (the low pair may be large; later sums absorb it)
+__device__ __forceinline__ cdp caccp_raw(caccp a) { return cdp{a.h, a.l}; }
+// normalised: (h, l) = fast two-sum of the high and low pairs
+__device__ __forceinline__ cdp caccp_done(caccp a) {
+    const float2 s = __fadd2_rn(a.h, a.l);
+    const float2 e = sub2(a.l, sub2(s, a.h));
+    return cdp{s, e};
 }
-__device__ __forceinline__ cd cacc_done(cacc a) { return mk(acc_done(a.r), acc_done(a.i)); }
+__device__ __forceinline__ cdp cdp_scale_half(cdp v) {
+    return cdp{__fmul2_rn(v.h, p2(0.5f, 0.5f)), __fmul2_rn(v.l, p2(0.5f, 0.5f))};
+}
+__device__ __forceinline__ cdp cdp_add(cdp a, cdp b) {  // normalised sum
+    caccp t{a.h, a.l};
+    accp_add(t, b.h, b.l);
+    return caccp_done(t);
+}
+__device__ __forceinline__ df cdp_norm2(cdp v) {
+    const df re(v.h.x, v.l.x), im(v.h.y, v.l.y);
+    return re * re + im * im;
+}
 
 // dynamic shared memory of the hop staging (two slots of 21 chunks per site)
 __host__ __device__ constexpr size_t df2_smem_bytes(int block) { return (size_t)2 * 21 * 16 * (block / 2); }
 
-// SITE = true: no hops, w = block h of `in` at the site (out = A^{-1} in).
-template <int EPI, bool SITE>
+// SITE = true: no hops, w = block h of `in` at the site (out = A^{-1} in). ROWPF: the
+// epilogue loads the entries of row i+1 while row i is computed (more registers in flight).
+template <int EPI, bool SITE, bool ROWPF = true>
 __global__ void __launch_bounds__(256, 2) wilson_dslash_df2_kernel(WilsonArgs a) {
     const int h = threadIdx.x & 1;
     const int k = blockIdx.y;
@@ -105,11 +133,11 @@ __global__ void __launch_bounds__(256, 2) wilson_dslash_df2_kernel(WilsonArgs a)
     const bool dag = a.dagger != 0;
     const float4* in = (const float4*)((const char*)a.in.data + (size_t)k * a.in.rhs_bytes);
 
-    cd w[6];   // chiral block h: spins 2h, 2h+1 (index 3 * spin' + colour)
-    cd yv[6];  // EPI_XPAY: block h of y, loaded while the pair exchanges its sums
+    cdp w[6];   // chiral block h: spins 2h, 2h+1 (index 3 * spin' + colour)
+    cdp yv[6];  // EPI_XPAY: block h of y, loaded while the pair exchanges its sums
     if constexpr (SITE) {
 #pragma unroll
-        for (int j = 0; j < 6; j++) w[j] = ld_cd(in, (size_t)(6 * h + j) * vh + s);
+        for (int j = 0; j < 6; j++) w[j] = ld_cdp(in, (size_t)(6 * h + j) * vh + s);
     } else {
         int c[4];
         cb_coords(a.g, s, a.parity, c);
@@ -135,9 +163,9 @@ __global__ void __launch_bounds__(256, 2) wilson_dslash_df2_kernel(WilsonArgs a)
             return bs;
         };
         // upper spin h, lower spins 2 and 3: lazily normalised sums over the eight hops
-        cacc upa[3], l2a[3], l3a[3];
+        caccp upa[3], l2a[3], l3a[3];
 #pragma unroll
-        for (int q = 0; q < 3; q++) upa[q] = l2a[q] = l3a[q] = cacc_zero();
+        for (int q = 0; q < 3; q++) upa[q] = l2a[q] = l3a[q] = caccp_zero();
         float bs_next = issue(0, 0);
 #pragma unroll 1
         for (int hop = 0; hop < 8; hop++) {
@@ -153,39 +181,33 @@ __global__ void __launch_bounds__(256, 2) wilson_dslash_df2_kernel(WilsonArgs a)
             }
             __syncwarp();  // the partner's copies of this hop are visible
             const float4* sl = stage + (size_t)((hop & 1) * 21) * spb + g;
-            cx<df> U[3][3];
+            cdp U[3][3];
 #pragma unroll
-            for (int k = 0; k < 9; k++) {
-                const float4 v = sl[k * spb];
-                U[k / 3][k % 3] = mk(df(v.x, v.y), df(v.z, v.w));
-            }
+            for (int k = 0; k < 9; k++) U[k / 3][k % 3] = cdp_of(sl[k * spb]);
             // projector (1 + sp g_mu): sp = +-1 forward / backward, flipped for the adjoint
             const bool neg_sp = fwd ? dag : !dag;
             // component h couples spin h with spin pb through +-1 or +-i (DeGrand-Rossi)
             const int pb = mu < 2 ? 3 - h : 2 + h;
             const bool ci = (mu == 0 || mu == 2);
             const bool cn = (mu == 1 && h == 0) || (mu == 2 && h == 1);
-            cd hv[3];
+            cdp hv[3];
 #pragma unroll
             for (int q = 0; q < 3; q++) {
-                const float4 va = sl[(9 + h * 3 + q) * spb];
-                const float4 vp = sl[(9 + pb * 3 + q) * spb];
                 // the sum stays unnormalised (exact high part, rounding in the low part)
-                cacc t = cacc_zero();
-                cacc_add(t, mk(df(va.x, va.y), df(va.z, va.w)));
-                cacc_add(t, cunit(mk(df(vp.x, vp.y), df(vp.z, vp.w)), cn != neg_sp, ci));
-                hv[q] = mk(df(t.r.hi, t.r.lo), df(t.i.hi, t.i.lo));
+                caccp t{cdp_of(sl[(9 + h * 3 + q) * spb]).h, cdp_of(sl[(9 + h * 3 + q) * spb]).l};
+                caccp_add(t, cdp_unit(cdp_of(sl[(9 + pb * 3 + q) * spb]), cn != neg_sp, ci));
+                hv[q] = caccp_raw(t);
             }
-            cd r[3];  // U hv or U^+ hv, unnormalised
+            cdp r[3];  // U hv or U^+ hv, unnormalised
 #pragma unroll
             for (int i = 0; i < 3; i++) {
-                cacc t = cacc_zero();
+                caccp t = caccp_zero();
 #pragma unroll
                 for (int j = 0; j < 3; j++) {
-                    if (fwd) cacc_mac(t, U[i][j], hv[j]);
-                    else cacc_cjmac(t, U[j][i], hv[j]);
+                    if (fwd) caccp_mac(t, U[i][j], hv[j]);
+                    else caccp_cjmac(t, U[j][i], hv[j]);
                 }
-                r[i] = mk(df(t.r.hi, t.r.lo), df(t.i.hi, t.i.lo));
+                r[i] = caccp_raw(t);
             }
             // rebuild: upper spin h gets r; lower spin (3 if to3 else 2) gets +-r or +-i r
             const bool flip = bs < 0.f;  // time boundary
@@ -194,35 +216,34 @@ __global__ void __launch_bounds__(256, 2) wilson_dslash_df2_kernel(WilsonArgs a)
             const bool en = mu == 0 || (mu == 1 && h == 0) || (mu == 2 && h == 0);
 #pragma unroll
             for (int q = 0; q < 3; q++) {
-                const cd rq = flip ? mk(-r[q].r, -r[q].i) : r[q];
-                cacc_add(upa[q], rq);
-                const cd e = cunit(rq, en != neg_sp, ei);
-                if (to3) cacc_add(l3a[q], e);
-                else cacc_add(l2a[q], e);
+                const cdp rq = flip ? cdp_neg(r[q]) : r[q];
+                caccp_add(upa[q], rq);
+                const cdp e = cdp_unit(rq, en != neg_sp, ei);
+                if (to3) caccp_add(l3a[q], e);
+                else caccp_add(l2a[q], e);
             }
         }
-        cd up[3], lo2[3], lo3[3];
+        cdp up[3], lo2[3], lo3[3];
 #pragma unroll
         for (int q = 0; q < 3; q++) {
-            up[q] = cacc_done(upa[q]);
-            lo2[q] = cacc_done(l2a[q]);
-            lo3[q] = cacc_done(l3a[q]);
+            up[q] = caccp_done(upa[q]);
+            lo2[q] = caccp_done(l2a[q]);
+            lo3[q] = caccp_done(l3a[q]);
         }
         if constexpr (EPI == EPI_XPAY) {
             const float4* yb = (const float4*)((const char*)a.y.data + (size_t)k * a.y.rhs_bytes);
 #pragma unroll
-            for (int j = 0; j < 6; j++) yv[j] = ld_cd(yb, (size_t)(6 * h + j) * vh + s);
+            for (int j = 0; j < 6; j++) yv[j] = ld_cdp(yb, (size_t)(6 * h + j) * vh + s);
         }
         // thread 0 takes the partner's upper spin (spin 1); thread 1 the partner's lower spins
-        const df half(0.5f);
 #pragma unroll
         for (int q = 0; q < 3; q++) {
-            const cd ra = pair_swap(h ? up[q] : lo2[q]);
-            const cd rb = pair_swap(lo3[q]);
-            const cd w0 = h ? lo2[q] + ra : up[q];
-            const cd w1 = h ? lo3[q] + rb : ra;
-            w[q] = mk(half * w0.r, half * w0.i);
-            w[3 + q] = mk(half * w1.r, half * w1.i);
+            const cdp ra = pair_swap(h ? up[q] : lo2[q]);
+            const cdp rb = pair_swap(lo3[q]);
+            const cdp w0 = h ? cdp_add(lo2[q], ra) : up[q];
+            const cdp w1 = h ? cdp_add(lo3[q], rb) : ra;
+            w[q] = cdp_scale_half(w0);
+            w[3 + q] = cdp_scale_half(w1);
         }
     }
 
@@ -232,8 +253,8 @@ __global__ void __launch_bounds__(256, 2) wilson_dslash_df2_kernel(WilsonArgs a)
     if constexpr (EPI == EPI_HOP) {
 #pragma unroll
         for (int i = 0; i < 6; i++) {
-            if (live) st_cd(out, (size_t)(6 * h + i) * vh + s, neg_out ? mk(-w[i].r, -w[i].i) : w[i]);
-            nrm = nrm + cnorm2(w[i]);
+            if (live) st_cdp(out, (size_t)(6 * h + i) * vh + s, neg_out ? cdp_neg(w[i]) : w[i]);
+            nrm = nrm + cdp_norm2(w[i]);
         }
     } else if constexpr (EPI == EPI_AINV) {
         if (a.has_clover) {
@@ -246,36 +267,44 @@ __global__ void __launch_bounds__(256, 2) wilson_dslash_df2_kernel(WilsonArgs a)
             for (int j = 0; j < 6; j++) cur[j] = __ldg(A + entry(0, j));
 #pragma unroll 1
             for (int i = 0; i < 6; i++) {
-                if (i < 5) {
+                if (ROWPF && i < 5) {
 #pragma unroll
                     for (int j = 0; j < 6; j++) nxt[j] = __ldg(A + entry(i + 1, j));
+                } else if (!ROWPF && i > 0) {
+#pragma unroll
+                    for (int j = 0; j < 6; j++) cur[j] = __ldg(A + entry(i, j));
                 }
-                cacc t = cacc_zero();
+                caccp t = caccp_zero();
 #pragma unroll
                 for (int j = 0; j < 6; j++) {
-                    const cd m = mk(df(cur[j].x, cur[j].y), df(cur[j].z, cur[j].w));
-                    if (dag) cacc_cjmac(t, m, w[j]);
-                    else cacc_mac(t, m, w[j]);
+                    const cdp m = cdp_of(cur[j]);
+                    if (dag) caccp_cjmac(t, m, w[j]);
+                    else caccp_mac(t, m, w[j]);
                 }
+                if (ROWPF) {
 #pragma unroll
-                for (int j = 0; j < 6; j++) cur[j] = nxt[j];
-                const cd acc = cacc_done(t);
-                if (live) st_cd(out, (size_t)(6 * h + i) * vh + s, neg_out ? mk(-acc.r, -acc.i) : acc);
-                nrm = nrm + cnorm2(acc);
+                    for (int j = 0; j < 6; j++) cur[j] = nxt[j];
+                }
+                const cdp acc = caccp_done(t);
+                if (live) st_cdp(out, (size_t)(6 * h + i) * vh + s, neg_out ? cdp_neg(acc) : acc);
+                nrm = nrm + cdp_norm2(acc);
             }
         } else {
             // A^{-1} = ((4+m) - i mu_h) / ((4+m)^2 + mu^2) on chiral block h (mu_0 = mu, mu_1 = mu1)
             const double inv = 1.0 / (a.m4 * a.m4 + a.mu * a.mu);
-            const cd f = mk(df(a.m4 * inv), df(-(h ? a.mu1 : a.mu) * inv));
+            const df fr(a.m4 * inv), fi(-(h ? a.mu1 : a.mu) * inv);
+            const cdp f{p2(fr.hi, fi.hi), p2(fr.lo, fi.lo)};
 #pragma unroll
             for (int i = 0; i < 6; i++) {
-                const cd o = f * w[i];
-                if (live) st_cd(out, (size_t)(6 * h + i) * vh + s, neg_out ? mk(-o.r, -o.i) : o);
-                nrm = nrm + cnorm2(o);
+                caccp t = caccp_zero();
+                caccp_mac(t, f, w[i]);
+                const cdp o = caccp_done(t);
+                if (live) st_cdp(out, (size_t)(6 * h + i) * vh + s, neg_out ? cdp_neg(o) : o);
+                nrm = nrm + cdp_norm2(o);
             }
         }
     } else {  // EPI_XPAY: out = ((4+m) + i mu_h + C) y - w on block h
-        const cd f = mk(df(a.m4), df(h ? a.mu1 : a.mu));
+        const df fr(a.m4), fi(h ? a.mu1 : a.mu);
         // C block h: 6 real diagonal entries (3 chunks) then the 15 upper entries
         // (row-major, i < j); chunk (i, j) of row i is the diagonal pair for j == i.
         // The chunks of row i+1 are in flight while row i is computed.
@@ -293,28 +322,35 @@ __global__ void __launch_bounds__(256, 2) wilson_dslash_df2_kernel(WilsonArgs a)
         }
 #pragma unroll 1
         for (int i = 0; i < 6; i++) {
-            if (clov && i < 5) {
+            if (ROWPF && clov && i < 5) {
 #pragma unroll
                 for (int j = 0; j < 6; j++) nxt[j] = __ldg(C + chunk(i + 1, j));
+            } else if (!ROWPF && clov && i > 0) {
+#pragma unroll
+                for (int j = 0; j < 6; j++) cur[j] = __ldg(C + chunk(i, j));
             }
-            cacc t = cacc_zero();
+            caccp t = caccp_zero();
 #pragma unroll
             for (int j = 0; j < 6; j++) {
                 if (j == i) {
-                    const df di = !clov ? df(0.f) : (i & 1) ? df(cur[j].z, cur[j].w) : df(cur[j].x, cur[j].y);
-                    cacc_mac(t, mk(f.r + di, f.i), yv[j]);
-                    cacc_add(t, mk(-w[j].r, -w[j].i));
+                    // diagonal: the two reals of chunk (i, i) are entries 2(i/2), 2(i/2)+1
+                    const df di = !clov ? df(0.f) : (i & 1) ? df(cur[j].y, cur[j].w) : df(cur[j].x, cur[j].z);
+                    const df dr = fr + di;
+                    caccp_mac(t, cdp{p2(dr.hi, fi.hi), p2(dr.lo, fi.lo)}, yv[j]);
+                    caccp_add(t, cdp_neg(w[j]));
                 } else if (clov) {
-                    const cd m = mk(df(cur[j].x, cur[j].y), df(cur[j].z, cur[j].w));
-                    if (i < j) cacc_mac(t, m, yv[j]);
-                    else cacc_cjmac(t, m, yv[j]);
+                    const cdp m = cdp_of(cur[j]);
+                    if (i < j) caccp_mac(t, m, yv[j]);
+                    else caccp_cjmac(t, m, yv[j]);
                 }
             }
+            if (ROWPF) {
 #pragma unroll
-            for (int j = 0; j < 6; j++) cur[j] = nxt[j];
-            const cd acc = cacc_done(t);
-            if (live) st_cd(out, (size_t)(6 * h + i) * vh + s, neg_out ? mk(-acc.r, -acc.i) : acc);
-            nrm = nrm + cnorm2(acc);
+                for (int j = 0; j < 6; j++) cur[j] = nxt[j];
+            }
+            const cdp acc = caccp_done(t);
+            if (live) st_cdp(out, (size_t)(6 * h + i) * vh + s, neg_out ? cdp_neg(acc) : acc);
+            nrm = nrm + cdp_norm2(acc);
         }
     }
     if (a.norm_out) {

@@ -127,7 +127,8 @@ def test_schur_operator(L, orc, prec):
 # in flight; 3000 - 6000 + block: the FP16 packed-pair kernels (128 / 85 registers with
 # two hops in flight, 102 / 85 registers with one)
 CODES = [(p, c) for p in (1, 2) for c in (64, 128, 256, 1064, 1128, 1256, 2064, 2128)] + \
-        [(2, c) for c in (3064, 3128, 4064, 4128, 5064, 5128, 6064, 6128, 7256)]
+        [(2, c) for c in (3064, 3128, 4064, 4128, 5064, 5128, 6064, 6128, 7256)] + \
+        [(3, c) for c in (64, 128, 256, 1064, 1128, 1256)]  # double-float; 1000 + block: no row prefetch
 
 
 @pytest.mark.parametrize("prec,code", CODES)
