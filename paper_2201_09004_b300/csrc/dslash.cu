@@ -4,6 +4,7 @@
 #include <string>
 
 #include "dslash_launch.cuh"
+#include "hisq_x2.cuh"
 #include "wilson_x2.cuh"
 
 namespace lq {
@@ -216,8 +217,23 @@ int hisq_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int epi,
     a.fin = FinArgs();  // the tuner's trial launches never finalise
     const int nb = (op.prec == LQ_F32 || op.prec == LQ_F16) ? pick_rg(a.nrhs) : 1;
     const char* name = hname(op.prec, epi);
+    // the packed-pair FP16 kernel (hisq_x2.cuh): R12 long links, one right-hand side;
+    // tuning codes 3000 + block (128 registers), 4000 + block (85) and 5000 + block (64)
+    const bool x2 = op.prec == LQ_F16 && op.recon == 12 && a.nrhs == 1 && lat.geo.fast;
     auto run = [&](int block) {
-        if (op.prec == LQ_F64) {
+        if (x2 && block >= 3000) {
+            const int bs = block % 1000, v = block / 1000;
+            dim3 grid((a.g.vh + bs - 1) / bs);
+            if (epi == EPI_XPAY) {
+                if (v == 5) launch(name, hisq_f16x2_kernel<EPI_XPAY, 8>, grid, dim3(bs), st, a);
+                else if (v == 4) launch(name, hisq_f16x2_kernel<EPI_XPAY, 6>, grid, dim3(bs), st, a);
+                else launch(name, hisq_f16x2_kernel<EPI_XPAY, 4>, grid, dim3(bs), st, a);
+            } else {
+                if (v == 5) launch(name, hisq_f16x2_kernel<EPI_HOP, 8>, grid, dim3(bs), st, a);
+                else if (v == 4) launch(name, hisq_f16x2_kernel<EPI_HOP, 6>, grid, dim3(bs), st, a);
+                else launch(name, hisq_f16x2_kernel<EPI_HOP, 4>, grid, dim3(bs), st, a);
+            }
+        } else if (op.prec == LQ_F64) {
             if (op.recon == 18) hl_epi<P64, 18>(name, a, epi, nb, block, st);
             else hl_epi<P64, 12>(name, a, epi, nb, block, st);
         } else if (op.prec == LQ_F32X2) {
@@ -234,10 +250,13 @@ int hisq_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int epi,
     };
     std::string key = std::string(name) + "/r" + std::to_string(op.recon) + "/nb" + std::to_string(nb) + "/v" +
                       std::to_string(lat.vh) + "/n" + std::to_string(norm_out != nullptr);
-    int block = tuned_block(key, st, run);
+    std::vector<int> cand = {64, 128, 256};
+    if (x2)
+        for (int c : {3064, 3128, 4064, 4128, 5064, 5128}) cand.push_back(c);
+    int block = tuned_block(key, st, run, cand);
     a.fin = norm_out ? fin : FinArgs();
     run(block);
-    return site_blocks(lat.vh, block, nb);
+    return site_blocks(lat.vh, block % 1000, nb);
 }
 
 }  // namespace lq

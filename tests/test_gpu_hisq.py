@@ -155,3 +155,35 @@ def test_hisq_full_size_sampled_sites(L, orc):
             sites = cand[par == p][:2000]
             ref = D.hop_sites(ph, sites)
             assert rel_err(got[sites], ref) < TOL[prec], (prec, p)
+
+
+@pytest.mark.parametrize("dims", DIMS)
+@pytest.mark.parametrize("code", [3064, 3128, 4128, 5128])
+def test_hisq_packed_pair_kernel_every_geometry(L, orc, dims, code):
+    """The FP16 packed-pair HISQ kernel (its own neighbour indexing at distances 1 and 3,
+    wrapping twice on extents of 2) for each tuning code: hopping term per parity and
+    adjoint, and the Schur operator, against the oracle."""
+    lat, V, W = make(L, dims, 51)
+    psi = synth.gaussian_field(dims, 52, ncomp=3).numpy()
+    m = 0.07
+    D = orc.Hisq(dims, V, W, 0.0)
+    op = L.op_params(L.HISQ, m, c_naik=-1.0 / 24.0)
+    mask = parity_mask(dims)
+    try:
+        L.tune_reset()
+        L.tune_force(code)
+        for dagger in (False, True):
+            ref = D.hop(psi, dagger=dagger)
+            for p in (0, 1):
+                got = lat.dslash_apply(op, p, psi, dagger=dagger, prec=2)
+                sel = mask == p
+                assert np.all(got[~sel] == 0)
+                assert rel_err(got[sel], ref[sel]) < TOL[2], (dims, code, dagger, p)
+        ve = np.where((mask == 0)[..., None], psi, 0)
+        Hv = D.hop(ve)
+        ref = m * m * ve - np.where((mask == 0)[..., None], D.hop(np.where((mask == 1)[..., None], Hv, 0)), 0)
+        got = lat.operator_apply(op, psi, form=L.OP_SCHUR, prec=2)
+        assert rel_err(got, ref) < 10 * TOL[2], (dims, code)
+    finally:
+        L.tune_force(0)
+        L.tune_reset()
