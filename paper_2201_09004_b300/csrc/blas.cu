@@ -65,9 +65,10 @@ __global__ void zero_kernel(FieldV d) {
     }
 }
 
-// y += a_k x  (host scalars)
+// y += a_k x  (host scalars); zero_x: then x = 0 (the reliable update's fold of the
+// sloppy solution into the accumulated one)
 template <int PY, int PX, int NR>
-__global__ void axpy_h_kernel(FieldV y, FieldV x, HostScalars h) {
+__global__ void axpy_h_kernel(FieldV y, FieldV x, HostScalars h, int zero_x) {
     typedef typename MathT<PY, PX>::T T;
     const int k = blockIdx.y;
     const T a = (T)h.a[k];
@@ -78,6 +79,11 @@ __global__ void axpy_h_kernel(FieldV y, FieldV x, HostScalars h) {
 #pragma unroll
         for (int q = 0; q < NR; q++) vy[q] = fma(a, vx[q], vy[q]);
         fstore<PY, NR, T>(y, k, s, vy);
+        if (zero_x) {
+#pragma unroll
+            for (int q = 0; q < NR; q++) vx[q] = (T)0;
+            fstore<PX, NR, T>(x, k, s, vx);
+        }
     }
 }
 
@@ -636,23 +642,27 @@ static HostScalars hs(const double* a, const double* b, int n) {
 }
 
 template <int PY>
-static void axpy_h_from(Field& y, const HostScalars& h, const Field& x, cudaStream_t st) {
+static void axpy_h_from(Field& y, const HostScalars& h, const Field& x, int zero_x, cudaStream_t st) {
     dim3 g = upd_grid(y.vh, y.nrhs);
 #define K(NR) axpy_h_kernel<PY, P_, NR>
-#define L(P) { constexpr int P_ = P; BY_KIND(y, "blas_axpy", K, g, y.view(), x.view(), h); }
+#define L(P) { constexpr int P_ = P; BY_KIND(y, "blas_axpy", K, g, y.view(), x.view(), h, zero_x); }
     DISPATCH_P(x.prec, L);
 #undef L
 #undef K
 }
 
-void blas_axpy_h(Field& y, const double* a, const Field& x, cudaStream_t st) {
+static void axpy_h_any(Field& y, const double* a, const Field& x, int zero_x, cudaStream_t st) {
     if (y.kind != x.kind || y.nrhs != x.nrhs) fail(LQ_EINVAL, "blas_axpy: shape mismatch");
     HostScalars h = hs(a, nullptr, y.nrhs);
-    if (y.prec == LQ_F64) axpy_h_from<P64>(y, h, x, st);
-    else if (y.prec == LQ_F32) axpy_h_from<P32>(y, h, x, st);
-    else if (y.prec == LQ_F16) axpy_h_from<P16>(y, h, x, st);
-    else axpy_h_from<PDF>(y, h, x, st);
+    if (y.prec == LQ_F64) axpy_h_from<P64>(y, h, x, zero_x, st);
+    else if (y.prec == LQ_F32) axpy_h_from<P32>(y, h, x, zero_x, st);
+    else if (y.prec == LQ_F16) axpy_h_from<P16>(y, h, x, zero_x, st);
+    else axpy_h_from<PDF>(y, h, x, zero_x, st);
 }
+
+void blas_axpy_h(Field& y, const double* a, const Field& x, cudaStream_t st) { axpy_h_any(y, a, x, 0, st); }
+
+void blas_axpy_h_zero(Field& y, const double* a, Field& x, cudaStream_t st) { axpy_h_any(y, a, x, 1, st); }
 
 void blas_axpby_h(Field& y, const double* a, const Field& x, const double* b, df* part, cudaStream_t st) {
     if (y.prec != x.prec || y.kind != x.kind || y.nrhs != x.nrhs) fail(LQ_EINVAL, "blas_axpby: field mismatch");

@@ -101,9 +101,17 @@ WilsonArgs wilson_args(Lattice& lat, const OpDesc& op, int parity, int dagger, i
 }
 
 int wilson_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int epi, const Field& in, Field& out,
-                  const Field* y, df* norm_out, cudaStream_t st, const FinArgs& fin) {
+                  const Field* y, df* norm_out, cudaStream_t st, const FinArgs& fin, const Field* rb, Field* lo) {
     WilsonArgs a = wilson_args(lat, op, parity, dagger, epi, in, out, y, st);
     a.norm_out = norm_out;
+    if (rb || lo) {  // the residual epilogue of the double-float A y - D kernel
+        if (!rb || op.prec != LQ_F32X2 || epi != EPI_XPAY || a.gamma5_out || rb->prec != LQ_F32X2 ||
+            rb->kind != LQ_WILSON_FIELD || rb->nrhs != out.nrhs || (lo && (lo->prec != LQ_F16 ||
+            lo->kind != LQ_WILSON_FIELD || lo->nrhs != out.nrhs)))
+            fail(LQ_EINVAL, "wilson_dslash: residual epilogue needs double-float A y - D, fields of its shape");
+        a.rb = rb->view();
+        if (lo) a.lo = lo->view();
+    }
     a.fin = FinArgs();  // the tuner's trial launches never finalise
     const int nb = (op.prec == LQ_F32 || op.prec == LQ_F16) ? pick_rg(a.nrhs) : 1;
     const char* name = wname(op.prec, epi);
@@ -135,7 +143,7 @@ int wilson_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int ep
     };
     std::string key = std::string(name) + "/r" + std::to_string(op.recon) + "/nb" + std::to_string(nb) + "/v" +
                       std::to_string(lat.vh) + "/c" + std::to_string(a.has_clover) + "/n" +
-                      std::to_string(norm_out != nullptr);
+                      std::to_string(norm_out != nullptr) + (rb ? (lo ? "/res16" : "/res") : "");
     std::vector<int> cand = {64, 128, 256};
     if ((op.prec == LQ_F32 || op.prec == LQ_F16) && nb != 2)
         for (int b : {64, 128, 256}) cand.push_back(kCapped + b);

@@ -81,12 +81,17 @@ __device__ __forceinline__ void hisq_process(const HisqArgs& a, const HPairRaw& 
     constexpr bool FWD = (Q & 1) == 0;
     cx<float> F[3][3], W[3][3];
     decode_link<P16, 18, float>(r.uf, a.fat.scale, F);
-    decode_link<P16, 12, float>(r.ul, a.lng.scale, W);
+    decode_r12_codes(r.ul, W);  // row 2 one factor scale/32767 short (applied on the long lane below)
+    const float2 f2l = make_float2(1.f, a.lng.scale * (1.f / 32767.f));
     float2 Vr[3], Vi[3], NV[3];
 #pragma unroll
     for (int b = 0; b < 3; b++) {
         Vr[b] = make_float2(s16lo(r.spf[b]), s16lo(r.spl[b]));
         Vi[b] = make_float2(s16hi(r.spf[b]), s16hi(r.spl[b]));
+        if (!FWD && b == 2) {  // conj(W[2][i]) multiplies component 2 of the long hop
+            Vr[b] = __fmul2_rn(Vr[b], f2l);
+            Vi[b] = __fmul2_rn(Vi[b], f2l);
+        }
         NV[b] = __fmul2_rn(FWD ? Vi[b] : Vr[b], bc2(-1.f));
     }
     float2 Rr[3], Ri[3];
@@ -110,6 +115,10 @@ __device__ __forceinline__ void hisq_process(const HisqArgs& a, const HPairRaw& 
                 Ri[i] = __ffma2_rn(Ui, NV[b], Ri[i]);
             }
         }
+    }
+    if constexpr (FWD) {  // row 2 of W
+        Rr[2] = __fmul2_rn(Rr[2], f2l);
+        Ri[2] = __fmul2_rn(Ri[2], f2l);
     }
     // forward hops add, backward hops subtract; FP16 scales, boundary signs and c_naik
     const float sg = FWD ? 1.f : -1.f;

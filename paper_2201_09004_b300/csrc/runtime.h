@@ -231,8 +231,10 @@ inline double mu_block1(const OpDesc& d) { return d.twist == LQ_TWIST_SCALAR ? d
 // out = epilogue(D in) for output parity; `y` used by EPI_XPAY (same parity as out).
 // norm_out: optional per-block partials of |out|^2 (nrhs * blocks).
 // Returns the number of thread blocks per right-hand side (the partial-sum stride).
+// rb, lo (double-float EPI_XPAY only): out = rb - (A y - D in) instead, and its FP16 copy into lo.
 int wilson_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int epi, const Field& in,
-                  Field& out, const Field* y, df* norm_out, cudaStream_t st, const FinArgs& fin = FinArgs());
+                  Field& out, const Field* y, df* norm_out, cudaStream_t st, const FinArgs& fin = FinArgs(),
+                  const Field* rb = nullptr, Field* lo = nullptr);
 // ak (device, optional): per-rhs XPAY scale at ak[k * SC_N], replacing a
 int hisq_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int epi, double a, const Field& in,
                 Field& out, const Field* y, df* norm_out, cudaStream_t st, const FinArgs& fin = FinArgs(),
@@ -263,6 +265,7 @@ void blas_norm2(const Field& x, df* part, cudaStream_t st, const FinArgs& fin = 
 void blas_copy(Field& dst, const Field& src, cudaStream_t st);           // with precision conversion
 void blas_zero(Field& x, cudaStream_t st);
 void blas_axpy_h(Field& y, const double* a_host, const Field& x, cudaStream_t st);  // y += a_k x (host scalars)
+void blas_axpy_h_zero(Field& y, const double* a_host, Field& x, cudaStream_t st);  // y += a_k x, then x = 0
 // y = a_k x + b_k y per right-hand side k (host scalars), optional partial |y|^2
 void blas_axpby_h(Field& y, const double* a, const Field& x, const double* b, df* part, cudaStream_t st);
 // s = b - q, with partial |s|^2

@@ -130,6 +130,23 @@ int schur_wilson(Lattice& lat, const OpDesc& op, int dagger, const Field& in, Fi
     return wilson_dslash(lat, op, 0, dagger, EPI_XPAY, tmp, out, &in, part, st, fin);
 }
 
+// s = b - Mhat x in FP64 accuracy, |s|^2 finalised as fin says (partials in part), and
+// s_lo = s in the sloppy precision. With the double-float operator the A y - D kernel
+// forms the residual and its FP16 copy in its epilogue; otherwise Mhat x is followed
+// by a subtraction and a copy.
+static void schur_residual(Lattice& lat, const OpDesc& op64, const Field& x, const Field& b, Field& s, Field& s_lo,
+                           Field& q64, Field& t64, df* part, cudaStream_t st, const FinArgs& fin) {
+    if (op64.prec == LQ_F32X2) {
+        wilson_dslash(lat, op64, 1, 0, EPI_AINV, x, t64, nullptr, nullptr, st);
+        wilson_dslash(lat, op64, 0, 0, EPI_XPAY, t64, s, &x, part, st, fin, &b, s_lo.prec == LQ_F16 ? &s_lo : nullptr);
+        if (s_lo.prec != LQ_F16) blas_copy(s_lo, s, st);
+    } else {
+        schur_wilson(lat, op64, 0, x, q64, t64, nullptr, st);
+        blas_xmy_norm(s, b, q64, part, st, fin);
+        blas_copy(s_lo, s, st);
+    }
+}
+
 // ------------------------------------------------------------ Krylov driver
 // The loop shared by the mixed-precision solvers. The host reads the residual
 // norms of iteration i while iteration i+1 runs: each iteration ends with an
@@ -290,12 +307,12 @@ static CgResult cgnr_mixed(Lattice& lat, const OpDesc& ops, const OpDesc& op64, 
     std::vector<double> ones(n, 1.0);
 
     if (guess) {  // x_hi holds the initial guess: s = bhat - Mhat x_hi in FP64 accuracy
-        schur_wilson(lat, op64, 0, x_hi, q64, t64, nullptr, st);
-        blas_xmy_norm(s_hi, bhat, q64, sc.part, st, sc.f(SC_SS, FIN_SET));
+        schur_residual(lat, op64, x_hi, bhat, s_hi, s_lo, q64, t64, sc.part, st, sc.f(SC_SS, FIN_SET));
     } else {
         blas_zero(x_hi, st);
         blas_copy(s_hi, bhat, st);
         blas_norm2(bhat, sc.part, st, sc.f(SC_SS, FIN_SET));
+        blas_copy(s_lo, s_hi, st);
     }
     // partial sums of |q|^2 and |r|^2 that the CG vector kernels finalise themselves
     const size_t nper = std::max<size_t>((size_t)(lat.vh + 7) / 8, (size_t)3 * RED_BLOCKS) * n;
@@ -305,7 +322,6 @@ static CgResult cgnr_mixed(Lattice& lat, const OpDesc& ops, const OpDesc& op64, 
         Lattice& l; void* a; void* b; cudaStream_t s;
         ~PartCleanup() { ws_put(l, a, s); ws_put(l, b, s); }
     } part_cleanup{lat, part_q, part_r, st};
-    blas_copy(s_lo, s_hi, st);
     blas_zero(x_lo, st);
     int nr = schur_wilson(lat, ops, 1, s_lo, r, t, part_r, st, sc.f(SC_RR, FIN_SET));
     blas_copy(p, r, st);
@@ -342,11 +358,8 @@ static CgResult cgnr_mixed(Lattice& lat, const OpDesc& ops, const OpDesc& op64, 
         if (dst) LQ_CUDA(cudaMemcpyAsync(dst, sc.dev, sizeof(double) * SC_N * n, cudaMemcpyDeviceToHost, st));
     };
     auto update = [&]() {
-        blas_axpy_h(x_hi, ones.data(), x_lo, st);
-        blas_zero(x_lo, st);
-        schur_wilson(lat, op64, 0, x_hi, q64, t64, nullptr, st);
-        blas_xmy_norm(s_hi, bhat, q64, sc.part, st, sc.f(SC_SS, FIN_SET));
-        blas_copy(s_lo, s_hi, st);
+        blas_axpy_h_zero(x_hi, ones.data(), x_lo, st);
+        schur_residual(lat, op64, x_hi, bhat, s_hi, s_lo, q64, t64, sc.part, st, sc.f(SC_SS, FIN_SET));
         nr = schur_wilson(lat, ops, 1, s_lo, r, t, part_r, st, sc.f(SC_RR, FIN_SET));
         for (int k = 0; k < n; k++)
             if (!ks.done[k]) res.applications[k] += 2;
@@ -405,11 +418,8 @@ static CgResult bicgstab_mixed(Lattice& lat, const OpDesc& ops, const OpDesc& op
         if (dst) LQ_CUDA(cudaMemcpyAsync(dst, sc.dev, sizeof(double) * SC_N * n, cudaMemcpyDeviceToHost, st));
     };
     auto update = [&]() {
-        blas_axpy_h(x_hi, ones.data(), x_lo, st);
-        blas_zero(x_lo, st);
-        schur_wilson(lat, op64, 0, x_hi, q64, t64, nullptr, st);
-        blas_xmy_norm(r_hi, bhat, q64, sc.part, st, sc.f(SC_SS, FIN_SET));
-        blas_copy(r, r_hi, st);
+        blas_axpy_h_zero(x_hi, ones.data(), x_lo, st);
+        schur_residual(lat, op64, x_hi, bhat, r_hi, r, q64, t64, sc.part, st, sc.f(SC_SS, FIN_SET));
         blas_bicg_rho(r, r0, sc.part, st, sc.f(0, FIN_BICG_RHO));
         for (int k = 0; k < n; k++)
             if (!ks.done[k]) res.applications[k] += 2;
@@ -578,8 +588,7 @@ static CgResult gcr_mixed(Lattice& lat, const OpDesc& ops, const OpDesc& op64, F
             if (restart || j + 1 == kmax || it >= maxiter) break;
         }
         // defect correction: x_hi += x_lo, r = bhat - Mhat x_hi in FP64 accuracy
-        blas_axpy_h(x_hi, ones.data(), x_lo, st);
-        blas_zero(x_lo, st);
+        blas_axpy_h_zero(x_hi, ones.data(), x_lo, st);
         schur_wilson(lat, op64, 0, x_hi, q64, t64, nullptr, st);
         blas_xmy_norm(r_hi, bhat, q64, part, st);
         blas_copy(r, r_hi, st);
@@ -689,12 +698,18 @@ int solve_wilson(Lattice& lat, const lq_op_params& opp, const lq_solve_params& s
             export_field(lat, xo, k, 1, x[k], st);
         }
         // FP64 true residual of the full system: r_p = b_p - (A_pp x_p - H_{p,1-p} x_{1-p})
-        wilson_dslash(lat, op64, 0, 0, EPI_XPAY, xo, te, &xe, nullptr, st);
-        blas_xmy_norm(te, be, te, sc.part, st);
-        sc.fin(RED_BLOCKS, SC_RR, st);
-        wilson_dslash(lat, op64, 1, 0, EPI_XPAY, xe, to, &xo, nullptr, st);
-        blas_xmy_norm(to, bo, to, sc.part, st);
-        sc.fin(RED_BLOCKS, SC_QQ, st);
+        // (formed in the double-float kernel's epilogue, or by a subtraction after it)
+        if (op64.prec == LQ_F32X2) {
+            wilson_dslash(lat, op64, 0, 0, EPI_XPAY, xo, te, &xe, sc.part, st, sc.f(SC_RR, FIN_SET), &be);
+            wilson_dslash(lat, op64, 1, 0, EPI_XPAY, xe, to, &xo, sc.part, st, sc.f(SC_QQ, FIN_SET), &bo);
+        } else {
+            wilson_dslash(lat, op64, 0, 0, EPI_XPAY, xo, te, &xe, nullptr, st);
+            blas_xmy_norm(te, be, te, sc.part, st);
+            sc.fin(RED_BLOCKS, SC_RR, st);
+            wilson_dslash(lat, op64, 1, 0, EPI_XPAY, xe, to, &xo, nullptr, st);
+            blas_xmy_norm(to, bo, to, sc.part, st);
+            sc.fin(RED_BLOCKS, SC_QQ, st);
+        }
         LQ_CUDA(cudaEventRecord(e1, st));
         sc.pull(st);
         float ms = 0.f;
@@ -1006,8 +1021,7 @@ static CgResult cg_hisq(Lattice& lat, const OpDesc& ops, const OpDesc& op64, con
         if (dst) LQ_CUDA(cudaMemcpyAsync(dst, sc.dev, sizeof(double) * SC_N * n, cudaMemcpyDeviceToHost, st));
     };
     auto update = [&]() {
-        blas_axpy_h(x_hi, ones.data(), x_lo, st);
-        blas_zero(x_lo, st);
+        blas_axpy_h_zero(x_hi, ones.data(), x_lo, st);
         true_residual();
         for (int k = 0; k < n; k++)
             if (!ks.done[k]) res.applications[k] += 1;

@@ -39,6 +39,11 @@ struct WilsonArgs {
     df* norm_out;       // if non-null: per-block partial sums of |out|^2, per rhs
     FinArgs fin;        // with norm_out: the last block finalises the sums
     float m4f, muf, mu1f;  // m4, mu, mu1 rounded to FP32 once on the host (FP32 kernels)
+    // double-float A y - D psi only: with rb.data set the kernel writes the residual
+    // out = rb - (A y - D psi) (and |out|^2 with norm_out); with lo.data set also its
+    // FP16 copy into lo (codes and per-site norm as the FP16 store writes them)
+    FieldV rb = {nullptr, nullptr, 0, 0};
+    FieldV lo = {nullptr, nullptr, 0, 0};
 };
 
 // spin projection h = top two spins of (1 + s g_mu) psi, for psi as cx[4][3]

@@ -310,6 +310,7 @@ __global__ void __launch_bounds__(256, 2) wilson_dslash_df2_kernel(WilsonArgs a)
         // The chunks of row i+1 are in flight while row i is computed.
         const float4* C = (const float4*)a.clov;
         const bool clov = a.has_clover != 0;
+        const float4* rb = a.rb.data ? (const float4*)((const char*)a.rb.data + (size_t)k * a.rb.rhs_bytes) : nullptr;
         auto chunk = [&](int i, int j) {
             const int lo = j < i ? j : i, hi = j < i ? i : j;
             const int q = lo * 5 - lo * (lo - 1) / 2 + (hi - lo - 1);
@@ -348,9 +349,41 @@ __global__ void __launch_bounds__(256, 2) wilson_dslash_df2_kernel(WilsonArgs a)
 #pragma unroll
                 for (int j = 0; j < 6; j++) cur[j] = nxt[j];
             }
-            const cdp acc = caccp_done(t);
-            if (live) st_cdp(out, (size_t)(6 * h + i) * vh + s, neg_out ? cdp_neg(acc) : acc);
+            cdp acc = caccp_done(t);
+            if (neg_out) acc = cdp_neg(acc);
+            if (rb) acc = cdp_add(ld_cdp(rb, (size_t)(6 * h + i) * vh + s), cdp_neg(acc));  // rb - (A y - w)
+            if (live) st_cdp(out, (size_t)(6 * h + i) * vh + s, acc);
             nrm = nrm + cdp_norm2(acc);
+        }
+        if (a.lo.data) {
+            // FP16 copy of the site: this thread's 12 reals read back from out (rounded to
+            // FP32 as the FP16 store rounds them), the site's max |v| over both threads
+            float v[12];
+#pragma unroll
+            for (int j = 0; j < 6; j++) {
+                const float4 c = live ? __ldcg(out + (size_t)(6 * h + j) * vh + s) : make_float4(0.f, 0.f, 0.f, 0.f);
+                v[2 * j] = __fadd_rn(c.x, c.z);
+                v[2 * j + 1] = __fadd_rn(c.y, c.w);
+            }
+            float m = 0.f;
+#pragma unroll
+            for (int j = 0; j < 12; j++) m = fmaxf(m, fabsf(v[j]));
+            m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+            const float f = m > 0.f ? __fdividef(32767.f, m) : 0.f;
+            // reals 0-11 of the site (h = 0) are chunk 0 and the first half of chunk 1,
+            // reals 12-23 (h = 1) the second half of chunk 1 and chunk 2
+            int4* lb = (int4*)((char*)a.lo.data + (size_t)k * a.lo.rhs_bytes);
+            const int4 full = h ? make_int4(pack16f(v[4], v[5], f), pack16f(v[6], v[7], f), pack16f(v[8], v[9], f),
+                                            pack16f(v[10], v[11], f))
+                                : make_int4(pack16f(v[0], v[1], f), pack16f(v[2], v[3], f), pack16f(v[4], v[5], f),
+                                            pack16f(v[6], v[7], f));
+            const int2 half = h ? make_int2(pack16f(v[0], v[1], f), pack16f(v[2], v[3], f))
+                                : make_int2(pack16f(v[8], v[9], f), pack16f(v[10], v[11], f));
+            if (live) {
+                lb[(size_t)(h ? 2 : 0) * vh + s] = full;
+                ((int2*)(lb + vh + s))[h] = half;
+                if (h == 0) a.lo.norm[(size_t)k * vh + s] = m;
+            }
         }
     }
     if (a.norm_out) {

@@ -130,6 +130,22 @@ __device__ __forceinline__ int spw(const int4 sp[3], int s, int c) {
     return r == 0 ? q.x : (r == 1 ? q.y : (r == 2 ? q.z : q.w));
 }
 
+// An R12 FP16 link as integer codes: rows 0 and 1 as stored, row 2 = conj(row 0 x row 1)
+// of the codes, which is one factor scale/32767 short of the other rows' units (the
+// caller applies it to the row-2 result, or to the component row 2 multiplies)
+__device__ __forceinline__ void decode_r12_codes(const int2 u[3], cx<float> U[3][3]) {
+    float lv[12];
+#pragma unroll
+    for (int k = 0; k < 3; k++) unpack_codes16<12, float>(u[k], lv + 4 * k);
+#pragma unroll
+    for (int r = 0; r < 2; r++)
+#pragma unroll
+        for (int q = 0; q < 3; q++) U[r][q] = mk(lv[(r * 3 + q) * 2], lv[(r * 3 + q) * 2 + 1]);
+    U[2][0] = cj(U[0][1] * U[1][2] - U[0][2] * U[1][1]);
+    U[2][1] = cj(U[0][2] * U[1][0] - U[0][0] * U[1][2]);
+    U[2][2] = cj(U[0][0] * U[1][1] - U[0][1] * U[1][0]);
+}
+
 template <int H, bool DAG>
 __device__ __forceinline__ void process16(const WilsonArgs& a, const HopRaw16& h, Acc2& A) {
     constexpr int MU = H >> 1;
@@ -165,10 +181,15 @@ __device__ __forceinline__ void process16(const WilsonArgs& a, const HopRaw16& h
         Hr[col] = __fmul2_rn(Hr[col], bc2(sg));
         Hi[col] = __fmul2_rn(Hi[col], bc2(sg));
     }
-    // link (integer codes; R12 third row rescaled once by decode_link)
+    // link (integer codes; the third row's missing factor goes on row 2 of U h, or on
+    // component 2 of h for U^+ h)
     cx<float> U[3][3];
-    decode_link<P16, 12, float>(h.u, a.U.scale, U);
+    decode_r12_codes(h.u, U);
     float2 Rr[3], Ri[3];
+    if constexpr (!FWD) {
+        Hr[2] = __fmul2_rn(Hr[2], bc2(fu));
+        Hi[2] = __fmul2_rn(Hi[2], bc2(fu));
+    }
     if constexpr (FWD) {  // r = U h
         float2 NHi[3];
 #pragma unroll
@@ -187,6 +208,8 @@ __device__ __forceinline__ void process16(const WilsonArgs& a, const HopRaw16& h
                 Ri[r] = __ffma2_rn(bc2(U[r][b].i), Hr[b], Ri[r]);
             }
         }
+        Rr[2] = __fmul2_rn(Rr[2], bc2(fu));
+        Ri[2] = __fmul2_rn(Ri[2], bc2(fu));
     } else {  // r = U^+ h
         float2 NHr[3];
 #pragma unroll
