@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(256, 2) wilson_dslash_df2_kernel(WilsonArgs a)
 #pragma unroll
         for (int q = 0; q < 3; q++) upa[q] = l2a[q] = l3a[q] = caccp_zero();
         float bs_next = issue(0, 0);
-#pragma unroll 1
+#pragma unroll
         for (int hop = 0; hop < 8; hop++) {
             const int mu = hop >> 1;
             const bool fwd = (hop & 1) == 0;
