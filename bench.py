@@ -681,6 +681,24 @@ def run_dslash(args):
         gbs = bps * vh / (us * 1e-6) / 1e9
         out[name] = {"us": round(us, 2), "launches": launches, "bytes_per_site": bps, "GB_s": round(gbs, 1),
                      "frac_of_measured": round(gbs / peak, 4), "frac_of_nominal_8tbs": round(gbs / 8000.0, 4)}
+    # the fused multi-right-hand-side kernels: the Schur operator on 12 right-hand sides in
+    # one call (three groups of four threads per site); the algorithmic bytes count the
+    # spinors per right-hand side and the links and clover records once per group
+    nr = 12
+    opw = lib.op_params(lib.WILSON_TM_CLOVER, MASS, MU, c_sw=C_SW, recon=12)
+    fi, fo, ft = (lib.Field(lat, lib.WILSON_FIELD, lib.F16, nr) for _ in range(3))
+    for k in range(nr):
+        fi.load(k, 0, synth.gaussian_field(dims, 220 + k, device="cuda"))
+    us = timed(lambda: lib.schur_field(lat, opw, fi, fo, ft, stream=stream))
+    groups = (nr + 3) // 4
+    bps = nr * (52 + 52 + 52 + 52 + 52) + groups * ((8 * 24 + 292) + (8 * 24 + 148))
+    gbs = bps * vh / (us * 1e-6) / 1e9
+    single = out["wilson_schur_f16_r12 (A^-1 D + A y - D)"]["us"]
+    out["wilson_schur_f16_r12_12rhs (A^-1 D + A y - D, 3 groups of 4 per site)"] = {
+        "us": round(us, 2), "us_per_rhs": round(us / nr, 2), "launches": 2, "bytes_per_site": bps,
+        "GB_s": round(gbs, 1), "frac_of_measured": round(gbs / peak, 4),
+        "per_rhs_speedup_over_single_rhs": round(single / (us / nr), 3)}
+    del fi, fo, ft
     line = {"workload": "dslash", "metric": "Dslash HBM GB/s vs roofline (algorithmic bytes, L2 flushed)",
             "config": {"dims": list(dims), "sites_per_parity": vh, "peak_gbs": peak, "peak_source": peak_kind,
                        "reps": reps, "l2": "flushed (256 MB write, then 256 MB read) before every timed launch"},

@@ -390,6 +390,110 @@ __device__ __forceinline__ void store16_blk(const WilsonArgs& a, int s, const Bl
     ob[2 * vh + s] = make_int4(w[8], w[9], w[10], w[11]);
 }
 
+// the shared-memory views of x2_site's epilogue records
+#define LQ_X2_SMEM_VIEWS \
+    constexpr int NREC = EPI == EPI_AINV ? 18 : (EPI == EPI_XPAY ? 9 : 0); /* int4 chunks of the record */ \
+    int4* sm_rec = (int4*)smem; \
+    int4* sm_y = sm_rec + NREC * spb_rec; \
+    float* sm_norm = (float*)(sm_y + (EPI == EPI_XPAY ? 3 : 0) * spb); /* [spb_rec] record, [spb] y norms */ \
+    (void)sm_y; (void)sm_norm
+
+// x2_site, step 1: asynchronous copies of the site's epilogue record (and y) into shared memory
+template <int EPI, bool CG = false, int RG = 1>
+__device__ __forceinline__ void x2_record(const WilsonArgs& a, int s, int g_rec, int spb_rec, int g, int spb, int lane,
+                                          unsigned char* smem) {
+    LQ_X2_SMEM_VIEWS;
+    if constexpr (EPI != EPI_HOP) {
+        const int4* gsrc = (const int4*)a.clov;
+#pragma unroll
+        for (int k = 0; k < NREC; k++)
+            if (RG == 1 || k % RG == lane) cp_async16(&sm_rec[k * spb_rec + g_rec], &gsrc[(size_t)k * a.g.vh + s]);
+        if (RG == 1 || lane == 0) cp_async4(&sm_norm[g_rec], a.clov_norm + s);
+        if constexpr (EPI == EPI_XPAY) {
+            const int4* ysrc = (const int4*)a.y.data;
+#pragma unroll
+            for (int k = 0; k < 3; k++) cp_async16(&sm_y[k * spb + g], &ysrc[(size_t)k * a.g.vh + s]);
+            // (the 4-byte asynchronous copy goes through L1, which may hold stale lines of a
+            // field written earlier in the same kernel)
+            if constexpr (CG) sm_norm[spb_rec + g] = __ldcg(a.y.norm + s);
+            else cp_async4(&sm_norm[spb_rec + g], a.y.norm + s);
+        }
+        cp_async_commit();
+    }
+}
+
+// x2_site, step 3: the epilogue on the accumulated hops A and the FP16 store
+template <int EPI, bool DAG, bool CG = false, int RG = 1>
+__device__ __forceinline__ void x2_epilogue(const WilsonArgs& a, int s, int g_rec, int spb_rec, int g, int spb,
+                                            unsigned gmask, unsigned char* smem, const Acc2& A, bool want_norm,
+                                            bool store, df& nrm) {
+    LQ_X2_SMEM_VIEWS;
+    // D psi as block pairs, times 1/2: block 0 = spins (0, 1), block 1 = spins (2, 3)
+    Blk2 d;
+#pragma unroll
+    for (int col = 0; col < 3; col++) {
+        d.r[col] = make_float2(A.a01r[col].x, A.a23r[col].x + A.a32r[col].y);
+        d.i[col] = make_float2(A.a01i[col].x, A.a23i[col].x + A.a32i[col].y);
+        d.r[3 + col] = make_float2(A.a01r[col].y, A.a23r[col].y + A.a32r[col].x);
+        d.i[3 + col] = make_float2(A.a01i[col].y, A.a23i[col].y + A.a32i[col].x);
+    }
+    Blk2 res;
+    if constexpr (EPI == EPI_HOP) {
+#pragma unroll
+        for (int j = 0; j < 6; j++) { res.r[j] = __fmul2_rn(d.r[j], bc2(0.5f)); res.i[j] = __fmul2_rn(d.i[j], bc2(0.5f)); }
+    } else if constexpr (EPI == EPI_AINV) {
+        cp_async_wait_all();
+        if constexpr (RG > 1) __syncwarp(gmask);  // the record chunks the other lanes copied
+        const float f = 0.5f * sm_norm[g_rec] * (1.f / 32767.f);
+#pragma unroll
+        for (int j = 0; j < 6; j++) { d.r[j] = __fmul2_rn(d.r[j], bc2(f)); d.i[j] = __fmul2_rn(d.i[j], bc2(f)); }
+        ainv_pairs<DAG>(sm_rec, spb_rec, g_rec, d, res);
+    } else {  // A y - D psi, A = (4+m) + i mu_b + C
+        cp_async_wait_all();
+        if constexpr (RG > 1) __syncwarp(gmask);
+        Blk2 y;
+        const float fy = sm_norm[spb_rec + g] * (1.f / 32767.f);
+        const float2 mag = bc2(-0.5f * LQ_MAG2);
+#pragma unroll
+        for (int col = 0; col < 3; col++) {
+#pragma unroll
+            for (int sp2 = 0; sp2 < 2; sp2++) {  // spin' within the block
+                const int4 yc0 = sm_y[((3 * sp2 + col) >> 2) * spb + g];
+                const int4 yc1 = sm_y[((3 * (2 + sp2) + col) >> 2) * spb + g];
+                const int r0 = (3 * sp2 + col) & 3, r1 = (3 * (2 + sp2) + col) & 3;
+                const int w0 = r0 == 0 ? yc0.x : (r0 == 1 ? yc0.y : (r0 == 2 ? yc0.z : yc0.w));
+                const int w1 = r1 == 0 ? yc1.x : (r1 == 1 ? yc1.y : (r1 == 2 ? yc1.z : yc1.w));
+                const int j = 3 * sp2 + col;
+                y.r[j] = __fmul2_rn(__fadd2_rn(make_float2(raw_lo(w0), raw_lo(w1)), mag), bc2(fy));
+                y.i[j] = __fmul2_rn(__fadd2_rn(make_float2(raw_hi(w0), raw_hi(w1)), mag), bc2(fy));
+            }
+        }
+        // res = (4+m) y + i mu_b y - D psi / 2, then + C y
+        const float m4 = a.m4f;
+        const float2 mub = make_float2(a.muf, a.mu1f);
+        const float2 nmub = make_float2(-a.muf, -a.mu1f);
+#pragma unroll
+        for (int j = 0; j < 6; j++) {
+            res.r[j] = __ffma2_rn(bc2(m4), y.r[j], __fmul2_rn(d.r[j], bc2(-0.5f)));
+            res.r[j] = __ffma2_rn(nmub, y.i[j], res.r[j]);
+            res.i[j] = __ffma2_rn(bc2(m4), y.i[j], __fmul2_rn(d.i[j], bc2(-0.5f)));
+            res.i[j] = __ffma2_rn(mub, y.r[j], res.i[j]);
+        }
+        // the clover record's scale goes on y (C's entries stay integer codes)
+        const float fc = sm_norm[g_rec] * (1.f / 32767.f);
+#pragma unroll
+        for (int j = 0; j < 6; j++) { y.r[j] = __fmul2_rn(y.r[j], bc2(fc)); y.i[j] = __fmul2_rn(y.i[j], bc2(fc)); }
+        clover_pairs(sm_rec, spb_rec, g_rec, y, res);
+    }
+    if (want_norm) {
+        float2 t = bc2(0.f);
+#pragma unroll
+        for (int j = 0; j < 6; j++) { t = __ffma2_rn(res.r[j], res.r[j], t); t = __ffma2_rn(res.i[j], res.i[j], t); }
+        nrm = nrm + df_of(t.x + t.y);
+    }
+    if (store) store16_blk(a, s, res);
+}
+
 // One output site s: the hops, the epilogue and the FP16 store (when `store`). The
 // fields of `a` are those of one right-hand side. The epilogue record of the site goes
 // through record slot g_rec of the block's shared memory (spb_rec slots; with RG > 1
@@ -399,101 +503,16 @@ __device__ __forceinline__ void store16_blk(const WilsonArgs& a, int s, const Bl
 template <int EPI, bool DAG, bool CG = false, int DEPTH = 2, int RG = 1>
 __device__ __forceinline__ void x2_site(const WilsonArgs& a, int s, int g_rec, int spb_rec, int g, int spb, int lane,
                                         unsigned gmask, unsigned char* smem, bool want_norm, bool store, df& nrm) {
-    constexpr int NREC = EPI == EPI_AINV ? 18 : (EPI == EPI_XPAY ? 9 : 0);  // int4 chunks of the record
-    int4* sm_rec = (int4*)smem;
-    int4* sm_y = sm_rec + NREC * spb_rec;
-    float* sm_norm = (float*)(sm_y + (EPI == EPI_XPAY ? 3 : 0) * spb);  // [spb_rec] record norms, [spb] y norms
-    {
-        if constexpr (EPI != EPI_HOP) {
-            const int4* gsrc = (const int4*)a.clov;
+    x2_record<EPI, CG, RG>(a, s, g_rec, spb_rec, g, spb, lane, smem);
+    int c[4], xh;
+    cb_coords_fast(a.g, s, a.parity, c, xh);
+    Acc2 A;
 #pragma unroll
-            for (int k = 0; k < NREC; k++)
-                if (RG == 1 || k % RG == lane) cp_async16(&sm_rec[k * spb_rec + g_rec], &gsrc[(size_t)k * a.g.vh + s]);
-            if (RG == 1 || lane == 0) cp_async4(&sm_norm[g_rec], a.clov_norm + s);
-            if constexpr (EPI == EPI_XPAY) {
-                const int4* ysrc = (const int4*)a.y.data;
-#pragma unroll
-                for (int k = 0; k < 3; k++) cp_async16(&sm_y[k * spb + g], &ysrc[(size_t)k * a.g.vh + s]);
-                // (the 4-byte asynchronous copy goes through L1, which may hold stale lines of a
-                // field written earlier in the same kernel)
-                if constexpr (CG) sm_norm[spb_rec + g] = __ldcg(a.y.norm + s);
-                else cp_async4(&sm_norm[spb_rec + g], a.y.norm + s);
-            }
-            cp_async_commit();
-        }
-        int c[4], xh;
-        cb_coords_fast(a.g, s, a.parity, c, xh);
-        Acc2 A;
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-            A.a01r[k] = A.a01i[k] = A.a23r[k] = A.a23i[k] = A.a32r[k] = A.a32i[k] = bc2(0.f);
-        }
-        hops16<DAG, CG, DEPTH>(a, s, c, xh, A);
-        // D psi as block pairs, times 1/2: block 0 = spins (0, 1), block 1 = spins (2, 3)
-        Blk2 d;
-#pragma unroll
-        for (int col = 0; col < 3; col++) {
-            d.r[col] = make_float2(A.a01r[col].x, A.a23r[col].x + A.a32r[col].y);
-            d.i[col] = make_float2(A.a01i[col].x, A.a23i[col].x + A.a32i[col].y);
-            d.r[3 + col] = make_float2(A.a01r[col].y, A.a23r[col].y + A.a32r[col].x);
-            d.i[3 + col] = make_float2(A.a01i[col].y, A.a23i[col].y + A.a32i[col].x);
-        }
-        Blk2 res;
-        if constexpr (EPI == EPI_HOP) {
-#pragma unroll
-            for (int j = 0; j < 6; j++) { res.r[j] = __fmul2_rn(d.r[j], bc2(0.5f)); res.i[j] = __fmul2_rn(d.i[j], bc2(0.5f)); }
-        } else if constexpr (EPI == EPI_AINV) {
-            cp_async_wait_all();
-            if constexpr (RG > 1) __syncwarp(gmask);  // the record chunks the other lanes copied
-            const float f = 0.5f * sm_norm[g_rec] * (1.f / 32767.f);
-#pragma unroll
-            for (int j = 0; j < 6; j++) { d.r[j] = __fmul2_rn(d.r[j], bc2(f)); d.i[j] = __fmul2_rn(d.i[j], bc2(f)); }
-            ainv_pairs<DAG>(sm_rec, spb_rec, g_rec, d, res);
-        } else {  // A y - D psi, A = (4+m) + i mu_b + C
-            cp_async_wait_all();
-            if constexpr (RG > 1) __syncwarp(gmask);
-            Blk2 y;
-            const float fy = sm_norm[spb_rec + g] * (1.f / 32767.f);
-            const float2 mag = bc2(-0.5f * LQ_MAG2);
-#pragma unroll
-            for (int col = 0; col < 3; col++) {
-#pragma unroll
-                for (int sp2 = 0; sp2 < 2; sp2++) {  // spin' within the block
-                    const int4 yc0 = sm_y[((3 * sp2 + col) >> 2) * spb + g];
-                    const int4 yc1 = sm_y[((3 * (2 + sp2) + col) >> 2) * spb + g];
-                    const int r0 = (3 * sp2 + col) & 3, r1 = (3 * (2 + sp2) + col) & 3;
-                    const int w0 = r0 == 0 ? yc0.x : (r0 == 1 ? yc0.y : (r0 == 2 ? yc0.z : yc0.w));
-                    const int w1 = r1 == 0 ? yc1.x : (r1 == 1 ? yc1.y : (r1 == 2 ? yc1.z : yc1.w));
-                    const int j = 3 * sp2 + col;
-                    y.r[j] = __fmul2_rn(__fadd2_rn(make_float2(raw_lo(w0), raw_lo(w1)), mag), bc2(fy));
-                    y.i[j] = __fmul2_rn(__fadd2_rn(make_float2(raw_hi(w0), raw_hi(w1)), mag), bc2(fy));
-                }
-            }
-            // res = (4+m) y + i mu_b y - D psi / 2, then + C y
-            const float m4 = a.m4f;
-            const float2 mub = make_float2(a.muf, a.mu1f);
-            const float2 nmub = make_float2(-a.muf, -a.mu1f);
-#pragma unroll
-            for (int j = 0; j < 6; j++) {
-                res.r[j] = __ffma2_rn(bc2(m4), y.r[j], __fmul2_rn(d.r[j], bc2(-0.5f)));
-                res.r[j] = __ffma2_rn(nmub, y.i[j], res.r[j]);
-                res.i[j] = __ffma2_rn(bc2(m4), y.i[j], __fmul2_rn(d.i[j], bc2(-0.5f)));
-                res.i[j] = __ffma2_rn(mub, y.r[j], res.i[j]);
-            }
-            // the clover record's scale goes on y (C's entries stay integer codes)
-            const float fc = sm_norm[g_rec] * (1.f / 32767.f);
-#pragma unroll
-            for (int j = 0; j < 6; j++) { y.r[j] = __fmul2_rn(y.r[j], bc2(fc)); y.i[j] = __fmul2_rn(y.i[j], bc2(fc)); }
-            clover_pairs(sm_rec, spb_rec, g_rec, y, res);
-        }
-        if (want_norm) {
-            float2 t = bc2(0.f);
-#pragma unroll
-            for (int j = 0; j < 6; j++) { t = __ffma2_rn(res.r[j], res.r[j], t); t = __ffma2_rn(res.i[j], res.i[j], t); }
-            nrm = nrm + df_of(t.x + t.y);
-        }
-        if (store) store16_blk(a, s, res);
+    for (int k = 0; k < 3; k++) {
+        A.a01r[k] = A.a01i[k] = A.a23r[k] = A.a23i[k] = A.a32r[k] = A.a32i[k] = bc2(0.f);
     }
+    hops16<DAG, CG, DEPTH>(a, s, c, xh, A);
+    x2_epilogue<EPI, DAG, CG, RG>(a, s, g_rec, spb_rec, g, spb, gmask, smem, A, want_norm, store, nrm);
 }
 
 // Grid: one thread per output site, blocks of consecutive sites. DAG: the adjoint.
