@@ -293,7 +293,11 @@ static CgResult cgnr_mixed(Lattice& lat, const OpDesc& ops, const OpDesc& op64, 
                            cudaStream_t st, bool guess = false, int persistent = 0) {
     const int n = bhat.nrhs;
     const int ps = ops.prec;
-    const int px = ps == LQ_F16 ? LQ_F32 : ps;  // the sloppy solution accumulates in at least FP32
+    // the sloppy solution x_lo in the sloppy precision (FP16 storage halves the bytes of its
+    // update in every iteration; the reliable update folds it into x_hi, which absorbs its
+    // rounding: the iteration count and the true residual stay those of FP32 storage);
+    // the persistent kernel keeps it in FP32
+    const int px = ps == LQ_F16 && persistent > 0 ? LQ_F32 : ps;
     const int WF = LQ_WILSON_FIELD;
     Pool pool(lat, st);
     const int ph = op64.prec;  // FP64, or double-float for the mixed solvers

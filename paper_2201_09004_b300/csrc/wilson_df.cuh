@@ -116,8 +116,10 @@ __device__ __forceinline__ df cdp_norm2(cdp v) {
     return re * re + im * im;
 }
 
-// dynamic shared memory of the hop staging (two slots of 21 chunks per site)
-__host__ __device__ constexpr size_t df2_smem_bytes(int block) { return (size_t)2 * 21 * 16 * (block / 2); }
+// dynamic shared memory: the hop staging (two slots of 21 chunks per site) and the 12
+// chunks per site of the residual's rb (used by A y - D with rb, copied at the start);
+// 110.6 KB for 256 threads, two blocks per SM as the launch bounds ask
+__host__ __device__ constexpr size_t df2_smem_bytes(int block) { return (size_t)(2 * 21 + 12) * 16 * (block / 2); }
 
 // SITE = true: no hops, w = block h of `in` at the site (out = A^{-1} in). ROWPF: the
 // epilogue loads the entries of row i+1 while row i is computed (more registers in flight).
@@ -135,6 +137,7 @@ __global__ void __launch_bounds__(256, 2) wilson_dslash_df2_kernel(WilsonArgs a)
 
     cdp w[6];   // chiral block h: spins 2h, 2h+1 (index 3 * spin' + colour)
     cdp yv[6];  // EPI_XPAY: block h of y, loaded while the pair exchanges its sums
+    const float4* rbs = nullptr;  // EPI_XPAY with rb: block h of rb in shared memory
     if constexpr (SITE) {
 #pragma unroll
         for (int j = 0; j < 6; j++) w[j] = ld_cdp(in, (size_t)(6 * h + j) * vh + s);
@@ -147,6 +150,15 @@ __global__ void __launch_bounds__(256, 2) wilson_dslash_df2_kernel(WilsonArgs a)
         extern __shared__ __align__(16) unsigned char lq_smem[];
         float4* stage = (float4*)lq_smem;
         const int g = threadIdx.x >> 1;
+        if (EPI == EPI_XPAY && a.rb.data) {
+            // rb of the residual: copied first, so that the hops' waits also cover it
+            float4* rbw = stage + (size_t)2 * 21 * spb;
+            const float4* src = (const float4*)((const char*)a.rb.data + (size_t)k * a.rb.rhs_bytes);
+#pragma unroll
+            for (int j = 0; j < 6; j++) cp_async16(&rbw[(6 * h + j) * spb + g], src + (size_t)(6 * h + j) * vh + s);
+            cp_async_commit();
+            rbs = rbw + g;
+        }
         auto issue = [&](int hop, int slot) -> float {
             const int mu = hop >> 1;
             const bool fwd = (hop & 1) == 0;
@@ -310,7 +322,7 @@ __global__ void __launch_bounds__(256, 2) wilson_dslash_df2_kernel(WilsonArgs a)
         // The chunks of row i+1 are in flight while row i is computed.
         const float4* C = (const float4*)a.clov;
         const bool clov = a.has_clover != 0;
-        const float4* rb = a.rb.data ? (const float4*)((const char*)a.rb.data + (size_t)k * a.rb.rhs_bytes) : nullptr;
+        const int spb2 = spb;
         auto chunk = [&](int i, int j) {
             const int lo = j < i ? j : i, hi = j < i ? i : j;
             const int q = lo * 5 - lo * (lo - 1) / 2 + (hi - lo - 1);
@@ -351,7 +363,7 @@ __global__ void __launch_bounds__(256, 2) wilson_dslash_df2_kernel(WilsonArgs a)
             }
             cdp acc = caccp_done(t);
             if (neg_out) acc = cdp_neg(acc);
-            if (rb) acc = cdp_add(ld_cdp(rb, (size_t)(6 * h + i) * vh + s), cdp_neg(acc));  // rb - (A y - w)
+            if (rbs) acc = cdp_add(cdp_of(rbs[(6 * h + i) * spb2]), cdp_neg(acc));  // rb - (A y - w)
             if (live) st_cdp(out, (size_t)(6 * h + i) * vh + s, acc);
             nrm = nrm + cdp_norm2(acc);
         }
