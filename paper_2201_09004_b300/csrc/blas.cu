@@ -140,6 +140,7 @@ __global__ void xmy_norm_kernel(FieldV sf, FieldV b, FieldV qf, df* part, FinArg
 // x += alpha p; s -= alpha q; partial |s|^2; alpha_k = sc[k*SC_N + SC_ALPHA]
 template <int PX, int P, int NR>
 __global__ void cg_xs_kernel(FieldV x, FieldV p, FieldV sf, FieldV qf, const double* sc, df* part, FinArgs fin) {
+    pdl_start();
     typedef typename RealT<P>::T T;
     typedef typename MathT<PX, P>::T TX;
     const int k = blockIdx.y;
@@ -198,6 +199,7 @@ __global__ void cg_p_norm_kernel(FieldV p, FieldV r, const double* sc, df* part,
 // p = r + beta p
 template <int P, int NR>
 __global__ void cg_p_kernel(FieldV p, FieldV r, const double* sc) {
+    pdl_start();
     typedef typename RealT<P>::T T;
     const int k = blockIdx.y;
     const T b = (T)sc[(size_t)k * SC_N + SC_BETA];
@@ -214,6 +216,7 @@ __global__ void cg_p_kernel(FieldV p, FieldV r, const double* sc) {
 // sum the partials of right-hand side blockIdx.x (double-float, fixed order),
 // then apply the scalar step in FP64
 __global__ void finalize_kernel(const df* part, int nblocks, double* sc, int slot, int op) {
+    pdl_start();
     const int k = blockIdx.x;
     const df* pk = part + (size_t)k * nblocks;
     df sum(0.f);
@@ -590,6 +593,12 @@ static dim3 upd_grid(int vh, int nrhs) {
         else { MACRO(PDF); }                        \
     } while (0)
 
+#define BY_KIND_PDL(f, NAME, KERNEL, GRID, ...)                                                                 \
+    do {                                                                                                        \
+        if ((f).kind == LQ_WILSON_FIELD) launch_pdl(NAME, KERNEL(24), GRID, dim3(RED_THREADS), 0, st, __VA_ARGS__); \
+        else launch_pdl(NAME, KERNEL(6), GRID, dim3(RED_THREADS), 0, st, __VA_ARGS__);                          \
+    } while (0)
+
 #define BY_KIND(f, NAME, KERNEL, GRID, ...)                                                     \
     do {                                                                                        \
         if ((f).kind == LQ_WILSON_FIELD) launch(NAME, KERNEL(24), GRID, dim3(RED_THREADS), st, __VA_ARGS__); \
@@ -688,7 +697,7 @@ template <int PX>
 static void cg_xs_from(Field& x, const Field& p, Field& s, const Field& q, const double* sc, df* part,
                        cudaStream_t st, const FinArgs& fin) {
 #define K(NR) cg_xs_kernel<PX, P_, NR>
-#define L(P) { constexpr int P_ = P; BY_KIND(x, "blas_cg_xs", K, red_grid(x.nrhs), x.view(), p.view(), s.view(), q.view(), sc, part, fin); }
+#define L(P) { constexpr int P_ = P; BY_KIND_PDL(x, "blas_cg_xs", K, red_grid(x.nrhs), x.view(), p.view(), s.view(), q.view(), sc, part, fin); }
     DISPATCH_P(p.prec, L);
 #undef L
 #undef K
@@ -813,14 +822,14 @@ void blas_cg_p(Field& p, const Field& r, const double* sc, cudaStream_t st) {
     if (p.prec != r.prec) fail(LQ_EINVAL, "blas_cg_p: precision mismatch");
     dim3 g = upd_grid(p.vh, p.nrhs);
 #define K(NR) cg_p_kernel<P_, NR>
-#define L(P) { constexpr int P_ = P; BY_KIND(p, "blas_cg_p", K, g, p.view(), r.view(), sc); }
+#define L(P) { constexpr int P_ = P; BY_KIND_PDL(p, "blas_cg_p", K, g, p.view(), r.view(), sc); }
     DISPATCH_P(p.prec, L);
 #undef L
 #undef K
 }
 
 void blas_finalize(const df* part, int nblocks, int nrhs, double* sc, int slot, int op, cudaStream_t st) {
-    launch("blas_finalize", finalize_kernel, dim3(nrhs), dim3(256), st, part, nblocks, sc, slot, op);
+    launch_pdl("blas_finalize", finalize_kernel, dim3(nrhs), dim3(256), 0, st, part, nblocks, sc, slot, op);
 }
 
 void blas_cdot_multi(const FieldV* vs_dev, int nv, const Field& w, df* part, cudaStream_t st) {

@@ -499,6 +499,16 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+// Programmatic dependent launch (kernels launched with launch_pdl): pdl_start() first lets
+// the next such kernel of the stream be scheduled once all blocks of this one have
+// started (its blocks then wait in their own pdl_start), and then waits until the
+// previous kernel of the stream has completed and its memory is visible. Without the
+// launch attribute both instructions do nothing.
+__device__ __forceinline__ void pdl_start() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // copy the NR-real record of site s (chunk-major global array with stride vh)

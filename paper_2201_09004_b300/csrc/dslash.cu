@@ -18,11 +18,12 @@ namespace lq {
 //      blocks, and so half the partial sums of a fused reduction).
 enum { kX2 = 3000, kX2c = 4000, kX2d = 5000, kX2e = 6000, kX2w = 7000 };
 
+// (programmatic dependent launch: the kernel begins with pdl_start)
 template <int EPI, bool DAG, int MINB, int DEPTH, int BT = 128>
 static void wl_x2(const char* name, const WilsonArgs& a, int block, cudaStream_t st) {
     dim3 grid((a.g.vh + block - 1) / block);
-    launch_smem(name, wilson_f16x2_kernel<EPI, DAG, MINB, DEPTH, BT>, grid, dim3(block), x2_smem_bytes<EPI>(block),
-                st, a);
+    launch_pdl(name, wilson_f16x2_kernel<EPI, DAG, MINB, DEPTH, BT>, grid, dim3(block), x2_smem_bytes<EPI>(block),
+               st, a);
 }
 
 // several right-hand sides, RG = 4 threads per site (variants 3 and 5 of the single-RHS codes)

@@ -73,6 +73,33 @@ inline void launch(const char* name, void (*kernel)(KArgs...), dim3 grid, dim3 b
     count_launch();
 }
 
+// Launch with programmatic stream serialization: the kernel may be scheduled while the
+// previous kernel of the stream is finishing, so it must begin with pdl_start()
+// (core.cuh), which waits for that kernel's completion before any memory access.
+// In a graph capture the dependency becomes a programmatic edge.
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(const char* name, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t st, Args&&... args) {
+    if (grid.x == 0 || grid.y == 0) return;
+    if (smem > 48 * 1024) opt_in_smem((const void*)kernel, smem);
+    int slot = prof_begin(name, st);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) fail(LQ_ECUDA, std::string("launch of ") + name + ": " + cudaGetErrorString(e));
+    prof_end(slot, st);
+    count_launch();
+}
+
 // ------------------------------------------------------------- CUDA graphs
 // A captured sequence of launches (solver iterations) replayed by one
 // cudaGraphLaunch. If profiling is on while it is captured, every kernel is

@@ -521,6 +521,7 @@ __device__ __forceinline__ void x2_site(const WilsonArgs& a, int s, int g_rec, i
 // flight; BT: the largest block size of the build (128 or 256).
 template <int EPI, bool DAG, int MINB, int DEPTH, int BT = 128>
 __global__ void __launch_bounds__(BT, MINB) wilson_f16x2_kernel(WilsonArgs a) {
+    pdl_start();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     extern __shared__ __align__(16) unsigned char lq_smem[];
     df nrm = df(0.f);
