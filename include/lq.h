@@ -158,6 +158,15 @@ typedef struct {
                          cooperative kernel (grid-wide barriers between the operator, vector and
                          reduction phases) instead of separate kernels and graphs; 0 = off. Other
                          configurations ignore it. */
+    double update_f32_below; /* LQ_MIXED_CGNR with sloppy FP32 or FP16: once the true residual of the
+                         last reliable update is below this fraction of |bhat| (for every right-hand
+                         side), a reliable update forms the new residual in correction form,
+                         s = s_prev - Mhat (x - x_prev), with the FP32 operator (x - x_prev, the sloppy
+                         solution, is exact in FP32; the error of the product, ~1e-7 of |s_prev|, stays
+                         below the target once |s_prev| is small); the solution still accumulates in
+                         FP64 accuracy and the final residual is recomputed from b in FP64 accuracy.
+                         0 = off: every update recomputes b - Mhat x in FP64 accuracy (Sec. 1,
+                         mixed-precision solvers). */
 } lq_solve_params;
 
 typedef struct {

@@ -288,9 +288,12 @@ static KrylovState krylov_start(Scalars& sc, CgResult& res, const std::vector<do
 // (alpha and beta stay on the device). A reliable update folds the sloppy
 // solution into x_hi, recomputes s = bhat - Mhat x_hi in FP64 accuracy, keeps
 // p and restarts the norm recurrence from the new r = Mhat^+ s.
+// f32_below > 0: a reliable update whose previous true residual is below f32_below |bhat|
+// (every right-hand side) forms s = s_prev - Mhat dx in correction form with the FP32
+// operator, dx = x_lo the sloppy solution since the previous update (exact in FP32).
 static CgResult cgnr_mixed(Lattice& lat, const OpDesc& ops, const OpDesc& op64, Field& bhat, Field& x_hi,
                            const std::vector<double>& tol_abs, double delta, int maxiter, int graph_iters,
-                           cudaStream_t st, bool guess = false, int persistent = 0) {
+                           cudaStream_t st, bool guess = false, int persistent = 0, double f32_below = 0.0) {
     const int n = bhat.nrhs;
     const int ps = ops.prec;
     // the sloppy solution x_lo in the sloppy precision (FP16 storage halves the bytes of its
@@ -331,6 +334,17 @@ static CgResult cgnr_mixed(Lattice& lat, const OpDesc& ops, const OpDesc& op64, 
     blas_copy(p, r, st);
     sc.pull(st);
     KrylovState ks = krylov_start(sc, res, tol_abs, st);
+    const std::vector<double> r_start = ks.rmax;  // |bhat - Mhat x_0| per right-hand side
+    // the correction-form updates: the FP32 operator and its fields
+    OpDesc op32 = ops;
+    op32.prec = LQ_F32;
+    const bool corr_ok = f32_below > 0 && (ps == LQ_F16 || ps == LQ_F32);
+    Field x32, q32, t32;
+    if (corr_ok) {
+        x32 = pool.get(WF, LQ_F32, n);
+        q32 = pool.get(WF, LQ_F32, n);
+        t32 = pool.get(WF, LQ_F32, n);
+    }
     // persistent: that many iterations per launch of one cooperative kernel (persistent.cu)
     const bool pers = persistent > 0 && persistent_cg_supported(lat, ops, n);
     unsigned* bar = nullptr;
@@ -362,8 +376,20 @@ static CgResult cgnr_mixed(Lattice& lat, const OpDesc& ops, const OpDesc& op64, 
         if (dst) LQ_CUDA(cudaMemcpyAsync(dst, sc.dev, sizeof(double) * SC_N * n, cudaMemcpyDeviceToHost, st));
     };
     auto update = [&]() {
-        blas_axpy_h_zero(x_hi, ones.data(), x_lo, st);
-        schur_residual(lat, op64, x_hi, bhat, s_hi, s_lo, q64, t64, sc.part, st, sc.f(SC_SS, FIN_SET));
+        bool corr = corr_ok;
+        for (int k = 0; k < n && corr; k++)
+            if (!ks.done[k] && !(ks.rmax[k] <= f32_below * r_start[k])) corr = false;
+        if (corr) {  // s = s_prev - Mhat_32 x_lo, then x_hi += x_lo
+            blas_copy(x32, x_lo, st);
+            blas_axpy_h_zero(x_hi, ones.data(), x_lo, st);
+            schur_wilson(lat, op32, 0, x32, q32, t32, nullptr, st);
+            blas_copy(q64, q32, st);
+            blas_xmy_norm(s_hi, s_hi, q64, sc.part, st, sc.f(SC_SS, FIN_SET));
+            blas_copy(s_lo, s_hi, st);
+        } else {
+            blas_axpy_h_zero(x_hi, ones.data(), x_lo, st);
+            schur_residual(lat, op64, x_hi, bhat, s_hi, s_lo, q64, t64, sc.part, st, sc.f(SC_SS, FIN_SET));
+        }
         nr = schur_wilson(lat, ops, 1, s_lo, r, t, part_r, st, sc.f(SC_RR, FIN_SET));
         for (int k = 0; k < n; k++)
             if (!ks.done[k]) res.applications[k] += 2;
@@ -691,7 +717,8 @@ int solve_wilson(Lattice& lat, const lq_op_params& opp, const lq_solve_params& s
                           ? gcr_mixed(lat, ops, op64, bhat, xe, tol_abs, delta, maxiter,
                                       sp.restart > 0 ? sp.restart : GCR_DEFAULT, st)
                           : cgnr_mixed(lat, ops, op64, bhat, xe, tol_abs, delta, maxiter, sp.graph_iters, st,
-                                       x0 != nullptr, sp.solver == LQ_MIXED_CGNR ? sp.persistent : 0);
+                                       x0 != nullptr, sp.solver == LQ_MIXED_CGNR ? sp.persistent : 0,
+                                       sp.solver == LQ_MIXED_CGNR ? sp.update_f32_below : 0.0);
 
         // x_o = A_oo^{-1} (b_o + H_oe x_e)
         wilson_dslash(lat, op64, 1, 0, EPI_HOP, xe, to, nullptr, nullptr, st);

@@ -62,7 +62,8 @@ class SolveParams(ctypes.Structure):
     _fields_ = [("solver", ctypes.c_int), ("tol", ctypes.c_double), ("delta", ctypes.c_double),
                 ("maxiter", ctypes.c_int), ("prec_sloppy", ctypes.c_int), ("recon_sloppy", ctypes.c_int),
                 ("nshift", ctypes.c_int), ("masses", ctypes.POINTER(ctypes.c_double)),
-                ("graph_iters", ctypes.c_int), ("restart", ctypes.c_int), ("persistent", ctypes.c_int)]
+                ("graph_iters", ctypes.c_int), ("restart", ctypes.c_int), ("persistent", ctypes.c_int),
+                ("update_f32_below", ctypes.c_double)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -157,9 +158,9 @@ def op_params(action, m, mu=0.0, c_sw=0.0, c_naik=-1.0 / 24.0, recon=0, twist_mo
 
 
 def solve_params(solver=MIXED_CGNR, tol=1e-10, delta=0.1, maxiter=100000, prec_sloppy=F32, recon_sloppy=R12,
-                 masses=None, graph_iters=0, restart=0, persistent=0):
+                 masses=None, graph_iters=0, restart=0, persistent=0, update_f32_below=0.0):
     sp = SolveParams(int(solver), float(tol), float(delta), int(maxiter), int(prec_sloppy), int(recon_sloppy), 0, None,
-                     int(graph_iters), int(restart), int(persistent))
+                     int(graph_iters), int(restart), int(persistent), float(update_f32_below))
     if masses is not None:
         arr = (ctypes.c_double * len(masses))(*[float(m) for m in masses])
         sp.nshift = len(masses)

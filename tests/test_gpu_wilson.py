@@ -469,6 +469,30 @@ def test_persistent_cg_solve(L, orc, per_launch):
     assert i1["iters"] >= i0["iters"] - 2
 
 
+@pytest.mark.parametrize("prec,nrhs", [(2, 1), (1, 1), (2, 5)])
+def test_correction_form_late_updates(L, orc, prec, nrhs):
+    """Reliable updates below 1e-4 |bhat| in correction form with the FP32 operator
+    (update_f32_below): every solution's true residual recomputed by the oracle meets
+    1e-10, the library's own final residual (recomputed from b) agrees with it, and the
+    solution agrees with the one of FP64-accuracy updates throughout."""
+    dims = (6, 4, 4, 10)
+    lat, U = make(L, dims, 41, c_sw=1.05)
+    C = orc.clover(dims, U, 1.05)
+    op = L.op_params(L.WILSON_TM_CLOVER, 0.05, 0.02, c_sw=1.05)
+    bs = [synth.z2_source(dims, 42 + k).numpy() for k in range(nrhs)]
+    base = L.solve_params(solver=L.MIXED_CGNR, tol=1e-10, prec_sloppy=prec)
+    corr = L.solve_params(solver=L.MIXED_CGNR, tol=1e-10, prec_sloppy=prec, update_f32_below=1e-4)
+    x0s, i0s = lat.solve(op, base, bs)
+    x1s, i1s = lat.solve(op, corr, bs)
+    for b, x0, x1, i0, i1 in zip(bs, x0s, x1s, i0s, i1s):
+        assert i1["status"] == 0
+        res = true_residual(orc, dims, U, C, 0.05, 0.02, b, x1)
+        assert res <= 1e-10, res
+        assert abs(res / i1["true_rel_residual"] - 1) < 0.01
+        assert rel_err(x1, x0) < 1e-8
+        assert i1["iters"] <= i0["iters"] + 4
+
+
 def test_bounded_grid_barrier_reports_a_wait_that_runs_out(L):
     """The barrier of the persistent kernel: complete when every block arrives, and
     a status (not a hang) when one never does."""
