@@ -273,7 +273,7 @@ class Hisq:
 # own coefficients.
 
 def hermitian_wilson(dims, U, rho, bc_t=-1):
-    """The operator v -> g5 D_w(-rho) v (D_w(-rho) = (4 - rho) - H in this build's sign reading)."""
+    """The operator v -> g5 D_w(-rho) v (D_w(-rho) = (4 - rho) - H in the sign reading of the Wilson operator used throughout)."""
     W = Wilson(dims, U, -rho, 0.0, bc_t=bc_t)
     g5 = np.array([1.0, 1.0, -1.0, -1.0])[:, None]
 
