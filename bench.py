@@ -1184,24 +1184,31 @@ def oracle_setup():
     return _ORACLE["W"], _ORACLE["b"]
 
 
-def oracle_seconds_per_iteration(threads, n1, n2):
+def oracle_seconds_per_iteration(threads, n1, n2, reps=1):
     """Seconds per FP64 CGNR iteration of the oracle on the full 24^3x64 system with
     `threads` OpenMP threads, taken differentially: runs of n1 and n2 iterations are
     timed and (t2 - t1) / (n2 - n1) is returned, so the setup that every run repeats
-    (allocation, the first M^+ b, the final residual) cancels."""
+    (allocation, the first M^+ b, the final residual) cancels; with reps > 1 the median
+    of that many such pairs (the host's other load makes single pairs noisy)."""
     import oracle
     W, b = oracle_setup()
     oracle.set_threads(threads)
-    ts = []
-    for n in (n1, n2):
-        t0 = time.perf_counter()
-        W.cgnr_fixed(b, n)
-        ts.append(time.perf_counter() - t0)
-    return (ts[1] - ts[0]) / (n2 - n1), sum(ts)
+    per, spent = [], 0.0
+    for _ in range(reps):
+        ts = []
+        for n in (n1, n2):
+            t0 = time.perf_counter()
+            W.cgnr_fixed(b, n)
+            ts.append(time.perf_counter() - t0)
+        per.append((ts[1] - ts[0]) / (n2 - n1))
+        spent += sum(ts)
+    return float(np.median(per)), spent
 
 
-# iterations of the two timed runs per core count: about 10-20 s of host time in all
+# iterations of the two timed runs per core count, and the pairs whose median is taken:
+# about 25 s of host time in all
 ORACLE_SAMPLE = {1: (1, 2), "all": (2, 6)}
+ORACLE_REPS = {1: 1, "all": 3}
 
 
 def cpu_baseline_runs(n1_all=None, n2_all=None):
@@ -1211,12 +1218,14 @@ def cpu_baseline_runs(n1_all=None, n2_all=None):
     out = []
     for cores in (1, os.cpu_count() or 1):
         n1, n2 = ORACLE_SAMPLE[1] if cores == 1 else (n1_all or ORACLE_SAMPLE["all"][0], n2_all or ORACLE_SAMPLE["all"][1])
-        per_it, spent = oracle_seconds_per_iteration(cores, n1, n2)
+        reps = ORACLE_REPS[1] if cores == 1 else ORACLE_REPS["all"]
+        per_it, spent = oracle_seconds_per_iteration(cores, n1, n2, reps)
+        med = f"median of {reps} pairs of " if reps > 1 else ""
         out.append({"value": round(1.0 / (per_it * full), 6), "unit": "solves/s", "cores": cores, "kind": "oracle",
                     "seconds_per_iteration": round(per_it, 4),
-                    "sample": f"FP64 CGNR of the oracle on the full 24^3x64 lattice: runs of {n1} and {n2} iterations "
-                              f"({spent:.1f} s), per iteration (t{n2} - t{n1}) / {n2 - n1}, scaled to its {full} "
-                              f"iterations per solve"})
+                    "sample": f"FP64 CGNR of the oracle on the full 24^3x64 lattice: {med}runs of {n1} and {n2} "
+                              f"iterations ({spent:.1f} s), per iteration (t{n2} - t{n1}) / {n2 - n1}, scaled to its "
+                              f"{full} iterations per solve"})
     return out
 
 
