@@ -630,7 +630,8 @@ def run_dslash(args):
     """The operator kernels alone on resident fields (24^3x64, one output parity per
     launch): FP16 / FP32 hopping term, the FP16 A^-1 D and A y - D kernels of the
     Schur operator, and the HISQ FP16 hopping term on the same volume, each with R12
-    and with R8 links (thin Wilson / long HISQ links). L2 is flushed
+    and with R8 links (thin Wilson / long HISQ links); the 12-right-hand-side Schur
+    operator; the FP16 hop and Schur operator on 32^3x96. L2 is flushed
     (a 256 MB write, then a 256 MB read) before every timed launch; each launch is timed alone with CUDA
     events on its stream. Reports algorithmic GB/s against the measured copy peak
     and the nominal 8 TB/s."""
@@ -727,6 +728,32 @@ def run_dslash(args):
         "GB_s": round(gbs, 1), "frac_of_measured": round(gbs / peak, 4),
         "per_rhs_speedup_over_single_rhs": round(single / (us / nr), 3)}
     del fi, fo, ft
+    # the same FP16 kernels on the multi-right-hand-side workload's 32^3x96 lattice
+    # (3.5x the sites: launch tails and block start-up weigh less)
+    dims2 = (32, 32, 32, 96)
+    vh2 = int(np.prod(dims2)) // 2
+    U2 = synth.thin_links(dims2, 103, device="cuda")
+    lat2 = lib.Lattice(dims2)
+    lat2.load_gauge(lib.THIN, U2)
+    lat2.load_clover(1.04)
+    del U2
+    op2 = lib.op_params(lib.WILSON_TM_CLOVER, 0.04, 0.008, c_sw=1.04, recon=12)
+    psi2 = synth.gaussian_field(dims2, 230, device="cuda")
+    fi, fo, ft = (lib.Field(lat2, lib.WILSON_FIELD, lib.F16) for _ in range(3))
+    for name, kind, bps in (("wilson_hop_f16_r12_32x32x32x96", "hop", 296),
+                            ("wilson_schur_f16_r12_32x32x32x96 (A^-1 D + A y - D)", "schur", 1084)):
+        if kind == "hop":
+            fi.load(0, 1, psi2)
+            us = timed(lambda: lib.dslash_field(lat2, op2, 0, fi, fo, stream=stream))
+        else:
+            fi.load(0, 0, psi2)
+            us = timed(lambda: lib.schur_field(lat2, op2, fi, fo, ft, stream=stream))
+        gbs = bps * vh2 / (us * 1e-6) / 1e9
+        out[name] = {"us": round(us, 2), "launches": 1 if kind == "hop" else 2, "bytes_per_site": bps,
+                     "GB_s": round(gbs, 1), "frac_of_measured": round(gbs / peak, 4),
+                     "frac_of_nominal_8tbs": round(gbs / 8000.0, 4)}
+    del fi, fo, ft, psi2
+    lat2.close()
     line = {"workload": "dslash", "metric": "Dslash HBM GB/s vs roofline (algorithmic bytes, L2 flushed)",
             "config": {"dims": list(dims), "sites_per_parity": vh, "peak_gbs": peak, "peak_source": peak_kind,
                        "reps": reps, "l2": "flushed (256 MB write, then 256 MB read) before every timed launch"},
