@@ -190,3 +190,81 @@ def test_hisq_multishift_down_to_the_lightest_mass(L, orc, prec):
         res = np.linalg.norm(bh - D.apply(xs[i].cpu().numpy())) / np.linalg.norm(bh)
         assert res <= 1e-10, (m, res)
     lat.close()
+
+
+# the 36-right-hand-side workload's lattice (the MILC09 shape of Table 1): 32^3x96
+MR_DIMS = (32, 32, 32, 96)
+MR_CSW, MR_M, MR_MU = 1.04, 0.04, 0.008
+
+
+@pytest.fixture(scope="module")
+def mr_lattice(L, orc):
+    U = synth.thin_links(MR_DIMS, 103, device="cuda")
+    lat = L.Lattice(MR_DIMS, -1)
+    lat.load_gauge(L.THIN, U)
+    lat.load_clover(MR_CSW)
+    Uh = U.cpu().numpy()
+    del U
+    W = orc.Wilson(MR_DIMS, Uh, MR_M, MR_MU, clover=orc.clover(MR_DIMS, Uh, MR_CSW))
+    yield lat, W
+    lat.close()
+
+
+def test_twelve_rhs_schur_on_the_multi_rhs_lattice(L, mr_lattice):
+    """The clover Schur operator (and its adjoint) on 12 right-hand sides in one call, the
+    fused FP16 multi-right-hand-side kernels at the 36-RHS workload's 32^3x96 size: the
+    first and the last right-hand side (first and third group of four) at 600 sampled
+    even sites against the oracle; and the double-float Schur operator on one of them."""
+    import torch
+    lat, W = mr_lattice
+    op = L.op_params(L.WILSON_TM_CLOVER, MR_M, MR_MU, c_sw=MR_CSW)
+    n = 12
+    V = int(np.prod(MR_DIMS))
+    vs = [synth.gaussian_field(MR_DIMS, 600 + k, device="cuda") for k in range(n)]
+    fi, fo, ft = (L.Field(lat, L.WILSON_FIELD, L.F16, n) for _ in range(3))
+    for k, v in enumerate(vs):
+        fi.load(k, 0, v)
+    sites = sample_sites(MR_DIMS, 0, 600, 81)
+    for dagger in (False, True):
+        L.schur_field(lat, op, fi, fo, ft, dagger=dagger)
+        for k in (0, n - 1):
+            got = fo.store(k, 0, torch.zeros_like(vs[k])).cpu().numpy().reshape(V, 12)
+            ref = schur_at_sites(W, MR_DIMS, vs[k].cpu().numpy(), sites, dagger)
+            assert rel_err(got[sites], ref) < 10 * TOL[2], (k, dagger)
+    got = lat.operator_apply(op, vs[3], form=L.OP_SCHUR, prec=L.F32X2).cpu().numpy().reshape(V, 12)
+    ref = schur_at_sites(W, MR_DIMS, vs[3].cpu().numpy(), sites, False)
+    assert rel_err(got[sites], ref) < 10 * TOL[3]
+
+
+def test_hisq_multishift_at_the_workload_size(L, orc):
+    """The HISQ multi-shift solve of the 48^3x144 workload (Sec. 2.2; fat and long links,
+    masses {0.002, 0.01, 0.02, 0.05}, FP16 sloppy, R12 long links, the benchmark's seeds):
+    every mass's true residual recomputed by the oracle on the whole lattice is at most
+    1e-10 and agrees with the library's own report."""
+    import torch
+    dims, masses = (48, 48, 48, 144), [0.002, 0.01, 0.02, 0.05]
+    lat = L.Lattice(dims, -1)
+    V = synth.fat_links(dims, 104, device="cuda")
+    lat.load_gauge(L.FAT, V)
+    Vh = V.cpu().numpy()
+    del V
+    W = synth.long_links(dims, 105, device="cuda")
+    lat.load_gauge(L.LONG, W)
+    Wh = W.cpu().numpy()
+    del W
+    torch.cuda.empty_cache()
+    b = synth.z2_source(dims, 204, ncomp=3, device="cuda")
+    sp = L.solve_params(solver=L.MULTISHIFT_CG, tol=1e-10, prec_sloppy=L.F16, recon_sloppy=12, masses=masses)
+    xs, info = lat.solve(L.op_params(L.HISQ, masses[0]), sp, [b])
+    assert info[0]["status"] == 0
+    bh = b.cpu().numpy()
+    del b
+    worst = 0.0
+    for i, m in enumerate(masses):
+        D = orc.Hisq(dims, Vh, Wh, m)
+        res = float(np.linalg.norm(bh - D.apply(xs[i].cpu().numpy())) / np.linalg.norm(bh))
+        assert res <= 1e-10, (m, res)
+        worst = max(worst, res)
+    # the library reports the largest true residual over the shifts
+    assert abs(worst / info[0]["true_rel_residual"] - 1) < 0.01, (worst, info[0]["true_rel_residual"])
+    lat.close()
