@@ -205,8 +205,9 @@ def mr_lattice(L, orc):
     lat.load_clover(MR_CSW)
     Uh = U.cpu().numpy()
     del U
-    W = orc.Wilson(MR_DIMS, Uh, MR_M, MR_MU, clover=orc.clover(MR_DIMS, Uh, MR_CSW))
-    yield lat, W
+    C = orc.clover(MR_DIMS, Uh, MR_CSW)
+    W = orc.Wilson(MR_DIMS, Uh, MR_M, MR_MU, clover=C)
+    yield lat, W, Uh, C
     lat.close()
 
 
@@ -216,7 +217,7 @@ def test_twelve_rhs_schur_on_the_multi_rhs_lattice(L, mr_lattice):
     first and the last right-hand side (first and third group of four) at 600 sampled
     even sites against the oracle; and the double-float Schur operator on one of them."""
     import torch
-    lat, W = mr_lattice
+    lat, W, _, _ = mr_lattice
     op = L.op_params(L.WILSON_TM_CLOVER, MR_M, MR_MU, c_sw=MR_CSW)
     n = 12
     V = int(np.prod(MR_DIMS))
@@ -268,3 +269,26 @@ def test_hisq_multishift_at_the_workload_size(L, orc):
     # the library reports the largest true residual over the shifts
     assert abs(worst / info[0]["true_rel_residual"] - 1) < 0.01, (worst, info[0]["true_rel_residual"])
     lat.close()
+
+
+def test_thirty_six_rhs_workload_solutions(L, orc, mr_lattice):
+    """The 36-RHS workload as the benchmark runs it (32^3x96, the 12 spin-colour point
+    sources at the seeded site, one call per twisted mass mu in {0.004, 0.008, 0.016},
+    mixed CGNR with FP16 storage): every solve converges, and for each mass one solution
+    per group of four right-hand sides has its true residual recomputed by the oracle on
+    the whole lattice at most 1e-10, agreeing with the library's report."""
+    import torch
+    lat, _, Uh, C = mr_lattice
+    site = synth.seeded_site(MR_DIMS, 303)
+    srcs = [synth.point_source(MR_DIMS, site, sp, c, device="cuda") for sp in range(4) for c in range(3)]
+    sp = L.solve_params(solver=L.MIXED_CGNR, tol=1e-10, prec_sloppy=L.F16, recon_sloppy=12)
+    for mu in (0.004, 0.008, 0.016):
+        op = L.op_params(L.WILSON_TM_CLOVER, MR_M, mu, c_sw=MR_CSW)
+        xs, info = lat.solve(op, sp, srcs)
+        assert all(i["status"] == 0 for i in info), mu
+        W = orc.Wilson(MR_DIMS, Uh, MR_M, mu, clover=C)
+        for k in (0, 5, 11):
+            bh = srcs[k].cpu().numpy()
+            res = float(np.linalg.norm(bh - W.apply(xs[k].cpu().numpy())) / np.linalg.norm(bh))
+            assert res <= 1e-10, (mu, k, res)
+            assert abs(res / info[k]["true_rel_residual"] - 1) < 0.01, (mu, k, res, info[k]["true_rel_residual"])
