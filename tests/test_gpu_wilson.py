@@ -385,6 +385,25 @@ def test_zero_source_and_nan_source(L):
     assert e.value.code == L.LQ_ENAN
 
 
+def test_largest_right_hand_side_count_per_call(L, orc):
+    """The largest number of right-hand sides one Wilson solve call takes (64): sixteen
+    groups of four threads per site on the FP16 multi-RHS kernels, every column's true
+    residual recomputed by the oracle at most 1e-10; one more is refused."""
+    dims = (4, 4, 4, 6)
+    lat, U = make(L, dims, 106, c_sw=1.05)
+    C = orc.clover(dims, U, 1.05)
+    op = L.op_params(L.WILSON_TM_CLOVER, 0.05, 0.01, c_sw=1.05)
+    bs = [synth.z2_source(dims, 700 + k).numpy() for k in range(64)]
+    sp = L.solve_params(solver=L.MIXED_CGNR, tol=1e-10, prec_sloppy=L.F16)
+    xs, info = lat.solve(op, sp, bs)
+    for b, x, inf in zip(bs, xs, info):
+        assert inf["status"] == 0
+        assert true_residual(orc, dims, U, C, 0.05, 0.01, b, x) <= 1e-10
+    with pytest.raises(L.LqError) as e:
+        lat.solve(op, sp, bs + [bs[0]])
+    assert e.value.code == L.LQ_EINVAL
+
+
 def test_maxiter_reports_not_converged(L):
     dims = (4, 4, 4, 4)
     lat, U = make(L, dims, 105)
