@@ -1046,7 +1046,11 @@ static CgResult cg_hisq(Lattice& lat, const OpDesc& ops, const OpDesc& op64, con
     sc.pull(st);
     KrylovState ks = krylov_start(sc, res, tol_abs, st);
     auto iteration = [&](double* dst) {
-        schur_hisq(lat, ops, 0.0, p, q, t, sc.part, st, falpha, sig);           // q = A p, alpha
+        // q = A p; alpha from the hop kernel's partials of |H_oe p|^2 by a one-block finalise
+        // kernel (a finalising last block would cost every block of the hop a fence and an
+        // atomic at its end)
+        const int nb = schur_hisq(lat, ops, 0.0, p, q, t, sc.part, st, FinArgs(), sig);
+        blas_finalize(sc.part, nb, n, sc.dev, falpha.slot, falpha.op, st);
         blas_cg_xs(x_lo, p, r, q, sc.dev, sc.part, st, sc.f(0, FIN_CG_BETA));   // x, r, |r|^2, beta
         blas_cg_p_norm(p, r, sc.dev, sc.part, st, sc.f(SC_PP, FIN_SET));         // p = r + beta p, |p|^2
         if (dst) LQ_CUDA(cudaMemcpyAsync(dst, sc.dev, sizeof(double) * SC_N * n, cudaMemcpyDeviceToHost, st));
