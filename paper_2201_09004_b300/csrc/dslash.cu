@@ -229,8 +229,31 @@ int hisq_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int epi,
     // the packed-pair FP16 kernel (hisq_x2.cuh): R12 long links, one right-hand side;
     // tuning codes 3000 + block (128 registers), 4000 + block (85) and 5000 + block (64)
     const bool x2 = op.prec == LQ_F16 && op.recon == 12 && a.nrhs == 1 && lat.geo.fast;
+    // 2 to 4 right-hand sides: the packed-pair kernel once per right-hand side (tuning codes
+    // 9000 + block) beside the scalar kernel with its lanes per site; its partial sums land
+    // in the layout of a multi-right-hand-side launch (rhs k at norm_out + k * blocks); not
+    // with a finalising last block
+    const bool x2m = op.prec == LQ_F16 && op.recon == 12 && a.nrhs >= 2 && a.nrhs <= 4 && lat.geo.fast &&
+                     fin.sc == nullptr;
     auto run = [&](int block) {
-        if (x2 && block >= 3000) {
+        if (x2m && block >= 9000) {
+            const int bs = block % 1000;
+            dim3 grid((a.g.vh + bs - 1) / bs);
+            for (int k = 0; k < a.nrhs; k++) {
+                HisqArgs ak_ = a;
+                ak_.nrhs = 1;
+                ak_.in.data = (char*)a.in.data + (size_t)k * a.in.rhs_bytes;
+                ak_.in.norm = a.in.norm + (size_t)k * a.g.vh;
+                ak_.out.data = (char*)a.out.data + (size_t)k * a.out.rhs_bytes;
+                ak_.out.norm = a.out.norm + (size_t)k * a.g.vh;
+                ak_.y.data = (char*)a.y.data + (size_t)k * a.y.rhs_bytes;
+                ak_.y.norm = a.y.norm + (size_t)k * a.g.vh;
+                if (a.ak) ak_.ak = a.ak + (size_t)k * SC_N;
+                if (a.norm_out) ak_.norm_out = a.norm_out + (size_t)k * grid.x;
+                if (epi == EPI_XPAY) launch(name, hisq_f16x2_kernel<EPI_XPAY, 4>, grid, dim3(bs), st, ak_);
+                else launch(name, hisq_f16x2_kernel<EPI_HOP, 4>, grid, dim3(bs), st, ak_);
+            }
+        } else if (x2 && block >= 3000) {
             const int bs = block % 1000, v = block / 1000;
             dim3 grid((a.g.vh + bs - 1) / bs);
             if (epi == EPI_XPAY) {
@@ -258,13 +281,17 @@ int hisq_dslash(Lattice& lat, const OpDesc& op, int parity, int dagger, int epi,
         }
     };
     std::string key = std::string(name) + "/r" + std::to_string(op.recon) + "/nb" + std::to_string(nb) + "/v" +
-                      std::to_string(lat.vh) + "/n" + std::to_string(norm_out != nullptr);
+                      std::to_string(lat.vh) + "/n" + std::to_string(norm_out != nullptr) + "/f" +
+                      std::to_string(fin.sc != nullptr);
     std::vector<int> cand = {64, 128, 256};
     if (x2)
         for (int c : {3064, 3128, 4064, 4128, 5064, 5128}) cand.push_back(c);
+    if (x2m)
+        for (int c : {9064, 9128}) cand.push_back(c);
     int block = tuned_block(key, st, run, cand);
     a.fin = norm_out ? fin : FinArgs();
     run(block);
+    if (x2m && block >= 9000) return site_blocks(lat.vh, block % 1000, 1);
     return site_blocks(lat.vh, block % 1000, nb);
 }
 
