@@ -123,12 +123,18 @@ __host__ __device__ constexpr size_t df2_smem_bytes(int block) { return (size_t)
 
 // SITE = true: no hops, w = block h of `in` at the site (out = A^{-1} in). ROWPF: the
 // epilogue loads the entries of row i+1 while row i is computed (more registers in flight).
+// The grid is (site blocks, right-hand sides); its blocks are taken in the order of their
+// linear index with the right-hand side varying fastest, so that the blocks of one site
+// block and all right-hand sides run together and meet the links (and the clover or
+// A^{-1} record) in L2.
 template <int EPI, bool SITE, bool ROWPF = true>
 __global__ void __launch_bounds__(256, 2) wilson_dslash_df2_kernel(WilsonArgs a) {
     const int h = threadIdx.x & 1;
-    const int k = blockIdx.y;
+    const int lin = blockIdx.y * gridDim.x + blockIdx.x;
+    const int k = lin % gridDim.y;   // right-hand side
+    const int sb = lin / gridDim.y;  // site block
     const int spb = blockDim.x >> 1;
-    const int s_raw = blockIdx.x * spb + (threadIdx.x >> 1);
+    const int s_raw = sb * spb + (threadIdx.x >> 1);
     const bool live = s_raw < a.g.vh;
     const int s = live ? s_raw : a.g.vh - 1;  // a pair past the end computes a valid site, stores nothing
     const size_t vh = (size_t)a.g.vh;
@@ -400,7 +406,7 @@ __global__ void __launch_bounds__(256, 2) wilson_dslash_df2_kernel(WilsonArgs a)
     }
     if (a.norm_out) {
         const df v[1] = {live ? nrm : df(0.f)};
-        reduce_norms_rg<1, 1>(v, a.norm_out, k, blockIdx.x, gridDim.x, a.nrhs);
+        reduce_norms_rg<1, 1>(v, a.norm_out, k, sb, gridDim.x, a.nrhs);
         fin_tail(a.norm_out, gridDim.x, a.nrhs, a.fin);
     }
 }
