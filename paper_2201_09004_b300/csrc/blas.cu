@@ -87,6 +87,47 @@ __global__ void axpy_h_kernel(FieldV y, FieldV x, HostScalars h, int zero_x) {
     }
 }
 
+// The vector updates of one multi-shift CG iteration in one pass, for shifts i < ns and
+// right-hand side k (blockIdx.y): y_i += a_ik p_i, then p_i = z_ik r + b_ik p_i (both
+// with the old p_i), and the per-block partial of |p_0|^2. Inactive pairs come with
+// a = 0, z = 0, b = 1 (nothing changes).
+struct MsUpdate {
+    FieldV y[LQ_MS_MAXS], p[LQ_MS_MAXS];
+    FieldV r;
+    int ns;
+    double a[LQ_MS_MAXS * LQ_MS_MAXK], z[LQ_MS_MAXS * LQ_MS_MAXK], b[LQ_MS_MAXS * LQ_MS_MAXK];
+};
+
+template <int P, int NR>
+__global__ void ms_update_kernel(MsUpdate m, df* part) {
+    typedef typename RealT<P>::T T;
+    const int k = blockIdx.y;
+    df acc(0.f);
+    SITE_LOOP(m.r.vh) {
+        T vr[NR];
+        fload<P, NR, T>(m.r, k, s, vr);
+#pragma unroll 1
+        for (int i = 0; i < m.ns; i++) {
+            const T a = (T)m.a[i * LQ_MS_MAXK + k], z = (T)m.z[i * LQ_MS_MAXK + k], b = (T)m.b[i * LQ_MS_MAXK + k];
+            T vp[NR], vy[NR];
+            fload<P, NR, T>(m.p[i], k, s, vp);
+            fload<P, NR, T>(m.y[i], k, s, vy);
+            T t = (T)0;
+#pragma unroll
+            for (int q = 0; q < NR; q++) {
+                vy[q] = fma(a, vp[q], vy[q]);
+                vp[q] = fma(b, vp[q], z * vr[q]);
+                t = fma(vp[q], vp[q], t);
+            }
+            if (i == 0) acc = acc + df_of(t);
+            fstore<P, NR, T>(m.y[i], k, s, vy);
+            fstore<P, NR, T>(m.p[i], k, s, vp);
+        }
+    }
+    df r = block_sum_df(acc);
+    if (threadIdx.x == 0) part[(size_t)k * gridDim.x + blockIdx.x] = r;
+}
+
 // y = a_k x + b_k y, optional partial |y|^2 (host scalars)
 template <int P, int NR>
 __global__ void axpby_h_kernel(FieldV y, FieldV x, HostScalars h, df* part) {
@@ -868,6 +909,35 @@ void blas_gcr_xr(Field& x, const Field& p, Field& r, const Field& q, const doubl
     else if (x.prec == LQ_F32) gcr_xr_from<P32>(x, p, r, q, alpha_dev, part, st);
     else if (x.prec == LQ_F16) gcr_xr_from<P16>(x, p, r, q, alpha_dev, part, st);
     else gcr_xr_from<PDF>(x, p, r, q, alpha_dev, part, st);
+}
+
+
+void blas_ms_update(std::vector<Field>& y, std::vector<Field>& p, const Field& r, const double* a, const double* z,
+                    const double* b, df* part, cudaStream_t st) {
+    const int ns = (int)p.size(), n = r.nrhs;
+    if (ns < 1 || ns > LQ_MS_MAXS || n > LQ_MS_MAXK || (int)y.size() != ns)
+        fail(LQ_EINVAL, "blas_ms_update: shift or right-hand-side count");
+    MsUpdate m;
+    m.ns = ns;
+    m.r = r.view();
+    for (int i = 0; i < ns; i++) {
+        if (y[i].prec != r.prec || p[i].prec != r.prec || y[i].nrhs != n || p[i].nrhs != n || p[i].kind != r.kind)
+            fail(LQ_EINVAL, "blas_ms_update: field mismatch");
+        m.y[i] = y[i].view();
+        m.p[i] = p[i].view();
+    }
+    for (int i = 0; i < LQ_MS_MAXS; i++)
+        for (int k = 0; k < LQ_MS_MAXK; k++) {
+            const bool in = i < ns && k < n;
+            m.a[i * LQ_MS_MAXK + k] = in ? a[i * n + k] : 0.0;
+            m.z[i * LQ_MS_MAXK + k] = in ? z[i * n + k] : 0.0;
+            m.b[i * LQ_MS_MAXK + k] = in ? b[i * n + k] : 1.0;
+        }
+#define K(NR) ms_update_kernel<P_, NR>
+#define L(P) { constexpr int P_ = P; BY_KIND(r, "blas_ms_update", K, red_grid(n), m, part); }
+    DISPATCH_P(r.prec, L);
+#undef L
+#undef K
 }
 
 }  // namespace lq

@@ -293,6 +293,13 @@ void blas_copy(Field& dst, const Field& src, cudaStream_t st);           // with
 void blas_zero(Field& x, cudaStream_t st);
 void blas_axpy_h(Field& y, const double* a_host, const Field& x, cudaStream_t st);  // y += a_k x (host scalars)
 void blas_axpy_h_zero(Field& y, const double* a_host, Field& x, cudaStream_t st);  // y += a_k x, then x = 0
+// the vector updates of a multi-shift CG iteration in one pass (at most LQ_MS_MAXS shifts and
+// LQ_MS_MAXK right-hand sides; coefficients [i * nrhs + k]): y_i += a p_i, p_i = z r + b p_i,
+// per-block partials of |p_0|^2 in part (RED_BLOCKS per rhs)
+#define LQ_MS_MAXS 8
+#define LQ_MS_MAXK 8
+void blas_ms_update(std::vector<Field>& y, std::vector<Field>& p, const Field& r, const double* a, const double* z,
+                    const double* b, df* part, cudaStream_t st);
 // y = a_k x + b_k y per right-hand side k (host scalars), optional partial |y|^2
 void blas_axpby_h(Field& y, const double* a, const Field& x, const double* b, df* part, cudaStream_t st);
 // s = b - q, with partial |s|^2

@@ -1101,6 +1101,7 @@ static int multishift_hisq(Lattice& lat, const OpDesc& op, const std::vector<dou
             for (int i = 0; i < ns; i++) active[i][k] = 0;
     }
     std::vector<double> a(n), bz(n), zz(n), ones(n, 1.0);
+    std::vector<double> ya((size_t)ns * n), pz((size_t)ns * n), pb((size_t)ns * n);  // fused-update coefficients
     auto any_active = [&]() {
         for (int i = 0; i < ns; i++)
             for (int k = 0; k < n; k++)
@@ -1122,11 +1123,14 @@ static int multishift_hisq(Lattice& lat, const OpDesc& op, const std::vector<dou
                 zn[i][k] = den != 0.0 ? zeta[i][k] * zeta_prev[i][k] * alpha_prev[k] / den : 0.0;
             }
         }
-        // y_i += alpha_i p_i, alpha_i = alpha zeta_i'/zeta_i
+        // y_i += alpha_i p_i, alpha_i = alpha zeta_i'/zeta_i (fused with the p_i updates below
+        // into one pass when the counts allow it)
+        const bool fused = ns <= LQ_MS_MAXS && n <= LQ_MS_MAXK;
         for (int i = 0; i < ns; i++) {
             for (int k = 0; k < n; k++)
                 a[k] = !active[i][k] ? 0.0 : (i == 0 ? alpha[k] : alpha[k] * zn[i][k] / zeta[i][k]);
-            blas_axpy_h(y[i], a.data(), p[i], st);
+            if (fused) std::copy(a.begin(), a.end(), ya.begin() + (size_t)i * n);
+            else blas_axpy_h(y[i], a.data(), p[i], st);
         }
         for (int k = 0; k < n; k++) a[k] = -alpha[k];
         blas_axpby_h(r, a.data(), q, ones.data(), sc.part, st);
@@ -1139,15 +1143,30 @@ static int multishift_hisq(Lattice& lat, const OpDesc& op, const std::vector<dou
             rr[k] = rn;
         }
         // p_0 = r + beta p_0 ; p_i = zeta_i' r + beta (zeta_i'/zeta_i)^2 p_i
-        blas_axpby_h(p[0], ones.data(), r, beta.data(), sc.part, st);
-        sc.fin(RED_BLOCKS, SC_PP, st);
-        for (int i = 1; i < ns; i++) {
+        if (fused) {
             for (int k = 0; k < n; k++) {
-                double zr = zeta[i][k] != 0.0 ? zn[i][k] / zeta[i][k] : 0.0;
-                zz[k] = active[i][k] ? zn[i][k] : 0.0;
-                bz[k] = active[i][k] ? beta[k] * zr * zr : 1.0;
+                pz[k] = 1.0;
+                pb[k] = beta[k];
             }
-            blas_axpby_h(p[i], zz.data(), r, bz.data(), nullptr, st);
+            for (int i = 1; i < ns; i++)
+                for (int k = 0; k < n; k++) {
+                    double zr = zeta[i][k] != 0.0 ? zn[i][k] / zeta[i][k] : 0.0;
+                    pz[(size_t)i * n + k] = active[i][k] ? zn[i][k] : 0.0;
+                    pb[(size_t)i * n + k] = active[i][k] ? beta[k] * zr * zr : 1.0;
+                }
+            blas_ms_update(y, p, r, ya.data(), pz.data(), pb.data(), sc.part, st);
+            sc.fin(RED_BLOCKS, SC_PP, st);
+        } else {
+            blas_axpby_h(p[0], ones.data(), r, beta.data(), sc.part, st);
+            sc.fin(RED_BLOCKS, SC_PP, st);
+            for (int i = 1; i < ns; i++) {
+                for (int k = 0; k < n; k++) {
+                    double zr = zeta[i][k] != 0.0 ? zn[i][k] / zeta[i][k] : 0.0;
+                    zz[k] = active[i][k] ? zn[i][k] : 0.0;
+                    bz[k] = active[i][k] ? beta[k] * zr * zr : 1.0;
+                }
+                blas_axpby_h(p[i], zz.data(), r, bz.data(), nullptr, st);
+            }
         }
         for (int k = 0; k < n; k++) {
             for (int i = 1; i < ns; i++) {
