@@ -870,7 +870,7 @@ void blas_cg_p(Field& p, const Field& r, const double* sc, cudaStream_t st) {
 }
 
 void blas_finalize(const df* part, int nblocks, int nrhs, double* sc, int slot, int op, cudaStream_t st) {
-    launch_pdl("blas_finalize", finalize_kernel, dim3(nrhs), dim3(256), 0, st, part, nblocks, sc, slot, op);
+    launch_pdl("blas_finalize", finalize_kernel, dim3(nrhs), dim3(512), 0, st, part, nblocks, sc, slot, op);
 }
 
 void blas_cdot_multi(const FieldV* vs_dev, int nv, const Field& w, df* part, cudaStream_t st) {

@@ -103,6 +103,26 @@ def test_hisq_multishift_solve(L, orc, prec):
             assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-10, (k, m)
 
 
+@pytest.mark.parametrize("nrhs,nmass", [(5, 4), (1, 9)])
+def test_hisq_multishift_beyond_the_fused_update(L, orc, nrhs, nmass):
+    """Multi-shift solves whose stage has more right-hand sides (2 x 5 = 10) or more
+    shifts (9) than the one-pass vector update takes, so that the separate updates run:
+    every mass of every right-hand side against the oracle."""
+    dims = (4, 4, 4, 8)
+    lat, V, W = make(L, dims, 57)
+    masses = [0.02 * (1 + i) for i in range(nmass)]
+    bs = [synth.z2_source(dims, 58 + k, ncomp=3).numpy() for k in range(nrhs)]
+    op = L.op_params(L.HISQ, masses[0])
+    sp = L.solve_params(solver=L.MULTISHIFT_CG, tol=1e-10, prec_sloppy=1, masses=masses)
+    xs, info = lat.solve(op, sp, bs)
+    for k, b in enumerate(bs):
+        assert info[k]["status"] == 0
+        for i, m in enumerate(masses):
+            D = orc.Hisq(dims, V, W, m)
+            r = b - D.apply(xs[k * nmass + i])
+            assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-10, (k, m)
+
+
 def test_hisq_repeated_solves_reuse_workspace(L, orc):
     """Consecutive solves on one lattice reuse its work buffers (including the
     pinned scalar block): single-mass CG with 1 and 4 right-hand sides, graph
