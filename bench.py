@@ -12,7 +12,9 @@ Printed as one JSON line (rank 0). Beside the headline solves/s it reports:
   * e2e: the same solves through the C ABI with host buffers (pinned), copies
     included;
   * cpu_baseline: the FP64 CPU oracle on a bounded sample of the same workload;
-  * clocks sampled with nvidia-smi during the timed region.
+  * clocks sampled with nvidia-smi during the timed region;
+  * with --with-configs (default): the 36-RHS 32^3x96 workload, the 48^3x144 HISQ
+    multi-shift workload and a short serving trace (p50/p99 latency, solves/s).
 --impl reference times the oracle itself (the reference arm).
 Multi-GPU (torchrun): every rank runs independent replicas of the same solve.
 """
@@ -436,6 +438,9 @@ def gpu_arm(args):
             torch.cuda.empty_cache()
             line["multirhs_32x32x32x96"] = run_multirhs(args)
             line["hisq_48x48x48x144"] = run_hisq(args)
+            if args.serving_requests > 0:  # the serving pattern's p50/p99 on a short Poisson trace
+                sargs = argparse.Namespace(**{**vars(args), "requests": args.serving_requests, "fifo_requests": 0})
+                line["serving_sample"] = run_serving(sargs)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
@@ -1187,7 +1192,9 @@ def run_serving(args):
             "fifo_fp64_one_at_a_time": summary(lf, wf, sf, len(reqs_f)),
             "p50_ratio_fifo_over_mixed": round(float(np.percentile(lf, 50) / np.percentile(lm, 50)), 2),
             "p99_ratio_fifo_over_mixed": round(float(np.percentile(lf, 99) / np.percentile(lm, 99)), 2)}
-    print(json.dumps(line), flush=True)
+    for lat in lats.values():
+        lat.close()
+    return line
 
 
 # ---------------------------------------------------------- oracle (CPU) arm
@@ -1311,7 +1318,7 @@ def main():
                     help="also time the mixed-precision restarted GCR solve of the same system")
     ap.add_argument("--gcr-restart", type=int, default=0, help="GCR directions before a restart (0 = 12)")
     ap.add_argument("--with-configs", type=int, default=1,
-                    help="1: also run the 36-RHS 32^3x96 and the 48^3x144 HISQ workloads into the line")
+                    help="1: also run the 36-RHS 32^3x96 and the 48^3x144 HISQ workloads and a short serving trace into the line")
     ap.add_argument("--persistent-steps", type=int, default=3,
                     help="also time the solve with the persistent CG kernel and with 1 / 4 iterations per graph")
     ap.add_argument("--ref-iters", type=int, default=2)
@@ -1329,6 +1336,8 @@ def main():
                          "dslash: the operator kernels alone; hisq3col: HISQ 3-column propagator 24^3x64; "
                          "overlap: g5 D_w and the sign function; tmms: twisted multi-mass solve")
     ap.add_argument("--requests", type=int, default=400, help="serving: number of requests")
+    ap.add_argument("--serving-requests", type=int, default=60,
+                    help="requests of the short serving trace inside the default line (0: skip)")
     ap.add_argument("--fifo-requests", type=int, default=40,
                     help="serving: requests of the trace at the FIFO FP64 server's sustainable rate (0: skip)")
     ap.add_argument("--graph-iters", type=int, default=0,
@@ -1351,7 +1360,7 @@ def main():
     elif args.workload == "tmms":
         run_twisted_multimass(args)
     elif args.workload == "serving":
-        run_serving(args)
+        print(json.dumps(run_serving(args)), flush=True)
     elif args.workload == "eigen":
         run_eigen(args)
     elif args.workload == "delta":
