@@ -121,6 +121,7 @@ extern "C" int lq_destroy_lattice(lq_lattice h) {
     cudaDeviceSynchronize();
     ws_release(L);
     if (L.own_stream) cudaStreamDestroy(L.own_stream);
+    if (L.copy_stream) cudaStreamDestroy(L.copy_stream);
     free_clover(L);
     for (auto& kv : L.packed) dev_free(&L, kv.second.data, kv.second.bytes);
     for (int k = 0; k < 3; k++) dev_free(&L, L.canon[k], (size_t)L.V * 4 * 18 * sizeof(double));
@@ -319,7 +320,10 @@ extern "C" int lq_solve(lq_lattice h, const lq_op_params* op, const lq_solve_par
     cudaStream_t st = as_stream(stream);
     if (st == nullptr || st == cudaStreamLegacy) {
         // run on the lattice's own stream, ordered after the caller's earlier default-stream work
-        if (!L.own_stream) LQ_CUDA(cudaStreamCreateWithFlags(&L.own_stream, cudaStreamNonBlocking));
+        {
+            std::lock_guard<std::mutex> g(L.mu);
+            if (!L.own_stream) LQ_CUDA(cudaStreamCreateWithFlags(&L.own_stream, cudaStreamNonBlocking));
+        }
         cudaEvent_t fork;
         LQ_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
         cudaEventRecord(fork, st);
@@ -347,13 +351,40 @@ extern "C" int lq_solve(lq_lattice h, const lq_op_params* op, const lq_solve_par
         for (int k = 0; k < nrhs; k++) db[k] = rhs[k];
         for (int k = 0; k < nsol; k++) dx[k] = x[k];
     }
+    // Host solutions: each one is copied back on the lattice's copy stream as soon as
+    // the solver has written it, beside the solve's remaining kernels (the final
+    // residual check, the next mass). The guard waits for the copies before the
+    // staging buffer returns to the pool, on every exit.
+    struct CopyBack {
+        cudaStream_t cs = nullptr;
+        cudaEvent_t ev = nullptr;
+        ~CopyBack() {
+            if (cs) cudaStreamSynchronize(cs);
+            if (ev) cudaEventDestroy(ev);
+        }
+    } cb;
+    SolutionReady ready;
+    if (loc == LQ_HOST) {
+        {
+            std::lock_guard<std::mutex> g(L.mu);
+            if (!L.copy_stream) LQ_CUDA(cudaStreamCreateWithFlags(&L.copy_stream, cudaStreamNonBlocking));
+        }
+        LQ_CUDA(cudaEventCreateWithFlags(&cb.ev, cudaEventDisableTiming));
+        cb.cs = L.copy_stream;
+        ready = [&](int k, cudaStream_t s) {
+            LQ_CUDA(cudaEventRecord(cb.ev, s));
+            LQ_CUDA(cudaStreamWaitEvent(cb.cs, cb.ev, 0));
+            LQ_CUDA(cudaMemcpyAsync(x[k], dx[k], bytes, cudaMemcpyDeviceToHost, cb.cs));
+        };
+    }
+    const SolutionReady* rp = loc == LQ_HOST ? &ready : nullptr;
     int ret;
-    if (op->action == LQ_HISQ) ret = solve_hisq(L, *op, *sp, nrhs, db.data(), dx.data(), info, st);
-    else if (sp->solver == LQ_MULTISHIFT_CG) ret = solve_wilson_multishift(L, *op, *sp, nrhs, db.data(), dx.data(), info, st);
-    else ret = solve_wilson(L, *op, *sp, nrhs, db.data(), dx.data(), info, st);
-    if (loc == LQ_HOST)
-        for (int k = 0; k < nsol; k++) LQ_CUDA(cudaMemcpyAsync(x[k], dx[k], bytes, cudaMemcpyDeviceToHost, st));
+    if (op->action == LQ_HISQ) ret = solve_hisq(L, *op, *sp, nrhs, db.data(), dx.data(), info, st, rp);
+    else if (sp->solver == LQ_MULTISHIFT_CG)
+        ret = solve_wilson_multishift(L, *op, *sp, nrhs, db.data(), dx.data(), info, st, rp);
+    else ret = solve_wilson(L, *op, *sp, nrhs, db.data(), dx.data(), info, st, nullptr, rp);
     LQ_CUDA(cudaStreamSynchronize(st));
+    if (cb.cs) LQ_CUDA(cudaStreamSynchronize(cb.cs));
     return ret;
     LQ_CATCH
 }

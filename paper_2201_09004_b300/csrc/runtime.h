@@ -203,6 +203,9 @@ struct Lattice {
     // solves issued on the legacy default stream run on this stream (created on
     // first use), which CUDA graphs can capture
     cudaStream_t own_stream = nullptr;
+    // device-to-host copies of finished solutions run here, beside the solve's
+    // remaining kernels (created on first use)
+    cudaStream_t copy_stream = nullptr;
     size_t bytes = 0;                                // device bytes held
     std::mutex mu;  // guards the lazily filled caches when several streams share the lattice
 };
@@ -367,13 +370,20 @@ void sign_apply_deflated(Lattice& lat, double rho, double lmax, double eps, cons
                          cudaStream_t st);
 // estimated device bytes of a solve's work fields
 size_t solve_workspace_bytes(const Lattice& lat, const lq_op_params& op, const lq_solve_params& sp, int nrhs);
+// Called from the solve's host thread once solution x[idx] is final in device
+// memory: everything that writes it has been enqueued on st, and nothing enqueued
+// later on st touches it. The caller may read it from another stream ordered
+// after an event recorded on st.
+using SolutionReady = std::function<void(int idx, cudaStream_t st)>;
 // x0 (optional, device canonical): initial guesses whose even sites start the even-odd CGNR
 int solve_wilson(Lattice& lat, const lq_op_params& op, const lq_solve_params& sp, int nrhs, const double* const* b,
-                 double* const* x, lq_solve_info* info, cudaStream_t st, const double* const* x0 = nullptr);
+                 double* const* x, lq_solve_info* info, cudaStream_t st, const double* const* x0 = nullptr,
+                 const SolutionReady* ready = nullptr);
 int solve_wilson_multishift(Lattice& lat, const lq_op_params& op, const lq_solve_params& sp, int nrhs,
-                            const double* const* b, double* const* x, lq_solve_info* info, cudaStream_t st);
+                            const double* const* b, double* const* x, lq_solve_info* info, cudaStream_t st,
+                            const SolutionReady* ready = nullptr);
 int solve_hisq(Lattice& lat, const lq_op_params& op, const lq_solve_params& sp, int nrhs, const double* const* b,
-               double* const* x, lq_solve_info* info, cudaStream_t st);
+               double* const* x, lq_solve_info* info, cudaStream_t st, const SolutionReady* ready = nullptr);
 
 }  // namespace lq
 

@@ -645,7 +645,8 @@ static CgResult gcr_mixed(Lattice& lat, const OpDesc& ops, const OpDesc& op64, F
 }
 
 int solve_wilson(Lattice& lat, const lq_op_params& opp, const lq_solve_params& sp, int nrhs, const double* const* b,
-                 double* const* x, lq_solve_info* info, cudaStream_t st, const double* const* x0) {
+                 double* const* x, lq_solve_info* info, cudaStream_t st, const double* const* x0,
+                 const SolutionReady* ready) {
     if (opp.action == LQ_WILSON_TM_CLOVER && !lat.has_clover) fail(LQ_EINVAL, "clover action without clover term");
     if (!lat.canon[LQ_THIN]) fail(LQ_EINVAL, "thin gauge field not loaded");
     if (nrhs < 1 || nrhs > 64) fail(LQ_EINVAL, "nrhs must be in [1, 64]");
@@ -727,6 +728,7 @@ int solve_wilson(Lattice& lat, const lq_op_params& opp, const lq_solve_params& s
         for (int k = 0; k < nrhs; k++) {
             export_field(lat, xe, k, 0, x[k], st);
             export_field(lat, xo, k, 1, x[k], st);
+            if (ready) (*ready)(k, st);
         }
         // FP64 true residual of the full system: r_p = b_p - (A_pp x_p - H_{p,1-p} x_{1-p})
         // (formed in the double-float kernel's epilogue, or by a subtraction after it)
@@ -781,7 +783,8 @@ int solve_wilson(Lattice& lat, const lq_op_params& opp, const lq_solve_params& s
 // The multi-shift stage runs in the sloppy precision; each x(mu_i) then starts the
 // mixed-precision even-odd CGNR of its own system, which brings it to the tolerance.
 int solve_wilson_multishift(Lattice& lat, const lq_op_params& opp, const lq_solve_params& sp, int nrhs,
-                            const double* const* b, double* const* x, lq_solve_info* info, cudaStream_t st) {
+                            const double* const* b, double* const* x, lq_solve_info* info, cudaStream_t st,
+                            const SolutionReady* ready) {
     if (opp.action != LQ_WILSON_TM) fail(LQ_EINVAL, "Wilson multi-shift: twisted mass without clover only");
     if (opp.twist_mode != LQ_TWIST_GAMMA5)
         fail(LQ_EINVAL, "Wilson multi-shift: M^+ M = M0^+ M0 + mu^2 holds for the i mu g5 twist only");
@@ -968,7 +971,10 @@ int solve_wilson_multishift(Lattice& lat, const lq_op_params& opp, const lq_solv
             x0[k] = x[k * ns + i];
         }
         std::vector<lq_solve_info> inf(nrhs);
-        int r = solve_wilson(lat, opi, spi, nrhs, b, xi.data(), inf.data(), st, x0.data());
+        // solution k of this mass is x[k * ns + i] of the caller's array
+        SolutionReady ready_i = [&](int k, cudaStream_t s) { (*ready)(k * ns + i, s); };
+        int r = solve_wilson(lat, opi, spi, nrhs, b, xi.data(), inf.data(), st, x0.data(),
+                             ready ? &ready_i : nullptr);
         if (r != LQ_OK && ret == LQ_OK) ret = r;
         for (int k = 0; k < nrhs; k++) {
             acc[k].iters += inf[k].iters;
@@ -1188,7 +1194,7 @@ static int multishift_hisq(Lattice& lat, const OpDesc& op, const std::vector<dou
 }
 
 int solve_hisq(Lattice& lat, const lq_op_params& opp, const lq_solve_params& sp, int nrhs, const double* const* b,
-               double* const* x, lq_solve_info* info, cudaStream_t st) {
+               double* const* x, lq_solve_info* info, cudaStream_t st, const SolutionReady* ready) {
     if (!lat.canon[LQ_FAT] || !lat.canon[LQ_LONG]) fail(LQ_EINVAL, "HISQ needs fat and long links loaded");
     if (nrhs < 1 || nrhs > 32) fail(LQ_EINVAL, "nrhs must be in [1, 32] for HISQ");
     if (sp.solver == LQ_BICGSTAB || sp.solver == LQ_GCR)
@@ -1298,6 +1304,7 @@ int solve_hisq(Lattice& lat, const lq_op_params& opp, const lq_solve_params& sp,
             for (int k = 0; k < nrhs; k++) {
                 export_field(lat, xe, k, 0, x[k * ns + i], st);
                 export_field(lat, xo, k, 1, x[k * ns + i], st);
+                if (ready) (*ready)(k * ns + i, st);
             }
             // FP64 true residual: r_p = b_p - (m x_p + H x_{1-p}); XPAY gives -(m x_p + H x_{1-p})
             hisq_dslash(lat, op64, 0, 0, EPI_XPAY, -m, xo, te, &xe, nullptr, st);
