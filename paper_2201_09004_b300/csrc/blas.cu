@@ -212,6 +212,57 @@ __global__ void cg_xs_kernel(FieldV x, FieldV p, FieldV sf, FieldV qf, const dou
     fin_tail(part, gridDim.x, gridDim.y, fin);
 }
 
+// s -= alpha q; partial |s|^2 (the x update of the same step goes with the next p update)
+template <int P, int NR>
+__global__ void cg_s_kernel(FieldV sf, FieldV qf, const double* sc, df* part, FinArgs fin) {
+    pdl_start();
+    typedef typename RealT<P>::T T;
+    const int k = blockIdx.y;
+    const T a = (T)sc[(size_t)k * SC_N + SC_ALPHA];
+    df acc(0.f);
+    SITE_LOOP(sf.vh) {
+        T vs[NR], vq[NR];
+        fload<P, NR, T>(sf, k, s, vs);
+        fload<P, NR, T>(qf, k, s, vq);
+        T t = (T)0;
+#pragma unroll
+        for (int q = 0; q < NR; q++) {
+            vs[q] = fma(-a, vq[q], vs[q]);
+            t = fma(vs[q], vs[q], t);
+        }
+        acc = acc + df_of(t);
+        fstore<P, NR, T>(sf, k, s, vs);
+    }
+    df r = block_sum_df(acc);
+    if (threadIdx.x == 0) part[(size_t)k * gridDim.x + blockIdx.x] = r;
+    fin_tail(part, gridDim.x, gridDim.y, fin);
+}
+
+// x += alpha p, then p = r + beta p: one read of p for both updates
+template <int PX, int P, int NR>
+__global__ void cg_xp_kernel(FieldV x, FieldV p, FieldV r, const double* sc) {
+    pdl_start();
+    typedef typename RealT<P>::T T;
+    typedef typename MathT<PX, P>::T TX;
+    const int k = blockIdx.y;
+    const TX ax = (TX)sc[(size_t)k * SC_N + SC_ALPHA];
+    const T b = (T)sc[(size_t)k * SC_N + SC_BETA];
+    SITE_LOOP(p.vh) {
+        T vp[NR], vr[NR];
+        TX vx[NR];
+        fload<P, NR, T>(p, k, s, vp);
+        fload<PX, NR, TX>(x, k, s, vx);
+        fload<P, NR, T>(r, k, s, vr);
+#pragma unroll
+        for (int q = 0; q < NR; q++) {
+            vx[q] = fma(ax, (TX)vp[q], vx[q]);
+            vp[q] = fma(b, vp[q], vr[q]);
+        }
+        fstore<PX, NR, TX>(x, k, s, vx);
+        fstore<P, NR, T>(p, k, s, vp);
+    }
+}
+
 // p = r + beta p with partial |p|^2
 template <int P, int NR>
 __global__ void cg_p_norm_kernel(FieldV p, FieldV r, const double* sc, df* part, FinArgs fin) {
@@ -751,6 +802,33 @@ void blas_cg_xs(Field& x, const Field& p, Field& s, const Field& q, const double
     else if (x.prec == LQ_F32) cg_xs_from<P32>(x, p, s, q, sc, part, st, fin);
     else if (x.prec == LQ_F16) cg_xs_from<P16>(x, p, s, q, sc, part, st, fin);
     else cg_xs_from<PDF>(x, p, s, q, sc, part, st, fin);
+}
+
+void blas_cg_s(Field& s, const Field& q, const double* sc, df* part, cudaStream_t st, const FinArgs& fin) {
+    if (s.prec != q.prec) fail(LQ_EINVAL, "blas_cg_s: precision mismatch");
+#define K(NR) cg_s_kernel<P_, NR>
+#define L(P) { constexpr int P_ = P; BY_KIND_PDL(s, "blas_cg_s", K, red_grid(s.nrhs), s.view(), q.view(), sc, part, fin); }
+    DISPATCH_P(s.prec, L);
+#undef L
+#undef K
+}
+
+template <int PX>
+static void cg_xp_from(Field& x, Field& p, const Field& r, const double* sc, cudaStream_t st) {
+    dim3 g = upd_grid(p.vh, p.nrhs);
+#define K(NR) cg_xp_kernel<PX, P_, NR>
+#define L(P) { constexpr int P_ = P; BY_KIND_PDL(p, "blas_cg_xp", K, g, x.view(), p.view(), r.view(), sc); }
+    DISPATCH_P(p.prec, L);
+#undef L
+#undef K
+}
+
+void blas_cg_xp(Field& x, Field& p, const Field& r, const double* sc, cudaStream_t st) {
+    if (p.prec != r.prec) fail(LQ_EINVAL, "blas_cg_xp: precision mismatch");
+    if (x.prec == LQ_F64) cg_xp_from<P64>(x, p, r, sc, st);
+    else if (x.prec == LQ_F32) cg_xp_from<P32>(x, p, r, sc, st);
+    else if (x.prec == LQ_F16) cg_xp_from<P16>(x, p, r, sc, st);
+    else cg_xp_from<PDF>(x, p, r, sc, st);
 }
 
 void blas_bicg_cdot(const Field& a, const Field& b, df* part, cudaStream_t st, const FinArgs& fin) {

@@ -332,6 +332,10 @@ void blas_caxpy_h(Field& y, const double* a_re, const double* a_im, const Field&
 void blas_cg_p_norm(Field& p, const Field& r, const double* sc, df* part, cudaStream_t st, const FinArgs& fin);
 // p = r + beta p, beta_k = sc[k*SC_N + SC_BETA]
 void blas_cg_p(Field& p, const Field& r, const double* sc, cudaStream_t st);
+// the CG step split around the second operator: s -= alpha q with partial |s|^2, and later
+// x += alpha p, p = r + beta p (one pass over p for both)
+void blas_cg_s(Field& s, const Field& q, const double* sc, df* part, cudaStream_t st, const FinArgs& fin);
+void blas_cg_xp(Field& x, Field& p, const Field& r, const double* sc, cudaStream_t st);
 
 // GCR and Gram-Schmidt steps. Partials of <v_i, w> (i < nv, fields listed in device
 // memory) at part[((k * nv + i) * 2 + re/im) * RED_BLOCKS + block]; q_j -= sum_{i<j} c_i q_i

@@ -368,10 +368,10 @@ static CgResult cgnr_mixed(Lattice& lat, const OpDesc& ops, const OpDesc& op64, 
             // wait for a memory fence and an atomic at its end)
             const int nq = schur_wilson(lat, ops, 0, p, q, t, part_q, st);
             blas_finalize(part_q, nq, n, sc.dev, 0, FIN_ALPHA, st);
-            blas_cg_xs(x_lo, p, s_lo, q, sc.dev, sc.part, st, sc.f(SC_SS, FIN_SET));
+            blas_cg_s(s_lo, q, sc.dev, sc.part, st, sc.f(SC_SS, FIN_SET));
             nr = schur_wilson(lat, ops, 1, s_lo, r, t, part_r, st);
             blas_finalize(part_r, nr, n, sc.dev, 0, FIN_BETA, st);
-            blas_cg_p(p, r, sc.dev, st);
+            blas_cg_xp(x_lo, p, r, sc.dev, st);  // x += alpha p with the p of this step, then p
         }
         if (dst) LQ_CUDA(cudaMemcpyAsync(dst, sc.dev, sizeof(double) * SC_N * n, cudaMemcpyDeviceToHost, st));
     };
