@@ -273,8 +273,8 @@ def gpu_arm(args):
                       "gbs": round(bytes_per_site(k, args.recon) * vh / (v[1] / v[0] * 1e-3) / 1e9, 1)} for k, v in kernels.items()}
     # device time per solve of every kernel family in the timed region
     breakdown = {}
-    for name in ["wilson_dslash_f16", "wilson_dslash_f32x2", "wilson_dslash_f32_", "wilson_ainv_site", "blas_cg_xs", "blas_cg_s", "blas_cg_xp",
-                 "blas_cg_p", "blas_finalize", "blas_norm2", "blas_copy", "blas_axpy", "blas_xmy_norm", "blas_zero",
+    for name in ["wilson_dslash_f16", "wilson_dslash_f32x2", "wilson_dslash_f32_", "wilson_ainv_site", "blas_cg_s", "blas_cg_xp",
+                 "blas_finalize", "blas_norm2", "blas_copy", "blas_axpy", "blas_xmy_norm", "blas_zero",
                  "import_field", "export_field"]:
         n_, t_ = lib.profile_query(name)
         if n_:
@@ -528,7 +528,7 @@ def run_multirhs(args):
         single.append(e0.elapsed_time(e1) * 1e-3 / 2)
     t_single36 = 12 * sum(single)
     # device time per right-hand side of each kernel family, batched (12 per call) and single
-    families = ["wilson_dslash_f16", "wilson_dslash_f32x2", "blas_cg_xs", "blas_cg_s", "blas_cg_xp", "blas_cg_p", "blas_finalize", "blas_",
+    families = ["wilson_dslash_f16", "wilson_dslash_f32x2", "blas_cg_s", "blas_cg_xp", "blas_finalize", "blas_",
                 "import_field", "export_field", "wilson_ainv_site"]
     per_rhs = {"batched_12": {}, "single": {}}
     for f in families:

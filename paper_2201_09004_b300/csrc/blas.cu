@@ -178,40 +178,6 @@ __global__ void xmy_norm_kernel(FieldV sf, FieldV b, FieldV qf, df* part, FinArg
     fin_tail(part, gridDim.x, gridDim.y, fin);
 }
 
-// x += alpha p; s -= alpha q; partial |s|^2; alpha_k = sc[k*SC_N + SC_ALPHA]
-template <int PX, int P, int NR>
-__global__ void cg_xs_kernel(FieldV x, FieldV p, FieldV sf, FieldV qf, const double* sc, df* part, FinArgs fin) {
-    pdl_start();
-    typedef typename RealT<P>::T T;
-    typedef typename MathT<PX, P>::T TX;
-    const int k = blockIdx.y;
-    const double al = sc[(size_t)k * SC_N + SC_ALPHA];
-    const T a = (T)al;
-    const TX ax = (TX)al;
-    df acc(0.f);
-    SITE_LOOP(x.vh) {
-        T vp[NR], vs[NR], vq[NR];
-        TX vx[NR];
-        fload<P, NR, T>(p, k, s, vp);
-        fload<P, NR, T>(sf, k, s, vs);
-        fload<P, NR, T>(qf, k, s, vq);
-        fload<PX, NR, TX>(x, k, s, vx);
-        T t = (T)0;
-#pragma unroll
-        for (int q = 0; q < NR; q++) {
-            vx[q] = fma(ax, (TX)vp[q], vx[q]);
-            vs[q] = fma(-a, vq[q], vs[q]);
-            t = fma(vs[q], vs[q], t);
-        }
-        acc = acc + df_of(t);
-        fstore<PX, NR, TX>(x, k, s, vx);
-        fstore<P, NR, T>(sf, k, s, vs);
-    }
-    df r = block_sum_df(acc);
-    if (threadIdx.x == 0) part[(size_t)k * gridDim.x + blockIdx.x] = r;
-    fin_tail(part, gridDim.x, gridDim.y, fin);
-}
-
 // s -= alpha q; partial |s|^2 (the x update of the same step goes with the next p update)
 template <int P, int NR>
 __global__ void cg_s_kernel(FieldV sf, FieldV qf, const double* sc, df* part, FinArgs fin) {
@@ -263,46 +229,35 @@ __global__ void cg_xp_kernel(FieldV x, FieldV p, FieldV r, const double* sc) {
     }
 }
 
-// p = r + beta p with partial |p|^2
-template <int P, int NR>
-__global__ void cg_p_norm_kernel(FieldV p, FieldV r, const double* sc, df* part, FinArgs fin) {
+// x += alpha p, then p = r + beta p with partial |p|^2
+template <int PX, int P, int NR>
+__global__ void cg_xp_norm_kernel(FieldV x, FieldV p, FieldV r, const double* sc, df* part, FinArgs fin) {
     typedef typename RealT<P>::T T;
+    typedef typename MathT<PX, P>::T TX;
     const int k = blockIdx.y;
+    const TX ax = (TX)sc[(size_t)k * SC_N + SC_ALPHA];
     const T b = (T)sc[(size_t)k * SC_N + SC_BETA];
     df acc(0.f);
     SITE_LOOP(p.vh) {
         T vp[NR], vr[NR];
+        TX vx[NR];
         fload<P, NR, T>(p, k, s, vp);
+        fload<PX, NR, TX>(x, k, s, vx);
         fload<P, NR, T>(r, k, s, vr);
         T t = (T)0;
 #pragma unroll
         for (int q = 0; q < NR; q++) {
+            vx[q] = fma(ax, (TX)vp[q], vx[q]);
             vp[q] = fma(b, vp[q], vr[q]);
             t = fma(vp[q], vp[q], t);
         }
         acc = acc + df_of(t);
+        fstore<PX, NR, TX>(x, k, s, vx);
         fstore<P, NR, T>(p, k, s, vp);
     }
     df rr = block_sum_df(acc);
     if (threadIdx.x == 0) part[(size_t)k * gridDim.x + blockIdx.x] = rr;
     fin_tail(part, gridDim.x, gridDim.y, fin);
-}
-
-// p = r + beta p
-template <int P, int NR>
-__global__ void cg_p_kernel(FieldV p, FieldV r, const double* sc) {
-    pdl_start();
-    typedef typename RealT<P>::T T;
-    const int k = blockIdx.y;
-    const T b = (T)sc[(size_t)k * SC_N + SC_BETA];
-    SITE_LOOP(p.vh) {
-        T vp[NR], vr[NR];
-        fload<P, NR, T>(p, k, s, vp);
-        fload<P, NR, T>(r, k, s, vr);
-#pragma unroll
-        for (int q = 0; q < NR; q++) vp[q] = fma(b, vp[q], vr[q]);
-        fstore<P, NR, T>(p, k, s, vp);
-    }
 }
 
 // sum the partials of right-hand side blockIdx.x (double-float, fixed order),
@@ -785,25 +740,6 @@ void blas_xmy_norm(Field& s, const Field& b, const Field& q, df* part, cudaStrea
 #undef K
 }
 
-template <int PX>
-static void cg_xs_from(Field& x, const Field& p, Field& s, const Field& q, const double* sc, df* part,
-                       cudaStream_t st, const FinArgs& fin) {
-#define K(NR) cg_xs_kernel<PX, P_, NR>
-#define L(P) { constexpr int P_ = P; BY_KIND_PDL(x, "blas_cg_xs", K, red_grid(x.nrhs), x.view(), p.view(), s.view(), q.view(), sc, part, fin); }
-    DISPATCH_P(p.prec, L);
-#undef L
-#undef K
-}
-
-void blas_cg_xs(Field& x, const Field& p, Field& s, const Field& q, const double* sc, df* part,
-                cudaStream_t st, const FinArgs& fin) {
-    if (p.prec != s.prec || p.prec != q.prec) fail(LQ_EINVAL, "blas_cg_xs: precision mismatch");
-    if (x.prec == LQ_F64) cg_xs_from<P64>(x, p, s, q, sc, part, st, fin);
-    else if (x.prec == LQ_F32) cg_xs_from<P32>(x, p, s, q, sc, part, st, fin);
-    else if (x.prec == LQ_F16) cg_xs_from<P16>(x, p, s, q, sc, part, st, fin);
-    else cg_xs_from<PDF>(x, p, s, q, sc, part, st, fin);
-}
-
 void blas_cg_s(Field& s, const Field& q, const double* sc, df* part, cudaStream_t st, const FinArgs& fin) {
     if (s.prec != q.prec) fail(LQ_EINVAL, "blas_cg_s: precision mismatch");
 #define K(NR) cg_s_kernel<P_, NR>
@@ -829,6 +765,25 @@ void blas_cg_xp(Field& x, Field& p, const Field& r, const double* sc, cudaStream
     else if (x.prec == LQ_F32) cg_xp_from<P32>(x, p, r, sc, st);
     else if (x.prec == LQ_F16) cg_xp_from<P16>(x, p, r, sc, st);
     else cg_xp_from<PDF>(x, p, r, sc, st);
+}
+
+template <int PX>
+static void cg_xp_norm_from(Field& x, Field& p, const Field& r, const double* sc, df* part, cudaStream_t st,
+                            const FinArgs& fin) {
+#define K(NR) cg_xp_norm_kernel<PX, P_, NR>
+#define L(P) { constexpr int P_ = P; BY_KIND(p, "blas_cg_xp", K, red_grid(p.nrhs), x.view(), p.view(), r.view(), sc, part, fin); }
+    DISPATCH_P(p.prec, L);
+#undef L
+#undef K
+}
+
+void blas_cg_xp_norm(Field& x, Field& p, const Field& r, const double* sc, df* part, cudaStream_t st,
+                     const FinArgs& fin) {
+    if (p.prec != r.prec) fail(LQ_EINVAL, "blas_cg_xp_norm: precision mismatch");
+    if (x.prec == LQ_F64) cg_xp_norm_from<P64>(x, p, r, sc, part, st, fin);
+    else if (x.prec == LQ_F32) cg_xp_norm_from<P32>(x, p, r, sc, part, st, fin);
+    else if (x.prec == LQ_F16) cg_xp_norm_from<P16>(x, p, r, sc, part, st, fin);
+    else cg_xp_norm_from<PDF>(x, p, r, sc, part, st, fin);
 }
 
 void blas_bicg_cdot(const Field& a, const Field& b, df* part, cudaStream_t st, const FinArgs& fin) {
@@ -897,15 +852,6 @@ void blas_bicg_rho(const Field& r, const Field& r0, df* part, cudaStream_t st, c
 #undef K
 }
 
-void blas_cg_p_norm(Field& p, const Field& r, const double* sc, df* part, cudaStream_t st, const FinArgs& fin) {
-    if (p.prec != r.prec) fail(LQ_EINVAL, "blas_cg_p_norm: precision mismatch");
-#define K(NR) cg_p_norm_kernel<P_, NR>
-#define L(P) { constexpr int P_ = P; BY_KIND(p, "blas_cg_p", K, red_grid(p.nrhs), p.view(), r.view(), sc, part, fin); }
-    DISPATCH_P(p.prec, L);
-#undef L
-#undef K
-}
-
 void blas_lincomb4(Field& out, double a0, const Field& v, double a1, const Field& t, double a2, const Field& w,
                    cudaStream_t st, bool sub_old) {
     if (out.prec != v.prec || out.prec != t.prec || out.prec != w.prec) fail(LQ_EINVAL, "blas_lincomb4: precision mismatch");
@@ -933,16 +879,6 @@ void blas_caxpy_h(Field& y, const double* a_re, const double* a_im, const Field&
 #define K(NR) caxpy_h_kernel<P_, NR>
 #define L(P) { constexpr int P_ = P; BY_KIND(y, "blas_caxpy", K, g, y.view(), x.view(), h); }
     DISPATCH_P(y.prec, L);
-#undef L
-#undef K
-}
-
-void blas_cg_p(Field& p, const Field& r, const double* sc, cudaStream_t st) {
-    if (p.prec != r.prec) fail(LQ_EINVAL, "blas_cg_p: precision mismatch");
-    dim3 g = upd_grid(p.vh, p.nrhs);
-#define K(NR) cg_p_kernel<P_, NR>
-#define L(P) { constexpr int P_ = P; BY_KIND_PDL(p, "blas_cg_p", K, g, p.view(), r.view(), sc); }
-    DISPATCH_P(p.prec, L);
 #undef L
 #undef K
 }

@@ -308,9 +308,6 @@ void blas_axpby_h(Field& y, const double* a, const Field& x, const double* b, df
 // s = b - q, with partial |s|^2
 void blas_xmy_norm(Field& s, const Field& b, const Field& q, df* part, cudaStream_t st,
                    const FinArgs& fin = FinArgs());
-// CG update: alpha_k = sc[k*SC_N + SC_ALPHA]; x += alpha p; s -= alpha q; partial |s|^2
-void blas_cg_xs(Field& x, const Field& p, Field& s, const Field& q, const double* sc, df* part,
-                cudaStream_t st, const FinArgs& fin = FinArgs());
 // BiCGStab vector steps (complex device scalars in the solver scalar block, see core.cuh):
 // (a, b) -> partials (2 per block), s = r - alpha v in place, (t, s) and |t|^2 (3),
 // x += alpha p + omega s with r = s - omega t and |r|^2, (r0, r) (3), p = r + beta (p - omega v),
@@ -328,14 +325,14 @@ void blas_lincomb4(Field& out, double a0, const Field& v, double a1, const Field
 // out = g5 in (Wilson fields); y += (a_re_k + i a_im_k) x per rhs (host scalars)
 void blas_gamma5(Field& out, const Field& in, cudaStream_t st);
 void blas_caxpy_h(Field& y, const double* a_re, const double* a_im, const Field& x, cudaStream_t st);
-// p = r + beta p with partial |p|^2
-void blas_cg_p_norm(Field& p, const Field& r, const double* sc, df* part, cudaStream_t st, const FinArgs& fin);
-// p = r + beta p, beta_k = sc[k*SC_N + SC_BETA]
-void blas_cg_p(Field& p, const Field& r, const double* sc, cudaStream_t st);
-// the CG step split around the second operator: s -= alpha q with partial |s|^2, and later
-// x += alpha p, p = r + beta p (one pass over p for both)
+// The CG vector step (alpha_k = sc[k*SC_N + SC_ALPHA], beta_k = sc[k*SC_N + SC_BETA]) in two
+// kernels: s -= alpha q with partial |s|^2, and later x += alpha p, p = r + beta p (one pass
+// over p for both)
 void blas_cg_s(Field& s, const Field& q, const double* sc, df* part, cudaStream_t st, const FinArgs& fin);
 void blas_cg_xp(Field& x, Field& p, const Field& r, const double* sc, cudaStream_t st);
+// the same with partial |p|^2 of the new p
+void blas_cg_xp_norm(Field& x, Field& p, const Field& r, const double* sc, df* part, cudaStream_t st,
+                     const FinArgs& fin);
 
 // GCR and Gram-Schmidt steps. Partials of <v_i, w> (i < nv, fields listed in device
 // memory) at part[((k * nv + i) * 2 + re/im) * RED_BLOCKS + block]; q_j -= sum_{i<j} c_i q_i

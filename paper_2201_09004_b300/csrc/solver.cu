@@ -1057,8 +1057,8 @@ static CgResult cg_hisq(Lattice& lat, const OpDesc& ops, const OpDesc& op64, con
         // atomic at its end)
         const int nb = schur_hisq(lat, ops, 0.0, p, q, t, sc.part, st, FinArgs(), sig);
         blas_finalize(sc.part, nb, n, sc.dev, falpha.slot, falpha.op, st);
-        blas_cg_xs(x_lo, p, r, q, sc.dev, sc.part, st, sc.f(0, FIN_CG_BETA));   // x, r, |r|^2, beta
-        blas_cg_p_norm(p, r, sc.dev, sc.part, st, sc.f(SC_PP, FIN_SET));         // p = r + beta p, |p|^2
+        blas_cg_s(r, q, sc.dev, sc.part, st, sc.f(0, FIN_CG_BETA));                // r, |r|^2, beta
+        blas_cg_xp_norm(x_lo, p, r, sc.dev, sc.part, st, sc.f(SC_PP, FIN_SET));  // x += alpha p, p = r + beta p, |p|^2
         if (dst) LQ_CUDA(cudaMemcpyAsync(dst, sc.dev, sizeof(double) * SC_N * n, cudaMemcpyDeviceToHost, st));
     };
     auto update = [&]() {
