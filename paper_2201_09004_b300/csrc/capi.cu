@@ -353,14 +353,23 @@ extern "C" int lq_solve(lq_lattice h, const lq_op_params* op, const lq_solve_par
     }
     // Host solutions: each one is copied back on the lattice's copy stream as soon as
     // the solver has written it, beside the solve's remaining kernels (the final
-    // residual check, the next mass). The guard waits for the copies before the
-    // staging buffer returns to the pool, on every exit.
+    // residual check, the next mass). The guard waits for this call's copies (an event
+    // after the last of them, so not for copies that other calls queue later) before
+    // the staging buffer returns to the pool, on every exit.
     struct CopyBack {
         cudaStream_t cs = nullptr;
-        cudaEvent_t ev = nullptr;
+        cudaEvent_t ev = nullptr, done = nullptr;
+        cudaError_t wait() {
+            if (!cs) return cudaSuccess;
+            cudaError_t e = cudaEventRecord(done, cs);
+            if (e == cudaSuccess) e = cudaEventSynchronize(done);
+            cs = nullptr;
+            return e;
+        }
         ~CopyBack() {
-            if (cs) cudaStreamSynchronize(cs);
+            wait();
             if (ev) cudaEventDestroy(ev);
+            if (done) cudaEventDestroy(done);
         }
     } cb;
     SolutionReady ready;
@@ -370,6 +379,7 @@ extern "C" int lq_solve(lq_lattice h, const lq_op_params* op, const lq_solve_par
             if (!L.copy_stream) LQ_CUDA(cudaStreamCreateWithFlags(&L.copy_stream, cudaStreamNonBlocking));
         }
         LQ_CUDA(cudaEventCreateWithFlags(&cb.ev, cudaEventDisableTiming));
+        LQ_CUDA(cudaEventCreateWithFlags(&cb.done, cudaEventDisableTiming));
         cb.cs = L.copy_stream;
         ready = [&](int k, cudaStream_t s) {
             LQ_CUDA(cudaEventRecord(cb.ev, s));
@@ -384,7 +394,7 @@ extern "C" int lq_solve(lq_lattice h, const lq_op_params* op, const lq_solve_par
         ret = solve_wilson_multishift(L, *op, *sp, nrhs, db.data(), dx.data(), info, st, rp);
     else ret = solve_wilson(L, *op, *sp, nrhs, db.data(), dx.data(), info, st, nullptr, rp);
     LQ_CUDA(cudaStreamSynchronize(st));
-    if (cb.cs) LQ_CUDA(cudaStreamSynchronize(cb.cs));
+    LQ_CUDA(cb.wait());
     return ret;
     LQ_CATCH
 }
